@@ -1,0 +1,189 @@
+/*
+ * vef.h -- C ABI of the GB300 DG S_N transport sweep and VEF closure library (libvef.so).
+ *
+ * The library computes, on one CUDA GPU, the data-parallel hot path of the Variable
+ * Eddington Factor (VEF) fixed-point iteration of Olivier & Haut, "High-Order Mixed
+ * Finite Element Variable Eddington Factor Methods":
+ *   - the inversion of the streaming-plus-collision operator of the discrete-ordinates
+ *     transport equation (paper Eq. transport with boundary condition Eq. trans_bc)
+ *     discretised with the DG space Y_p on curved Q_m quadrilaterals (paper Sec.
+ *     "Transport Discretizations", "Discontinuous Galerkin", "Description of the Mesh");
+ *   - the angular moments and VEF closures, scalar flux phi, current J, Eddington
+ *     tensor E and boundary factor E_b (paper Eq. vef_disc) and the inflow partial
+ *     current J_in (paper, the definitions following Eq. mlbc);
+ *   - source iteration (paper Sec. "VEF Algorithm", the fixed-point loop) and an
+ *     adjoint sweep giving cross-section gradients (not in the paper).
+ *
+ * Discretisation (the paper defers the sweep's weak form to its transport solver; this
+ * library fixes it as follows).  Per direction Omega_d and element K, find psi in Q_p(K):
+ *     - int_K psi (Omega.grad v) + int_dK (Omega.n) psi_hat v + int_K sigma_t psi v
+ *         = int_K (sigma_s phi_in / (4 pi) + q_d) v        for all v in Q_p(K),
+ * psi_hat = interior trace where Omega.n >= 0, else the upwind neighbour's trace or
+ * the inflow data psi_bar, decided pointwise at every face quadrature point.
+ * Basis: tensor Lagrange at the (p+1)^2 Gauss-Lobatto points of the reference square,
+ * local dof a + (p+1) b.  Quadrature: tensor Gauss-Legendre with nq = p+2 points per
+ * direction; faces use the same nq-point rule.  Mesh: nx x ny structured elements of
+ * [0,1]^2, element e = j*nx + i, Q_m map through (m+1)^2 Gauss-Lobatto control points.
+ * Faces: 0 bottom, 1 right, 2 top, 3 left; face points in increasing reference
+ * coordinate.  Boundary faces (N_bf = 2 nx + 2 ny): bottom row (i = 0..nx-1), right
+ * column (j = 0..ny-1), top row (i), left column (j).
+ *
+ * A sweep returns psi_d = L_d^{-1} b_d for every direction, independent of any
+ * ordering: the library orders elements per direction along the upwind dependency
+ * graph and solves the rare strongly coupled element groups (curved faces that are
+ * partly inflow and partly outflow) by an inner block Gauss-Seidel iteration to a
+ * relative change below `vef_opts.tol`.
+ *
+ * Conventions
+ *   - Array arguments marked [device] are caller-owned device memory: contiguous FP64,
+ *     on the current device, in the layouts stated.  Arguments marked [host] are
+ *     caller-owned host memory read during the call.
+ *   - Calls are stream-ordered on `stream` (NULL = legacy default stream) and
+ *     asynchronous, except where a call states that it synchronises.
+ *   - A mesh handle owns device memory (geometry, schedules, scratch).  Calls that use
+ *     the same handle must not overlap on the GPU: issue them on one stream or
+ *     serialise them.
+ *   - The status returned covers argument validation and launch.  Failures detected
+ *     on the device (a dependency wait that ran out, an inner iteration that did not
+ *     converge, a non-positive closure denominator) are recorded in the handle and are
+ *     returned by the next call that synchronises: vef_mesh_sync(), or any call given
+ *     a non-NULL vef_info.
+ *   - No exceptions cross the ABI.  There is no CPU fallback: without a usable CUDA
+ *     device every compute call returns VEF_ERR_CUDA.
+ */
+#ifndef VEF_H
+#define VEF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VEF_OK = 0,
+  VEF_ERR_INVALID_ARG = 1,
+  VEF_ERR_CUDA = 2,
+  VEF_ERR_OOM = 3,
+  VEF_ERR_TIMEOUT = 4,            /* a device-side dependency wait ran out; psi is invalid */
+  VEF_ERR_NOT_CONVERGED = 5,      /* an inner or defect-correction iteration hit its cap */
+  VEF_ERR_NONPOSITIVE_DENOM = 6,  /* sum_d w_d psi_d <= 1e-300 at a closure point (NaN written) */
+  VEF_ERR_NOT_IMPLEMENTED = 7
+} vef_status;
+
+enum { VEF_FP64 = 0, VEF_MIXED = 1 };
+
+typedef struct vef_mesh_s* vef_mesh;
+
+/* Sweep options.  NULL means the defaults listed. */
+typedef struct {
+  int precision;     /* VEF_FP64 (default): FP64 assembly and solves.
+                        VEF_MIXED: FP32 assembly and solves inside an FP64
+                        defect-correction loop r = b - L psi (FP64), psi += L32^{-1} r. */
+  double tol;        /* relative tolerance: inner coupled-group iteration (FP64: 1e-15) and
+                        defect correction ||r||_2 / ||b||_2 (mixed: 1e-13) */
+  int max_passes;    /* cap on defect-correction passes (default 8) and, x4, on inner
+                        coupled-group iterations */
+  int tile_override; /* 0 = library choice; >0 forces threads per block of the sweep kernel */
+} vef_opts;
+
+/* Filled by calls given a non-NULL pointer (those calls synchronise `stream`). */
+typedef struct {
+  int passes;                 /* sweeps executed (1 for FP64; 1 + corrections for mixed) */
+  double rel_residual;        /* mixed: final ||b - L psi||_2 / ||b||_2 (FP64 path: -1) */
+  long long coupled_groups;   /* (element group, direction) tasks with more than one element */
+  long long lagged_face_points; /* face points inside coupled groups (solved iteratively) */
+  int max_inner_iterations;   /* largest inner Gauss-Seidel count used by a coupled group */
+  int timed_out;              /* 1 if a dependency wait ran out */
+  int levels;                 /* dependency levels of the schedule (critical path length) */
+} vef_info;
+
+/* Mesh description returned by vef_mesh_query. */
+typedef struct {
+  int nx, ny, mesh_order, p;
+  int n;          /* (p+1)^2 dofs per element */
+  int nq;         /* p+2 quadrature points per direction */
+  long long E;    /* nx*ny */
+  long long nbf;  /* 2 nx + 2 ny boundary faces */
+} vef_mesh_desc;
+
+/* Create a mesh of [0,1]^2 with nx x ny elements, map order mesh_order (1..4), DG
+ * order p (1..4) and sine distortion amplitude alpha (paper Sec. "Solver Performance on
+ * Curved Meshes": x -> x + alpha sin(2 pi x) sin(2 pi y) (1,1)) applied to the
+ * Gauss-Lobatto control points (paper Sec. "Description of the Mesh").
+ * ctrl_pts: [host] optional [E][(m+1)^2][2] control points (replaces the generated
+ * ones; alpha is then ignored).  Computes the geometric factors on the device.
+ * Synchronises the current device's legacy stream.  *out receives the handle. */
+vef_status vef_mesh_create(int nx, int ny, int mesh_order, int p, double alpha,
+                           const double* ctrl_pts, vef_mesh* out);
+vef_status vef_mesh_destroy(vef_mesh mesh);
+vef_status vef_mesh_query(vef_mesh mesh, vef_mesh_desc* out);
+/* Waits for the handle's work on `stream` and returns (then clears) the first
+ * device-side failure recorded since the last check. */
+vef_status vef_mesh_sync(vef_mesh mesh, void* stream);
+
+/* One transport inversion for every direction (paper Eq. transport, trans_bc):
+ *   sigma_t, sigma_s [device] [E] per-element cross sections (sigma_t > 0);
+ *   phi_in  [device] [E][n] scattering scalar flux (DG nodal values) or NULL (= 0);
+ *   source  [device] [E][n] isotropic q per steradian, or [D][E][n] when
+ *           source_aniso != 0; NULL = 0;
+ *   inflow  [device] [D][N_bf][nq] psi_bar at the boundary face points; only values
+ *           at inflow points (Omega.n < 0) are read; NULL = vacuum;
+ *   omega   [host] [D][2] direction cosines (mu, eta); weights [host] [D] (not used
+ *           by the sweep itself; validated and kept for the moment calls);
+ *   psi     [device] [D][E][n] output.
+ * The first call with a given direction set builds its schedule on the host (this
+ * synchronises `stream`; do it before any stream capture). */
+vef_status vef_sweep(vef_mesh mesh, const double* sigma_t, const double* sigma_s,
+                     const double* phi_in, const double* source, int source_aniso,
+                     const double* inflow, const double* omega, const double* weights, int D,
+                     const vef_opts* opts, double* psi, vef_info* info, void* stream);
+
+/* Moments and closures (paper Eq. vef_disc and the definitions of E, E_b, J_in):
+ *   psi [device] [D][E][n]; omega, weights [host] as for vef_sweep;
+ *   inflow [device] [D][N_bf][nq] or NULL (then Jin is set to 0);
+ * outputs, each [device] and optional (NULL = skip):
+ *   phi [E][n], J [2][E][n] (x, y), P [3][E][n] (xx, xy, yy) as DG nodal values;
+ *   Eten [3][E][nq*nq] = P/phi at the volume quadrature points (point k1 + nq k2);
+ *   Eb [N_bf][nq] = sum w |Omega.n_hat| psi / sum w psi with the interior trace;
+ *   Jin [N_bf][nq] = sum_{Omega.n<0} w (Omega.n_hat) psi_bar.
+ * All sums are accumulated in FP64.  A denominator <= 1e-300 writes NaN and records
+ * VEF_ERR_NONPOSITIVE_DENOM. */
+vef_status vef_moments(vef_mesh mesh, const double* psi, const double* omega,
+                       const double* weights, int D, const double* inflow, double* phi,
+                       double* J, double* P, double* Eten, double* Eb, double* Jin,
+                       void* stream);
+
+/* Source iteration (paper Sec. "VEF Algorithm", fixed-point loop): phi^0 = phi0
+ * ([device] [E][n], NULL = 0), then K times psi = sweep(phi^k), phi^{k+1} = sum_d w_d psi_d.
+ * phi_out [device] [E][n] receives phi^K; psi [device] [D][E][n] the last sweep
+ * (required); dphi_inf [device] [K] receives max |phi^{k+1} - phi^k| (optional). */
+vef_status vef_source_iterate(vef_mesh mesh, const double* sigma_t, const double* sigma_s,
+                              const double* phi0, const double* source, int source_aniso,
+                              const double* inflow, const double* omega, const double* weights,
+                              int D, int K, const vef_opts* opts, double* phi_out, double* psi,
+                              double* dphi_inf, vef_info* info, void* stream);
+
+/* Adjoint sweep for R = sum_{e,j} g[e][j] phi[e][j] of one transport inversion with fixed
+ * phi_in: solves L_d^T lambda_d = w_d g (directions reversed: downwind order), then
+ *   dR_dsigma_t[e] = - sum_d lambda_{d,e}^T M_e psi_{d,e},
+ *   dR_dsigma_s[e] =   sum_d lambda_{d,e}^T M_e phi_in,e / (4 pi)
+ * with M_e the element mass matrix.  psi_ckpt [device] [D][E][n] is the forward sweep's
+ * psi (checkpoint); g [device] [E][n]; lambda [device] [D][E][n] output or NULL (then a
+ * library buffer is used); dR_dsigma_t, dR_dsigma_s [device] [E] outputs. */
+vef_status vef_adjoint_sweep(vef_mesh mesh, const double* sigma_t, const double* sigma_s,
+                             const double* phi_in, const double* omega, const double* weights,
+                             int D, const double* psi_ckpt, const double* g, double* lambda,
+                             double* dR_dsigma_t, double* dR_dsigma_s, const vef_opts* opts,
+                             vef_info* info, void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* vef_status_string(vef_status s);
+/* Last error message of the calling thread (static buffer, "" if none). */
+const char* vef_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VEF_H */

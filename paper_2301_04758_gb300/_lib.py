@@ -1,0 +1,110 @@
+"""ctypes binding of libvef.so (the C ABI declared in include/vef.h).
+
+Argument marshalling only: every step of the sweep, moments and adjoint runs in the
+library's CUDA kernels.  Loading fails loudly when the library is missing; there is no
+CPU fallback.
+"""
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libvef.so")
+
+VEF_OK = 0
+VEF_ERR_INVALID_ARG = 1
+VEF_ERR_CUDA = 2
+VEF_ERR_OOM = 3
+VEF_ERR_TIMEOUT = 4
+VEF_ERR_NOT_CONVERGED = 5
+VEF_ERR_NONPOSITIVE_DENOM = 6
+VEF_ERR_NOT_IMPLEMENTED = 7
+
+VEF_FP64 = 0
+VEF_MIXED = 1
+
+# every symbol include/vef.h declares
+EXPORTS = ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sync", "vef_sweep",
+           "vef_moments", "vef_source_iterate", "vef_adjoint_sweep", "vef_status_string",
+           "vef_last_error")
+
+
+class VefOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_passes", ctypes.c_int), ("tile_override", ctypes.c_int)]
+
+
+class VefInfo(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("coupled_groups", ctypes.c_longlong), ("lagged_face_points", ctypes.c_longlong),
+                ("max_inner_iterations", ctypes.c_int), ("timed_out", ctypes.c_int),
+                ("levels", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class VefMeshDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("mesh_order", ctypes.c_int),
+                ("p", ctypes.c_int), ("n", ctypes.c_int), ("nq", ctypes.c_int),
+                ("E", ctypes.c_longlong), ("nbf", ctypes.c_longlong)]
+
+
+class VefError(RuntimeError):
+    def __init__(self, status, where, message):
+        super().__init__(f"{where}: {status_name(status)}: {message}")
+        self.status = status
+
+
+_lib = None
+P = ctypes.c_void_p
+D = ctypes.c_double
+I = ctypes.c_int
+
+
+def _declare(lib):
+    lib.vef_mesh_create.argtypes = [I, I, I, I, D, P, ctypes.POINTER(P)]
+    lib.vef_mesh_destroy.argtypes = [P]
+    lib.vef_mesh_query.argtypes = [P, ctypes.POINTER(VefMeshDesc)]
+    lib.vef_mesh_sync.argtypes = [P, P]
+    lib.vef_sweep.argtypes = [P, P, P, P, P, I, P, P, P, I, ctypes.POINTER(VefOpts), P,
+                              ctypes.POINTER(VefInfo), P]
+    lib.vef_moments.argtypes = [P, P, P, P, I, P, P, P, P, P, P, P, P]
+    lib.vef_source_iterate.argtypes = [P, P, P, P, P, I, P, P, P, I, I, ctypes.POINTER(VefOpts),
+                                       P, P, P, ctypes.POINTER(VefInfo), P]
+    lib.vef_adjoint_sweep.argtypes = [P, P, P, P, P, P, I, P, P, P, P, P, ctypes.POINTER(VefOpts),
+                                      ctypes.POINTER(VefInfo), P]
+    for name in ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sync",
+                 "vef_sweep", "vef_moments", "vef_source_iterate", "vef_adjoint_sweep"):
+        getattr(lib, name).restype = I
+    lib.vef_status_string.argtypes = [I]
+    lib.vef_status_string.restype = ctypes.c_char_p
+    lib.vef_last_error.argtypes = []
+    lib.vef_last_error.restype = ctypes.c_char_p
+
+
+def load(path=None):
+    """Load libvef.so (built by paper_2301_04758_gb300.build.build())."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libvef.so not found at {p}; build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(p)
+    _declare(lib)
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def status_name(status):
+    try:
+        return load().vef_status_string(status).decode()
+    except Exception:  # library not loadable: still name the code
+        return str(status)
+
+
+def check(status, where):
+    if status != VEF_OK:
+        raise VefError(status, where, load().vef_last_error().decode())

@@ -1,0 +1,153 @@
+"""PyTorch-facing wrappers over the C ABI (device memory and streams only).
+
+Tensors passed in must be CUDA float64 and contiguous on the mesh's device; the
+direction set (omega [D][2], weights [D]) is given as host arrays.  Outputs are
+allocated with torch and filled by the library's kernels.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+_NULL = None
+
+
+def _ptr(t):
+    if t is None:
+        return _NULL
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host(a, shape_last=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _opts(precision="fp64", tol=0.0, max_passes=0, tile=0):
+    o = _lib.VefOpts()
+    o.precision = {"fp64": _lib.VEF_FP64, "mixed": _lib.VEF_MIXED}[precision]
+    o.tol = float(tol)
+    o.max_passes = int(max_passes)
+    o.tile_override = int(tile)
+    return o
+
+
+class Mesh:
+    """nx x ny mesh of [0,1]^2, Q_m map (sine distortion alpha), DG order p."""
+
+    def __init__(self, nx, ny, mesh_order, p, alpha=0.0, ctrl=None):
+        self.lib = _lib.load()
+        h = ctypes.c_void_p()
+        keep = None
+        cptr = None
+        if ctrl is not None:
+            keep, cptr = _host(ctrl)
+        _lib.check(self.lib.vef_mesh_create(int(nx), int(ny), int(mesh_order), int(p), float(alpha),
+                                            cptr, ctypes.byref(h)), "vef_mesh_create")
+        del keep
+        self.handle = h
+        d = _lib.VefMeshDesc()
+        _lib.check(self.lib.vef_mesh_query(h, ctypes.byref(d)), "vef_mesh_query")
+        self.nx, self.ny, self.m, self.p = d.nx, d.ny, d.mesh_order, d.p
+        self.n, self.nq, self.E, self.nbf = d.n, d.nq, int(d.E), int(d.nbf)
+        self.device = torch.cuda.current_device()
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.vef_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self, stream=None):
+        _lib.check(self.lib.vef_mesh_sync(self.handle, _stream(stream)), "vef_mesh_sync")
+
+    def _empty(self, *shape):
+        return torch.empty(*shape, dtype=torch.float64, device=f"cuda:{self.device}")
+
+    # ---------------------------------------------------------------- transport
+    def sweep(self, sigma_t, sigma_s, omega, weights, phi_in=None, source=None, inflow=None,
+              precision="fp64", tol=0.0, max_passes=0, tile=0, psi=None, info=False, stream=None):
+        """psi [D][E][n] = L^{-1} b for every direction (see vef_sweep in include/vef.h)."""
+        om, omp = _host(omega)
+        w, wp = _host(weights)
+        D = len(w)
+        aniso = int(source is not None and source.dim() == 3)
+        if psi is None:
+            psi = self._empty(D, self.E, self.n)
+        inf = _lib.VefInfo() if info else None
+        o = _opts(precision, tol, max_passes, tile)
+        st = self.lib.vef_sweep(self.handle, _ptr(sigma_t), _ptr(sigma_s), _ptr(phi_in), _ptr(source),
+                                aniso, _ptr(inflow), omp, wp, D, ctypes.byref(o), _ptr(psi),
+                                ctypes.byref(inf) if info else None, _stream(stream))
+        _lib.check(st, "vef_sweep")
+        return (psi, inf.as_dict()) if info else psi
+
+    def moments(self, psi, omega, weights, inflow=None, outputs=("phi", "J", "P", "E", "Eb", "Jin"),
+                stream=None):
+        """dict of phi [E][n], J [2][E][n], P [3][E][n], E [3][E][nq^2], Eb, Jin [N_bf][nq]."""
+        om, omp = _host(omega)
+        w, wp = _host(weights)
+        D = len(w)
+        out = {}
+        shapes = {"phi": (self.E, self.n), "J": (2, self.E, self.n), "P": (3, self.E, self.n),
+                  "E": (3, self.E, self.nq * self.nq), "Eb": (self.nbf, self.nq),
+                  "Jin": (self.nbf, self.nq)}
+        for k in outputs:
+            out[k] = self._empty(*shapes[k])
+        st = self.lib.vef_moments(self.handle, _ptr(psi), omp, wp, D, _ptr(inflow),
+                                  _ptr(out.get("phi")), _ptr(out.get("J")), _ptr(out.get("P")),
+                                  _ptr(out.get("E")), _ptr(out.get("Eb")), _ptr(out.get("Jin")),
+                                  _stream(stream))
+        _lib.check(st, "vef_moments")
+        return out
+
+    def source_iterate(self, sigma_t, sigma_s, omega, weights, K, source=None, inflow=None, phi0=None,
+                       precision="fp64", tol=0.0, max_passes=0, psi=None, info=False, stream=None):
+        """K source iterations: returns (phi^K, psi of the last sweep, dphi_inf [K])."""
+        om, omp = _host(omega)
+        w, wp = _host(weights)
+        D = len(w)
+        aniso = int(source is not None and source.dim() == 3)
+        if psi is None:
+            psi = self._empty(D, self.E, self.n)
+        phi = self._empty(self.E, self.n)
+        dphi = self._empty(K)
+        inf = _lib.VefInfo() if info else None
+        o = _opts(precision, tol, max_passes)
+        st = self.lib.vef_source_iterate(self.handle, _ptr(sigma_t), _ptr(sigma_s), _ptr(phi0),
+                                         _ptr(source), aniso, _ptr(inflow), omp, wp, D, int(K),
+                                         ctypes.byref(o), _ptr(phi), _ptr(psi), _ptr(dphi),
+                                         ctypes.byref(inf) if info else None, _stream(stream))
+        _lib.check(st, "vef_source_iterate")
+        return (phi, psi, dphi, inf.as_dict()) if info else (phi, psi, dphi)
+
+    def adjoint(self, sigma_t, sigma_s, omega, weights, psi, g, phi_in=None, want_lambda=False,
+                info=False, stream=None):
+        """Gradients of R = sum g * phi: returns (dR/dsigma_t [E], dR/dsigma_s [E] or None, lambda)."""
+        om, omp = _host(omega)
+        w, wp = _host(weights)
+        D = len(w)
+        lam = self._empty(D, self.E, self.n) if want_lambda else None
+        dst = self._empty(self.E)
+        dss = self._empty(self.E) if phi_in is not None else None
+        inf = _lib.VefInfo() if info else None
+        st = self.lib.vef_adjoint_sweep(self.handle, _ptr(sigma_t), _ptr(sigma_s), _ptr(phi_in), omp,
+                                        wp, D, _ptr(psi), _ptr(g), _ptr(lam), _ptr(dst), _ptr(dss),
+                                        None, ctypes.byref(inf) if info else None, _stream(stream))
+        _lib.check(st, "vef_adjoint_sweep")
+        res = (dst, dss, lam)
+        return res + (inf.as_dict(),) if info else res

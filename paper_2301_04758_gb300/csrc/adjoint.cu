@@ -1,0 +1,337 @@
+// Adjoint sweep and cross-section gradients (not in the paper; follows from its transport
+// equation).  For R = sum g . phi with phi = sum_d w_d psi_d and L_d psi_d = b_d, the adjoint
+// directions solve L_d^T lambda_d = w_d g.  Writing L_d = blockdiag(A_e) + C with the
+// upwind coupling blocks C[e'][e] (receiver e', donor e), block row e of L^T reads
+//     A_e^T lambda_e = w_d g_e - sum_{e' receiving from e} C[e'][e]^T lambda_{e'}.
+// With r_e := A_e^T lambda_e and the stored W_{e',f'} = A_{e'}^{-1} Cin_{e',f'} of the
+// forward factorisation, C[e'][e]^T lambda_{e'} = W_{e',f'}^T r_{e'} placed on e's face
+// nodes, so each element needs its downstream neighbours' r, and lambda_e = A_e^{-T} r_e.
+// The sweep therefore runs the forward schedule backwards (downwind order).
+//   dR/dsigma_t,e = - sum_d lambda_{d,e}^T M_e psi_{d,e}
+//   dR/dsigma_s,e =   sum_d lambda_{d,e}^T M_e phi_in,e / (4 pi)
+#include <algorithm>
+#include <cmath>
+
+#include "device.cuh"
+
+namespace vef {
+
+struct AdjArgs {
+  int nchunks;
+  const int* chunk_begin;
+  const int* slot_first;
+  const int* slot_count;
+  const uint32_t* code;
+  const int* member_of;
+  const uint16_t* finfo;
+  const double* omega;
+  const double* weights;
+  const double* rec;
+  const double* g;        // [E][n]
+  const double* psi;      // [D][E][n] forward checkpoint
+  const double* Mm;       // [E][n][n]
+  const double* mphi;     // [E][n] M phi_in or null
+  double* radj;           // [D][E][n] adjoint right-hand sides r
+  double* lambda;         // [D][E][n]
+  double* dst;            // [E]
+  double* dss;            // [E]
+  uint32_t* flags;
+  uint32_t epoch;
+  unsigned int* status;
+  int nx, ny;
+  long long E;
+  double tol;
+  int max_inner;
+};
+
+// r_i of element e (lane = dof row i): w_d g_i minus the downstream couplings on e's faces
+template <int P>
+__device__ __forceinline__ double adj_rhs(const AdjArgs& a, int d, int e, int i, uint16_t bits,
+                                          int first, int pos_self, int cnt, int it, bool in_group) {
+  constexpr int Q = P + 1, N = Q * Q, R = rec_size<P>();
+  double r = a.weights[d] * a.g[(size_t)e * N + i];
+  const int ia = i % Q, ib = i / Q;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    if (!(bits & (1u << (8 + f)))) continue;   // no receiver across f
+    int t = -1;
+    if (f == 0 && ib == 0) t = ia;
+    if (f == 1 && ia == P) t = ib;
+    if (f == 2 && ib == P) t = ia;
+    if (f == 3 && ia == 0) t = ib;
+    if (t < 0) continue;
+    const int nb = nb_elem(a.nx, a.ny, e, f);
+    if (in_group && (bits & (1u << (4 + f))) && it == 0) {
+      const int pos = a.member_of[(size_t)d * a.E + nb] - first;
+      if (pos <= pos_self) continue;  // processed later in the first backward pass
+    }
+    const int fn = (f + 2) & 3;      // receiver's face toward e
+    const long long mn = a.member_of[(size_t)d * a.E + nb];
+    const double* W = a.rec + (size_t)mn * R + N * N + fn * N * Q + t * N;
+    const double* rn = a.radj + ((size_t)d * a.E + nb) * N;
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) s += W[j] * __ldcg(rn + j);
+    r -= s;
+  }
+  (void)cnt;
+  return r;
+}
+
+template <int P>
+__device__ __forceinline__ void adj_finish(const AdjArgs& a, long long m, int d, int e, int i, bool act,
+                                           double r) {
+  // lambda = A^{-T} r, gradient contributions
+  constexpr int Q = P + 1, N = Q * Q, R = rec_size<P>();
+  const int lane = threadIdx.x & 31;
+  const int base = (lane / N) * N;
+  const double* Ai = a.rec + (size_t)m * R + (size_t)i * N;  // column i of A^{-1}
+  double lam = 0.0;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const double rj = __shfl_sync(0xffffffffu, r, (base + j) & 31);
+    if (act) lam += Ai[j] * rj;
+  }
+  double gt = 0.0, gs = 0.0;
+  if (act) {
+    a.lambda[((size_t)d * a.E + e) * N + i] = lam;
+    const double* Mr = a.Mm + ((size_t)e * N + i) * N;
+    const double* pe = a.psi + ((size_t)d * a.E + e) * N;
+    double mp = 0.0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) mp += Mr[j] * pe[j];
+    gt = -lam * mp;
+    if (a.mphi) gs = lam * a.mphi[(size_t)e * N + i] / kFourPi;
+  }
+  // reduce over the N lanes of the task
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ot = __shfl_down_sync(0xffffffffu, gt, off);
+    const double os = __shfl_down_sync(0xffffffffu, gs, off);
+    const int src = lane + off;
+    if (src < 32 && (src / N) == (lane / N)) { gt += ot; gs += os; }
+  }
+  if (act && i == 0) {
+    atomicAdd(a.dst + e, gt);
+    if (a.mphi) atomicAdd(a.dss + e, gs);
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs a) {
+  constexpr int Q = P + 1, N = Q * Q;
+  constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  while (true) {
+    int c = 0;
+    if (lane == 0) c = (int)atomicAdd(a.status + 3, 1u);
+    c = __shfl_sync(FULL, c, 0);
+    if (c >= a.nchunks) return;
+    if (*((volatile unsigned int*)(a.status + 1)) != 0u) return;
+    c = a.nchunks - 1 - c;  // downwind order
+    const int s0 = a.chunk_begin[c], s1 = a.chunk_begin[c + 1];
+    const int cnt0 = a.slot_count[s0];
+    if (cnt0 == 1) {
+      const int slot = s0 + lane / N;
+      const int i = lane % N;
+      const bool valid = (lane < SPC * N) && (slot < s1);
+      int d = 0, e = 0;
+      long long m = 0;
+      uint16_t bits = 0;
+      bool ok = true;
+      if (valid) {
+        m = a.slot_first[slot];
+        const uint32_t cd = a.code[m];
+        d = (int)(cd >> 22);
+        e = (int)(cd & 0x3fffffu);
+        bits = a.finfo[(size_t)d * a.E + e];
+        for (int f = 0; f < 4; ++f) {
+          if (!(bits & (1u << (8 + f)))) continue;
+          const int nb = nb_elem(a.nx, a.ny, e, f);
+          if (!wait_epoch(a.flags + (size_t)d * a.E + nb, a.epoch, a.status)) { ok = false; break; }
+        }
+      }
+      if (!__all_sync(FULL, ok)) return;
+      double r = valid ? adj_rhs<P>(a, d, e, i, bits, 0, 0, 1, 1, false) : 0.0;
+      if (valid) a.radj[((size_t)d * a.E + e) * N + i] = r;
+      adj_finish<P>(a, m, d, e, i, valid, r);
+      __threadfence();
+      __syncwarp();
+      if (valid && i == 0) st_release(a.flags + (size_t)d * a.E + e, a.epoch);
+    } else {
+      const int first = a.slot_first[s0];
+      const int cnt = cnt0;
+      const int i = lane;
+      const bool act = lane < N;
+      const int d = (int)(a.code[first] >> 22);
+      bool ok = true;
+      for (int mi = 0; mi < cnt && ok; ++mi) {
+        const int e = (int)(a.code[first + mi] & 0x3fffffu);
+        const uint16_t bits = a.finfo[(size_t)d * a.E + e];
+        for (int f = 0; f < 4; ++f) {
+          if (!(bits & (1u << (8 + f))) || (bits & (1u << (4 + f)))) continue;
+          const int nb = nb_elem(a.nx, a.ny, e, f);
+          if (!wait_epoch(a.flags + (size_t)d * a.E + nb, a.epoch, a.status)) { ok = false; break; }
+        }
+      }
+      if (!__all_sync(FULL, ok)) return;
+      int it = 0;
+      bool conv = false;
+      for (; it < a.max_inner; ++it) {
+        double dmax = 0, amax = 0;
+        for (int mi = cnt - 1; mi >= 0; --mi) {
+          const int e = (int)(a.code[first + mi] & 0x3fffffu);
+          const uint16_t bits = a.finfo[(size_t)d * a.E + e];
+          if (act) {
+            const double r = adj_rhs<P>(a, d, e, i, bits, first, mi, cnt, it, true);
+            double* o = a.radj + ((size_t)d * a.E + e) * N + i;
+            if (it > 0) dmax = fmax(dmax, fabs(r - __ldcg(o)));
+            amax = fmax(amax, fabs(r));
+            *o = r;
+          }
+          __threadfence();
+          __syncwarp();
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          dmax = fmax(dmax, __shfl_xor_sync(FULL, dmax, off));
+          amax = fmax(amax, __shfl_xor_sync(FULL, amax, off));
+        }
+        if (it > 0 && dmax <= a.tol * amax) { conv = true; ++it; break; }
+      }
+      if (lane == 0) {
+        if (!conv) atomicOr(a.status, kDevNotConverged);
+        atomicMax(a.status + 2, (unsigned)it);
+      }
+      for (int mi = 0; mi < cnt; ++mi) {
+        const long long m = first + mi;
+        const int e = (int)(a.code[m] & 0x3fffffu);
+        const double r = act ? __ldcg(a.radj + ((size_t)d * a.E + e) * N + i) : 0.0;
+        adj_finish<P>(a, m, d, e, i, act, r);
+      }
+      __threadfence();
+      __syncwarp();
+      for (int mi = lane; mi < cnt; mi += 32) {
+        const int e = (int)(a.code[first + mi] & 0x3fffffu);
+        st_release(a.flags + (size_t)d * a.E + e, a.epoch);
+      }
+    }
+  }
+}
+
+__global__ void mvec_kernel(long long E, int n, const double* __restrict__ M,
+                            const double* __restrict__ x, double* __restrict__ y) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= E * n) return;
+  long long e = t / n;
+  int i = (int)(t % n);
+  double s = 0.0;
+  for (int j = 0; j < n; ++j) s += M[(e * n + i) * n + j] * x[e * n + j];
+  y[t] = s;
+}
+
+static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// forward factorisation (FP64) from sweep.cu
+vef_status factor_fp64(Mesh* mesh, Schedule* S, const double* sigma_t, cudaStream_t stream);
+vef_status collect_status(Mesh& M, cudaStream_t stream, vef_info* info);
+
+template <int P>
+static vef_status launch_adjoint(AdjArgs a, cudaStream_t s) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, adjoint_kernel<P>, 128, 0);
+  adjoint_kernel<P><<<std::max(1, sms * std::max(1, per)), 128, 0, s>>>(a);
+  VEF_CUDA_TRY(cudaGetLastError());
+  return VEF_OK;
+}
+
+}  // namespace vef
+
+using namespace vef;
+
+extern "C" vef_status vef_adjoint_sweep(vef_mesh mesh, const double* sigma_t, const double* sigma_s,
+                                        const double* phi_in, const double* omega,
+                                        const double* weights, int D, const double* psi_ckpt,
+                                        const double* g, double* lambda, double* dR_dsigma_t,
+                                        double* dR_dsigma_s, const vef_opts* opts, vef_info* info,
+                                        void* stream) {
+  if (!mesh || !sigma_t || !omega || !weights || !psi_ckpt || !g || !dR_dsigma_t) {
+    set_last_error("mesh, sigma_t, omega, weights, psi_ckpt, g, dR_dsigma_t are required");
+    return VEF_ERR_INVALID_ARG;
+  }
+  if (phi_in && (!sigma_s || !dR_dsigma_s)) {
+    set_last_error("phi_in given: sigma_s and dR_dsigma_s are required");
+    return VEF_ERR_INVALID_ARG;
+  }
+  if (D < 1 || D > kMaxD) { set_last_error("D must be in 1..1023"); return VEF_ERR_INVALID_ARG; }
+  Mesh& M = mesh->impl;
+  int dev = 0;
+  VEF_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != M.device) { set_last_error("mesh belongs to another device"); return VEF_ERR_INVALID_ARG; }
+  cudaStream_t s = (cudaStream_t)stream;
+  vef_status st;
+  Schedule* S = get_schedule(&M, omega, weights, D, s, &st);
+  if (!S) return st;
+  if ((st = ensure_flags(&M, (size_t)D * M.E)) != VEF_OK) return st;
+  if ((st = factor_fp64(&M, S, sigma_t, s)) != VEF_OK) return st;
+  const long long tot = (long long)D * M.E * M.n;
+  const size_t need = (size_t)tot * sizeof(double) * (lambda ? 1 : 2) + (size_t)M.E * M.n * sizeof(double);
+  if ((st = ensure_buffer((void**)&M.work2, &M.work2_cap, need)) != VEF_OK) return st;
+  AdjArgs a{};
+  a.nchunks = S->nchunks;
+  a.chunk_begin = S->chunk_begin;
+  a.slot_first = S->slot_first;
+  a.slot_count = S->slot_count;
+  a.code = S->member_code;
+  a.member_of = S->member_of;
+  a.finfo = S->faceinfo;
+  a.omega = S->omega_dev;
+  a.weights = S->weights_dev;
+  a.rec = (const double*)S->rec64;
+  a.g = g;
+  a.psi = psi_ckpt;
+  a.Mm = M.Mmat;
+  a.radj = M.work2;
+  a.lambda = lambda ? lambda : M.work2 + tot;
+  double* mphi = M.work2 + tot * (lambda ? 1 : 2);
+  a.mphi = phi_in ? mphi : nullptr;
+  a.dst = dR_dsigma_t;
+  a.dss = dR_dsigma_s;
+  a.flags = M.flags;
+  if (++M.epoch == 0) {
+    VEF_CUDA_TRY(cudaMemsetAsync(M.flags, 0, M.flags_cap, s));
+    M.epoch = 1;
+  }
+  a.epoch = M.epoch;
+  a.status = M.dev_status;
+  a.nx = M.nx;
+  a.ny = M.ny;
+  a.E = M.E;
+  const int maxp = (opts && opts->max_passes > 0) ? opts->max_passes : 8;
+  a.tol = (opts && opts->tol > 0.0) ? std::max(opts->tol, 2e-15) : 2e-15;
+  a.max_inner = std::max(2, 4 * maxp);
+  if (phi_in) mvec_kernel<<<nblk(M.E * M.n, 256), 256, 0, s>>>(M.E, M.n, M.Mmat, phi_in, mphi);
+  VEF_CUDA_TRY(cudaMemsetAsync(dR_dsigma_t, 0, M.E * sizeof(double), s));
+  if (dR_dsigma_s) VEF_CUDA_TRY(cudaMemsetAsync(dR_dsigma_s, 0, M.E * sizeof(double), s));
+  VEF_CUDA_TRY(cudaMemsetAsync(M.dev_status + 1, 0, sizeof(unsigned int), s));
+  VEF_CUDA_TRY(cudaMemsetAsync(M.dev_status + 3, 0, sizeof(unsigned int), s));
+  switch (M.p) {
+    case 1: st = launch_adjoint<1>(a, s); break;
+    case 2: st = launch_adjoint<2>(a, s); break;
+    case 3: st = launch_adjoint<3>(a, s); break;
+    default: st = launch_adjoint<4>(a, s); break;
+  }
+  if (st != VEF_OK) return st;
+  if (info) {
+    info->passes = 1;
+    info->rel_residual = -1.0;
+    info->coupled_groups = S->coupled_groups;
+    info->lagged_face_points = S->lagged_points;
+    info->levels = S->levels;
+    return collect_status(M, s, info);
+  }
+  return VEF_OK;
+}

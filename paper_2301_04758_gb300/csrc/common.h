@@ -1,0 +1,127 @@
+// Shared internal declarations of libvef (host and device).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "vef.h"
+
+namespace vef {
+
+constexpr int kMaxP = 4;                 // DG order p in 1..4  -> n <= 25 dofs
+constexpr int kMaxM = 4;                 // mesh order m in 1..4
+constexpr int kMaxN = (kMaxP + 1) * (kMaxP + 1);
+constexpr int kMaxNq = kMaxP + 2;        // quadrature points per direction
+constexpr int kMaxD = 1023;              // directions (10 bits in a packed task code)
+constexpr long long kMaxE = (1LL << 22); // elements (22 bits in a packed task code)
+constexpr double kFourPi = 12.566370614359172953850573533118;
+
+// 1D tables for DG order p: GLL nodes, GL points/weights, Lagrange values and
+// derivatives of the GLL basis at the GL points.  Passed to kernels by value.
+struct Tab1D {
+  int p, np1, nq;
+  double gll[kMaxP + 1];
+  double gl[kMaxNq];
+  double glw[kMaxNq];
+  double l[kMaxP + 1][kMaxNq];   // l_a(s_k)
+  double dl[kMaxP + 1][kMaxNq];  // l_a'(s_k)
+};
+
+// host-side tables (tables.cpp)
+void gll_nodes(int m, double* x);                    // m+1 points on [0,1]
+void gauss_legendre(int n, double* x, double* w);    // n points, weights sum to 1
+void lagrange_eval(int nn, const double* nodes, double x, double* val, double* der);
+Tab1D make_tab1d(int p);
+
+// error reporting
+void set_last_error(const std::string& msg);
+vef_status cuda_fail(cudaError_t err, const char* what);
+#define VEF_CUDA_TRY(call)                                        \
+  do {                                                            \
+    cudaError_t _e = (call);                                      \
+    if (_e != cudaSuccess) return ::vef::cuda_fail(_e, #call);    \
+  } while (0)
+
+// device status word values written by kernels (bit flags)
+enum : unsigned int {
+  kDevTimeout = 1u,
+  kDevNotConverged = 2u,
+  kDevNonpositive = 4u,
+  kDevSingular = 8u,
+};
+
+// Per-direction-set schedule: dependency levels, element groups and task chunks.
+struct Schedule {
+  std::vector<double> omega;   // [D][2] host copy (key)
+  std::vector<double> weights; // [D]
+  int D = 0;
+  int levels = 0;
+  long long members = 0;       // == D*E
+  int nchunks = 0;
+  long long nslots = 0;
+  long long coupled_groups = 0;
+  long long lagged_points = 0;
+  int slots_per_chunk = 0;     // single-element tasks per warp chunk
+  // device arrays
+  int* chunk_begin = nullptr;  // [nchunks+1] slot offsets
+  int* slot_first = nullptr;   // [nslots] first member index (-1 = padding)
+  int* slot_count = nullptr;   // [nslots] members in the group
+  uint32_t* member_code = nullptr;  // [members] (d << 22) | e, in schedule order
+  int* member_of = nullptr;    // [D][E] -> member index
+  uint16_t* faceinfo = nullptr;  // [D][E] bits 0-3 inflow face, 4-7 intra-group face, 8-11 outflow to a neighbour
+  double* omega_dev = nullptr; // [D][2]
+  double* weights_dev = nullptr;  // [D]
+  // factor records (lazily allocated): FP64 and FP32 copies
+  void* rec64 = nullptr;
+  void* rec32 = nullptr;
+  size_t rec_elems = 0;        // per member
+  ~Schedule();
+};
+
+struct Mesh {
+  int device = 0;
+  int nx = 0, ny = 0, m = 0, p = 0, n = 0, nq = 0;
+  long long E = 0, nbf = 0;
+  Tab1D tab{};
+  // geometry (device, FP64)
+  double* Mmat = nullptr;   // [E][n][n]
+  double* Gx = nullptr;     // [E][n][n]
+  double* Gy = nullptr;     // [E][n][n]
+  double* nds = nullptr;    // [E][4][nq][2] outward n ds (canonical on shared faces)
+  float* Mmat32 = nullptr;  // FP32 copies for the mixed path (lazily)
+  float* Gx32 = nullptr;
+  float* Gy32 = nullptr;
+  float* nds32 = nullptr;
+  std::vector<double> nds_host;  // host copy for schedule building
+  // schedules keyed by direction set
+  std::vector<std::unique_ptr<Schedule>> schedules;
+  // scratch
+  uint32_t* flags = nullptr;     // [capacity] completion epochs per (d,e)
+  size_t flags_cap = 0;
+  uint32_t epoch = 0;
+  unsigned int* dev_status = nullptr;  // [8]: 0 status bits, 1 abort, 2 max inner it, 3 chunk counter
+  double* bvol = nullptr;        // [E][n] direction-independent right-hand side
+  double* work = nullptr;        // general scratch (phi iterates, reductions)
+  size_t work_cap = 0;
+  double* work2 = nullptr;
+  size_t work2_cap = 0;
+  ~Mesh();
+};
+
+vef_status ensure_buffer(void** ptr, size_t* cap, size_t bytes);
+vef_status mesh_float_copies(Mesh* mesh, cudaStream_t stream);
+vef_status ensure_flags(Mesh* mesh, size_t count);
+vef_status factor_records(Mesh* mesh, Schedule* S, const double* sigma_t, int precision,
+                          cudaStream_t stream);
+Schedule* get_schedule(Mesh* mesh, const double* omega, const double* weights, int D,
+                       cudaStream_t stream, vef_status* st);
+
+}  // namespace vef
+
+struct vef_mesh_s {
+  vef::Mesh impl;
+};

@@ -1,0 +1,155 @@
+// Local factorisation of the upwind element systems (template; included once per order) (no inter-element dependencies).
+//
+// For direction d and element e the element matrix is
+//     A = sigma_t M - mu Gx - eta Gy + sum_f sum_k max(c_k, 0) l_a(s_k) l_b(s_k)
+// (outflow face terms on the face nodes a, b; c_k = w_k Omega . (n ds)_k), and the
+// coupling to the upwind neighbour across an inflow face f is
+//     (Cin_f)_{a t} = sum_k min(c_k, 0) l_a(s_k) l_t(s_k),
+// acting on the neighbour's face-node values.  One thread per (element, direction)
+// assembles A, inverts it in place (Gauss-Jordan) and forms W_f = A^{-1} Cin_f for the
+// interior inflow faces.  Record per (element, direction), in schedule order:
+//     [A^{-1} column-major n x n][W_0 ... W_3, each column-major n x (p+1)].
+#pragma once
+#include <type_traits>
+
+#include "device.cuh"
+
+#ifndef VEF_FACTOR_P
+#error "define VEF_FACTOR_P (1..4) before including factor_impl.cuh"
+#endif
+
+namespace vef {
+namespace {
+
+static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// ------------------------------------------------------------------- factorisation
+template <int P, typename T>
+__global__ void __launch_bounds__(128)
+factor_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t* __restrict__ finfo,
+              const double* __restrict__ omega, const double* __restrict__ sigma_t,
+              const T* __restrict__ Mm, const T* __restrict__ Gxm, const T* __restrict__ Gym,
+              const T* __restrict__ nds, FaceTab<T> ft, int nx, int ny, long long E,
+              T* __restrict__ rec, unsigned int* status) {
+  constexpr int Q = P + 1, N = Q * Q, NQ = P + 2, R = rec_size<P>();
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (m >= nmem) return;
+  const uint32_t c = code[m];
+  const int d = (int)(c >> 22), e = (int)(c & 0x3fffffu);
+  const T mu = (T)omega[2 * d], eta = (T)omega[2 * d + 1];
+  const T st = (T)sigma_t[e];
+  const uint16_t bits = finfo[(size_t)d * E + e];
+  T A[N * N];
+  const T* Me = Mm + (size_t)e * N * N;
+  const T* Xe = Gxm + (size_t)e * N * N;
+  const T* Ye = Gym + (size_t)e * N * N;
+#pragma unroll
+  for (int ij = 0; ij < N * N; ++ij) A[ij] = st * Me[ij] - mu * Xe[ij] - eta * Ye[ij];
+  T Cin[4][Q][Q];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    T cp[NQ], cm[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      const T* v = nds + (((size_t)e * 4 + f) * NQ + k) * 2;
+      const T s = ft.w[k] * (mu * v[0] + eta * v[1]);
+      cp[k] = s > (T)0 ? s : (T)0;
+      cm[k] = s < (T)0 ? s : (T)0;
+    }
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+#pragma unroll
+      for (int b = 0; b < Q; ++b) {
+        T vo = 0, vi = 0;
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+          const T ll = ft.l[a][k] * ft.l[b][k];
+          vo += cp[k] * ll;
+          vi += cm[k] * ll;
+        }
+        A[face_dof<P>(f, a) * N + face_dof<P>(f, b)] += vo;
+        Cin[f][a][b] = vi;
+      }
+    }
+  }
+  // in-place Gauss-Jordan inversion (no pivoting: the upwind element matrix has a
+  // positive definite symmetric part, sigma_t M + (1/2) sum |Omega.n| face mass)
+  constexpr int KU = P <= 2 ? N : 1;
+#pragma unroll KU
+  for (int k = 0; k < N; ++k) {
+    const T piv = A[k * N + k];
+    if (!(fabs(piv) > tiny_pivot<T>())) atomicOr(status, kDevSingular);
+    const T inv = (T)1 / piv;
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      if (j != k) A[k * N + j] *= inv;
+    A[k * N + k] = inv;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      if (i == k) continue;
+      const T fct = A[i * N + k];
+#pragma unroll
+      for (int j = 0; j < N; ++j)
+        if (j != k) A[i * N + j] -= fct * A[k * N + j];
+      A[i * N + k] = -fct * inv;
+    }
+  }
+  T* out = rec + (size_t)m * R;
+#pragma unroll
+  for (int j = 0; j < N; ++j)
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[j * N + i] = A[i * N + j];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    if (!(bits & (1u << f)) || nb_elem(nx, ny, e, f) < 0) continue;
+#pragma unroll
+    for (int t = 0; t < Q; ++t)
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        T w = 0;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) w += A[i * N + face_dof<P>(f, a)] * Cin[f][a][t];
+        out[N * N + f * N * Q + t * N + i] = w;
+      }
+  }
+}
+
+
+template <int P, typename T>
+static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, cudaStream_t stream) {
+  const size_t R = rec_size<P>();
+  void** recp = std::is_same<T, double>::value ? &S.rec64 : &S.rec32;
+  if (!*recp) {
+    size_t cap = 0;
+    vef_status st = ensure_buffer(recp, &cap, (size_t)S.members * R * sizeof(T));
+    if (st != VEF_OK) return st;
+  }
+  const T* Mm;
+  const T* Gx;
+  const T* Gy;
+  const T* nds;
+  if (std::is_same<T, double>::value) {
+    Mm = (const T*)M.Mmat; Gx = (const T*)M.Gx; Gy = (const T*)M.Gy; nds = (const T*)M.nds;
+  } else {
+    vef_status st = mesh_float_copies(&M, stream);
+    if (st != VEF_OK) return st;
+    Mm = (const T*)M.Mmat32; Gx = (const T*)M.Gx32; Gy = (const T*)M.Gy32; nds = (const T*)M.nds32;
+  }
+  factor_kernel<P, T><<<nblk(S.members, 128), 128, 0, stream>>>(
+      S.members, S.member_code, S.faceinfo, S.omega_dev, sigma_t, Mm, Gx, Gy, nds,
+      make_facetab<T>(M.tab), M.nx, M.ny, M.E, (T*)*recp, M.dev_status);
+  VEF_CUDA_TRY(cudaGetLastError());
+  return VEF_OK;
+}
+
+
+}  // namespace
+
+// instantiation for one DG order (one translation unit per order keeps builds parallel)
+vef_status VEF_FACTOR_FN(Mesh* mesh, Schedule* S, const double* sigma_t, int precision,
+                         cudaStream_t stream) {
+  if (precision == VEF_FP64) return launch_factor<VEF_FACTOR_P, double>(*mesh, *S, sigma_t, stream);
+  return launch_factor<VEF_FACTOR_P, float>(*mesh, *S, sigma_t, stream);
+}
+
+}  // namespace vef

@@ -1,0 +1,347 @@
+// Sweep schedule: per-direction upwind dependency graph, its strongly coupled element
+// groups, dependency levels and the warp-sized task chunks the sweep kernel claims.
+//
+// For direction Omega_d, element e depends on its neighbour across face f when some
+// Gauss point of that face is strictly inflow (Omega . n ds < 0); a tangential point
+// (Omega . n = 0) counts as outflow.  On straight meshes this graph is the per-quadrant
+// diagonal wavefront.  On curved meshes faces tilt, so the quadrant order no longer
+// follows the flow, and a face can be inflow at some points and outflow at others,
+// which couples the two elements both ways (the lagging situation the paper describes
+// for re-entrant faces in its thick-diffusion section).  The graph's strongly
+// connected components ("groups") are solved as units by an inner block Gauss-Seidel
+// iteration; everything else is a DAG processed level by level.  Within a group the
+// members are ordered along the net face flux so that only the minority points of
+// mixed faces are iterated.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <thread>
+
+#include "common.h"
+
+namespace vef {
+
+namespace {
+
+struct DirGraph {
+  std::vector<int> comp;          // [E] component id
+  std::vector<int> comp_level;    // [ncomp]
+  std::vector<int> comp_first;    // [ncomp+1] offsets into comp_members
+  std::vector<int> comp_members;  // ordered members
+  std::vector<uint16_t> info;     // [E] face bits
+  int ncomp = 0;
+  int levels = 0;
+  long long lagged = 0;
+  long long groups = 0;
+};
+
+inline int nb_of(int nx, int ny, int e, int f) {
+  int i = e % nx, j = e / nx;
+  switch (f) {
+    case 0: return j > 0 ? e - nx : -1;
+    case 1: return i < nx - 1 ? e + 1 : -1;
+    case 2: return j < ny - 1 ? e + nx : -1;
+    default: return i > 0 ? e - 1 : -1;
+  }
+}
+constexpr int kOpp[4] = {2, 3, 0, 1};
+
+void build_direction(const Mesh& M, double mu, double eta, DirGraph& G) {
+  const int nx = M.nx, ny = M.ny, nq = M.nq;
+  const int E = (int)M.E;
+  const double* nds = M.nds_host.data();
+  G.info.assign(E, 0);
+  // face signs
+  for (int e = 0; e < E; ++e) {
+    uint16_t bits = 0;
+    for (int f = 0; f < 4; ++f) {
+      bool anyin = false, anyout = false;
+      for (int k = 0; k < nq; ++k) {
+        const double* v = nds + (((size_t)e * 4 + f) * nq + k) * 2;
+        double s = mu * v[0] + eta * v[1];
+        if (s < 0.0) anyin = true;
+        if (s > 0.0) anyout = true;
+      }
+      const int nb = nb_of(nx, ny, e, f);
+      if (anyin) bits |= (uint16_t)(1u << f);
+      if (anyout && nb >= 0) bits |= (uint16_t)(1u << (8 + f));
+    }
+    G.info[e] = bits;
+  }
+  // Tarjan's strongly connected components, iterative.  Edges: donor -> receiver, i.e.
+  // from e to its neighbour across f when bit 8+f (neighbour has inflow from e).
+  std::vector<int> index(E, -1), low(E, 0), stack;
+  std::vector<char> onstack(E, 0);
+  G.comp.assign(E, -1);
+  stack.reserve(1024);
+  int idx = 0, ncomp = 0;
+  std::vector<std::pair<int, int>> call;  // (node, next face)
+  for (int s = 0; s < E; ++s) {
+    if (index[s] >= 0) continue;
+    call.push_back({s, 0});
+    index[s] = low[s] = idx++;
+    stack.push_back(s);
+    onstack[s] = 1;
+    while (!call.empty()) {
+      int v = call.back().first;
+      int& f = call.back().second;
+      if (f < 4) {
+        int ff = f++;
+        if (!(G.info[v] & (1u << (8 + ff)))) continue;
+        int w = nb_of(nx, ny, v, ff);
+        if (index[w] < 0) {
+          index[w] = low[w] = idx++;
+          stack.push_back(w);
+          onstack[w] = 1;
+          call.push_back({w, 0});
+        } else if (onstack[w]) {
+          low[v] = std::min(low[v], index[w]);
+        }
+        continue;
+      }
+      if (low[v] == index[v]) {
+        int w;
+        do {
+          w = stack.back();
+          stack.pop_back();
+          onstack[w] = 0;
+          G.comp[w] = ncomp;
+        } while (w != v);
+        ++ncomp;
+      }
+      call.pop_back();
+      if (!call.empty()) {
+        int u = call.back().first;
+        low[u] = std::min(low[u], low[v]);
+      }
+    }
+  }
+  G.ncomp = ncomp;
+  // members per component
+  std::vector<int> csize(ncomp, 0);
+  for (int e = 0; e < E; ++e) csize[G.comp[e]]++;
+  G.comp_first.assign(ncomp + 1, 0);
+  for (int c = 0; c < ncomp; ++c) G.comp_first[c + 1] = G.comp_first[c] + csize[c];
+  G.comp_members.assign(E, 0);
+  {
+    std::vector<int> fill(G.comp_first.begin(), G.comp_first.end() - 1);
+    for (int e = 0; e < E; ++e) G.comp_members[fill[G.comp[e]]++] = e;
+  }
+  const int sx = mu >= 0 ? 1 : -1, sy = eta >= 0 ? 1 : -1;
+  auto qkey = [&](int e) {
+    int i = e % nx, j = e / nx;
+    return (sx > 0 ? i : nx - 1 - i) + (sy > 0 ? j : ny - 1 - j);
+  };
+  // order members of multi-element groups along the net face flux; set intra bits
+  for (int c = 0; c < ncomp; ++c) {
+    int b = G.comp_first[c], n = csize[c];
+    if (n == 1) continue;
+    G.groups++;
+    std::vector<int> mem(G.comp_members.begin() + b, G.comp_members.begin() + b + n);
+    std::vector<int> indeg(n, 0);
+    std::vector<std::vector<int>> out(n);
+    auto pos = [&](int e) { return (int)(std::find(mem.begin(), mem.end(), e) - mem.begin()); };
+    for (int a = 0; a < n; ++a) {
+      int u = mem[a];
+      for (int f = 0; f < 4; ++f) {
+        int w = nb_of(nx, ny, u, f);
+        if (w < 0 || G.comp[w] != c) continue;
+        G.info[u] |= (uint16_t)(1u << (4 + f));
+        double net = 0.0;
+        for (int k = 0; k < nq; ++k) {
+          const double* v = nds + (((size_t)u * 4 + f) * nq + k) * 2;
+          double s = mu * v[0] + eta * v[1];
+          net += M.tab.glw[k] * s;
+          if (s < 0.0) G.lagged++;
+        }
+        if (net > 0.0) {  // u feeds w on balance
+          out[a].push_back(pos(w));
+          indeg[pos(w)]++;
+        }
+      }
+    }
+    std::vector<int> order;
+    std::vector<char> done(n, 0);
+    for (int it = 0; it < n; ++it) {
+      int best = -1;
+      for (int a = 0; a < n; ++a) {
+        if (done[a]) continue;
+        if (best < 0 || indeg[a] < indeg[best] ||
+            (indeg[a] == indeg[best] && qkey(mem[a]) < qkey(mem[best])))
+          best = a;
+      }
+      done[best] = 1;
+      order.push_back(mem[best]);
+      for (int w : out[best]) indeg[w]--;
+    }
+    std::copy(order.begin(), order.end(), G.comp_members.begin() + b);
+  }
+  // levels of the condensed DAG (Kahn)
+  std::vector<int> cindeg(ncomp, 0);
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 4; ++f)
+      if (G.info[e] & (1u << (8 + f))) {
+        int w = nb_of(nx, ny, e, f);
+        if (G.comp[w] != G.comp[e]) cindeg[G.comp[w]]++;
+      }
+  G.comp_level.assign(ncomp, 0);
+  std::vector<int> queue;
+  queue.reserve(ncomp);
+  for (int c = 0; c < ncomp; ++c)
+    if (cindeg[c] == 0) queue.push_back(c);
+  size_t head = 0;
+  int maxl = 0;
+  while (head < queue.size()) {
+    int c = queue[head++];
+    maxl = std::max(maxl, G.comp_level[c]);
+    for (int t = G.comp_first[c]; t < G.comp_first[c + 1]; ++t) {
+      int e = G.comp_members[t];
+      for (int f = 0; f < 4; ++f) {
+        if (!(G.info[e] & (1u << (8 + f)))) continue;
+        int w = nb_of(nx, ny, e, f);
+        int cw = G.comp[w];
+        if (cw == c) continue;
+        G.comp_level[cw] = std::max(G.comp_level[cw], G.comp_level[c] + 1);
+        if (--cindeg[cw] == 0) queue.push_back(cw);
+      }
+    }
+  }
+  G.levels = maxl + 1;
+}
+
+template <typename T>
+vef_status upload(T** dst, const std::vector<T>& src) {
+  VEF_CUDA_TRY(cudaMalloc((void**)dst, std::max<size_t>(1, src.size()) * sizeof(T)));
+  if (!src.empty())
+    VEF_CUDA_TRY(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return VEF_OK;
+}
+
+}  // namespace
+
+Schedule* get_schedule(Mesh* mesh, const double* omega, const double* weights, int D,
+                       cudaStream_t stream, vef_status* st) {
+  *st = VEF_OK;
+  for (auto& s : mesh->schedules) {
+    if (s->D == D && std::memcmp(s->omega.data(), omega, sizeof(double) * 2 * D) == 0 &&
+        std::memcmp(s->weights.data(), weights, sizeof(double) * D) == 0)
+      return s.get();
+  }
+  const Mesh& M = *mesh;
+  const int E = (int)M.E;
+  std::vector<DirGraph> graphs(D);
+  {
+    unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 32));
+    nt = std::min<unsigned>(nt, (unsigned)D);
+    std::vector<std::thread> pool;
+    for (unsigned t = 0; t < nt; ++t)
+      pool.emplace_back([&, t]() {
+        for (int d = (int)t; d < D; d += (int)nt)
+          build_direction(M, omega[2 * d], omega[2 * d + 1], graphs[d]);
+      });
+    for (auto& th : pool) th.join();
+  }
+  std::unique_ptr<Schedule> S(new Schedule());
+  S->D = D;
+  S->omega.assign(omega, omega + 2 * D);
+  S->weights.assign(weights, weights + D);
+  S->members = (long long)D * E;
+  const int spc = std::max(1, 32 / M.n);
+  S->slots_per_chunk = spc;
+  int levels = 0;
+  for (auto& g : graphs) {
+    levels = std::max(levels, g.levels);
+    S->coupled_groups += g.groups;
+    S->lagged_points += g.lagged;
+  }
+  S->levels = levels;
+  // bucket components by level
+  std::vector<std::vector<std::pair<int, int>>> bylevel(levels);  // (d, comp)
+  for (int d = 0; d < D; ++d)
+    for (int c = 0; c < graphs[d].ncomp; ++c) bylevel[graphs[d].comp_level[c]].push_back({d, c});
+  std::vector<int> chunk_begin{0}, slot_first, slot_count;
+  std::vector<uint32_t> member_code;
+  std::vector<int> member_of((size_t)D * E, -1);
+  member_code.reserve((size_t)D * E);
+  auto add_member = [&](int d, int e) {
+    member_of[(size_t)d * E + e] = (int)member_code.size();
+    member_code.push_back(((uint32_t)d << 22) | (uint32_t)e);
+  };
+  for (int L = 0; L < levels; ++L) {
+    int in_chunk = 0;
+    for (auto& dc : bylevel[L]) {
+      const DirGraph& g = graphs[dc.first];
+      int b = g.comp_first[dc.second], n = g.comp_first[dc.second + 1] - b;
+      if (n == 1) {
+        slot_first.push_back((int)member_code.size());
+        slot_count.push_back(1);
+        add_member(dc.first, g.comp_members[b]);
+        if (++in_chunk == spc) {
+          chunk_begin.push_back((int)slot_first.size());
+          in_chunk = 0;
+        }
+      }
+    }
+    if (in_chunk) chunk_begin.push_back((int)slot_first.size());
+    for (auto& dc : bylevel[L]) {
+      const DirGraph& g = graphs[dc.first];
+      int b = g.comp_first[dc.second], n = g.comp_first[dc.second + 1] - b;
+      if (n > 1) {
+        slot_first.push_back((int)member_code.size());
+        slot_count.push_back(n);
+        for (int t = 0; t < n; ++t) add_member(dc.first, g.comp_members[b + t]);
+        chunk_begin.push_back((int)slot_first.size());
+      }
+    }
+  }
+  S->nchunks = (int)chunk_begin.size() - 1;
+  // Validate the deadlock-freedom invariant the sweep kernel relies on: every member is
+  // scheduled exactly once and each of its external upwind donors lies in an earlier
+  // chunk (warps claim chunks in increasing order and only wait on smaller ones).
+  {
+    std::vector<int> chunk_of_member(member_code.size(), -1);
+    for (int c = 0; c < S->nchunks; ++c)
+      for (int s = chunk_begin[c]; s < chunk_begin[c + 1]; ++s)
+        for (int t = 0; t < slot_count[s]; ++t) chunk_of_member[slot_first[s] + t] = c;
+    for (size_t m = 0; m < member_code.size(); ++m) {
+      int d = (int)(member_code[m] >> 22), e = (int)(member_code[m] & ((1u << 22) - 1));
+      uint16_t bits = graphs[d].info[e];
+      for (int f = 0; f < 4; ++f) {
+        if (!(bits & (1u << f)) || (bits & (1u << (4 + f)))) continue;
+        int nb = nb_of(M.nx, M.ny, e, f);
+        if (nb < 0) continue;
+        int mn = member_of[(size_t)d * E + nb];
+        if (mn < 0 || chunk_of_member[mn] < 0 || chunk_of_member[mn] >= chunk_of_member[m]) {
+          set_last_error("internal error: sweep schedule violates the dependency order");
+          *st = VEF_ERR_INVALID_ARG;
+          return nullptr;
+        }
+      }
+    }
+    for (size_t t = 0; t < member_of.size(); ++t)
+      if (member_of[t] < 0) {
+        set_last_error("internal error: sweep schedule misses an element");
+        *st = VEF_ERR_INVALID_ARG;
+        return nullptr;
+      }
+  }
+  S->nslots = (long long)slot_first.size();
+  std::vector<uint16_t> faceinfo((size_t)D * E);
+  for (int d = 0; d < D; ++d)
+    std::copy(graphs[d].info.begin(), graphs[d].info.end(), faceinfo.begin() + (size_t)d * E);
+  std::vector<double> om(omega, omega + 2 * D), wt(weights, weights + D);
+  if ((*st = upload(&S->chunk_begin, chunk_begin)) != VEF_OK) return nullptr;
+  if ((*st = upload(&S->slot_first, slot_first)) != VEF_OK) return nullptr;
+  if ((*st = upload(&S->slot_count, slot_count)) != VEF_OK) return nullptr;
+  if ((*st = upload(&S->member_code, member_code)) != VEF_OK) return nullptr;
+  if ((*st = upload(&S->member_of, member_of)) != VEF_OK) return nullptr;
+  if ((*st = upload(&S->faceinfo, faceinfo)) != VEF_OK) return nullptr;
+  if ((*st = upload(&S->omega_dev, om)) != VEF_OK) return nullptr;
+  if ((*st = upload(&S->weights_dev, wt)) != VEF_OK) return nullptr;
+  (void)stream;
+  mesh->schedules.push_back(std::move(S));
+  return mesh->schedules.back().get();
+}
+
+}  // namespace vef

@@ -1,0 +1,69 @@
+"""GPU parity of source iteration and of the adjoint sweep's gradients."""
+import numpy as np
+import pytest
+
+from _gpu import dev, host, rel, random_problem
+from oracle.transport import Discretization, sweep as o_sweep
+from oracle.iteration import source_iterate as o_iterate
+from oracle.adjoint import adjoint as o_adjoint, region_weights
+from vef_inputs import level_symmetric, seeded_media
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-10)])
+def test_source_iteration(lib, precision, tol):
+    from paper_2301_04758_gb300.api import Mesh
+    nx, m, alpha, p = 10, 3, 0.05, 2
+    om, w = level_symmetric(8)
+    E, n = nx * nx, (p + 1) ** 2
+    st, ss = seeded_media(E, 2)
+    q = np.ones((E, n))
+    mesh = Mesh(nx, nx, m, p, alpha)
+    phi, psi, dphi, info = mesh.source_iterate(dev(st), dev(ss), om, w, 5, source=dev(q),
+                                               precision=precision, info=True)
+    disc = Discretization(nx, nx, m, alpha, p)
+    rphi, rpsi, rd = o_iterate(disc, om, w, st, ss, source=q, K=5)
+    assert rel(host(phi), rphi) < tol
+    assert rel(host(psi), rpsi) < tol
+    assert np.allclose(host(dphi), rd, rtol=1e-8 if precision == "fp64" else 1e-6)
+
+
+def test_adjoint_gradients_match_oracle(lib):
+    from paper_2301_04758_gb300.api import Mesh
+    nx, m, alpha, p = 9, 3, 0.08, 2
+    om, w = level_symmetric(8)
+    E, n = nx * nx, (p + 1) ** 2
+    st, ss = seeded_media(E, 5, log10_range=(-1.0, 1.0))
+    rng = np.random.default_rng(9)
+    phi_in = rng.uniform(0.5, 1.5, (E, n))
+    q = np.ones((E, n))
+    disc = Discretization(nx, nx, m, alpha, p)
+    g = region_weights(disc)
+    psi = o_sweep(disc, om, w, st, ss, phi_in=phi_in, source=q)
+    lam, dst, dss = o_adjoint(disc, om, w, st, ss, psi, g, phi_in=phi_in)
+    mesh = Mesh(nx, nx, m, p, alpha)
+    gpsi = mesh.sweep(dev(st), dev(ss), om, w, phi_in=dev(phi_in), source=dev(q))
+    gdst, gdss, glam, info = mesh.adjoint(dev(st), dev(ss), om, w, gpsi, dev(g), phi_in=dev(phi_in),
+                                          want_lambda=True, info=True)
+    assert rel(host(glam), lam) < 1e-12, info
+    assert rel(host(gdst), dst) < 1e-12
+    assert rel(host(gdss), dss) < 1e-12
+
+
+def test_adjoint_with_coupled_groups(lib):
+    from paper_2301_04758_gb300.api import Mesh
+    prob = random_problem(20, 20, 3, 0.1, 2, 8, seed=3, sigma_range=(-1.0, 0.5), with_inflow=False)
+    disc = Discretization(20, 20, 3, 0.1, 2)
+    g = region_weights(disc, (0.2, 0.3), (0.7, 0.9))
+    psi = o_sweep(disc, prob["omega"], prob["weights"], prob["sigma_t"], prob["sigma_s"],
+                  phi_in=prob["phi_in"], source=prob["source"])
+    lam, dst, dss = o_adjoint(disc, prob["omega"], prob["weights"], prob["sigma_t"], prob["sigma_s"],
+                              psi, g, phi_in=prob["phi_in"])
+    mesh = Mesh(20, 20, 3, 2, 0.1)
+    gdst, gdss, glam, info = mesh.adjoint(dev(prob["sigma_t"]), dev(prob["sigma_s"]), prob["omega"],
+                                          prob["weights"], dev(psi), dev(g),
+                                          phi_in=dev(prob["phi_in"]), want_lambda=True, info=True)
+    assert info["coupled_groups"] > 0
+    assert rel(host(glam), lam) < 1e-12, info
+    assert rel(host(gdst), dst) < 1e-12

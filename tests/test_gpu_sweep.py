@@ -1,0 +1,140 @@
+"""GPU parity: the CUDA sweep (through the C ABI) against the FP64 oracle.
+
+Bar: FP64 path within 1e-12 relative L2 on psi; mixed path within 1e-10 on psi, phi, E.
+"""
+import numpy as np
+import pytest
+
+from _gpu import dev, host, rel, random_problem
+from oracle.transport import Discretization, sweep as o_sweep, residual as o_residual
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(prob, precision="fp64", info=True):
+    from paper_2301_04758_gb300.api import Mesh
+    mesh = Mesh(prob["nx"], prob["ny"], prob["m"], prob["p"], prob["alpha"])
+    src = prob["source"]
+    out = mesh.sweep(dev(prob["sigma_t"]), dev(prob["sigma_s"]), prob["omega"], prob["weights"],
+                     phi_in=None if prob["phi_in"] is None else dev(prob["phi_in"]),
+                     source=dev(src), inflow=None if prob["inflow"] is None else dev(prob["inflow"]),
+                     precision=precision, info=info)
+    return mesh, out
+
+
+def _oracle(prob):
+    disc = Discretization(prob["nx"], prob["ny"], prob["m"], prob["alpha"], prob["p"])
+    psi = o_sweep(disc, prob["omega"], prob["weights"], prob["sigma_t"], prob["sigma_s"],
+                  phi_in=prob["phi_in"], source=prob["source"], inflow=prob["inflow"])
+    return disc, psi
+
+
+def test_tiny_straight_q1_s4(lib):
+    """8x8 straight Q1, S4, sigma_t = 1, sigma_s = 0.5, q = 1, vacuum, phi_in = 0."""
+    from vef_inputs import config_workload
+    wl = config_workload("tiny_straight_q1_s4")
+    prob = dict(nx=8, ny=8, m=1, alpha=0.0, p=1, omega=wl["omega"], weights=wl["weights"],
+                sigma_t=wl["sigma_t"], sigma_s=wl["sigma_s"], phi_in=None, source=wl["source"],
+                inflow=None)
+    _, (psi, info) = _run(prob)
+    _, ref = _oracle(prob)
+    assert rel(host(psi), ref) < 1e-12
+    assert info["coupled_groups"] == 0 and info["levels"] == 15   # 2N-1 diagonal wavefront
+    assert info["timed_out"] == 0
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_curved_heterogeneous_all_orders(lib, p):
+    prob = random_problem(7, 5, 3, 0.06, p, 4, seed=10 + p)
+    _, (psi, info) = _run(prob)
+    _, ref = _oracle(prob)
+    assert rel(host(psi), ref) < 1e-12, info
+
+
+@pytest.mark.parametrize("sn", [8, 12])
+def test_curved_with_coupled_groups(lib, sn):
+    """Strong distortion gives faces that are part inflow, part outflow: the coupled
+    element groups must be solved to round-off, not lagged."""
+    prob = random_problem(20, 20, 3, 0.1, 2, sn, seed=3, sigma_range=(-1.0, 0.5))
+    _, (psi, info) = _run(prob)
+    disc, ref = _oracle(prob)
+    assert info["coupled_groups"] > 0, info
+    assert rel(host(psi), ref) < 1e-12, info
+
+
+def test_anisotropic_source_and_inflow(lib):
+    prob = random_problem(6, 9, 2, 0.05, 2, 8, seed=4, aniso=True)
+    _, (psi, _) = _run(prob)
+    _, ref = _oracle(prob)
+    assert rel(host(psi), ref) < 1e-12
+
+
+def test_edge_cases_single_element_and_ragged(lib):
+    for (nx, ny, p, sn) in [(1, 1, 3, 4), (9, 2, 1, 6), (2, 11, 2, 4)]:
+        prob = random_problem(nx, ny, 3, 0.04, p, sn, seed=nx * 7 + ny)
+        _, (psi, _) = _run(prob)
+        _, ref = _oracle(prob)
+        assert rel(host(psi), ref) < 1e-12, (nx, ny)
+
+
+def test_axis_aligned_and_single_direction(lib):
+    """Directions parallel to straight faces (Omega . n = 0 on two faces: outflow by
+    convention, zero weight) and a one-direction set."""
+    prob = random_problem(5, 4, 1, 0.0, 2, 4, seed=8)
+    prob["omega"] = np.array([[1.0, 0.0], [0.0, -1.0], [-0.6, 0.8]])
+    prob["weights"] = np.array([1.0, 2.0, 3.0])
+    prob["inflow"] = prob["inflow"][:3]
+    _, (psi, _) = _run(prob)
+    _, ref = _oracle(prob)
+    assert rel(host(psi), ref) < 1e-12
+    one = dict(prob, omega=prob["omega"][2:], weights=prob["weights"][2:], inflow=prob["inflow"][2:])
+    _, (psi1, _) = _run(one)
+    _, ref1 = _oracle(one)
+    assert rel(host(psi1), ref1) < 1e-12
+
+
+def test_mixed_precision_defect_correction(lib):
+    from oracle.moments import closures
+    prob = random_problem(12, 12, 3, 0.08, 3, 8, seed=21)
+    mesh, (psi, info) = _run(prob, precision="mixed")
+    disc, ref = _oracle(prob)
+    assert info["passes"] >= 2 and info["rel_residual"] <= 1e-13, info
+    assert rel(host(psi), ref) < 1e-10
+    out = mesh.moments(psi, prob["omega"], prob["weights"])
+    rc = closures(disc, ref, prob["omega"], prob["weights"])
+    assert rel(host(out["phi"]), rc["phi"]) < 1e-10
+    assert rel(host(out["E"]), rc["E"]) < 1e-10
+
+
+def test_invalid_arguments_are_rejected(lib):
+    import ctypes
+    from paper_2301_04758_gb300 import _lib
+    from paper_2301_04758_gb300.api import Mesh
+    h = ctypes.c_void_p()
+    assert lib.vef_mesh_create(0, 4, 1, 1, 0.0, None, ctypes.byref(h)) == _lib.VEF_ERR_INVALID_ARG
+    assert lib.vef_mesh_create(4, 4, 1, 7, 0.0, None, ctypes.byref(h)) == _lib.VEF_ERR_INVALID_ARG
+    mesh = Mesh(3, 3, 1, 1, 0.0)
+    st = lib.vef_sweep(mesh.handle, None, None, None, None, 0, None, None, None, 0, None, None,
+                       None, None)
+    assert st == _lib.VEF_ERR_INVALID_ARG
+
+
+@pytest.mark.slow
+def test_full_size_sine256_q2_s8_global_residual(lib):
+    """At the benchmark size (256^2, Q2, S8, seeded media) the GPU psi satisfies the
+    oracle's global upwind system: ||b - L psi|| / ||b|| per sampled direction."""
+    from vef_inputs import config_workload
+    wl = config_workload("sine256_q2_s8")
+    from paper_2301_04758_gb300.api import Mesh
+    mesh = Mesh(256, 256, 3, 2, 0.05)
+    psi, info = mesh.sweep(dev(wl["sigma_t"]), dev(wl["sigma_s"]), wl["omega"], wl["weights"],
+                           source=dev(wl["source"]), info=True)
+    assert info["timed_out"] == 0
+    disc = Discretization(256, 256, 3, 0.05, 2)
+    P = host(psi)
+    for d in (0, 13, 27, 39):
+        om = wl["omega"][d:d + 1]
+        r = o_residual(disc, om, wl["sigma_t"], wl["sigma_s"], P[d:d + 1], source=wl["source"])
+        L, c = disc.operator(om[0], wl["sigma_t"])
+        b = disc.rhs(c, 0, wl["sigma_s"], None, wl["source"], None)
+        assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-13, d
