@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Benchmark: DG S_N sweep + VEF closure pass on one GB300 (or N replicas).
+
+Workload (one "step"): the 256 x 256 sine-curved (alpha = 0.05, third-order map) mesh of
+[0,1]^2, DG Q2, level-symmetric S8 (40 directions), per-element sigma_t log-uniform in
+[0.1, 100] and sigma_s/sigma_t uniform in [0.9, 0.9999] (seed 2), isotropic source 1,
+vacuum inflow: 10 source iterations (local factorisation once, 10 sweeps, 10 scalar-flux
+updates) followed by the closure pass (phi, J, E, E_b, J_in).  Metric: angular-DOF
+updates per second = E (p+1)^2 D * 10 / step time, FP64 (`value`) and mixed precision
+(`mixed`).  Inputs live in HBM for `value`; `e2e` adds the host->device copy of the
+step's inputs and the device->host copy of its outputs through the same C-ABI calls.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "sine256_q2_s8"
+K_ITER = 10
+# FP64 peak from unit counts: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2070 MHz
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ accounting
+def flops_factor(p, inflow_faces=2.0):
+    """Algorithmic flops of one (element, direction) factorisation (FMA = 2 flops):
+    assembly sigma_t M - mu Gx - eta Gy (5 n^2), four faces' outflow/inflow face
+    matrices (4 [4 nq + 5 (p+1)^2 nq + (p+1)^2]), in-place Gauss-Jordan inversion
+    (n [(n-1) + (n-1)(2n-1)]) and W_f = A^{-1} Cin_f per interior inflow face (2 n (p+1)^2)."""
+    n, q, nq = (p + 1) ** 2, p + 1, p + 2
+    return (5 * n * n + 4 * (4 * nq + 5 * q * q * nq + q * q)
+            + n * ((n - 1) + (n - 1) * (2 * n - 1)) + inflow_faces * 2 * n * q * q)
+
+
+def flops_sweep(p, inflow_faces=2.0):
+    """Per (element, direction) sweep flops: psi = A^{-1} b (2 n^2) and the upwind
+    couplings W_f u_f (2 n (p+1) per inflow face)."""
+    n = (p + 1) ** 2
+    return 2 * n * n + inflow_faces * 2 * n * (p + 1)
+
+
+def bytes_sweep(p, D, word=8, inflow_faces=2.0):
+    """Per (element, direction) sweep DRAM bytes: the factor record's A^{-1} and used W_f,
+    psi written, upwind face traces read, plus the direction-independent rhs / D."""
+    n = (p + 1) ** 2
+    return word * (n * n + inflow_faces * n * (p + 1)) + 8 * n + 8 * inflow_faces * (p + 1) + 8 * n / D
+
+
+def src_hash(*names):
+    h = hashlib.sha256()
+    for nm in names:
+        with open(os.path.join(ROOT, "paper_2301_04758_gb300", "csrc", nm), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel, source_files):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is
+    unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = src_hash(*source_files)
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == WORKLOAD:
+            return float(parts[2]) if parts[3] == want else None
+    return None
+
+
+# ----------------------------------------------------------------------- clocks
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = [l.strip().split(",") for l in open(self.tmp.name) if l.strip()]
+        os.unlink(self.tmp.name)
+        sm, mx, reasons = [], 0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2301_04758_gb300 import build as vbuild
+    vbuild.build()
+    from paper_2301_04758_gb300.api import Mesh, fma_peak
+    from vef_inputs import config_workload
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wl = config_workload(WORKLOAD)
+    om, w = wl["omega"], wl["weights"]
+    E, n, D, p = wl["E"], wl["n"], wl["D"], wl["p"]
+    updates = E * n * D * K_ITER
+    mesh = Mesh(wl["nx"], wl["ny"], wl["mesh_order"], p, wl["alpha"])
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev).contiguous()
+    st, ss, q = T(wl["sigma_t"]), T(wl["sigma_s"]), T(wl["source"])
+    psi = torch.empty(D, E, n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(precision, st_=None, ss_=None, q_=None):
+        phi, ps, dphi = mesh.source_iterate(st_ if st_ is not None else st, ss_ if ss_ is not None else ss,
+                                            om, w, K_ITER, source=q_ if q_ is not None else q,
+                                            precision=precision, psi=psi)
+        out = mesh.moments(ps, om, w, outputs=("phi", "J", "E", "Eb", "Jin"))
+        return phi, out, dphi
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(precision, steps, profile=False):
+        for _ in range(args.warmup):
+            step(precision)
+        torch.cuda.synchronize()
+        mesh.sync()
+        if profile:
+            mesh.profile(True)
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            res = step(precision)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        prof = mesh.profile_read() if profile else None
+        if profile:
+            mesh.profile(False)
+        mesh.sync()
+        return ms, prof, res
+
+    clocks = Clocks(local_rank)
+    clocks.start()
+    ms64, prof64, res64 = timed("fp64", args.steps, profile=True)
+    clk = clocks.stop()
+    clocks2 = Clocks(local_rank)
+    clocks2.start()
+    ms32, prof32, res32 = timed("mixed", args.steps, profile=True)
+    clk2 = clocks2.stop()
+
+    # errors of the mixed path against the FP64 path (same inputs)
+    def relerr(a, b):
+        return float(torch.linalg.norm((a - b).flatten()) / torch.linalg.norm(b.flatten()))
+    mixed_err = {"phi": relerr(res32[1]["phi"], res64[1]["phi"]), "J": relerr(res32[1]["J"], res64[1]["J"]),
+                 "E": relerr(res32[1]["E"], res64[1]["E"]), "Eb": relerr(res32[1]["Eb"], res64[1]["Eb"])}
+
+    # end to end through the public API: pinned host inputs -> device, outputs -> host
+    h_st = torch.tensor(wl["sigma_t"], dtype=torch.float64).pin_memory()
+    h_ss = torch.tensor(wl["sigma_s"], dtype=torch.float64).pin_memory()
+    h_q = torch.tensor(wl["source"], dtype=torch.float64).pin_memory()
+    d_st, d_ss, d_q = torch.empty_like(st), torch.empty_like(ss), torch.empty_like(q)
+    outs_host = None
+
+    def e2e_step():
+        nonlocal outs_host
+        d_st.copy_(h_st, non_blocking=True)
+        d_ss.copy_(h_ss, non_blocking=True)
+        d_q.copy_(h_q, non_blocking=True)
+        phi, out, _ = step("fp64", d_st, d_ss, d_q)
+        if outs_host is None:
+            outs_host = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
+        for k, v in out.items():
+            outs_host[k].copy_(v, non_blocking=True)
+        return out
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        out = e2e_step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = t0.elapsed_time(t1)
+    h2d = 8 * (2 * E + E * n)
+    d2h = sum(8 * v.numel() for v in out.values())
+
+    # max over ranks
+    def rmax(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+    ms64, ms32, ms_e2e = rmax(ms64), rmax(ms32), rmax(ms_e2e)
+
+    steps = args.steps
+    value = world * updates * steps / (ms64 * 1e-3)
+    mixed_value = world * updates * steps / (ms32 * 1e-3)
+    e2e_value = world * updates * steps / (ms_e2e * 1e-3)
+
+    # roofline of the dominant kernel (FP64 run), from the live per-kernel CUDA events
+    fp64_meas = fma_peak("fp64") / 1e9
+    kern = {k: v for k, v in prof64.items() if v[0] > 0}
+    dom = max(kern, key=lambda k: kern[k][1])
+    nfac = prof64["factor"][0]
+    nsw = prof64["sweep"][0]
+    roof = {}
+    if nfac:
+        avg = prof64["factor"][1] / nfac
+        fl = flops_factor(p) * E * D
+        roof["factor"] = {"bound": "alu", "achieved": fl / (avg * 1e-3) / 1e12, "unit": "TFLOP/s",
+                          "peak": FP64_PEAK_GFLOPS / 1e3, "avg_ms": avg, "flops_per_launch": fl}
+    if nsw:
+        avg = prof64["sweep"][1] / nsw
+        fl = flops_sweep(p) * E * D
+        by = bytes_sweep(p, D) * E * D
+        roof["sweep"] = {"bound": "alu", "achieved": fl / (avg * 1e-3) / 1e12, "unit": "TFLOP/s",
+                         "peak": FP64_PEAK_GFLOPS / 1e3, "avg_ms": avg, "flops_per_launch": fl,
+                         "hbm_GBps": by / (avg * 1e-3) / 1e9, "bytes_per_launch": by}
+    for k, r in roof.items():
+        r["frac"] = r["achieved"] / r["peak"]
+        r["peak_measured_fma"] = fp64_meas / 1e3
+    main = roof.get(dom) or roof.get("factor")
+    srcmap = {"factor": ["factor_impl.cuh", "factor_p2.cu"], "sweep": ["sweep.cu", "device.cuh"]}
+    roofline = None
+    if main:
+        roofline = {"bound": main["bound"], "achieved": round(main["achieved"], 4),
+                    "peak": round(main["peak"], 4), "unit": main["unit"],
+                    "frac": round(main["frac"], 4),
+                    "traffic": ncu_traffic(dom, srcmap.get(dom, [])),
+                    "kernel": dom, "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
+                    "peak_measured_fma_tflops": round(fp64_meas / 1e3, 4)}
+    launches = sum(v[0] for v in prof64.values())
+
+    line = {
+        "metric": "sweep angular-DOF updates/s (10 source iterations + closures)",
+        "value": value, "unit": "angular-DOF updates/s", "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms64 / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "256x256 sine-curved Q3 mesh (alpha 0.05), DG Q2, S8 (40 dirs), "
+                               "seeded sigma_t/sigma_s (seed 2), q=1, vacuum, 10 source iterations + closures",
+                   "nx": 256, "ny": 256, "p": p, "mesh_order": 3, "directions": D,
+                   "source_iterations": K_ITER, "angular_dof_updates_per_step": updates,
+                   "l2": "inputs larger than L2 (factor records ~4 GB)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "mixed": {"value": mixed_value, "ms_per_step": ms32 / steps, "dtype": "f32 solve + f64 defect correction",
+                  "rel_err_vs_fp64": mixed_err, "clocks": clk2,
+                  "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof32.items() if v[0]}},
+        "e2e": {"value": e2e_value, "unit": "angular-DOF updates/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e / steps},
+        "roofline": roofline,
+        "roofline_kernels": roof,
+        "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof64.items() if v[0]},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "info": {"coupled_groups_and_levels": None},
+    }
+    _, info = mesh.sweep(st, ss, om, w, source=q, info=True, psi=psi)
+    line["info"] = {"levels": info["levels"], "coupled_groups": info["coupled_groups"],
+                    "lagged_face_points": info["lagged_face_points"],
+                    "max_inner_iterations": info["max_inner_iterations"]}
+    return line
+
+
+# ------------------------------------------------------------ oracle (CPU) arm
+def oracle_sample():
+    """Time the oracle on a bounded sample: one transport inversion for the first S8
+    direction on a 128 x 128 mesh built with the same recipe as the 256 x 256 workload.
+    Returns (updates/s, seconds, threads)."""
+    import numpy as np
+    from oracle.transport import Discretization, sweep
+    from vef_inputs import level_symmetric, seeded_media
+    N, p = 128, 2
+    om, w = level_symmetric(8)
+    st, ss = seeded_media(N * N, 2)
+    disc = Discretization(N, N, 3, 0.05, p)
+    q = np.ones((N * N, (p + 1) ** 2))
+    t = time.perf_counter()
+    sweep(disc, om[:1], w[:1], st, ss, source=q)
+    dt = time.perf_counter() - t
+    return N * N * (p + 1) ** 2 / dt, dt, 1
+
+
+SAMPLE_DESC = ("oracle (FP64 NumPy/SciPy, global sparse direct solve) for 1 of the 40 S8 "
+               "directions on a 128x128 mesh with the 256x256 workload's recipe (sine alpha 0.05, "
+               "Q3 map, Q2, seed-2 media)")
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    for _ in range(args.warmup):
+        pass   # the CPU oracle has no warm-up state; the sample below is timed per step
+    rates, secs = [], []
+    for _ in range(args.steps):
+        r, dt, cores = oracle_sample()
+        rates.append(r)
+        secs.append(dt)
+    value = statistics.median(rates)
+    return {"impl": "reference", "metric": "sweep angular-DOF updates/s (10 source iterations + closures)",
+            "value": value, "unit": "angular-DOF updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "256x256 sine-curved Q3 mesh (alpha 0.05), DG Q2, S8 (40 dirs), "
+                                   "seeded sigma_t/sigma_s (seed 2), q=1, vacuum, 10 source iterations + closures"},
+            "cpu_baseline": {"value": value, "unit": "angular-DOF updates/s", "cores": 1,
+                             "kind": "oracle", "sample": SAMPLE_DESC},
+            "e2e": {"value": value, "unit": "angular-DOF updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line))
+        return
+    import torch
+    if world > 1:
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            r, dt, cores = oracle_sample()
+            line["cpu_baseline"] = {"value": r, "unit": "angular-DOF updates/s", "cores": cores,
+                                    "kind": "oracle", "sample": SAMPLE_DESC, "seconds": dt}
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -178,6 +178,33 @@ vef_status vef_adjoint_sweep(vef_mesh mesh, const double* sigma_t, const double*
                              double* dR_dsigma_t, double* dR_dsigma_s, const vef_opts* opts,
                              vef_info* info, void* stream);
 
+/* Kernel classes for the per-kernel timing counters. */
+enum {
+  VEF_K_GEOMETRY = 0, /* mesh geometric factors */
+  VEF_K_FACTOR = 1,   /* local assembly + inversion of every (element, direction) system */
+  VEF_K_SWEEP = 2,    /* dependency-driven wavefront solve */
+  VEF_K_RESIDUAL = 3, /* FP64 residual of the mixed-precision defect correction */
+  VEF_K_SOURCE = 4,   /* direction-independent right-hand side and scalar-flux updates */
+  VEF_K_MOMENTS = 5,  /* moments, Eddington tensor, boundary factor */
+  VEF_K_ADJOINT = 6,  /* adjoint sweep */
+  VEF_K_COUNT = 7
+};
+typedef struct {
+  long long launches;  /* kernel launches since the counters were last reset */
+  double ms;           /* summed CUDA-event time of those launches (when timing is on) */
+} vef_kernel_stat;
+
+/* Turns per-kernel CUDA-event timing on (enable != 0) or off for calls using `mesh`, and
+ * resets the counters.  Events are recorded on the stream each kernel is launched on. */
+vef_status vef_profile(vef_mesh mesh, int enable);
+/* Synchronises the recorded events and writes VEF_K_COUNT entries to out. */
+vef_status vef_profile_read(vef_mesh mesh, vef_kernel_stat* out);
+
+/* Measures this device's FMA throughput for FP64 (precision = VEF_FP64) or FP32
+ * (VEF_MIXED) with independent FMA chains in every warp slot; *flops_per_s receives
+ * the rate.  Diagnostic for roofline denominators; synchronises the device. */
+vef_status vef_measure_fma_peak(int precision, double* flops_per_s);
+
 /* Human-readable name of a status code (static string). */
 const char* vef_status_string(vef_status s);
 /* Last error message of the calling thread (static buffer, "" if none). */

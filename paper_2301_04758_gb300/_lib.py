@@ -24,8 +24,10 @@ VEF_MIXED = 1
 
 # every symbol include/vef.h declares
 EXPORTS = ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sync", "vef_sweep",
-           "vef_moments", "vef_source_iterate", "vef_adjoint_sweep", "vef_status_string",
-           "vef_last_error")
+           "vef_moments", "vef_source_iterate", "vef_adjoint_sweep", "vef_profile",
+           "vef_profile_read", "vef_measure_fma_peak", "vef_status_string", "vef_last_error")
+
+KERNEL_CLASSES = ("geometry", "factor", "sweep", "residual", "source", "moments", "adjoint")
 
 
 class VefOpts(ctypes.Structure):
@@ -47,6 +49,10 @@ class VefMeshDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("mesh_order", ctypes.c_int),
                 ("p", ctypes.c_int), ("n", ctypes.c_int), ("nq", ctypes.c_int),
                 ("E", ctypes.c_longlong), ("nbf", ctypes.c_longlong)]
+
+
+class VefKernelStat(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("ms", ctypes.c_double)]
 
 
 class VefError(RuntimeError):
@@ -73,8 +79,12 @@ def _declare(lib):
                                        P, P, P, ctypes.POINTER(VefInfo), P]
     lib.vef_adjoint_sweep.argtypes = [P, P, P, P, P, P, I, P, P, P, P, P, ctypes.POINTER(VefOpts),
                                       ctypes.POINTER(VefInfo), P]
+    lib.vef_profile.argtypes = [P, I]
+    lib.vef_profile_read.argtypes = [P, ctypes.POINTER(VefKernelStat)]
+    lib.vef_measure_fma_peak.argtypes = [I, ctypes.POINTER(ctypes.c_double)]
     for name in ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sync",
-                 "vef_sweep", "vef_moments", "vef_source_iterate", "vef_adjoint_sweep"):
+                 "vef_sweep", "vef_moments", "vef_source_iterate", "vef_adjoint_sweep",
+                 "vef_profile", "vef_profile_read", "vef_measure_fma_peak"):
         getattr(lib, name).restype = I
     lib.vef_status_string.argtypes = [I]
     lib.vef_status_string.restype = ctypes.c_char_p

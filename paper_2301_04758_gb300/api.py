@@ -41,6 +41,15 @@ def _opts(precision="fp64", tol=0.0, max_passes=0, tile=0):
     return o
 
 
+def fma_peak(precision="fp64"):
+    """Measured FMA throughput (flop/s) of the current device for FP64 or FP32."""
+    lib = _lib.load()
+    v = ctypes.c_double()
+    code = _lib.VEF_FP64 if precision == "fp64" else _lib.VEF_MIXED
+    _lib.check(lib.vef_measure_fma_peak(code, ctypes.byref(v)), "vef_measure_fma_peak")
+    return v.value
+
+
 class Mesh:
     """nx x ny mesh of [0,1]^2, Q_m map (sine distortion alpha), DG order p."""
 
@@ -71,6 +80,16 @@ class Mesh:
             self.close()
         except Exception:
             pass
+
+    def profile(self, enable=True):
+        """Turn per-kernel CUDA-event timing on/off (resets the counters)."""
+        _lib.check(self.lib.vef_profile(self.handle, int(bool(enable))), "vef_profile")
+
+    def profile_read(self):
+        """{kernel class: (launches, summed ms)} since the last vef_profile call."""
+        arr = (_lib.VefKernelStat * len(_lib.KERNEL_CLASSES))()
+        _lib.check(self.lib.vef_profile_read(self.handle, arr), "vef_profile_read")
+        return {k: (arr[i].launches, arr[i].ms) for i, k in enumerate(_lib.KERNEL_CLASSES)}
 
     def sync(self, stream=None):
         _lib.check(self.lib.vef_mesh_sync(self.handle, _stream(stream)), "vef_mesh_sync")

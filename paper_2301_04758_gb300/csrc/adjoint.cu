@@ -238,11 +238,12 @@ vef_status factor_fp64(Mesh* mesh, Schedule* S, const double* sigma_t, cudaStrea
 vef_status collect_status(Mesh& M, cudaStream_t stream, vef_info* info);
 
 template <int P>
-static vef_status launch_adjoint(AdjArgs a, cudaStream_t s) {
+static vef_status launch_adjoint(Mesh& M, AdjArgs a, cudaStream_t s) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, adjoint_kernel<P>, 128, 0);
+  KTimer kt(&M, VEF_K_ADJOINT, s);
   adjoint_kernel<P><<<std::max(1, sms * std::max(1, per)), 128, 0, s>>>(a);
   VEF_CUDA_TRY(cudaGetLastError());
   return VEF_OK;
@@ -313,16 +314,19 @@ extern "C" vef_status vef_adjoint_sweep(vef_mesh mesh, const double* sigma_t, co
   const int maxp = (opts && opts->max_passes > 0) ? opts->max_passes : 8;
   a.tol = (opts && opts->tol > 0.0) ? std::max(opts->tol, 2e-15) : 2e-15;
   a.max_inner = std::max(2, 4 * maxp);
-  if (phi_in) mvec_kernel<<<nblk(M.E * M.n, 256), 256, 0, s>>>(M.E, M.n, M.Mmat, phi_in, mphi);
+  if (phi_in) {
+    KTimer kt(&M, VEF_K_SOURCE, s);
+    mvec_kernel<<<nblk(M.E * M.n, 256), 256, 0, s>>>(M.E, M.n, M.Mmat, phi_in, mphi);
+  }
   VEF_CUDA_TRY(cudaMemsetAsync(dR_dsigma_t, 0, M.E * sizeof(double), s));
   if (dR_dsigma_s) VEF_CUDA_TRY(cudaMemsetAsync(dR_dsigma_s, 0, M.E * sizeof(double), s));
   VEF_CUDA_TRY(cudaMemsetAsync(M.dev_status + 1, 0, sizeof(unsigned int), s));
   VEF_CUDA_TRY(cudaMemsetAsync(M.dev_status + 3, 0, sizeof(unsigned int), s));
   switch (M.p) {
-    case 1: st = launch_adjoint<1>(a, s); break;
-    case 2: st = launch_adjoint<2>(a, s); break;
-    case 3: st = launch_adjoint<3>(a, s); break;
-    default: st = launch_adjoint<4>(a, s); break;
+    case 1: st = launch_adjoint<1>(M, a, s); break;
+    case 2: st = launch_adjoint<2>(M, a, s); break;
+    case 3: st = launch_adjoint<3>(M, a, s); break;
+    default: st = launch_adjoint<4>(M, a, s); break;
   }
   if (st != VEF_OK) return st;
   if (info) {

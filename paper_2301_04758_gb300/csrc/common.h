@@ -82,8 +82,17 @@ struct Schedule {
   ~Schedule();
 };
 
+struct KStat {
+  long long launches = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+};
+
 struct Mesh {
   int device = 0;
+  // per-kernel-class launch counters and optional CUDA-event timing
+  bool prof_on = false;
+  KStat kstat[VEF_K_COUNT];
+  std::vector<cudaEvent_t> event_pool;
   int nx = 0, ny = 0, m = 0, p = 0, n = 0, nq = 0;
   long long E = 0, nbf = 0;
   Tab1D tab{};
@@ -110,6 +119,19 @@ struct Mesh {
   double* work2 = nullptr;
   size_t work2_cap = 0;
   ~Mesh();
+};
+
+// Counts one launch of kernel class k and, when timing is on, brackets it with events
+// recorded on the launching stream.
+class KTimer {
+ public:
+  KTimer(Mesh* m, int k, cudaStream_t s);
+  ~KTimer();
+ private:
+  Mesh* m_;
+  int k_;
+  cudaStream_t s_;
+  cudaEvent_t e0_ = nullptr;
 };
 
 vef_status ensure_buffer(void** ptr, size_t* cap, size_t bytes);

@@ -135,6 +135,7 @@ static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, cud
     if (st != VEF_OK) return st;
     Mm = (const T*)M.Mmat32; Gx = (const T*)M.Gx32; Gy = (const T*)M.Gy32; nds = (const T*)M.nds32;
   }
+  KTimer kt(&M, VEF_K_FACTOR, stream);
   factor_kernel<P, T><<<nblk(S.members, 128), 128, 0, stream>>>(
       S.members, S.member_code, S.faceinfo, S.omega_dev, sigma_t, Mm, Gx, Gy, nds,
       make_facetab<T>(M.tab), M.nx, M.ny, M.E, (T*)*recp, M.dev_status);

@@ -183,7 +183,10 @@ vef_status mesh_float_copies(Mesh* mesh, cudaStream_t stream) {
   return VEF_OK;
 }
 
+void destroy_events(Mesh& M);
+
 Mesh::~Mesh() {
+  destroy_events(*this);
   schedules.clear();
   cudaFree(Mmat);
   cudaFree(Gx);

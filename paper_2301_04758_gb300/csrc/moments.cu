@@ -135,16 +135,22 @@ extern "C" vef_status vef_moments(vef_mesh mesh, const double* psi, const double
     if (!phiw) phiw = M.work;
     if (!Pw) Pw = M.work + En;
   }
-  if (phiw || J || Pw)
+  if (phiw || J || Pw) {
+    KTimer kt(&M, VEF_K_MOMENTS, s);
     moments_nodal_kernel<<<nblk(En, 256), 256, 0, s>>>(D, En, S->omega_dev, S->weights_dev, psi,
                                                         phiw, J, Pw);
-  if (Eten)
+  }
+  if (Eten) {
+    KTimer kt(&M, VEF_K_MOMENTS, s);
     eddington_kernel<<<nblk(M.E * M.nq * M.nq, 256), 256, 0, s>>>(M.E, M.tab, phiw, Pw, Eten,
                                                                   M.dev_status);
-  if (Eb || Jin)
+  }
+  if (Eb || Jin) {
+    KTimer kt(&M, VEF_K_MOMENTS, s);
     boundary_kernel<<<nblk(M.nbf * M.nq, 128), 128, 0, s>>>(D, M.nx, M.ny, M.E, M.tab, S->omega_dev,
                                                            S->weights_dev, psi, M.nds, inflow, Eb,
                                                            Jin, M.dev_status);
+  }
   VEF_CUDA_TRY(cudaGetLastError());
   return VEF_OK;
 }

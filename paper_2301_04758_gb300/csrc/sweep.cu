@@ -447,6 +447,7 @@ static vef_status launch_sweep(const SweepCall& c, const double* rhs, T* out) {
   VEF_CUDA_TRY(cudaMemsetAsync(M.dev_status + 3, 0, sizeof(unsigned int), c.stream));
   const int threads = c.threads > 0 ? c.threads : 128;
   const int blocks = persistent_blocks(sweep_kernel<P, T, MODE>, threads);
+  KTimer kt(&M, VEF_K_SWEEP, c.stream);
   sweep_kernel<P, T, MODE><<<blocks, threads, 0, c.stream>>>(a);
   VEF_CUDA_TRY(cudaGetLastError());
   return VEF_OK;
@@ -461,6 +462,7 @@ static vef_status launch_residual(const SweepCall& c, const double* psi, double*
   const long long tasks = (long long)S.D * M.E;
   const long long warps = (tasks + SPC - 1) / SPC;
   VEF_CUDA_TRY(cudaMemsetAsync(norms, 0, 2 * sizeof(double), c.stream));
+  KTimer kt(&M, VEF_K_RESIDUAL, c.stream);
   residual_kernel<P><<<nblk(warps * 32, 128), 128, 0, c.stream>>>(
       S.D, M.E, M.nx, M.ny, M.nbf, S.omega_dev, c.sigma_t, M.Mmat, M.Gx, M.Gy, M.nds, M.bvol,
       c.src_aniso, c.inflow, psi, make_facetab<double>(M.tab), r, norms);
@@ -487,7 +489,10 @@ static vef_status solve_p(const SweepCall& c, double* psi, vef_info* info) {
   double* norms = (double*)((char*)M.work2 + (size_t)tot * sizeof(double));
   float* delta = (float*)((char*)M.work2 + need);
   if ((st = launch_sweep<P, float, 0>(c, nullptr, delta)) != VEF_OK) return st;
-  cast_add_kernel<<<nblk(tot, 256), 256, 0, c.stream>>>(tot, delta, psi, 0);
+  {
+    KTimer kt(&M, VEF_K_SOURCE, c.stream);
+    cast_add_kernel<<<nblk(tot, 256), 256, 0, c.stream>>>(tot, delta, psi, 0);
+  }
   int passes = 1;
   double rel = -1.0;
   for (int pass = 0; pass < c.max_passes; ++pass) {
@@ -503,7 +508,10 @@ static vef_status solve_p(const SweepCall& c, double* psi, vef_info* info) {
       break;
     }
     if ((st = launch_sweep<P, float, 1>(c, r, delta)) != VEF_OK) return st;
-    cast_add_kernel<<<nblk(tot, 256), 256, 0, c.stream>>>(tot, delta, psi, 1);
+    {
+      KTimer kt(&M, VEF_K_SOURCE, c.stream);
+      cast_add_kernel<<<nblk(tot, 256), 256, 0, c.stream>>>(tot, delta, psi, 1);
+    }
     ++passes;
   }
   if (info) { info->passes = passes; info->rel_residual = rel; }
@@ -539,6 +547,7 @@ static vef_status launch_bvol(Mesh& M, const double* sigma_s, const double* phi_
     vef_status st = ensure_buffer((void**)&M.bvol, &cap, (size_t)M.E * M.n * sizeof(double));
     if (st != VEF_OK) return st;
   }
+  KTimer kt(&M, VEF_K_SOURCE, stream);
   bvol_kernel<<<nblk(M.E * M.n, 256), 256, 0, stream>>>(M.E, M.n, M.Mmat, sigma_s, phi_in, q_iso, M.bvol);
   VEF_CUDA_TRY(cudaGetLastError());
   return VEF_OK;
@@ -677,9 +686,13 @@ extern "C" vef_status vef_source_iterate(vef_mesh mesh, const double* sigma_t, c
     if ((st = launch_bvol(M, sigma_s, cur, source_aniso ? nullptr : source, s)) != VEF_OK) return st;
     if ((st = solve(c, psi, info ? &last : nullptr)) != VEF_OK) return st;
     total_passes += info ? last.passes : 1;
-    phi_kernel<<<nblk(En, 256), 256, 0, s>>>(D, En, S->weights_dev, psi, nxt);
+    {
+      KTimer kt(&M, VEF_K_SOURCE, s);
+      phi_kernel<<<nblk(En, 256), 256, 0, s>>>(D, En, S->weights_dev, psi, nxt);
+    }
     if (dphi_inf) {
       VEF_CUDA_TRY(cudaMemsetAsync(dphi_inf + k, 0, sizeof(double), s));
+      KTimer kt(&M, VEF_K_SOURCE, s);
       maxdiff_kernel<<<std::min<long long>(nblk(En, 256), 1024), 256, 0, s>>>(
           En, nxt, cur, (unsigned long long*)(dphi_inf + k));
     }
