@@ -205,6 +205,26 @@ vef_status vef_profile_read(vef_mesh mesh, vef_kernel_stat* out);
  * the rate.  Diagnostic for roofline denominators; synchronises the device. */
 vef_status vef_measure_fma_peak(int precision, double* flops_per_s);
 
+/* Eddington tensor without device allocation (the paper has no counterpart: this is a
+ * library interface).  Same result as vef_moments with only Eten requested:
+ *   Eten [device] [3][E][(p+2)^2] = P / phi at the volume Gauss points, from
+ *   psi [device] [D][E][(p+1)^2]; omega [host] [D][2] and weights [host] [D].
+ * For callers that cannot allocate device memory: applications that hand all device
+ * memory to their own pool at start-up, or loops that must avoid the device-wide
+ * synchronisation cudaMalloc / cudaFree can cause.  Such callers cannot create a mesh
+ * handle either, so the mesh enters only through E and p.  The call allocates nothing:
+ * the nodal moments go through one fixed 16 MiB device array that every GPU loading
+ * the library holds until the process exits.  Limits: D <= 256 and
+ * E * (p+1)^2 <= 524288; larger inputs return VEF_ERR_INVALID_ARG.
+ * The first call on a device looks up that array's device address (with the device
+ * current); make that first call before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU (different streams or devices' work racing on
+ * one device) corrupt each other's result, so serialise them.  Each call writes every
+ * scratch entry it reads, so nothing carries over between calls.  A non-positive
+ * denominator writes NaN at that point.  Stream-ordered on `stream`. */
+vef_status vef_eddington_noalloc(const double* psi, const double* omega, const double* weights,
+                                 int D, long long E, int p, double* Eten, void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* vef_status_string(vef_status s);
 /* Last error message of the calling thread (static buffer, "" if none). */

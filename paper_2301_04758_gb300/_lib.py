@@ -25,7 +25,8 @@ VEF_MIXED = 1
 # every symbol include/vef.h declares
 EXPORTS = ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sync", "vef_sweep",
            "vef_moments", "vef_source_iterate", "vef_adjoint_sweep", "vef_profile",
-           "vef_profile_read", "vef_measure_fma_peak", "vef_status_string", "vef_last_error")
+           "vef_profile_read", "vef_measure_fma_peak", "vef_eddington_noalloc",
+           "vef_status_string", "vef_last_error")
 
 KERNEL_CLASSES = ("geometry", "factor", "sweep", "residual", "source", "moments", "adjoint")
 
@@ -82,9 +83,11 @@ def _declare(lib):
     lib.vef_profile.argtypes = [P, I]
     lib.vef_profile_read.argtypes = [P, ctypes.POINTER(VefKernelStat)]
     lib.vef_measure_fma_peak.argtypes = [I, ctypes.POINTER(ctypes.c_double)]
+    lib.vef_eddington_noalloc.argtypes = [P, P, P, I, ctypes.c_longlong, I, P, P]
     for name in ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sync",
                  "vef_sweep", "vef_moments", "vef_source_iterate", "vef_adjoint_sweep",
-                 "vef_profile", "vef_profile_read", "vef_measure_fma_peak"):
+                 "vef_profile", "vef_profile_read", "vef_measure_fma_peak",
+                 "vef_eddington_noalloc"):
         getattr(lib, name).restype = I
     lib.vef_status_string.argtypes = [I]
     lib.vef_status_string.restype = ctypes.c_char_p
