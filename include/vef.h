@@ -30,9 +30,10 @@
  *
  * A sweep returns psi_d = L_d^{-1} b_d for every direction, independent of any
  * ordering: the library orders elements per direction along the upwind dependency
- * graph and solves the rare strongly coupled element groups (curved faces that are
- * partly inflow and partly outflow) by an inner block Gauss-Seidel iteration to a
- * relative change below `vef_opts.tol`.
+ * graph (one thread-block cluster per direction walks its levels) and solves the rare
+ * strongly coupled element groups (curved faces that are partly inflow and partly
+ * outflow) by an inner block Gauss-Seidel iteration to a relative change below
+ * `vef_opts.tol`.
  *
  * Conventions
  *   - Array arguments marked [device] are caller-owned device memory: contiguous FP64,
@@ -44,8 +45,8 @@
  *     the same handle must not overlap on the GPU: issue them on one stream or
  *     serialise them.
  *   - The status returned covers argument validation and launch.  Failures detected
- *     on the device (a dependency wait that ran out, an inner iteration that did not
- *     converge, a non-positive closure denominator) are recorded in the handle and are
+ *     on the device (an inner iteration that did not converge, a singular local
+ *     system, a non-positive closure denominator) are recorded in the handle and are
  *     returned by the next call that synchronises: vef_mesh_sync(), or any call given
  *     a non-NULL vef_info.
  *   - No exceptions cross the ABI.  There is no CPU fallback: without a usable CUDA
@@ -66,7 +67,7 @@ typedef enum {
   VEF_ERR_INVALID_ARG = 1,
   VEF_ERR_CUDA = 2,
   VEF_ERR_OOM = 3,
-  VEF_ERR_TIMEOUT = 4,            /* a device-side dependency wait ran out; psi is invalid */
+  VEF_ERR_TIMEOUT = 4,            /* reserved: no kernel waits on another (cluster barriers only) */
   VEF_ERR_NOT_CONVERGED = 5,      /* an inner or defect-correction iteration hit its cap */
   VEF_ERR_NONPOSITIVE_DENOM = 6,  /* sum_d w_d psi_d <= 1e-300 at a closure point (NaN written) */
   VEF_ERR_NOT_IMPLEMENTED = 7
@@ -85,7 +86,8 @@ typedef struct {
                         defect correction ||r||_2 / ||b||_2 (mixed: 1e-13) */
   int max_passes;    /* cap on defect-correction passes (default 8) and, x4, on inner
                         coupled-group iterations */
-  int tile_override; /* 0 = library choice; >0 forces threads per block of the sweep kernel */
+  int tile_override; /* 0 = library choice; else 100 * (CTAs per direction cluster, 1..16)
+                        + (warps per CTA, 1..8) of the sweep kernel */
 } vef_opts;
 
 /* Filled by calls given a non-NULL pointer (those calls synchronise `stream`). */
@@ -95,7 +97,7 @@ typedef struct {
   long long coupled_groups;   /* (element group, direction) tasks with more than one element */
   long long lagged_face_points; /* face points inside coupled groups (solved iteratively) */
   int max_inner_iterations;   /* largest inner Gauss-Seidel count used by a coupled group */
-  int timed_out;              /* 1 if a dependency wait ran out */
+  int timed_out;              /* reserved, always 0 (no device-side waits) */
   int levels;                 /* dependency levels of the schedule (critical path length) */
 } vef_info;
 

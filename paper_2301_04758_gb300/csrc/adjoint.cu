@@ -6,7 +6,8 @@
 // With r_e := A_e^T lambda_e and the stored W_{e',f'} = A_{e'}^{-1} Cin_{e',f'} of the
 // forward factorisation, C[e'][e]^T lambda_{e'} = W_{e',f'}^T r_{e'} placed on e's face
 // nodes, so each element needs its downstream neighbours' r, and lambda_e = A_e^{-T} r_e.
-// The sweep therefore runs the forward schedule backwards (downwind order).
+// The sweep therefore runs the forward schedule backwards (downwind order), one
+// thread-block cluster per direction as in the forward sweep.
 //   dR/dsigma_t,e = - sum_d lambda_{d,e}^T M_e psi_{d,e}
 //   dR/dsigma_s,e =   sum_d lambda_{d,e}^T M_e phi_in,e / (4 pi)
 #include <algorithm>
@@ -17,8 +18,10 @@
 namespace vef {
 
 struct AdjArgs {
-  int nchunks;
-  const int* chunk_begin;
+  const int* dir_lev0;
+  const int* lev_begin;
+  const int* lev_gbegin;
+  int cluster_size;
   const int* slot_first;
   const int* slot_count;
   const uint32_t* code;
@@ -26,7 +29,9 @@ struct AdjArgs {
   const uint16_t* finfo;
   const double* omega;
   const double* weights;
-  const double* rec;
+  const double* rec;      // staged record array S (see Rec)
+  const double* recx;     // extra record array X
+  long long nmem;
   const double* g;        // [E][n]
   const double* psi;      // [D][E][n] forward checkpoint
   const double* Mm;       // [E][n][n]
@@ -35,8 +40,6 @@ struct AdjArgs {
   double* lambda;         // [D][E][n]
   double* dst;            // [E]
   double* dss;            // [E]
-  uint32_t* flags;
-  uint32_t epoch;
   unsigned int* status;
   int nx, ny;
   long long E;
@@ -48,7 +51,8 @@ struct AdjArgs {
 template <int P>
 __device__ __forceinline__ double adj_rhs(const AdjArgs& a, int d, int e, int i, uint16_t bits,
                                           int first, int pos_self, int cnt, int it, bool in_group) {
-  constexpr int Q = P + 1, N = Q * Q, R = rec_size<P>();
+  constexpr int Q = P + 1, N = Q * Q;
+  using L = Rec<P, double>;
   double r = a.weights[d] * a.g[(size_t)e * N + i];
   const int ia = i % Q, ib = i / Q;
 #pragma unroll
@@ -67,7 +71,10 @@ __device__ __forceinline__ double adj_rhs(const AdjArgs& a, int d, int e, int i,
     }
     const int fn = (f + 2) & 3;      // receiver's face toward e
     const long long mn = a.member_of[(size_t)d * a.E + nb];
-    const double* W = a.rec + (size_t)mn * R + N * N + fn * N * Q + t * N;
+    const char* rr = L::s_at(a.rec, mn);
+    const int sl = rec_slot_of(reinterpret_cast<const uint4*>(rr)->z, fn);
+    if (sl < 0) continue;
+    const double* W = L::slot(rr, L::x_at(a.recx, mn), sl) + t * N;
     const double* rn = a.radj + ((size_t)d * a.E + nb) * N;
     double s = 0.0;
 #pragma unroll
@@ -82,10 +89,12 @@ template <int P>
 __device__ __forceinline__ void adj_finish(const AdjArgs& a, long long m, int d, int e, int i, bool act,
                                            double r) {
   // lambda = A^{-T} r, gradient contributions
-  constexpr int Q = P + 1, N = Q * Q, R = rec_size<P>();
+  constexpr int Q = P + 1, N = Q * Q;
+  using L = Rec<P, double>;
+  (void)Q;
   const int lane = threadIdx.x & 31;
   const int base = (lane / N) * N;
-  const double* Ai = a.rec + (size_t)m * R + (size_t)i * N;  // column i of A^{-1}
+  const double* Ai = L::ainv(L::x_at(a.recx, m)) + (size_t)i * N;  // column i of A^{-1}
   double lam = 0.0;
 #pragma unroll
   for (int j = 0; j < N; ++j) {
@@ -117,106 +126,84 @@ __device__ __forceinline__ void adj_finish(const AdjArgs& a, long long m, int d,
   }
 }
 
+// One thread-block cluster per direction walks the direction's levels backwards; the
+// receivers of a task sit at later levels, so they are complete after the previous
+// cluster barrier.
 template <int P>
-__global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs a) {
+__device__ __forceinline__ void adj_group(const AdjArgs& a, int d, int s0) {
   constexpr int Q = P + 1, N = Q * Q;
-  constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  while (true) {
-    int c = 0;
-    if (lane == 0) c = (int)atomicAdd(a.status + 3, 1u);
-    c = __shfl_sync(FULL, c, 0);
-    if (c >= a.nchunks) return;
-    if (*((volatile unsigned int*)(a.status + 1)) != 0u) return;
-    c = a.nchunks - 1 - c;  // downwind order
-    const int s0 = a.chunk_begin[c], s1 = a.chunk_begin[c + 1];
-    const int cnt0 = a.slot_count[s0];
-    if (cnt0 == 1) {
-      const int slot = s0 + lane / N;
-      const int i = lane % N;
-      const bool valid = (lane < SPC * N) && (slot < s1);
-      int d = 0, e = 0;
+  const int first = a.slot_first[s0];
+  const int cnt = a.slot_count[s0];
+  const int i = lane;
+  const bool act = lane < N;
+  int it = 0;
+  bool conv = false;
+  for (; it < a.max_inner; ++it) {
+    double dmax = 0, amax = 0;
+    for (int mi = cnt - 1; mi >= 0; --mi) {
+      const int e = (int)(a.code[first + mi] & 0x3fffffu);
+      const uint16_t bits = a.finfo[(size_t)d * a.E + e];
+      if (act) {
+        const double r = adj_rhs<P>(a, d, e, i, bits, first, mi, cnt, it, true);
+        double* o = a.radj + ((size_t)d * a.E + e) * N + i;
+        if (it > 0) dmax = fmax(dmax, fabs(r - __ldcg(o)));
+        amax = fmax(amax, fabs(r));
+        *o = r;
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      dmax = fmax(dmax, __shfl_xor_sync(FULL, dmax, off));
+      amax = fmax(amax, __shfl_xor_sync(FULL, amax, off));
+    }
+    if (it > 0 && dmax <= a.tol * amax) { conv = true; ++it; break; }
+  }
+  if (lane == 0) {
+    if (!conv) atomicOr(a.status, kDevNotConverged);
+    atomicMax(a.status + 2, (unsigned)it);
+  }
+  for (int mi = 0; mi < cnt; ++mi) {
+    const long long m = first + mi;
+    const int e = (int)(a.code[m] & 0x3fffffu);
+    const double r = act ? __ldcg(a.radj + ((size_t)d * a.E + e) * N + i) : 0.0;
+    adj_finish<P>(a, m, d, e, i, act, r);
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) adjoint_kernel(AdjArgs a) {
+  constexpr int Q = P + 1, N = Q * Q;
+  constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
+  (void)Q;
+  const int lane = threadIdx.x & 31;
+  const int cs = a.cluster_size;
+  const int d = blockIdx.x / cs;
+  const int nw = cs * (blockDim.x >> 5);
+  const int gw = (blockIdx.x % cs) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int k0 = a.dir_lev0[d], k1 = a.dir_lev0[d + 1];
+  const int i = lane % N;
+  for (int k = k1 - 1; k >= k0; --k) {
+    const int sb = a.lev_begin[k], sg = a.lev_gbegin[k], se = a.lev_begin[k + 1];
+    for (int base = sb + gw * SPC; base < sg; base += nw * SPC) {
+      const int slot = base + lane / N;
+      const bool valid = (lane < SPC * N) && (slot < sg);
       long long m = 0;
-      uint16_t bits = 0;
-      bool ok = true;
+      int e = 0;
+      double r = 0.0;
       if (valid) {
         m = a.slot_first[slot];
-        const uint32_t cd = a.code[m];
-        d = (int)(cd >> 22);
-        e = (int)(cd & 0x3fffffu);
-        bits = a.finfo[(size_t)d * a.E + e];
-        for (int f = 0; f < 4; ++f) {
-          if (!(bits & (1u << (8 + f)))) continue;
-          const int nb = nb_elem(a.nx, a.ny, e, f);
-          if (!wait_epoch(a.flags + (size_t)d * a.E + nb, a.epoch, a.status)) { ok = false; break; }
-        }
-      }
-      if (!__all_sync(FULL, ok)) return;
-      double r = valid ? adj_rhs<P>(a, d, e, i, bits, 0, 0, 1, 1, false) : 0.0;
-      if (valid) a.radj[((size_t)d * a.E + e) * N + i] = r;
-      adj_finish<P>(a, m, d, e, i, valid, r);
-      __threadfence();
-      __syncwarp();
-      if (valid && i == 0) st_release(a.flags + (size_t)d * a.E + e, a.epoch);
-    } else {
-      const int first = a.slot_first[s0];
-      const int cnt = cnt0;
-      const int i = lane;
-      const bool act = lane < N;
-      const int d = (int)(a.code[first] >> 22);
-      bool ok = true;
-      for (int mi = 0; mi < cnt && ok; ++mi) {
-        const int e = (int)(a.code[first + mi] & 0x3fffffu);
+        e = (int)(a.code[m] & 0x3fffffu);
         const uint16_t bits = a.finfo[(size_t)d * a.E + e];
-        for (int f = 0; f < 4; ++f) {
-          if (!(bits & (1u << (8 + f))) || (bits & (1u << (4 + f)))) continue;
-          const int nb = nb_elem(a.nx, a.ny, e, f);
-          if (!wait_epoch(a.flags + (size_t)d * a.E + nb, a.epoch, a.status)) { ok = false; break; }
-        }
+        r = adj_rhs<P>(a, d, e, i, bits, 0, 0, 1, 1, false);
+        a.radj[((size_t)d * a.E + e) * N + i] = r;
       }
-      if (!__all_sync(FULL, ok)) return;
-      int it = 0;
-      bool conv = false;
-      for (; it < a.max_inner; ++it) {
-        double dmax = 0, amax = 0;
-        for (int mi = cnt - 1; mi >= 0; --mi) {
-          const int e = (int)(a.code[first + mi] & 0x3fffffu);
-          const uint16_t bits = a.finfo[(size_t)d * a.E + e];
-          if (act) {
-            const double r = adj_rhs<P>(a, d, e, i, bits, first, mi, cnt, it, true);
-            double* o = a.radj + ((size_t)d * a.E + e) * N + i;
-            if (it > 0) dmax = fmax(dmax, fabs(r - __ldcg(o)));
-            amax = fmax(amax, fabs(r));
-            *o = r;
-          }
-          __threadfence();
-          __syncwarp();
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          dmax = fmax(dmax, __shfl_xor_sync(FULL, dmax, off));
-          amax = fmax(amax, __shfl_xor_sync(FULL, amax, off));
-        }
-        if (it > 0 && dmax <= a.tol * amax) { conv = true; ++it; break; }
-      }
-      if (lane == 0) {
-        if (!conv) atomicOr(a.status, kDevNotConverged);
-        atomicMax(a.status + 2, (unsigned)it);
-      }
-      for (int mi = 0; mi < cnt; ++mi) {
-        const long long m = first + mi;
-        const int e = (int)(a.code[m] & 0x3fffffu);
-        const double r = act ? __ldcg(a.radj + ((size_t)d * a.E + e) * N + i) : 0.0;
-        adj_finish<P>(a, m, d, e, i, act, r);
-      }
-      __threadfence();
-      __syncwarp();
-      for (int mi = lane; mi < cnt; mi += 32) {
-        const int e = (int)(a.code[first + mi] & 0x3fffffu);
-        st_release(a.flags + (size_t)d * a.E + e, a.epoch);
-      }
+      adj_finish<P>(a, m, d, e, i, valid, r);
     }
+    for (int gs = sg + gw; gs < se; gs += nw) adj_group<P>(a, d, gs);
+    cluster_barrier();
   }
 }
 
@@ -238,14 +225,24 @@ vef_status factor_fp64(Mesh* mesh, Schedule* S, const double* sigma_t, cudaStrea
 vef_status collect_status(Mesh& M, cudaStream_t stream, vef_info* info);
 
 template <int P>
-static vef_status launch_adjoint(Mesh& M, AdjArgs a, cudaStream_t s) {
-  int dev = 0, sms = 0, per = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, adjoint_kernel<P>, 128, 0);
+static vef_status launch_adjoint(Mesh& M, AdjArgs a, int D, int cs, int warps, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(D * cs));
+  cfg.blockDim = dim3((unsigned)(32 * warps));
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cs > 8)
+    VEF_CUDA_TRY(cudaFuncSetAttribute(adjoint_kernel<P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  a.cluster_size = cs;
+  a.recx = (const double*)((const char*)a.rec + a.nmem * (long long)Rec<P, double>::kStaged);
   KTimer kt(&M, VEF_K_ADJOINT, s);
-  adjoint_kernel<P><<<std::max(1, sms * std::max(1, per)), 128, 0, s>>>(a);
-  VEF_CUDA_TRY(cudaGetLastError());
+  VEF_CUDA_TRY(cudaLaunchKernelEx(&cfg, adjoint_kernel<P>, a));
   return VEF_OK;
 }
 
@@ -276,14 +273,14 @@ extern "C" vef_status vef_adjoint_sweep(vef_mesh mesh, const double* sigma_t, co
   vef_status st;
   Schedule* S = get_schedule(&M, omega, weights, D, s, &st);
   if (!S) return st;
-  if ((st = ensure_flags(&M, (size_t)D * M.E)) != VEF_OK) return st;
   if ((st = factor_fp64(&M, S, sigma_t, s)) != VEF_OK) return st;
   const long long tot = (long long)D * M.E * M.n;
   const size_t need = (size_t)tot * sizeof(double) * (lambda ? 1 : 2) + (size_t)M.E * M.n * sizeof(double);
   if ((st = ensure_buffer((void**)&M.work2, &M.work2_cap, need)) != VEF_OK) return st;
   AdjArgs a{};
-  a.nchunks = S->nchunks;
-  a.chunk_begin = S->chunk_begin;
+  a.dir_lev0 = S->dir_lev0;
+  a.lev_begin = S->lev_begin;
+  a.lev_gbegin = S->lev_gbegin;
   a.slot_first = S->slot_first;
   a.slot_count = S->slot_count;
   a.code = S->member_code;
@@ -292,6 +289,7 @@ extern "C" vef_status vef_adjoint_sweep(vef_mesh mesh, const double* sigma_t, co
   a.omega = S->omega_dev;
   a.weights = S->weights_dev;
   a.rec = (const double*)S->rec64;
+  a.nmem = S->members;
   a.g = g;
   a.psi = psi_ckpt;
   a.Mm = M.Mmat;
@@ -301,12 +299,6 @@ extern "C" vef_status vef_adjoint_sweep(vef_mesh mesh, const double* sigma_t, co
   a.mphi = phi_in ? mphi : nullptr;
   a.dst = dR_dsigma_t;
   a.dss = dR_dsigma_s;
-  a.flags = M.flags;
-  if (++M.epoch == 0) {
-    VEF_CUDA_TRY(cudaMemsetAsync(M.flags, 0, M.flags_cap, s));
-    M.epoch = 1;
-  }
-  a.epoch = M.epoch;
   a.status = M.dev_status;
   a.nx = M.nx;
   a.ny = M.ny;
@@ -320,13 +312,13 @@ extern "C" vef_status vef_adjoint_sweep(vef_mesh mesh, const double* sigma_t, co
   }
   VEF_CUDA_TRY(cudaMemsetAsync(dR_dsigma_t, 0, M.E * sizeof(double), s));
   if (dR_dsigma_s) VEF_CUDA_TRY(cudaMemsetAsync(dR_dsigma_s, 0, M.E * sizeof(double), s));
-  VEF_CUDA_TRY(cudaMemsetAsync(M.dev_status + 1, 0, sizeof(unsigned int), s));
-  VEF_CUDA_TRY(cudaMemsetAsync(M.dev_status + 3, 0, sizeof(unsigned int), s));
+  const int tile = (opts && opts->tile_override > 0) ? opts->tile_override : 804;
+  const int cs = std::min(16, std::max(1, tile / 100)), warps = std::min(8, std::max(1, tile % 100));
   switch (M.p) {
-    case 1: st = launch_adjoint<1>(M, a, s); break;
-    case 2: st = launch_adjoint<2>(M, a, s); break;
-    case 3: st = launch_adjoint<3>(M, a, s); break;
-    default: st = launch_adjoint<4>(M, a, s); break;
+    case 1: st = launch_adjoint<1>(M, a, D, cs, warps, s); break;
+    case 2: st = launch_adjoint<2>(M, a, D, cs, warps, s); break;
+    case 3: st = launch_adjoint<3>(M, a, D, cs, warps, s); break;
+    default: st = launch_adjoint<4>(M, a, D, cs, warps, s); break;
   }
   if (st != VEF_OK) return st;
   if (info) {

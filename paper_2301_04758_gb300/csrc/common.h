@@ -48,7 +48,7 @@ vef_status cuda_fail(cudaError_t err, const char* what);
 
 // device status word values written by kernels (bit flags)
 enum : unsigned int {
-  kDevTimeout = 1u,
+  kDevTimeout = 1u,        // reserved: the current kernels never wait on each other
   kDevNotConverged = 2u,
   kDevNonpositive = 4u,
   kDevSingular = 8u,
@@ -59,15 +59,19 @@ struct Schedule {
   std::vector<double> omega;   // [D][2] host copy (key)
   std::vector<double> weights; // [D]
   int D = 0;
-  int levels = 0;
+  int levels = 0;              // max dependency levels over the directions
   long long members = 0;       // == D*E
-  int nchunks = 0;
+  int total_levels = 0;        // sum over directions of their level counts
   long long nslots = 0;
   long long coupled_groups = 0;
   long long lagged_points = 0;
-  int slots_per_chunk = 0;     // single-element tasks per warp chunk
   // device arrays
-  int* chunk_begin = nullptr;  // [nchunks+1] slot offsets
+  int* dir_lev0 = nullptr;     // [D+1] first level of each direction in lev_begin
+  int* lev_begin = nullptr;    // [total_levels+1] first slot of each level
+  int* lev_gbegin = nullptr;   // [total_levels] first coupled-group slot of each level
+  int* lev_mbegin = nullptr;   // [total_levels] first member of each level (its singles)
+  uint2* member_info = nullptr;  // [members] (element, face bits) in schedule order
+  uint32_t* member_nbpos = nullptr;  // [members] per face: in-group position of the neighbour or 255
   int* slot_first = nullptr;   // [nslots] first member index (-1 = padding)
   int* slot_count = nullptr;   // [nslots] members in the group
   uint32_t* member_code = nullptr;  // [members] (d << 22) | e, in schedule order
@@ -109,15 +113,14 @@ struct Mesh {
   // schedules keyed by direction set
   std::vector<std::unique_ptr<Schedule>> schedules;
   // scratch
-  uint32_t* flags = nullptr;     // [capacity] completion epochs per (d,e)
-  size_t flags_cap = 0;
-  uint32_t epoch = 0;
-  unsigned int* dev_status = nullptr;  // [8]: 0 status bits, 1 abort, 2 max inner it, 3 chunk counter
+  unsigned int* dev_status = nullptr;  // [8]: 0 status bits, 2 max inner iterations, 4 host-set bits
   double* bvol = nullptr;        // [E][n] direction-independent right-hand side
   double* work = nullptr;        // general scratch (phi iterates, reductions)
   size_t work_cap = 0;
   double* work2 = nullptr;
   size_t work2_cap = 0;
+  void* ybuf = nullptr;          // [D][E][n] A^{-1} b of the current sweep (FP64 or FP32)
+  size_t ybuf_cap = 0;
   ~Mesh();
 };
 
@@ -136,7 +139,6 @@ class KTimer {
 
 vef_status ensure_buffer(void** ptr, size_t* cap, size_t bytes);
 vef_status mesh_float_copies(Mesh* mesh, cudaStream_t stream);
-vef_status ensure_flags(Mesh* mesh, size_t count);
 vef_status factor_records(Mesh* mesh, Schedule* S, const double* sigma_t, int precision,
                           cudaStream_t stream);
 Schedule* get_schedule(Mesh* mesh, const double* omega, const double* weights, int D,

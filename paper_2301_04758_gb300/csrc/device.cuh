@@ -8,11 +8,50 @@
 
 namespace vef {
 
-// floats per factor record of one (element, direction): A^{-1} (n x n) followed by the
-// four inflow-coupling maps W_f (n x (p+1) each)
-template <int P>
-__host__ __device__ constexpr int rec_size() {
-  return (P + 1) * (P + 1) * (P + 1) * (P + 1) + 4 * (P + 1) * (P + 1) * (P + 1);
+// Factor records of all (element, direction) pairs, in schedule order, as two arrays of
+// 16-byte-aligned blocks so the sweep can stage a run of consecutive tasks with one bulk
+// copy:
+//   staged array S, per task: [info: element, face bits, face of each W slot (4 x u8),
+//                               pad: 16 bytes][W slots 0, 1: n x (p+1) each, column-major]
+//   extra array X, per task:  [W slots 2, 3][A^{-1}: n x n column-major]
+// W slot s holds W_f = A^{-1} Cin_f for the s-th interior inflow face f (in face order);
+// slots 2 and 3 exist only on curved meshes (a face partly inflow).
+template <int P, typename T>
+struct Rec {
+  static constexpr int Q = P + 1, N = Q * Q;
+  static constexpr int r16(int b) { return (b + 15) / 16 * 16; }
+  static constexpr int kSlot = N * Q;                                   // elements per W slot
+  static constexpr int kStaged = r16(16 + 2 * kSlot * (int)sizeof(T));  // bytes per task in S
+  static constexpr int kExtra = r16(2 * kSlot * (int)sizeof(T));
+  static constexpr int kAinv = r16(N * N * (int)sizeof(T));
+  static constexpr int kX = kExtra + kAinv;                             // bytes per task in X
+  static constexpr int kYBytes = r16(N * (int)sizeof(T));               // padded y row
+  static constexpr int kYStride = kYBytes / (int)sizeof(T);
+  __host__ __device__ static const char* s_at(const void* S, long long m) {
+    return (const char*)S + m * (long long)kStaged;
+  }
+  __host__ __device__ static char* s_at(void* S, long long m) { return (char*)S + m * (long long)kStaged; }
+  __host__ __device__ static const char* x_at(const void* X, long long m) {
+    return (const char*)X + m * (long long)kX;
+  }
+  __host__ __device__ static char* x_at(void* X, long long m) { return (char*)X + m * (long long)kX; }
+  // W slot s of the task whose staged block is at s_rec and extra block at x_rec
+  __host__ __device__ static const T* slot(const char* s_rec, const char* x_rec, int s) {
+    return (const T*)(s < 2 ? s_rec + 16 + s * kSlot * (int)sizeof(T) : x_rec + (s - 2) * kSlot * (int)sizeof(T));
+  }
+  __host__ __device__ static T* slot(char* s_rec, char* x_rec, int s) {
+    return (T*)(s < 2 ? s_rec + 16 + s * kSlot * (int)sizeof(T) : x_rec + (s - 2) * kSlot * (int)sizeof(T));
+  }
+  __host__ __device__ static const T* ainv(const char* x_rec) { return (const T*)(x_rec + kExtra); }
+  __host__ __device__ static T* ainv(char* x_rec) { return (T*)(x_rec + kExtra); }
+};
+
+// slot holding face f according to the record's face list (info.z bytes), or -1
+__host__ __device__ __forceinline__ int rec_slot_of(unsigned faces, int f) {
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+    if (((faces >> (8 * s)) & 0xffu) == (unsigned)f) return s;
+  return -1;
 }
 
 template <typename T> __host__ __device__ constexpr T tiny_pivot();
@@ -40,38 +79,53 @@ __device__ __forceinline__ int bface(int nx, int ny, int e, int f) {
   return f == 0 ? i : f == 1 ? nx + j : f == 2 ? nx + ny + i : 2 * nx + ny + j;
 }
 
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
+// barrier over all threads of the thread-block cluster, release / acquire at cluster scope
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// Spin (bounded) until *flag == epoch.  Returns false if the wait ran out (records
-// kDevTimeout and raises the abort word) or another warp aborted.
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
-constexpr uint32_t kWaitLimitIters = 200000000u;
-__device__ __forceinline__ bool wait_epoch(const uint32_t* flag, uint32_t epoch,
-                                           unsigned int* status) {
-  if (ld_acquire(flag) == epoch) return true;
-  const uint64_t t0 = global_ns();
-  for (uint32_t it = 1; it < kWaitLimitIters; ++it) {
-    if (ld_acquire(flag) == epoch) return true;
-    if ((it & 63u) == 0) {
-      if (*((volatile unsigned int*)(status + 1)) != 0u) return false;
-      if (global_ns() - t0 > kWaitLimitNs) break;
-    }
-  }
-  atomicOr(status, kDevTimeout);
-  atomicExch(status + 1, 1u);
-  return false;
+// mbarrier and bulk-copy (TMA) helpers for staging records into shared memory
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// 1D bulk copy global -> this CTA's shared memory, completion counted on bar (bytes and
+// both addresses must be multiples of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 template <typename T>

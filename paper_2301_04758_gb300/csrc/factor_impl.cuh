@@ -8,7 +8,8 @@
 // acting on the neighbour's face-node values.  One thread per (element, direction)
 // assembles A, inverts it in place (Gauss-Jordan) and forms W_f = A^{-1} Cin_f for the
 // interior inflow faces.  Record per (element, direction), in schedule order:
-//     [A^{-1} column-major n x n][W_0 ... W_3, each column-major n x (p+1)].
+//     [element, face bits, slot faces][W slots, column-major n x (p+1)][A^{-1} column-major]
+// (see Rec in device.cuh).
 #pragma once
 #include <type_traits>
 
@@ -31,7 +32,8 @@ factor_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t*
               const T* __restrict__ Mm, const T* __restrict__ Gxm, const T* __restrict__ Gym,
               const T* __restrict__ nds, FaceTab<T> ft, int nx, int ny, long long E,
               T* __restrict__ rec, unsigned int* status) {
-  constexpr int Q = P + 1, N = Q * Q, NQ = P + 2, R = rec_size<P>();
+  constexpr int Q = P + 1, N = Q * Q, NQ = P + 2;
+  using L = Rec<P, T>;
   const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (m >= nmem) return;
   const uint32_t c = code[m];
@@ -94,14 +96,21 @@ factor_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t*
       A[i * N + k] = -fct * inv;
     }
   }
-  T* out = rec + (size_t)m * R;
+  char* out = L::s_at(rec, m);
+  char* outx = L::x_at((char*)rec + nmem * (long long)L::kStaged, m);
+  T* ai = L::ainv(outx);
 #pragma unroll
   for (int j = 0; j < N; ++j)
 #pragma unroll
-    for (int i = 0; i < N; ++i) out[j * N + i] = A[i * N + j];
+    for (int i = 0; i < N; ++i) ai[j * N + i] = A[i * N + j];
+  unsigned faces = 0xffffffffu;
+  int slot = 0;
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
     if (!(bits & (1u << f)) || nb_elem(nx, ny, e, f) < 0) continue;
+    T* W = L::slot(out, outx, slot);
+    faces = (faces & ~(0xffu << (8 * slot))) | ((unsigned)f << (8 * slot));
+    ++slot;
 #pragma unroll
     for (int t = 0; t < Q; ++t)
 #pragma unroll
@@ -109,19 +118,18 @@ factor_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t*
         T w = 0;
 #pragma unroll
         for (int a = 0; a < Q; ++a) w += A[i * N + face_dof<P>(f, a)] * Cin[f][a][t];
-        out[N * N + f * N * Q + t * N + i] = w;
+        W[t * N + i] = w;
       }
   }
+  *reinterpret_cast<uint4*>(out) = make_uint4((unsigned)e, (unsigned)bits, faces, 0u);
 }
-
 
 template <int P, typename T>
 static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, cudaStream_t stream) {
-  const size_t R = rec_size<P>();
   void** recp = std::is_same<T, double>::value ? &S.rec64 : &S.rec32;
   if (!*recp) {
     size_t cap = 0;
-    vef_status st = ensure_buffer(recp, &cap, (size_t)S.members * R * sizeof(T));
+    vef_status st = ensure_buffer(recp, &cap, (size_t)S.members * (Rec<P, T>::kStaged + Rec<P, T>::kX));
     if (st != VEF_OK) return st;
   }
   const T* Mm;

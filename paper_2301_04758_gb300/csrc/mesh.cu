@@ -196,15 +196,20 @@ Mesh::~Mesh() {
   cudaFree(Gx32);
   cudaFree(Gy32);
   cudaFree(nds32);
-  cudaFree(flags);
   cudaFree(dev_status);
   cudaFree(bvol);
   cudaFree(work);
   cudaFree(work2);
+  cudaFree(ybuf);
 }
 
 Schedule::~Schedule() {
-  cudaFree(chunk_begin);
+  cudaFree(dir_lev0);
+  cudaFree(lev_begin);
+  cudaFree(lev_gbegin);
+  cudaFree(lev_mbegin);
+  cudaFree(member_info);
+  cudaFree(member_nbpos);
   cudaFree(slot_first);
   cudaFree(slot_count);
   cudaFree(member_code);

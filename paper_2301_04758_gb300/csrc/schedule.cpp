@@ -1,5 +1,5 @@
 // Sweep schedule: per-direction upwind dependency graph, its strongly coupled element
-// groups, dependency levels and the warp-sized task chunks the sweep kernel claims.
+// groups and the dependency levels the sweep kernel walks (one cluster per direction).
 //
 // For direction Omega_d, element e depends on its neighbour across face f when some
 // Gauss point of that face is strictly inflow (Omega . n ds < 0); a tangential point
@@ -247,8 +247,6 @@ Schedule* get_schedule(Mesh* mesh, const double* omega, const double* weights, i
   S->omega.assign(omega, omega + 2 * D);
   S->weights.assign(weights, weights + D);
   S->members = (long long)D * E;
-  const int spc = std::max(1, 32 / M.n);
-  S->slots_per_chunk = spc;
   int levels = 0;
   for (auto& g : graphs) {
     levels = std::max(levels, g.levels);
@@ -256,82 +254,104 @@ Schedule* get_schedule(Mesh* mesh, const double* omega, const double* weights, i
     S->lagged_points += g.lagged;
   }
   S->levels = levels;
-  // bucket components by level
-  std::vector<std::vector<std::pair<int, int>>> bylevel(levels);  // (d, comp)
-  for (int d = 0; d < D; ++d)
-    for (int c = 0; c < graphs[d].ncomp; ++c) bylevel[graphs[d].comp_level[c]].push_back({d, c});
-  std::vector<int> chunk_begin{0}, slot_first, slot_count;
+  // Per direction, its levels in order; inside a level the single-element tasks first,
+  // then the coupled groups.  Slots, members and factor records all follow this order.
+  std::vector<int> dir_lev0(D + 1, 0), lev_begin, lev_gbegin, lev_mbegin, slot_first, slot_count;
   std::vector<uint32_t> member_code;
   std::vector<int> member_of((size_t)D * E, -1);
+  std::vector<int> level_of((size_t)D * E, -1);
   member_code.reserve((size_t)D * E);
-  auto add_member = [&](int d, int e) {
+  auto add_member = [&](int d, int e, int L) {
     member_of[(size_t)d * E + e] = (int)member_code.size();
+    level_of[(size_t)d * E + e] = L;
     member_code.push_back(((uint32_t)d << 22) | (uint32_t)e);
   };
-  for (int L = 0; L < levels; ++L) {
-    int in_chunk = 0;
-    for (auto& dc : bylevel[L]) {
-      const DirGraph& g = graphs[dc.first];
-      int b = g.comp_first[dc.second], n = g.comp_first[dc.second + 1] - b;
-      if (n == 1) {
+  for (int d = 0; d < D; ++d) {
+    const DirGraph& g = graphs[d];
+    dir_lev0[d] = (int)lev_begin.size();
+    std::vector<std::vector<int>> bylevel(g.levels);
+    for (int c = 0; c < g.ncomp; ++c) bylevel[g.comp_level[c]].push_back(c);
+    for (int L = 0; L < g.levels; ++L) {
+      lev_begin.push_back((int)slot_first.size());
+      lev_mbegin.push_back((int)member_code.size());
+      for (int c : bylevel[L]) {
+        const int b = g.comp_first[c], n = g.comp_first[c + 1] - b;
+        if (n != 1) continue;
         slot_first.push_back((int)member_code.size());
         slot_count.push_back(1);
-        add_member(dc.first, g.comp_members[b]);
-        if (++in_chunk == spc) {
-          chunk_begin.push_back((int)slot_first.size());
-          in_chunk = 0;
-        }
+        add_member(d, g.comp_members[b], L);
       }
-    }
-    if (in_chunk) chunk_begin.push_back((int)slot_first.size());
-    for (auto& dc : bylevel[L]) {
-      const DirGraph& g = graphs[dc.first];
-      int b = g.comp_first[dc.second], n = g.comp_first[dc.second + 1] - b;
-      if (n > 1) {
+      lev_gbegin.push_back((int)slot_first.size());
+      for (int c : bylevel[L]) {
+        const int b = g.comp_first[c], n = g.comp_first[c + 1] - b;
+        if (n == 1) continue;
         slot_first.push_back((int)member_code.size());
         slot_count.push_back(n);
-        for (int t = 0; t < n; ++t) add_member(dc.first, g.comp_members[b + t]);
-        chunk_begin.push_back((int)slot_first.size());
+        for (int t = 0; t < n; ++t) add_member(d, g.comp_members[b + t], L);
       }
     }
   }
-  S->nchunks = (int)chunk_begin.size() - 1;
-  // Validate the deadlock-freedom invariant the sweep kernel relies on: every member is
-  // scheduled exactly once and each of its external upwind donors lies in an earlier
-  // chunk (warps claim chunks in increasing order and only wait on smaller ones).
-  {
-    std::vector<int> chunk_of_member(member_code.size(), -1);
-    for (int c = 0; c < S->nchunks; ++c)
-      for (int s = chunk_begin[c]; s < chunk_begin[c + 1]; ++s)
-        for (int t = 0; t < slot_count[s]; ++t) chunk_of_member[slot_first[s] + t] = c;
-    for (size_t m = 0; m < member_code.size(); ++m) {
-      int d = (int)(member_code[m] >> 22), e = (int)(member_code[m] & ((1u << 22) - 1));
-      uint16_t bits = graphs[d].info[e];
+  dir_lev0[D] = (int)lev_begin.size();
+  lev_begin.push_back((int)slot_first.size());
+  S->total_levels = dir_lev0[D];
+  // Validate the order the sweep relies on: every element is scheduled once, and each
+  // external upwind donor sits at an earlier level of the same direction.
+  for (size_t t = 0; t < member_of.size(); ++t)
+    if (member_of[t] < 0) {
+      set_last_error("internal error: sweep schedule misses an element");
+      *st = VEF_ERR_INVALID_ARG;
+      return nullptr;
+    }
+  for (int d = 0; d < D; ++d)
+    for (int e = 0; e < E; ++e) {
+      const uint16_t bits = graphs[d].info[e];
       for (int f = 0; f < 4; ++f) {
         if (!(bits & (1u << f)) || (bits & (1u << (4 + f)))) continue;
-        int nb = nb_of(M.nx, M.ny, e, f);
+        const int nb = nb_of(M.nx, M.ny, e, f);
         if (nb < 0) continue;
-        int mn = member_of[(size_t)d * E + nb];
-        if (mn < 0 || chunk_of_member[mn] < 0 || chunk_of_member[mn] >= chunk_of_member[m]) {
+        if (level_of[(size_t)d * E + nb] >= level_of[(size_t)d * E + e]) {
           set_last_error("internal error: sweep schedule violates the dependency order");
           *st = VEF_ERR_INVALID_ARG;
           return nullptr;
         }
       }
     }
-    for (size_t t = 0; t < member_of.size(); ++t)
-      if (member_of[t] < 0) {
-        set_last_error("internal error: sweep schedule misses an element");
-        *st = VEF_ERR_INVALID_ARG;
-        return nullptr;
-      }
-  }
   S->nslots = (long long)slot_first.size();
   std::vector<uint16_t> faceinfo((size_t)D * E);
   for (int d = 0; d < D; ++d)
     std::copy(graphs[d].info.begin(), graphs[d].info.end(), faceinfo.begin() + (size_t)d * E);
   std::vector<double> om(omega, omega + 2 * D), wt(weights, weights + D);
-  if ((*st = upload(&S->chunk_begin, chunk_begin)) != VEF_OK) return nullptr;
+  if ((*st = upload(&S->dir_lev0, dir_lev0)) != VEF_OK) return nullptr;
+  if ((*st = upload(&S->lev_begin, lev_begin)) != VEF_OK) return nullptr;
+  if ((*st = upload(&S->lev_gbegin, lev_gbegin)) != VEF_OK) return nullptr;
+  if ((*st = upload(&S->lev_mbegin, lev_mbegin)) != VEF_OK) return nullptr;
+  {
+    std::vector<uint2> minfo(member_code.size());
+    for (size_t m = 0; m < member_code.size(); ++m) {
+      const int d = (int)(member_code[m] >> 22), e = (int)(member_code[m] & ((1u << 22) - 1));
+      minfo[m] = make_uint2((unsigned)e, (unsigned)graphs[d].info[e]);
+    }
+    if ((*st = upload(&S->member_info, minfo)) != VEF_OK) return nullptr;
+    // byte f of member_nbpos: position inside the member's group of its neighbour across
+    // face f when that neighbour is in the same group, else 255
+    std::vector<uint32_t> nbpos(member_code.size(), 0xffffffffu);
+    for (size_t sl = 0; sl < slot_first.size(); ++sl) {
+      if (slot_count[sl] == 1) continue;
+      const int first = slot_first[sl], cnt = slot_count[sl];
+      for (int t = 0; t < cnt; ++t) {
+        const int m = first + t;
+        const int d = (int)(member_code[m] >> 22), e = (int)(member_code[m] & ((1u << 22) - 1));
+        uint32_t packed = 0xffffffffu;
+        for (int f = 0; f < 4; ++f) {
+          if (!(graphs[d].info[e] & (1u << (4 + f)))) continue;
+          const int pos = member_of[(size_t)d * E + nb_of(M.nx, M.ny, e, f)] - first;
+          if (pos >= 0 && pos < 255) packed = (packed & ~(0xffu << (8 * f))) | ((uint32_t)pos << (8 * f));
+        }
+        nbpos[m] = packed;
+      }
+    }
+    if ((*st = upload(&S->member_nbpos, nbpos)) != VEF_OK) return nullptr;
+  }
   if ((*st = upload(&S->slot_first, slot_first)) != VEF_OK) return nullptr;
   if ((*st = upload(&S->slot_count, slot_count)) != VEF_OK) return nullptr;
   if ((*st = upload(&S->member_code, member_code)) != VEF_OK) return nullptr;

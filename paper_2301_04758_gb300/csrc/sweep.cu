@@ -1,5 +1,5 @@
-// Transport sweep: local factorisation, dependency-driven wavefront solve, FP64 residual
-// and mixed-precision defect correction, and source iteration.
+// Transport sweep: dependency-free right-hand-side apply, cluster wavefront solve, FP64
+// residual and mixed-precision defect correction, and source iteration.
 //
 // The element equations (upwind DG, pointwise upwinding at face Gauss points) give, for
 // direction d and element e,
@@ -9,25 +9,24 @@
 // with u_f the upwind neighbour's face-node values (GLL basis: its trace on the shared face
 // is spanned by its p+1 face nodes).  Only the u_f terms depend on other elements.
 //
-// factor_kernel (factor.cu; no dependencies, one thread per (element, direction)) assembles
-// A and inverts it in place by Gauss-Jordan elimination, and forms W_f = A^{-1} Cin_f for the
-// interior inflow faces.  The record per (element, direction) is
-//     [A^{-1} column-major n x n][W_0 ... W_3, each column-major n x (p+1)].
-// sweep_kernel then only does, per element, psi = A^{-1} b - sum_f W_f u_f, one lane per
-// dof row, so that the chain of dependent work per wavefront level is a few FMAs (on this
-// GPU a warp-wide FP64 FMA occupies its SM sub-partition for ~64 cycles, so per-element
-// latency, not total flops, bounds a naive wavefront).
-//
-// Warps claim warp-sized chunks of independent tasks in increasing order from one
-// counter; each task waits (bounded) on the completion epochs of its upwind donors,
-// which the schedule places in earlier chunks, so the kernel makes progress without any
-// assumption on block residency.
+// factor_kernel (factor_impl.cuh) stores per (element, direction) A^{-1} and
+// W_f = A^{-1} Cin_f.  apply_kernel forms y = A^{-1} b for every (element, direction) with
+// no dependencies; sweep_kernel then only computes psi = y - sum_f W_f u_f along the
+// dependency levels, one lane per dof row, so the chain of dependent work per level is a
+// few FMAs (on this GPU a warp-wide FP64 FMA occupies its SM sub-partition for ~64
+// cycles, so per-element latency, not total flops, bounds a wavefront).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "device.cuh"
 
 namespace vef {
+
+// sweep launch defaults, 100 * (CTAs per direction cluster) + (warps per CTA), measured
+// on the 256 x 256 Q2 S8 sine-mesh sweep (FP64: 4 x 8 warps, FP32: 8 x 8 warps)
+constexpr int kDefaultTile64 = 408;
+constexpr int kDefaultTile32 = 808;
 
 
 // ----------------------------------------------------------------- right-hand sides
@@ -53,15 +52,21 @@ __global__ void bvol_kernel(long long E, int n, const double* __restrict__ M,
 // --------------------------------------------------------------------------- sweep
 template <typename T>
 struct SweepArgs {
-  int nchunks;
-  const int* chunk_begin;
+  const int* dir_lev0;
+  const int* lev_begin;
+  const int* lev_gbegin;
+  const int* lev_mbegin;
+  const uint2* member_info;
+  const uint32_t* member_nbpos;
+  int cluster_size;
   const int* slot_first;
   const int* slot_count;
   const uint32_t* code;
   const int* member_of;
   const uint16_t* finfo;
   const double* omega;
-  const T* rec;
+  const T* rec;             // staged record array S (see Rec)
+  const T* recx;            // extra record array X
   const double* bvol;      // [E][n] (mode 0)
   const double* src_aniso; // [D][E][n] or null (mode 0)
   const double* Mm;        // FP64 mass matrices (anisotropic source)
@@ -69,9 +74,8 @@ struct SweepArgs {
   const T* nds;            // [E][4][nq][2]
   const double* rhs;       // [D][E][n] (mode 1)
   T* out;                  // [D][E][n]
-  uint32_t* flags;         // [D][E]
-  uint32_t epoch;
-  unsigned int* status;    // [0] bits, [1] abort, [2] max inner iterations, [3] chunk counter
+  T* y;                    // [D][E][n] A^{-1} b (apply_kernel)
+  unsigned int* status;    // [0] status bits, [2] max inner iterations
   int nx, ny;
   long long E, nbf;
   T tol;
@@ -119,154 +123,400 @@ __device__ __forceinline__ T rhs_entry(const SweepArgs<T>& a, int d, int e, int 
   return bt;
 }
 
+// y = A^{-1} b for every (element, direction): no dependencies, one lane per dof row,
+// records read in schedule order (consecutive members are adjacent in memory); y rows are
+// written in schedule order with a 16-byte-aligned stride.
 template <int P, typename T, int MODE>
-__global__ void __launch_bounds__(128) sweep_kernel(SweepArgs<T> a) {
-  constexpr int Q = P + 1, N = Q * Q, R = rec_size<P>();
+__global__ void __launch_bounds__(128) apply_kernel(SweepArgs<T> a, long long nmem) {
+  constexpr int Q = P + 1, N = Q * Q;
+  using L = Rec<P, T>;
   constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
   constexpr unsigned FULL = 0xffffffffu;
+  (void)Q;
   const int lane = threadIdx.x & 31;
-  while (true) {
-    int c = 0;
-    if (lane == 0) c = (int)atomicAdd(a.status + 3, 1u);
-    c = __shfl_sync(FULL, c, 0);
-    if (c >= a.nchunks) return;
-    if (*((volatile unsigned int*)(a.status + 1)) != 0u) return;
-    const int s0 = a.chunk_begin[c], s1 = a.chunk_begin[c + 1];
-    const int cnt0 = a.slot_count[s0];
-    if (cnt0 == 1) {
-      // ---- up to SPC independent single-element tasks, N lanes each
-      const int slot = s0 + lane / N;
-      const int i = lane % N;
-      const bool valid = (lane < SPC * N) && (slot < s1);
-      int d = 0, e = 0;
-      long long m = 0;
-      uint16_t bits = 0;
-      T mu = 0, eta = 0;
-      T bi = 0;
-      if (valid) {
-        m = a.slot_first[slot];
-        const uint32_t cd = a.code[m];
-        d = (int)(cd >> 22);
-        e = (int)(cd & 0x3fffffu);
-        bits = a.finfo[(size_t)d * a.E + e];
-        mu = (T)a.omega[2 * d];
-        eta = (T)a.omega[2 * d + 1];
-        bi = rhs_entry<P, T, MODE>(a, d, e, i, bits, mu, eta);
-      }
-      const T* rec = a.rec + (size_t)m * R;
-      const int base = (lane / N) * N;
-      T y = 0;
+  const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long m = gw * SPC + lane / N;
+  const int i = lane % N;
+  const bool valid = (lane < SPC * N) && (m < nmem);
+  T bi = 0;
+  if (valid) {
+    const uint32_t cd = a.code[m];
+    const int d = (int)(cd >> 22);
+    const int e = (int)(cd & 0x3fffffu);
+    const uint16_t bits = a.finfo[(size_t)d * a.E + e];
+    bi = rhs_entry<P, T, MODE>(a, d, e, i, bits, (T)a.omega[2 * d], (T)a.omega[2 * d + 1]);
+  }
+  const T* ai = L::ainv(L::x_at(a.recx, valid ? m : 0));
+  const int base = (lane / N) * N;
+  T y = 0;
 #pragma unroll
-      for (int j = 0; j < N; ++j) {
-        const T bj = __shfl_sync(FULL, bi, (base + j) & 31);
-        if (valid) y += rec[j * N + i] * bj;
-      }
-      bool ok = true;
-      if (valid) {
+  for (int j = 0; j < N; ++j) {
+    const T bj = __shfl_sync(FULL, bi, (base + j) & 31);
+    if (valid) y += ai[j * N + i] * bj;
+  }
+  if (valid) a.y[(size_t)m * L::kYStride + i] = y;
+}
+
+// upwind correction of row i for face f of member record r: sum_t W_f[t][i] u_t
+template <int P, typename T>
+__device__ __forceinline__ T face_term(const T* W, const T* un, int f, int i) {
+  constexpr int Q = P + 1, N = Q * Q;
+  T acc = 0;
 #pragma unroll
+  for (int t = 0; t < Q; ++t) acc += W[t * N + i] * ldcg(un + face_dof<P>((f + 2) & 3, t));
+  return acc;
+}
+
+// Coupled group, global-memory form (groups larger than the shared-memory capacity).
+template <int P, typename T, int MODE>
+__device__ __forceinline__ void group_solve(const SweepArgs<T>& a, int d, int s0) {
+  constexpr int Q = P + 1, N = Q * Q;
+  using L = Rec<P, T>;
+  constexpr unsigned FULL = 0xffffffffu;
+  (void)Q;
+  const int lane = threadIdx.x & 31;
+  const int first = a.slot_first[s0];
+  const int cnt = a.slot_count[s0];
+  const int i = lane;
+  const bool act = lane < N;
+  int it = 0;
+  bool conv = false;
+  for (; it < a.max_inner; ++it) {
+    T dmax = 0, amax = 0;
+    for (int mi = 0; mi < cnt; ++mi) {
+      const char* r = L::s_at(a.rec, first + mi);
+      const char* rx = L::x_at(a.recx, first + mi);
+      const uint4 info = *reinterpret_cast<const uint4*>(r);
+      const int e = (int)info.x;
+      const unsigned bits = info.y;
+      if (act) {
+        T y = a.y[(size_t)(first + mi) * L::kYStride + i];
         for (int f = 0; f < 4; ++f) {
-          if (!(bits & (1u << f))) continue;
+          const int sl = rec_slot_of(info.z, f);
+          if (sl < 0) continue;
           const int nb = nb_elem(a.nx, a.ny, e, f);
-          if (nb < 0) continue;
-          if (!wait_epoch(a.flags + (size_t)d * a.E + nb, a.epoch, a.status)) { ok = false; break; }
-        }
-      }
-      if (!__all_sync(FULL, ok)) return;
-      if (valid) {
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          if (!(bits & (1u << f))) continue;
-          const int nb = nb_elem(a.nx, a.ny, e, f);
-          if (nb < 0) continue;
-          const T* un = a.out + ((size_t)d * a.E + nb) * N;
-          const T* W = rec + N * N + f * N * Q;
-#pragma unroll
-          for (int t = 0; t < Q; ++t) y -= W[t * N + i] * ldcg(un + face_dof<P>((f + 2) & 3, t));
-        }
-        a.out[((size_t)d * a.E + e) * N + i] = y;
-      }
-      __threadfence();
-      __syncwarp();
-      if (valid && i == 0) st_release(a.flags + (size_t)d * a.E + e, a.epoch);
-    } else {
-      // ---- one strongly coupled group: members in order, block Gauss-Seidel to tol
-      const int first = a.slot_first[s0];
-      const int cnt = cnt0;
-      const int i = lane;
-      const bool act = lane < N;
-      const uint32_t c0 = a.code[first];
-      const int d = (int)(c0 >> 22);
-      const T mu = (T)a.omega[2 * d], eta = (T)a.omega[2 * d + 1];
-      bool ok = true;
-      // wait on every external donor first
-      for (int mi = 0; mi < cnt && ok; ++mi) {
-        const int e = (int)(a.code[first + mi] & 0x3fffffu);
-        const uint16_t bits = a.finfo[(size_t)d * a.E + e];
-        for (int f = 0; f < 4; ++f) {
-          if (!(bits & (1u << f)) || (bits & (1u << (4 + f)))) continue;
-          const int nb = nb_elem(a.nx, a.ny, e, f);
-          if (nb < 0) continue;
-          if (!wait_epoch(a.flags + (size_t)d * a.E + nb, a.epoch, a.status)) { ok = false; break; }
-        }
-      }
-      if (!__all_sync(FULL, ok)) return;
-      int it = 0;
-      bool conv = false;
-      for (; it < a.max_inner; ++it) {
-        T dmax = 0, amax = 0;
-        for (int mi = 0; mi < cnt; ++mi) {
-          const long long m = first + mi;
-          const int e = (int)(a.code[m] & 0x3fffffu);
-          const uint16_t bits = a.finfo[(size_t)d * a.E + e];
-          const T* rec = a.rec + (size_t)m * R;
-          T bi = act ? rhs_entry<P, T, MODE>(a, d, e, i, bits, mu, eta) : (T)0;
-          T y = 0;
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            const T bj = __shfl_sync(FULL, bi, j & 31);
-            if (act) y += rec[j * N + i] * bj;
+          if ((bits & (1u << (4 + f))) && it == 0) {
+            const int pos = a.member_of[(size_t)d * a.E + nb] - first;
+            if (pos >= mi) continue;  // not computed yet in the first sweep
           }
-          if (act) {
-            for (int f = 0; f < 4; ++f) {
-              if (!(bits & (1u << f))) continue;
-              const int nb = nb_elem(a.nx, a.ny, e, f);
-              if (nb < 0) continue;
-              if ((bits & (1u << (4 + f))) && it == 0) {
-                const int pos = a.member_of[(size_t)d * a.E + nb] - first;
-                if (pos >= mi) continue;  // not computed yet in the first sweep
-              }
-              const T* un = a.out + ((size_t)d * a.E + nb) * N;
-              const T* W = rec + N * N + f * N * Q;
-#pragma unroll
-              for (int t = 0; t < Q; ++t) y -= W[t * N + i] * ldcg(un + face_dof<P>((f + 2) & 3, t));
-            }
-            T* o = a.out + ((size_t)d * a.E + e) * N + i;
-            if (it > 0) dmax = fmax(dmax, fabs(y - ldcg(o)));
-            amax = fmax(amax, fabs(y));
-            *o = y;
-          }
-          __threadfence();
-          __syncwarp();
+          y -= face_term<P, T>(L::slot(r, rx, sl), a.out + ((size_t)d * a.E + nb) * N, f, i);
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          dmax = fmax(dmax, __shfl_xor_sync(FULL, dmax, off));
-          amax = fmax(amax, __shfl_xor_sync(FULL, amax, off));
-        }
-        if (it > 0 && dmax <= a.tol * amax) { conv = true; ++it; break; }
+        T* o = a.out + ((size_t)d * a.E + e) * N + i;
+        if (it > 0) dmax = fmax(dmax, fabs(y - ldcg(o)));
+        amax = fmax(amax, fabs(y));
+        *o = y;
       }
-      if (lane == 0) {
-        if (!conv) atomicOr(a.status, kDevNotConverged);
-        atomicMax(a.status + 2, (unsigned)it);
-      }
-      __threadfence();
       __syncwarp();
-      for (int mi = lane; mi < cnt; mi += 32) {
-        const int e = (int)(a.code[first + mi] & 0x3fffffu);
-        st_release(a.flags + (size_t)d * a.E + e, a.epoch);
-      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      dmax = fmax(dmax, __shfl_xor_sync(FULL, dmax, off));
+      amax = fmax(amax, __shfl_xor_sync(FULL, amax, off));
+    }
+    if (it > 0 && dmax <= a.tol * amax) { conv = true; ++it; break; }
+  }
+  if (lane == 0) {
+    if (!conv) atomicOr(a.status, kDevNotConverged);
+    atomicMax(a.status + 2, (unsigned)it);
+  }
+}
+
+// Coupled group held in shared memory: members' y rows, current iterates and external
+// upwind traces are staged once, so each inner Gauss-Seidel step touches only shared
+// memory (and the L1-resident W rows).
+template <int P, typename T>
+__host__ __device__ constexpr int group_smem_max() { return P <= 2 ? 16 : 8; }
+
+template <int P, typename T>
+struct GroupSmem {
+  T y[group_smem_max<P, T>() * (P + 1) * (P + 1)];
+  T psi[group_smem_max<P, T>() * (P + 1) * (P + 1)];
+  T ext[group_smem_max<P, T>() * 4 * (P + 1)];
+  uint4 info[group_smem_max<P, T>()];
+  uint32_t nbpos[group_smem_max<P, T>()];
+};
+
+// members' record info, in-group neighbour positions and y rows: none of it depends on
+// earlier levels, so a group warp stages it ahead of its level
+template <int P, typename T>
+__device__ __forceinline__ void group_stage_static(const SweepArgs<T>& a, int s0, GroupSmem<P, T>& g) {
+  constexpr int Q = P + 1, N = Q * Q;
+  using L = Rec<P, T>;
+  (void)Q;
+  const int lane = threadIdx.x & 31;
+  const int first = a.slot_first[s0];
+  const int cnt = a.slot_count[s0];
+  for (int mi = lane; mi < cnt; mi += 32) {
+    g.info[mi] = *reinterpret_cast<const uint4*>(L::s_at(a.rec, first + mi));
+    g.nbpos[mi] = a.member_nbpos[first + mi];
+  }
+  for (int t = lane; t < cnt * N; t += 32) g.y[t] = a.y[(size_t)(first + t / N) * L::kYStride + t % N];
+  __syncwarp();
+}
+
+template <int P, typename T, int MODE>
+__device__ __forceinline__ void group_solve_smem(const SweepArgs<T>& a, int d, int s0,
+                                                 GroupSmem<P, T>& g) {
+  constexpr int Q = P + 1, N = Q * Q;
+  using L = Rec<P, T>;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int first = a.slot_first[s0];
+  const int cnt = a.slot_count[s0];
+  const int i = lane;
+  const bool act = lane < N;
+  for (int mi = 0; mi < cnt; ++mi) {
+    const int e = (int)g.info[mi].x;
+    const unsigned bits = g.info[mi].y;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      if (!(bits & (1u << f)) || ((g.nbpos[mi] >> (8 * f)) & 0xffu) != 0xffu) continue;
+      const int nb = nb_elem(a.nx, a.ny, e, f);
+      if (nb < 0 || lane >= Q) continue;
+      g.ext[(mi * 4 + f) * Q + lane] = ldcg(a.out + ((size_t)d * a.E + nb) * N + face_dof<P>((f + 2) & 3, lane));
     }
   }
+  __syncwarp();
+  int it = 0;
+  bool conv = false;
+  for (; it < a.max_inner; ++it) {
+    T dmax = 0, amax = 0;
+    for (int mi = 0; mi < cnt; ++mi) {
+      const char* r = L::s_at(a.rec, first + mi);
+      const char* rx = L::x_at(a.recx, first + mi);
+      const unsigned faces = g.info[mi].z;
+      if (act) {
+        T y = g.y[mi * N + i];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const int sl = rec_slot_of(faces, f);
+          if (sl < 0) continue;
+          const T* W = L::slot(r, rx, sl);
+          const unsigned pos = (g.nbpos[mi] >> (8 * f)) & 0xffu;
+          if (pos != 0xffu) {
+            if (it == 0 && (int)pos >= mi) continue;  // not computed yet in the first sweep
+#pragma unroll
+            for (int t = 0; t < Q; ++t) y -= W[t * N + i] * g.psi[pos * N + face_dof<P>((f + 2) & 3, t)];
+          } else {
+#pragma unroll
+            for (int t = 0; t < Q; ++t) y -= W[t * N + i] * g.ext[(mi * 4 + f) * Q + t];
+          }
+        }
+        if (it > 0) dmax = fmax(dmax, fabs(y - g.psi[mi * N + i]));
+        amax = fmax(amax, fabs(y));
+        g.psi[mi * N + i] = y;
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      dmax = fmax(dmax, __shfl_xor_sync(FULL, dmax, off));
+      amax = fmax(amax, __shfl_xor_sync(FULL, amax, off));
+    }
+    if (it > 0 && dmax <= a.tol * amax) { conv = true; ++it; break; }
+  }
+  if (lane == 0) {
+    if (!conv) atomicOr(a.status, kDevNotConverged);
+    atomicMax(a.status + 2, (unsigned)it);
+  }
+  if (act)
+    for (int mi = 0; mi < cnt; ++mi)
+      a.out[((size_t)d * a.E + g.info[mi].x) * N + i] = g.psi[mi * N + i];
+  __syncwarp();
+}
+
+// Per warp: the staged prefixes of its single-element tasks' records (info + W slots 0, 1)
+// and their y rows, for kSweepRounds rounds of two levels, filled by bulk copies (TMA)
+// whose completion is counted on one mbarrier per level buffer.
+constexpr int kSweepRounds = 2;
+
+template <int P, typename T>
+struct SweepSmem {
+  static constexpr int SPC = (32 / ((P + 1) * (P + 1))) > 0 ? (32 / ((P + 1) * (P + 1))) : 1;
+  alignas(16) unsigned char rec[2][kSweepRounds][SPC][Rec<P, T>::kStaged];
+  alignas(16) unsigned char y[2][kSweepRounds][SPC][Rec<P, T>::kYBytes];
+  uint64_t bar[2];
+  GroupSmem<P, T> group;
+};
+
+constexpr uint32_t kStageWaitIters = 1u << 26;
+
+// Warps [0, nws) of a cluster take the single-element tasks; the last ng warps take the
+// coupled groups, so a group's inner iteration never delays a warp's singles and its
+// static data is staged while the previous level finishes.
+template <int P, typename T, int MODE>
+__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
+  constexpr int Q = P + 1, N = Q * Q;
+  using L = Rec<P, T>;
+  constexpr int SPC = SweepSmem<P, T>::SPC;
+  extern __shared__ __align__(16) unsigned char sweep_smem[];
+  const int lane = threadIdx.x & 31;
+  SweepSmem<P, T>& sm = reinterpret_cast<SweepSmem<P, T>*>(sweep_smem)[threadIdx.x >> 5];
+  const int cs = a.cluster_size;
+  const int d = blockIdx.x / cs;
+  const int nw = cs * (blockDim.x >> 5);
+  const int gw = (blockIdx.x % cs) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int ng = nw >= 16 ? nw / 16 : 1;
+  const int nws = nw > ng ? nw - ng : nw;   // one-warp clusters do both kinds
+  const bool singles = gw < nws;
+  const bool groups = gw >= nws || nw == 1;
+  const int gidx = nw == 1 ? 0 : gw - nws;
+  const int k0 = a.dir_lev0[d], k1 = a.dir_lev0[d + 1];
+  const int i = lane % N;
+  const int s_lane = lane / N;              // task slot of this lane inside a round
+  const int stride = nws * SPC;
+  const bool lane_ok = singles && lane < SPC * N;
+  if (lane == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+  unsigned phase[2] = {0u, 0u};
+  bool pending[2] = {false, false};
+  // stage level k into buffer b: up to kSweepRounds rounds of SPC consecutive members
+  auto stage_level = [&](int k, int b) {
+    const int n = a.lev_gbegin[k] - a.lev_begin[k], mb = a.lev_mbegin[k];
+    unsigned bytes = 0;
+    int cnt[kSweepRounds];
+#pragma unroll
+    for (int r = 0; r < kSweepRounds; ++r) {
+      const int t0 = gw * SPC + r * stride;
+      cnt[r] = singles ? max(0, min(SPC, n - t0)) : 0;
+      bytes += (unsigned)cnt[r] * (L::kStaged + L::kYBytes);
+    }
+    pending[b] = bytes > 0;
+    if (!bytes) return;
+    __syncwarp();
+    if (lane == 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&sm.bar[b], bytes);
+#pragma unroll
+      for (int r = 0; r < kSweepRounds; ++r) {
+        if (!cnt[r]) continue;
+        const long long m0 = mb + gw * SPC + r * stride;
+        bulk_g2s(sm.rec[b][r][0], L::s_at(a.rec, m0), (unsigned)cnt[r] * L::kStaged, &sm.bar[b]);
+        bulk_g2s(sm.y[b][r][0], a.y + m0 * L::kYStride, (unsigned)cnt[r] * L::kYBytes, &sm.bar[b]);
+      }
+    }
+  };
+  auto wait_level = [&](int b) {
+    if (!pending[b]) return;
+    uint32_t n = 0;
+    while (!mbar_try_wait(&sm.bar[b], phase[b]) && ++n < kStageWaitIters) {
+    }
+    if (n >= kStageWaitIters && lane == 0) atomicOr(a.status, kDevTimeout);
+    phase[b] ^= 1u;
+    pending[b] = false;
+  };
+  if (singles) {
+    stage_level(k0, 0);
+    if (k0 + 1 < k1) stage_level(k0 + 1, 1);
+  }
+  int staged = -1;   // group slot whose static data sits in sm.group
+  if (groups) {
+    const int g0 = a.lev_gbegin[k0] + gidx;
+    if (g0 < a.lev_begin[k0 + 1] && a.slot_count[g0] <= group_smem_max<P, T>()) {
+      group_stage_static<P, T>(a, g0, sm.group);
+      staged = g0;
+    }
+  }
+  for (int k = k0; k < k1; ++k) {
+    const int b = (k - k0) & 1;
+    const int sb = a.lev_begin[k], sg = a.lev_gbegin[k], se = a.lev_begin[k + 1];
+    if (singles) {
+      const int nsingle = sg - sb, mb = a.lev_mbegin[k];
+      wait_level(b);
+      // staged rounds: issue every upwind load first, then the FMAs
+      T u[kSweepRounds][2][Q];
+      bool has[kSweepRounds];
+#pragma unroll
+      for (int r = 0; r < kSweepRounds; ++r) {
+        has[r] = lane_ok && gw * SPC + r * stride + s_lane < nsingle;
+        if (!has[r]) continue;
+        const uint4 info = *reinterpret_cast<const uint4*>(sm.rec[b][r][s_lane]);
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl) {
+          const unsigned f = (info.z >> (8 * sl)) & 0xffu;
+          if (f == 0xffu) continue;
+          const T* un = a.out + ((size_t)d * a.E + nb_elem(a.nx, a.ny, (int)info.x, (int)f)) * N;
+#pragma unroll
+          for (int t = 0; t < Q; ++t) u[r][sl][t] = ldcg(un + face_dof<P>(((int)f + 2) & 3, t));
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kSweepRounds; ++r) {
+        if (!has[r]) continue;
+        const char* rs = (const char*)sm.rec[b][r][s_lane];
+        const uint4 info = *reinterpret_cast<const uint4*>(rs);
+        T y0 = reinterpret_cast<const T*>(sm.y[b][r][s_lane])[i], y1 = 0;
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl) {
+          if (((info.z >> (8 * sl)) & 0xffu) == 0xffu) continue;
+          const T* W = L::slot(rs, nullptr, sl);
+          T acc = 0;
+#pragma unroll
+          for (int t = 0; t < Q; ++t) acc += W[t * N + i] * u[r][sl][t];
+          if (sl == 0) y0 -= acc; else y1 -= acc;
+        }
+        T y = y0 + y1;
+        if (((info.z >> 16) & 0xffu) != 0xffu) {   // rare: more than two interior inflow faces
+          const char* rg = L::x_at(a.recx, mb + gw * SPC + r * stride + s_lane);
+          for (int sl = 2; sl < 4; ++sl) {
+            const unsigned f = (info.z >> (8 * sl)) & 0xffu;
+            if (f == 0xffu) continue;
+            y -= face_term<P, T>(L::slot(nullptr, rg, sl),
+                                 a.out + ((size_t)d * a.E + nb_elem(a.nx, a.ny, (int)info.x, (int)f)) * N,
+                                 (int)f, i);
+          }
+        }
+        a.out[((size_t)d * a.E + info.x) * N + i] = y;
+      }
+      // rounds beyond the staged ones (levels wider than kSweepRounds * stride)
+      for (int r = kSweepRounds; gw * SPC + r * stride < nsingle; ++r) {
+        const int tl = gw * SPC + r * stride + s_lane;
+        if (lane_ok && tl < nsingle) {
+          const char* rg = L::s_at(a.rec, mb + tl);
+          const char* rgx = L::x_at(a.recx, mb + tl);
+          const uint4 info = *reinterpret_cast<const uint4*>(rg);
+          T y = a.y[(size_t)(mb + tl) * L::kYStride + i];
+          for (int sl = 0; sl < 4; ++sl) {
+            const unsigned f = (info.z >> (8 * sl)) & 0xffu;
+            if (f == 0xffu) continue;
+            y -= face_term<P, T>(L::slot(rg, rgx, sl),
+                                 a.out + ((size_t)d * a.E + nb_elem(a.nx, a.ny, (int)info.x, (int)f)) * N,
+                                 (int)f, i);
+          }
+          a.out[((size_t)d * a.E + info.x) * N + i] = y;
+        }
+      }
+    }
+    if (groups) {
+      for (int g = sg + gidx; g < se; g += ng) {
+        if (a.slot_count[g] <= group_smem_max<P, T>()) {
+          if (staged != g) group_stage_static<P, T>(a, g, sm.group);
+          group_solve_smem<P, T, MODE>(a, d, g, sm.group);
+        } else {
+          group_solve<P, T, MODE>(a, d, g);
+        }
+        staged = -1;
+      }
+    }
+    // publish this level; stage what later levels need while the barrier completes
+    cluster_arrive();
+    if (singles && k + 2 < k1) stage_level(k + 2, b);
+    if (groups && k + 1 < k1) {
+      const int g1 = a.lev_gbegin[k + 1] + gidx;
+      if (g1 < a.lev_begin[k + 2] && a.slot_count[g1] <= group_smem_max<P, T>()) {
+        group_stage_static<P, T>(a, g1, sm.group);
+        staged = g1;
+      }
+    }
+    cluster_wait();
+  }
+  // drain copies still in flight (none are issued for levels past the last one)
+  wait_level(0);
+  wait_level(1);
 }
 
 // -------------------------------------------------------------- FP64 residual (mixed)
@@ -382,15 +632,6 @@ __global__ void maxdiff_kernel(long long n, const double* __restrict__ a, const 
 // ------------------------------------------------------------------------ host side
 static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
-template <typename K>
-static int persistent_blocks(K kernel, int threads) {
-  int dev = 0, sms = 0, per = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0);
-  return std::max(1, sms * std::max(1, per));
-}
-
 struct SweepCall {
   Mesh* mesh;
   Schedule* S;
@@ -402,7 +643,8 @@ struct SweepCall {
   double tol;
   int max_passes;
   int precision;
-  int threads;
+  int cluster_size;  // CTAs per direction cluster
+  int cta_warps;     // warps per CTA
 };
 
 template <int P, typename T, int MODE>
@@ -410,8 +652,12 @@ static vef_status launch_sweep(const SweepCall& c, const double* rhs, T* out) {
   Mesh& M = *c.mesh;
   Schedule& S = *c.S;
   SweepArgs<T> a{};
-  a.nchunks = S.nchunks;
-  a.chunk_begin = S.chunk_begin;
+  a.dir_lev0 = S.dir_lev0;
+  a.lev_begin = S.lev_begin;
+  a.lev_gbegin = S.lev_gbegin;
+  a.lev_mbegin = S.lev_mbegin;
+  a.member_info = S.member_info;
+  a.member_nbpos = S.member_nbpos;
   a.slot_first = S.slot_first;
   a.slot_count = S.slot_count;
   a.code = S.member_code;
@@ -419,6 +665,7 @@ static vef_status launch_sweep(const SweepCall& c, const double* rhs, T* out) {
   a.finfo = S.faceinfo;
   a.omega = S.omega_dev;
   a.rec = (const T*)(std::is_same<T, double>::value ? S.rec64 : S.rec32);
+  a.recx = (const T*)((const char*)a.rec + S.members * (long long)Rec<P, T>::kStaged);
   a.bvol = M.bvol;
   a.src_aniso = c.src_aniso;
   a.Mm = M.Mmat;
@@ -426,12 +673,9 @@ static vef_status launch_sweep(const SweepCall& c, const double* rhs, T* out) {
   a.nds = (const T*)(std::is_same<T, double>::value ? (const void*)M.nds : (const void*)M.nds32);
   a.rhs = rhs;
   a.out = out;
-  a.flags = M.flags;
-  if (++M.epoch == 0) {
-    VEF_CUDA_TRY(cudaMemsetAsync(M.flags, 0, M.flags_cap, c.stream));
-    M.epoch = 1;
-  }
-  a.epoch = M.epoch;
+  vef_status st = ensure_buffer(&M.ybuf, &M.ybuf_cap, (size_t)S.members * Rec<P, T>::kYBytes);
+  if (st != VEF_OK) return st;
+  a.y = (T*)M.ybuf;
   a.status = M.dev_status;
   a.nx = M.nx;
   a.ny = M.ny;
@@ -441,15 +685,34 @@ static vef_status launch_sweep(const SweepCall& c, const double* rhs, T* out) {
   a.tol = (T)std::max(c.tol, 8.0 * eps);
   a.max_inner = std::max(2, 4 * c.max_passes);
   a.ft = make_facetab<T>(M.tab);
-  // reset abort word and chunk counter (status bits [0] and max-inner [2] accumulate
-  // until the next synchronising call)
-  VEF_CUDA_TRY(cudaMemsetAsync(M.dev_status + 1, 0, sizeof(unsigned int), c.stream));
-  VEF_CUDA_TRY(cudaMemsetAsync(M.dev_status + 3, 0, sizeof(unsigned int), c.stream));
-  const int threads = c.threads > 0 ? c.threads : 128;
-  const int blocks = persistent_blocks(sweep_kernel<P, T, MODE>, threads);
+  constexpr int N = (P + 1) * (P + 1);
+  constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
+  {
+    KTimer kt(&M, VEF_K_SOURCE, c.stream);
+    const long long warps = (S.members + SPC - 1) / SPC;
+    apply_kernel<P, T, MODE><<<nblk(warps * 32, 128), 128, 0, c.stream>>>(a, S.members);
+  }
+  a.cluster_size = c.cluster_size;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(S.D * c.cluster_size));
+  cfg.blockDim = dim3((unsigned)(32 * c.cta_warps));
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = c.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)c.cluster_size;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.dynamicSmemBytes = sizeof(SweepSmem<P, T>) * (size_t)c.cta_warps;
+  VEF_CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<P, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)cfg.dynamicSmemBytes));
+  if (c.cluster_size > 8)
+    VEF_CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<P, T, MODE>,
+                                      cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   KTimer kt(&M, VEF_K_SWEEP, c.stream);
-  sweep_kernel<P, T, MODE><<<blocks, threads, 0, c.stream>>>(a);
-  VEF_CUDA_TRY(cudaGetLastError());
+  VEF_CUDA_TRY(cudaLaunchKernelEx(&cfg, sweep_kernel<P, T, MODE>, a));
   return VEF_OK;
 }
 
@@ -531,15 +794,6 @@ static vef_status factor(const SweepCall& c) {
   return factor_records(c.mesh, c.S, c.sigma_t, c.precision, c.stream);
 }
 
-vef_status ensure_flags(Mesh* mesh, size_t count) {
-  if (mesh->flags_cap >= count * sizeof(uint32_t)) return VEF_OK;
-  vef_status st = ensure_buffer((void**)&mesh->flags, &mesh->flags_cap, count * sizeof(uint32_t));
-  if (st != VEF_OK) return st;
-  VEF_CUDA_TRY(cudaMemset(mesh->flags, 0, mesh->flags_cap));
-  mesh->epoch = 0;
-  return VEF_OK;
-}
-
 static vef_status launch_bvol(Mesh& M, const double* sigma_s, const double* phi_in,
                               const double* q_iso, cudaStream_t stream) {
   size_t cap = 0;
@@ -599,8 +853,11 @@ static void fill_opts(const vef_opts* o, SweepCall& c) {
   const double deftol = c.precision == VEF_FP64 ? 1e-15 : 1e-13;
   c.tol = (o && o->tol > 0.0) ? o->tol : deftol;
   c.max_passes = (o && o->max_passes > 0) ? o->max_passes : 8;
-  c.threads = (o && o->tile_override > 0) ? o->tile_override : 0;
-  if (c.threads % 32 != 0 || c.threads > 1024) c.threads = 0;
+  // tile_override = 100 * (CTAs per direction cluster) + (warps per CTA)
+  const int t = (o && o->tile_override > 0) ? o->tile_override
+                                             : (c.precision == VEF_FP64 ? kDefaultTile64 : kDefaultTile32);
+  c.cluster_size = std::min(16, std::max(1, t / 100));
+  c.cta_warps = std::min(8, std::max(1, t % 100));
 }
 
 static void schedule_info(const Schedule& S, vef_info* info) {
@@ -626,7 +883,6 @@ extern "C" vef_status vef_sweep(vef_mesh mesh, const double* sigma_t, const doub
   cudaStream_t s = (cudaStream_t)stream;
   Schedule* S = get_schedule(&M, omega, weights, D, s, &st);
   if (!S) return st;
-  if ((st = ensure_flags(&M, (size_t)D * M.E)) != VEF_OK) return st;
   SweepCall c{};
   c.mesh = &M;
   c.S = S;
@@ -662,7 +918,6 @@ extern "C" vef_status vef_source_iterate(vef_mesh mesh, const double* sigma_t, c
   cudaStream_t s = (cudaStream_t)stream;
   Schedule* S = get_schedule(&M, omega, weights, D, s, &st);
   if (!S) return st;
-  if ((st = ensure_flags(&M, (size_t)D * M.E)) != VEF_OK) return st;
   SweepCall c{};
   c.mesh = &M;
   c.S = S;
