@@ -40,6 +40,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep-only", type=int, default=0, metavar="NX",
+                    help="profiling driver: build an NX x NX mesh with the workload's recipe and run "
+                         "--steps FP64 sweeps (no timing line)")
+    ap.add_argument("--mixed-tol", type=float, default=1e-12,
+                    help="relative residual target of the mixed-precision defect correction")
     return ap.parse_args()
 
 
@@ -54,35 +59,63 @@ def flops_factor(p, inflow_faces=2.0):
             + n * ((n - 1) + (n - 1) * (2 * n - 1)) + inflow_faces * 2 * n * q * q)
 
 
+def flops_apply(p):
+    """Per (element, direction) flops of the dependency-free apply: y = A^{-1} b (2 n^2)."""
+    n = (p + 1) ** 2
+    return 2 * n * n
+
+
+def bytes_apply(p, D, word=8):
+    """Per (element, direction) apply bytes: A^{-1} read, y row written (16-byte padded),
+    the direction-independent rhs read once per element (/ D)."""
+    n = (p + 1) ** 2
+    pad = lambda b: (b + 15) // 16 * 16
+    return word * n * n + pad(word * n) + 8 * n / D
+
+
 def flops_sweep(p, inflow_faces=2.0):
-    """Per (element, direction) sweep flops: psi = A^{-1} b (2 n^2) and the upwind
-    couplings W_f u_f (2 n (p+1) per inflow face)."""
+    """Per (element, direction) sweep flops: psi = y - sum_f W_f u_f (2 n (p+1) per
+    interior inflow face)."""
     n = (p + 1) ** 2
-    return 2 * n * n + inflow_faces * 2 * n * (p + 1)
+    return inflow_faces * 2 * n * (p + 1)
 
 
-def bytes_sweep(p, D, word=8, inflow_faces=2.0):
-    """Per (element, direction) sweep DRAM bytes: the factor record's A^{-1} and used W_f,
-    psi written, upwind face traces read, plus the direction-independent rhs / D."""
+def bytes_sweep(p, word=8, inflow_faces=2.0):
+    """Per (element, direction) sweep DRAM bytes: the staged record prefix (16 bytes of
+    element info + two W slots), the padded y row, the upwind face traces read and psi
+    written."""
     n = (p + 1) ** 2
-    return word * (n * n + inflow_faces * n * (p + 1)) + 8 * n + 8 * inflow_faces * (p + 1) + 8 * n / D
+    pad = lambda b: (b + 15) // 16 * 16
+    return pad(16 + 2 * word * n * (p + 1)) + pad(word * n) + 8 * inflow_faces * (p + 1) + 8 * n
 
 
-def src_hash(*names):
+SWEEP_REGION = ("// Coupled group, global-memory form",
+                "// -------------------------------------------------------------- FP64 residual (mixed)")
+
+
+def src_hash(kernel):
+    """Hash of the source a kernel is built from (its region of sweep.cu plus device.cuh for
+    the sweep; its files for the factorisation)."""
+    csrc = os.path.join(ROOT, "paper_2301_04758_gb300", "csrc")
     h = hashlib.sha256()
-    for nm in names:
-        with open(os.path.join(ROOT, "paper_2301_04758_gb300", "csrc", nm), "rb") as f:
-            h.update(f.read())
+    if kernel == "sweep":
+        src = open(os.path.join(csrc, "sweep.cu")).read()
+        a, b = src.index(SWEEP_REGION[0]), src.index(SWEEP_REGION[1])
+        h.update(src[a:b].encode())
+        h.update(open(os.path.join(csrc, "device.cuh"), "rb").read())
+    else:
+        for nm in ("factor_impl.cuh", "device.cuh"):
+            h.update(open(os.path.join(csrc, nm), "rb").read())
     return h.hexdigest()[:12]
 
 
-def ncu_traffic(kernel, source_files):
+def ncu_traffic(kernel):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source is
     unchanged since the capture (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
-    want = src_hash(*source_files)
+    want = src_hash(kernel)
     for line in open(path):
         parts = line.split()
         if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == WORKLOAD:
@@ -163,7 +196,8 @@ def run_ours(args, rank, world, local_rank):
     def step(precision, st_=None, ss_=None, q_=None):
         phi, ps, dphi = mesh.source_iterate(st_ if st_ is not None else st, ss_ if ss_ is not None else ss,
                                             om, w, K_ITER, source=q_ if q_ is not None else q,
-                                            precision=precision, psi=psi)
+                                            precision=precision, psi=psi,
+                                            tol=args.mixed_tol if precision == "mixed" else 0.0)
         out = mesh.moments(ps, om, w, outputs=("phi", "J", "E", "Eb", "Jin"))
         return phi, out, dphi
 
@@ -260,35 +294,40 @@ def run_ours(args, rank, world, local_rank):
 
     # roofline of the dominant kernel (FP64 run), from the live per-kernel CUDA events
     fp64_meas = fma_peak("fp64") / 1e9
+    hbm_peak = 6694.8
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        pass
     kern = {k: v for k, v in prof64.items() if v[0] > 0}
     dom = max(kern, key=lambda k: kern[k][1])
-    nfac = prof64["factor"][0]
-    nsw = prof64["sweep"][0]
+    work = {"factor": (flops_factor(p), 8.0 * (3 * n * n) / D + 8.0 * (n * n + 4 * n * (p + 1))),
+            "sweep": (flops_sweep(p), bytes_sweep(p))}
     roof = {}
-    if nfac:
-        avg = prof64["factor"][1] / nfac
-        fl = flops_factor(p) * E * D
-        roof["factor"] = {"bound": "alu", "achieved": fl / (avg * 1e-3) / 1e12, "unit": "TFLOP/s",
-                          "peak": FP64_PEAK_GFLOPS / 1e3, "avg_ms": avg, "flops_per_launch": fl}
-    if nsw:
-        avg = prof64["sweep"][1] / nsw
-        fl = flops_sweep(p) * E * D
-        by = bytes_sweep(p, D) * E * D
-        roof["sweep"] = {"bound": "alu", "achieved": fl / (avg * 1e-3) / 1e12, "unit": "TFLOP/s",
-                         "peak": FP64_PEAK_GFLOPS / 1e3, "avg_ms": avg, "flops_per_launch": fl,
-                         "hbm_GBps": by / (avg * 1e-3) / 1e9, "bytes_per_launch": by}
-    for k, r in roof.items():
-        r["frac"] = r["achieved"] / r["peak"]
-        r["peak_measured_fma"] = fp64_meas / 1e3
-    main = roof.get(dom) or roof.get("factor")
-    srcmap = {"factor": ["factor_impl.cuh", "factor_p2.cu"], "sweep": ["sweep.cu", "device.cuh"]}
+    for k, (fl_u, by_u) in work.items():
+        cnt, tms = prof64.get(k, (0, 0.0))
+        if not cnt:
+            continue
+        avg = tms / cnt
+        fl, by = fl_u * E * D, by_u * E * D
+        t_alu, t_hbm = fl / (FP64_PEAK_GFLOPS * 1e9), by / (hbm_peak * 1e9)
+        if t_alu >= t_hbm:
+            r = {"bound": "alu", "achieved": fl / (avg * 1e-3) / 1e12, "peak": FP64_PEAK_GFLOPS / 1e3,
+                 "unit": "TFLOP/s"}
+        else:
+            r = {"bound": "hbm", "achieved": by / (avg * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s"}
+        r.update(frac=r["achieved"] / r["peak"], avg_ms=avg, flops_per_launch=fl, bytes_per_launch=by,
+                 tflops=fl / (avg * 1e-3) / 1e12, gbps=by / (avg * 1e-3) / 1e9)
+        roof[k] = r
+    main = roof.get(dom) or roof.get("sweep")
     roofline = None
     if main:
+        kname = dom if dom in roof else "sweep"
         roofline = {"bound": main["bound"], "achieved": round(main["achieved"], 4),
-                    "peak": round(main["peak"], 4), "unit": main["unit"],
-                    "frac": round(main["frac"], 4),
-                    "traffic": ncu_traffic(dom, srcmap.get(dom, [])),
-                    "kernel": dom, "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
+                    "peak": round(main["peak"], 4), "unit": main["unit"], "frac": round(main["frac"], 4),
+                    "traffic": ncu_traffic(kname), "kernel": kname,
+                    "peak_source": ("MEASURED_PEAKS.json hbm_gbs (measured)" if main["bound"] == "hbm" else
+                                    "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2070 MHz"),
                     "peak_measured_fma_tflops": round(fp64_meas / 1e3, 4)}
     launches = sum(v[0] for v in prof64.values())
 
@@ -304,6 +343,7 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "inputs larger than L2 (factor records ~4 GB)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "mixed": {"value": mixed_value, "ms_per_step": ms32 / steps, "dtype": "f32 solve + f64 defect correction",
+                  "defect_correction_rel_residual_target": args.mixed_tol,
                   "rel_err_vs_fp64": mixed_err, "clocks": clk2,
                   "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof32.items() if v[0]}},
         "e2e": {"value": e2e_value, "unit": "angular-DOF updates/s", "h2d_bytes_per_step": h2d,
@@ -370,8 +410,33 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+def sweep_only(args):
+    """Small driver for ncu captures: NX x NX sine mesh (alpha 0.05, Q3 map), Q2, S8,
+    seed-2 media, q = 1; runs --steps FP64 sweeps through the public API."""
+    import torch
+
+    from paper_2301_04758_gb300 import build as vbuild
+    vbuild.build()
+    from paper_2301_04758_gb300.api import Mesh
+    from vef_inputs import level_symmetric, seeded_media
+    N = args.sweep_only
+    om, w = level_symmetric(8)
+    st, ss = seeded_media(N * N, 2)
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda").contiguous()
+    mesh = Mesh(N, N, 3, 2, 0.05)
+    q = torch.ones(N * N, 9, dtype=torch.float64, device="cuda")
+    psi = torch.empty(len(w), N * N, 9, dtype=torch.float64, device="cuda")
+    for _ in range(args.steps):
+        mesh.sweep(T(st), T(ss), om, w, source=q, psi=psi)
+    torch.cuda.synchronize()
+    mesh.sync()
+
+
 def main():
     args = parse()
+    if args.sweep_only:
+        sweep_only(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

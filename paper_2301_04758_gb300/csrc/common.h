@@ -82,7 +82,7 @@ struct Schedule {
   // factor records (lazily allocated): FP64 and FP32 copies
   void* rec64 = nullptr;
   void* rec32 = nullptr;
-  size_t rec_elems = 0;        // per member
+  void* a64 = nullptr;         // FP64 element matrices + inflow couplings (mixed residual)
   ~Schedule();
 };
 

@@ -124,6 +124,58 @@ factor_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t*
   *reinterpret_cast<uint4*>(out) = make_uint4((unsigned)e, (unsigned)bits, faces, 0u);
 }
 
+// FP64 element matrix and inflow couplings of every (element, direction), for the FP64
+// residual of the mixed-precision defect correction: per task [A (n x n, row-major)]
+// [Cin of W slots 0..3 ((p+1) x (p+1), row a = own face node, column t = neighbour's)].
+template <int P>
+__global__ void __launch_bounds__(128)
+assemble64_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t* __restrict__ finfo,
+                  const double* __restrict__ omega, const double* __restrict__ sigma_t,
+                  const double* __restrict__ Mm, const double* __restrict__ Gxm,
+                  const double* __restrict__ Gym, const double* __restrict__ nds, FaceTab<double> ft,
+                  int nx, int ny, long long E, double* __restrict__ out) {
+  constexpr int Q = P + 1, N = Q * Q, NQ = P + 2, B = N * N + 4 * Q * Q;
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (m >= nmem) return;
+  const uint32_t c = code[m];
+  const int d = (int)(c >> 22), e = (int)(c & 0x3fffffu);
+  const double mu = omega[2 * d], eta = omega[2 * d + 1], st = sigma_t[e];
+  const uint16_t bits = finfo[(size_t)d * E + e];
+  double* A = out + m * (long long)B;
+  const double* Me = Mm + (size_t)e * N * N;
+  const double* Xe = Gxm + (size_t)e * N * N;
+  const double* Ye = Gym + (size_t)e * N * N;
+  for (int ij = 0; ij < N * N; ++ij) A[ij] = st * Me[ij] - mu * Xe[ij] - eta * Ye[ij];
+  int slot = 0;
+  for (int f = 0; f < 4; ++f) {
+    double cp[NQ], cm[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      const double* v = nds + (((size_t)e * 4 + f) * NQ + k) * 2;
+      const double sv = ft.w[k] * (mu * v[0] + eta * v[1]);
+      cp[k] = sv > 0.0 ? sv : 0.0;
+      cm[k] = sv < 0.0 ? sv : 0.0;
+    }
+    const bool inflow_nb = (bits & (1u << f)) && nb_elem(nx, ny, e, f) >= 0;
+    double* C = A + N * N + slot * Q * Q;
+#pragma unroll
+    for (int a = 0; a < Q; ++a)
+#pragma unroll
+      for (int b = 0; b < Q; ++b) {
+        double vo = 0, vi = 0;
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+          const double ll = ft.l[a][k] * ft.l[b][k];
+          vo += cp[k] * ll;
+          vi += cm[k] * ll;
+        }
+        A[face_dof<P>(f, a) * N + face_dof<P>(f, b)] += vo;
+        if (inflow_nb) C[a * Q + b] = vi;
+      }
+    if (inflow_nb) ++slot;
+  }
+}
+
 template <int P, typename T>
 static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, cudaStream_t stream) {
   void** recp = std::is_same<T, double>::value ? &S.rec64 : &S.rec32;
@@ -142,6 +194,18 @@ static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, cud
     vef_status st = mesh_float_copies(&M, stream);
     if (st != VEF_OK) return st;
     Mm = (const T*)M.Mmat32; Gx = (const T*)M.Gx32; Gy = (const T*)M.Gy32; nds = (const T*)M.nds32;
+  }
+  if (!std::is_same<T, double>::value) {
+    constexpr int Q = P + 1, N = Q * Q;
+    if (!S.a64) {
+      size_t cap = 0;
+      vef_status st = ensure_buffer(&S.a64, &cap, (size_t)S.members * (N * N + 4 * Q * Q) * sizeof(double));
+      if (st != VEF_OK) return st;
+    }
+    KTimer kt(&M, VEF_K_FACTOR, stream);
+    assemble64_kernel<P><<<nblk(S.members, 128), 128, 0, stream>>>(
+        S.members, S.member_code, S.faceinfo, S.omega_dev, sigma_t, M.Mmat, M.Gx, M.Gy, M.nds,
+        make_facetab<double>(M.tab), M.nx, M.ny, M.E, (double*)S.a64);
   }
   KTimer kt(&M, VEF_K_FACTOR, stream);
   factor_kernel<P, T><<<nblk(S.members, 128), 128, 0, stream>>>(

@@ -219,6 +219,7 @@ Schedule::~Schedule() {
   cudaFree(weights_dev);
   cudaFree(rec64);
   cudaFree(rec32);
+  cudaFree(a64);
 }
 
 }  // namespace vef

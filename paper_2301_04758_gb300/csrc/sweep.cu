@@ -520,39 +520,44 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
 }
 
 // -------------------------------------------------------------- FP64 residual (mixed)
-// r = b - L psi for all (d, e), one lane per dof row; accumulates ||r||^2, ||b||^2.
+// r = b - L psi for every (element, direction) in schedule order, one lane per dof row,
+// from the stored FP64 element matrix and inflow couplings; accumulates ||r||^2, ||b||^2.
 template <int P>
 __global__ void __launch_bounds__(128)
-residual_kernel(int D, long long E, int nx, int ny, long long nbf, const double* __restrict__ omega,
-                const double* __restrict__ sigma_t, const double* __restrict__ Mm,
-                const double* __restrict__ Gxm, const double* __restrict__ Gym,
+residual_kernel(long long nmem, long long E, int nx, int ny, long long nbf,
+                const uint32_t* __restrict__ code, const uint16_t* __restrict__ finfo,
+                const double* __restrict__ omega, const double* __restrict__ Mm,
                 const double* __restrict__ nds, const double* __restrict__ bvol,
                 const double* __restrict__ src_aniso, const double* __restrict__ inflow,
+                const double* __restrict__ a64, const float* __restrict__ rec32,
                 const double* __restrict__ psi, FaceTab<double> ft, double* __restrict__ r,
                 double* __restrict__ norms) {
-  constexpr int Q = P + 1, N = Q * Q, NQ = P + 2;
+  constexpr int Q = P + 1, N = Q * Q, NQ = P + 2, B = N * N + 4 * Q * Q;
   constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
   const int lane = threadIdx.x & 31;
-  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const long long task = warp * SPC + lane / N;
   const int i = lane % N;
   double rr = 0.0, bb = 0.0;
-  if (lane < SPC * N && task < (long long)D * E) {
-    const int d = (int)(task / E);
-    const int e = (int)(task % E);
-    const double mu = omega[2 * d], eta = omega[2 * d + 1], st = sigma_t[e];
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+       warp * SPC < nmem; warp += nwarps) {
+  const long long m = warp * SPC + lane / N;
+  if (lane < SPC * N && m < nmem) {
+    const uint32_t cd = code[m];
+    const int d = (int)(cd >> 22), e = (int)(cd & 0x3fffffu);
+    const uint16_t bits = finfo[(size_t)d * E + e];
+    const double mu = omega[2 * d], eta = omega[2 * d + 1];
     const double* pe = psi + ((size_t)d * E + e) * N;
+    const double* blk = a64 + m * (long long)B;
+    const unsigned faces = reinterpret_cast<const uint4*>(Rec<P, float>::s_at(rec32, m))->z;
     double b = bvol[(size_t)e * N + i];
-    const double* Mr = Mm + ((size_t)e * N + i) * N;
-    const double* Xr = Gxm + ((size_t)e * N + i) * N;
-    const double* Yr = Gym + ((size_t)e * N + i) * N;
     if (src_aniso) {
+      const double* Mr = Mm + ((size_t)e * N + i) * N;
       const double* qd = src_aniso + ((size_t)d * E + e) * N;
       for (int j = 0; j < N; ++j) b += Mr[j] * qd[j];
     }
     double Apsi = 0.0;
 #pragma unroll
-    for (int j = 0; j < N; ++j) Apsi += (st * Mr[j] - mu * Xr[j] - eta * Yr[j]) * pe[j];
+    for (int j = 0; j < N; ++j) Apsi += blk[i * N + j] * pe[j];
     const int ia = i % Q, ib = i / Q;
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
@@ -561,42 +566,50 @@ residual_kernel(int D, long long E, int nx, int ny, long long nbf, const double*
       if (f == 1 && ia == P) pos = ib;
       if (f == 2 && ib == P) pos = ia;
       if (f == 3 && ia == 0) pos = ib;
-      if (pos < 0) continue;
+      if (pos < 0 || !(bits & (1u << f))) continue;
       const int nb = nb_elem(nx, ny, e, f);
-      const double* pn = nb >= 0 ? psi + ((size_t)d * E + nb) * N : nullptr;
-      const double* pb = (nb < 0 && inflow) ? inflow + ((size_t)d * nbf + bface(nx, ny, e, f)) * NQ : nullptr;
+      if (nb >= 0) {
+        const int sl = rec_slot_of(faces, f);
+        const double* C = blk + N * N + sl * Q * Q + pos * Q;
+        const double* pn = psi + ((size_t)d * E + nb) * N;
 #pragma unroll
-      for (int k = 0; k < NQ; ++k) {
-        const double* v = nds + (((size_t)e * 4 + f) * NQ + k) * 2;
-        const double s = ft.w[k] * (mu * v[0] + eta * v[1]);
-        if (s >= 0.0) {
-          double tr = 0.0;
+        for (int t = 0; t < Q; ++t) Apsi += C[t] * pn[face_dof<P>((f + 2) & 3, t)];
+      } else if (inflow) {
+        const double* pb = inflow + ((size_t)d * nbf + bface(nx, ny, e, f)) * NQ;
 #pragma unroll
-          for (int t = 0; t < Q; ++t) tr += ft.l[t][k] * pe[face_dof<P>(f, t)];
-          Apsi += s * tr * ft.l[pos][k];
-        } else if (pn) {
-          double tr = 0.0;
-#pragma unroll
-          for (int t = 0; t < Q; ++t) tr += ft.l[t][k] * pn[face_dof<P>((f + 2) & 3, t)];
-          Apsi += s * tr * ft.l[pos][k];  // upwind coupling belongs to L psi
-        } else if (pb) {
-          b -= s * pb[k] * ft.l[pos][k];
+        for (int k = 0; k < NQ; ++k) {
+          const double* v = nds + (((size_t)e * 4 + f) * NQ + k) * 2;
+          const double sv = ft.w[k] * (mu * v[0] + eta * v[1]);
+          if (sv < 0.0) b -= sv * pb[k] * ft.l[pos][k];
         }
       }
     }
     const double ri = b - Apsi;
     r[((size_t)d * E + e) * N + i] = ri;
-    rr = ri * ri;
-    bb = b * b;
+    rr += ri * ri;
+    bb += b * b;
   }
+  }
+  // block reduction, then one atomic pair per block
+  __shared__ double red[2][32];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     rr += __shfl_xor_sync(0xffffffffu, rr, off);
     bb += __shfl_xor_sync(0xffffffffu, bb, off);
   }
-  if (lane == 0 && (rr != 0.0 || bb != 0.0)) {
-    atomicAdd(norms, rr);
-    atomicAdd(norms + 1, bb);
+  if (lane == 0) {
+    red[0][threadIdx.x >> 5] = rr;
+    red[1][threadIdx.x >> 5] = bb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sr = 0.0, sb = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      sr += red[0][w];
+      sb += red[1][w];
+    }
+    atomicAdd(norms, sr);
+    atomicAdd(norms + 1, sb);
   }
 }
 
@@ -722,13 +735,17 @@ static vef_status launch_residual(const SweepCall& c, const double* psi, double*
   Schedule& S = *c.S;
   constexpr int N = (P + 1) * (P + 1);
   constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
-  const long long tasks = (long long)S.D * M.E;
-  const long long warps = (tasks + SPC - 1) / SPC;
+  const long long warps = (S.members + SPC - 1) / SPC;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned grid = (unsigned)std::min<long long>(nblk(warps * 32, 128), (long long)sms * 16);
   VEF_CUDA_TRY(cudaMemsetAsync(norms, 0, 2 * sizeof(double), c.stream));
   KTimer kt(&M, VEF_K_RESIDUAL, c.stream);
-  residual_kernel<P><<<nblk(warps * 32, 128), 128, 0, c.stream>>>(
-      S.D, M.E, M.nx, M.ny, M.nbf, S.omega_dev, c.sigma_t, M.Mmat, M.Gx, M.Gy, M.nds, M.bvol,
-      c.src_aniso, c.inflow, psi, make_facetab<double>(M.tab), r, norms);
+  residual_kernel<P><<<grid, 128, 0, c.stream>>>(
+      S.members, M.E, M.nx, M.ny, M.nbf, S.member_code, S.faceinfo, S.omega_dev, M.Mmat, M.nds,
+      M.bvol, c.src_aniso, c.inflow, (const double*)S.a64, (const float*)S.rec32, psi,
+      make_facetab<double>(M.tab), r, norms);
   VEF_CUDA_TRY(cudaGetLastError());
   return VEF_OK;
 }
