@@ -180,6 +180,29 @@ vef_status vef_adjoint_sweep(vef_mesh mesh, const double* sigma_t, const double*
                              double* dR_dsigma_t, double* dR_dsigma_s, const vef_opts* opts,
                              vef_info* info, void* stream);
 
+/* Batches of independent problems (uneven mesh sizes, DG orders and direction sets).
+ * Each problem has its own mesh handle (distinct handles); the batch fixes each problem's direction set
+ * (omega[k] [host] [D[k]][2], weights[k] [host] [D[k]]) and builds its schedule.  One
+ * vef_batch_sweep call runs, per problem, the dependency-free kernels (right-hand side,
+ * local factorisation, apply), then one cluster launch per DG order sweeps every
+ * (problem, direction) of that order.  FP64 only.  No device synchronisation unless info
+ * is given, so a call can be captured in a CUDA graph after a first (allocating) call. */
+typedef struct vef_batch_s* vef_batch;
+vef_status vef_batch_create(const vef_mesh* meshes, int nprob, const double* const* omega,
+                            const double* const* weights, const int* D, vef_batch* out);
+vef_status vef_batch_destroy(vef_batch batch);
+/* Per-problem arrays of [device] pointers, layouts as in vef_sweep (isotropic source,
+ * entries of phi_in / source / inflow may be NULL, and so may these arrays). */
+vef_status vef_batch_sweep(vef_batch batch, const double* const* sigma_t, const double* const* sigma_s,
+                           const double* const* phi_in, const double* const* source,
+                           const double* const* inflow, double* const* psi, const vef_opts* opts,
+                           vef_info* info, void* stream);
+/* Autotuner: times the batched sweep of each DG order for a set of cluster shapes
+ * (CTAs per direction x warps per CTA) on the data of the last vef_batch_sweep call and
+ * keeps the fastest for later calls; tiles_out (optional, [4]) receives the choice per
+ * order p = 1..4 (0 = no problem of that order).  Synchronises `stream`. */
+vef_status vef_batch_tune(vef_batch batch, void* stream, int* tiles_out);
+
 /* Kernel classes for the per-kernel timing counters. */
 enum {
   VEF_K_GEOMETRY = 0, /* mesh geometric factors */

@@ -26,6 +26,7 @@ VEF_MIXED = 1
 EXPORTS = ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sync", "vef_sweep",
            "vef_moments", "vef_source_iterate", "vef_adjoint_sweep", "vef_profile",
            "vef_profile_read", "vef_measure_fma_peak", "vef_eddington_noalloc",
+           "vef_batch_create", "vef_batch_destroy", "vef_batch_sweep", "vef_batch_tune",
            "vef_status_string", "vef_last_error")
 
 KERNEL_CLASSES = ("geometry", "factor", "sweep", "residual", "source", "moments", "adjoint")
@@ -84,10 +85,17 @@ def _declare(lib):
     lib.vef_profile_read.argtypes = [P, ctypes.POINTER(VefKernelStat)]
     lib.vef_measure_fma_peak.argtypes = [I, ctypes.POINTER(ctypes.c_double)]
     lib.vef_eddington_noalloc.argtypes = [P, P, P, I, ctypes.c_longlong, I, P, P]
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    lib.vef_batch_create.argtypes = [PP, I, PP, PP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(P)]
+    lib.vef_batch_destroy.argtypes = [P]
+    lib.vef_batch_sweep.argtypes = [P, PP, PP, PP, PP, PP, PP, ctypes.POINTER(VefOpts),
+                                    ctypes.POINTER(VefInfo), P]
+    lib.vef_batch_tune.argtypes = [P, P, ctypes.POINTER(ctypes.c_int)]
     for name in ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sync",
                  "vef_sweep", "vef_moments", "vef_source_iterate", "vef_adjoint_sweep",
                  "vef_profile", "vef_profile_read", "vef_measure_fma_peak",
-                 "vef_eddington_noalloc"):
+                 "vef_eddington_noalloc", "vef_batch_create", "vef_batch_destroy",
+                 "vef_batch_sweep", "vef_batch_tune"):
         getattr(lib, name).restype = I
     lib.vef_status_string.argtypes = [I]
     lib.vef_status_string.restype = ctypes.c_char_p

@@ -170,3 +170,60 @@ class Mesh:
         _lib.check(st, "vef_adjoint_sweep")
         res = (dst, dss, lam)
         return res + (inf.as_dict(),) if info else res
+
+
+def _ptr_array(items):
+    arr = (ctypes.c_void_p * len(items))()
+    for k, t in enumerate(items):
+        arr[k] = None if t is None else _ptr(t).value
+    return arr
+
+
+class Batch:
+    """Independent problems swept together (one cluster launch per DG order)."""
+
+    def __init__(self, meshes, omegas, weights):
+        self.lib = _lib.load()
+        self.meshes = list(meshes)
+        self._om = [np.ascontiguousarray(np.asarray(o, np.float64)) for o in omegas]
+        self._w = [np.ascontiguousarray(np.asarray(w, np.float64)) for w in weights]
+        n = len(self.meshes)
+        mh = (ctypes.c_void_p * n)(*[m.handle.value for m in self.meshes])
+        op = (ctypes.c_void_p * n)(*[o.ctypes.data for o in self._om])
+        wp = (ctypes.c_void_p * n)(*[w.ctypes.data for w in self._w])
+        D = (ctypes.c_int * n)(*[len(w) for w in self._w])
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.vef_batch_create(mh, n, op, wp, D, ctypes.byref(h)), "vef_batch_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.vef_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, sigma_t, sigma_s, phi_in=None, source=None, inflow=None, psi=None, tile=0,
+              info=False, stream=None):
+        """Lists of per-problem tensors; returns the list of psi [D_k][E_k][n_k]."""
+        n = len(self.meshes)
+        if psi is None:
+            psi = [m._empty(len(w), m.E, m.n) for m, w in zip(self.meshes, self._w)]
+        none = lambda lst: None if lst is None else _ptr_array(lst)
+        o = _opts("fp64", 0.0, 0, tile)
+        inf = _lib.VefInfo() if info else None
+        st = self.lib.vef_batch_sweep(self.handle, _ptr_array(sigma_t), _ptr_array(sigma_s), none(phi_in),
+                                      none(source), none(inflow), _ptr_array(psi), ctypes.byref(o),
+                                      ctypes.byref(inf) if info else None, _stream(stream))
+        _lib.check(st, "vef_batch_sweep")
+        return (psi, inf.as_dict()) if info else psi
+
+    def tune(self, stream=None):
+        """Autotune the cluster shape per DG order; returns {p: tile}."""
+        tiles = (ctypes.c_int * 4)()
+        _lib.check(self.lib.vef_batch_tune(self.handle, _stream(stream), tiles), "vef_batch_tune")
+        return {p + 1: tiles[p] for p in range(4) if tiles[p]}

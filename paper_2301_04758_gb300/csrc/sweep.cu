@@ -345,7 +345,7 @@ constexpr uint32_t kStageWaitIters = 1u << 26;
 // coupled groups, so a group's inner iteration never delays a warp's singles and its
 // static data is staged while the previous level finishes.
 template <int P, typename T, int MODE>
-__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
+__device__ __forceinline__ void sweep_direction(const SweepArgs<T>& a, int d) {
   constexpr int Q = P + 1, N = Q * Q;
   using L = Rec<P, T>;
   constexpr int SPC = SweepSmem<P, T>::SPC;
@@ -353,7 +353,6 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
   const int lane = threadIdx.x & 31;
   SweepSmem<P, T>& sm = reinterpret_cast<SweepSmem<P, T>*>(sweep_smem)[threadIdx.x >> 5];
   const int cs = a.cluster_size;
-  const int d = blockIdx.x / cs;
   const int nw = cs * (blockDim.x >> 5);
   const int gw = (blockIdx.x % cs) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int ng = nw >= 16 ? nw / 16 : 1;
@@ -519,6 +518,21 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
   wait_level(1);
 }
 
+// one cluster per direction of one problem
+template <int P, typename T, int MODE>
+__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
+  sweep_direction<P, T, MODE>(a, blockIdx.x / a.cluster_size);
+}
+
+// batch of independent problems of one DG order: cluster c runs direction cmap[c].y of
+// problem cmap[c].x, whose arguments sit in tab
+template <int P, typename T, int MODE>
+__global__ void __launch_bounds__(256)
+sweep_batch_kernel(const SweepArgs<T>* __restrict__ tab, const int2* __restrict__ cmap, int cluster_size) {
+  const int2 pd = cmap[blockIdx.x / cluster_size];
+  sweep_direction<P, T, MODE>(tab[pd.x], pd.y);
+}
+
 // -------------------------------------------------------------- FP64 residual (mixed)
 // r = b - L psi for every (element, direction) in schedule order, one lane per dof row,
 // from the stored FP64 element matrix and inflow couplings; accumulates ||r||^2, ||b||^2.
@@ -660,11 +674,12 @@ struct SweepCall {
   int cta_warps;     // warps per CTA
 };
 
-template <int P, typename T, int MODE>
-static vef_status launch_sweep(const SweepCall& c, const double* rhs, T* out) {
+// Host-side arguments of one problem's sweep (also the batch table entries).
+template <int P, typename T>
+static vef_status make_sweep_args(const SweepCall& c, const double* rhs, T* out, SweepArgs<T>& a) {
   Mesh& M = *c.mesh;
   Schedule& S = *c.S;
-  SweepArgs<T> a{};
+  a = SweepArgs<T>{};
   a.dir_lev0 = S.dir_lev0;
   a.lev_begin = S.lev_begin;
   a.lev_gbegin = S.lev_gbegin;
@@ -698,33 +713,54 @@ static vef_status launch_sweep(const SweepCall& c, const double* rhs, T* out) {
   a.tol = (T)std::max(c.tol, 8.0 * eps);
   a.max_inner = std::max(2, 4 * c.max_passes);
   a.ft = make_facetab<T>(M.tab);
+  a.cluster_size = c.cluster_size;
+  return VEF_OK;
+}
+
+template <int P, typename T, int MODE>
+static vef_status launch_apply(const SweepCall& c, const SweepArgs<T>& a) {
   constexpr int N = (P + 1) * (P + 1);
   constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
-  {
-    KTimer kt(&M, VEF_K_SOURCE, c.stream);
-    const long long warps = (S.members + SPC - 1) / SPC;
-    apply_kernel<P, T, MODE><<<nblk(warps * 32, 128), 128, 0, c.stream>>>(a, S.members);
-  }
-  a.cluster_size = c.cluster_size;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(S.D * c.cluster_size));
-  cfg.blockDim = dim3((unsigned)(32 * c.cta_warps));
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = c.stream;
-  cudaLaunchAttribute attr[1];
+  KTimer kt(c.mesh, VEF_K_SOURCE, c.stream);
+  const long long warps = (c.S->members + SPC - 1) / SPC;
+  apply_kernel<P, T, MODE><<<nblk(warps * 32, 128), 128, 0, c.stream>>>(a, c.S->members);
+  VEF_CUDA_TRY(cudaGetLastError());
+  return VEF_OK;
+}
+
+// cluster launch configuration of the sweep kernels (clusters x cs CTAs of warps x 32)
+template <int P, typename T, typename K>
+static vef_status cluster_config(K kernel, long long clusters, int cs, int warps, cudaStream_t stream,
+                                 cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr) {
+  cfg = cudaLaunchConfig_t{};
+  cfg.gridDim = dim3((unsigned)(clusters * cs));
+  cfg.blockDim = dim3((unsigned)(32 * warps));
+  cfg.stream = stream;
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)c.cluster_size;
+  attr[0].val.clusterDim.x = (unsigned)cs;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cfg.dynamicSmemBytes = sizeof(SweepSmem<P, T>) * (size_t)c.cta_warps;
-  VEF_CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<P, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cfg.dynamicSmemBytes = sizeof(SweepSmem<P, T>) * (size_t)warps;
+  VEF_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)cfg.dynamicSmemBytes));
-  if (c.cluster_size > 8)
-    VEF_CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<P, T, MODE>,
-                                      cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  KTimer kt(&M, VEF_K_SWEEP, c.stream);
+  if (cs > 8) VEF_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  return VEF_OK;
+}
+
+template <int P, typename T, int MODE>
+static vef_status launch_sweep(const SweepCall& c, const double* rhs, T* out) {
+  SweepArgs<T> a;
+  vef_status st = make_sweep_args<P, T>(c, rhs, out, a);
+  if (st != VEF_OK) return st;
+  if ((st = launch_apply<P, T, MODE>(c, a)) != VEF_OK) return st;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  if ((st = cluster_config<P, T>(sweep_kernel<P, T, MODE>, c.S->D, c.cluster_size, c.cta_warps, c.stream,
+                                 cfg, attr)) != VEF_OK)
+    return st;
+  KTimer kt(c.mesh, VEF_K_SWEEP, c.stream);
   VEF_CUDA_TRY(cudaLaunchKernelEx(&cfg, sweep_kernel<P, T, MODE>, a));
   return VEF_OK;
 }
@@ -999,3 +1035,240 @@ vef_status factor_fp64(Mesh* mesh, Schedule* S, const double* sigma_t, cudaStrea
   return factor(c);
 }
 }  // namespace vef
+
+// ------------------------------------------------------------------------- batches
+// Many independent problems: per problem the dependency-free kernels (right-hand side,
+// factorisation, apply) run as usual; the sweep of all problems of one DG order is one
+// cluster launch with a cluster per (problem, direction).
+namespace vef {
+
+struct BatchClass {
+  std::vector<int> probs;          // problem indices of this DG order
+  int2* cmap = nullptr;            // [clusters] (position in probs, direction)
+  long long clusters = 0;
+  SweepArgs<double>* tab_dev = nullptr;
+  SweepArgs<double>* tab_host = nullptr;   // pinned
+  int tile = 0;                    // tuned cluster shape (0 = library default)
+};
+
+}  // namespace vef
+
+struct vef_batch_s {
+  int device = 0;
+  std::vector<vef::Mesh*> meshes;
+  std::vector<vef::Schedule*> scheds;
+  vef::BatchClass cls[vef::kMaxP + 1];
+  bool swept = false;
+  ~vef_batch_s() {
+    for (auto& c : cls) {
+      cudaFree(c.cmap);
+      cudaFree(c.tab_dev);
+      cudaFreeHost(c.tab_host);
+    }
+  }
+};
+
+namespace vef {
+
+template <int P>
+static vef_status batch_launch_class(vef_batch_s& B, BatchClass& C, int tile, cudaStream_t s) {
+  const int cs = std::min(16, std::max(1, tile / 100)), warps = std::min(8, std::max(1, tile % 100));
+  for (size_t j = 0; j < C.probs.size(); ++j) C.tab_host[j].cluster_size = cs;
+  VEF_CUDA_TRY(cudaMemcpyAsync(C.tab_dev, C.tab_host, C.probs.size() * sizeof(SweepArgs<double>),
+                               cudaMemcpyHostToDevice, s));
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  vef_status st = cluster_config<P, double>(sweep_batch_kernel<P, double, 0>, C.clusters, cs, warps, s, cfg, attr);
+  if (st != VEF_OK) return st;
+  KTimer kt(B.meshes[C.probs[0]], VEF_K_SWEEP, s);
+  VEF_CUDA_TRY(cudaLaunchKernelEx(&cfg, sweep_batch_kernel<P, double, 0>, (const SweepArgs<double>*)C.tab_dev,
+                                  (const int2*)C.cmap, cs));
+  return VEF_OK;
+}
+
+static vef_status batch_launch(vef_batch_s& B, int p, int tile, cudaStream_t s) {
+  BatchClass& C = B.cls[p];
+  switch (p) {
+    case 1: return batch_launch_class<1>(B, C, tile, s);
+    case 2: return batch_launch_class<2>(B, C, tile, s);
+    case 3: return batch_launch_class<3>(B, C, tile, s);
+    default: return batch_launch_class<4>(B, C, tile, s);
+  }
+}
+
+template <int P>
+static vef_status batch_prepare(const SweepCall& c, double* psi, SweepArgs<double>& a) {
+  vef_status st = make_sweep_args<P, double>(c, nullptr, psi, a);
+  if (st != VEF_OK) return st;
+  return launch_apply<P, double, 0>(c, a);
+}
+
+}  // namespace vef
+
+extern "C" vef_status vef_batch_create(const vef_mesh* meshes, int nprob, const double* const* omega,
+                                       const double* const* weights, const int* D, vef_batch* out) {
+  if (!meshes || !omega || !weights || !D || !out || nprob < 1) {
+    set_last_error("meshes, omega, weights, D, out are required and nprob >= 1");
+    return VEF_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  int dev = 0;
+  VEF_CUDA_TRY(cudaGetDevice(&dev));
+  std::unique_ptr<vef_batch_s> B(new vef_batch_s());
+  B->device = dev;
+  for (int k = 0; k < nprob; ++k) {
+    vef_status st = check_common(meshes[k], omega[k], weights[k], D[k], nullptr);
+    if (st != VEF_OK) return st;
+    for (int j = 0; j < k; ++j)
+      if (meshes[j] == meshes[k]) {
+        set_last_error("each problem of a batch needs its own mesh handle");
+        return VEF_ERR_INVALID_ARG;
+      }
+    Mesh* M = &meshes[k]->impl;
+    Schedule* S = get_schedule(M, omega[k], weights[k], D[k], 0, &st);
+    if (!S) return st;
+    B->meshes.push_back(M);
+    B->scheds.push_back(S);
+    B->cls[M->p].probs.push_back(k);
+  }
+  for (int p = 1; p <= kMaxP; ++p) {
+    BatchClass& C = B->cls[p];
+    if (C.probs.empty()) continue;
+    std::vector<int2> cmap;
+    for (size_t j = 0; j < C.probs.size(); ++j)
+      for (int d = 0; d < B->scheds[C.probs[j]]->D; ++d) cmap.push_back(make_int2((int)j, d));
+    C.clusters = (long long)cmap.size();
+    VEF_CUDA_TRY(cudaMalloc(&C.cmap, cmap.size() * sizeof(int2)));
+    VEF_CUDA_TRY(cudaMemcpy(C.cmap, cmap.data(), cmap.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    VEF_CUDA_TRY(cudaMalloc(&C.tab_dev, C.probs.size() * sizeof(SweepArgs<double>)));
+    VEF_CUDA_TRY(cudaMallocHost(&C.tab_host, C.probs.size() * sizeof(SweepArgs<double>)));
+  }
+  *out = B.release();
+  return VEF_OK;
+}
+
+extern "C" vef_status vef_batch_destroy(vef_batch batch) {
+  if (!batch) return VEF_OK;
+  cudaDeviceSynchronize();
+  delete batch;
+  return VEF_OK;
+}
+
+extern "C" vef_status vef_batch_sweep(vef_batch batch, const double* const* sigma_t,
+                                      const double* const* sigma_s, const double* const* phi_in,
+                                      const double* const* source, const double* const* inflow,
+                                      double* const* psi, const vef_opts* opts, vef_info* info,
+                                      void* stream) {
+  if (!batch || !sigma_t || !sigma_s || !psi) {
+    set_last_error("batch, sigma_t, sigma_s and psi are required");
+    return VEF_ERR_INVALID_ARG;
+  }
+  if (opts && opts->precision != VEF_FP64) {
+    set_last_error("batched sweeps run in FP64");
+    return VEF_ERR_NOT_IMPLEMENTED;
+  }
+  int dev = 0;
+  VEF_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != batch->device) { set_last_error("batch belongs to another device"); return VEF_ERR_INVALID_ARG; }
+  cudaStream_t s = (cudaStream_t)stream;
+  vef_batch_s& B = *batch;
+  const int n = (int)B.meshes.size();
+  for (int k = 0; k < n; ++k)
+    if (!sigma_t[k] || !sigma_s[k] || !psi[k]) {
+      set_last_error("sigma_t, sigma_s and psi entries are required for every problem");
+      return VEF_ERR_INVALID_ARG;
+    }
+  for (int p = 1; p <= kMaxP; ++p) {
+    BatchClass& C = B.cls[p];
+    for (size_t j = 0; j < C.probs.size(); ++j) {
+      const int k = C.probs[j];
+      SweepCall c{};
+      c.mesh = B.meshes[k];
+      c.S = B.scheds[k];
+      c.sigma_t = sigma_t[k];
+      c.sigma_s = sigma_s[k];
+      c.src_aniso = nullptr;
+      c.inflow = inflow ? inflow[k] : nullptr;
+      c.stream = s;
+      fill_opts(opts, c);
+      vef_status st = launch_bvol(*c.mesh, sigma_s[k], phi_in ? phi_in[k] : nullptr,
+                                  source ? source[k] : nullptr, s);
+      if (st != VEF_OK) return st;
+      if ((st = factor(c)) != VEF_OK) return st;
+      switch (p) {
+        case 1: st = batch_prepare<1>(c, psi[k], C.tab_host[j]); break;
+        case 2: st = batch_prepare<2>(c, psi[k], C.tab_host[j]); break;
+        case 3: st = batch_prepare<3>(c, psi[k], C.tab_host[j]); break;
+        default: st = batch_prepare<4>(c, psi[k], C.tab_host[j]); break;
+      }
+      if (st != VEF_OK) return st;
+    }
+  }
+  for (int p = 1; p <= kMaxP; ++p) {
+    BatchClass& C = B.cls[p];
+    if (C.probs.empty()) continue;
+    const int tile = (opts && opts->tile_override > 0) ? opts->tile_override : (C.tile ? C.tile : kDefaultTile64);
+    vef_status st = batch_launch(B, p, tile, s);
+    if (st != VEF_OK) return st;
+  }
+  B.swept = true;
+  if (info) {
+    info->passes = 1;
+    info->rel_residual = -1.0;
+    info->coupled_groups = 0;
+    info->lagged_face_points = 0;
+    info->levels = 0;
+    info->max_inner_iterations = 0;
+    info->timed_out = 0;
+    vef_status worst = VEF_OK;
+    for (int k = 0; k < n; ++k) {
+      vef_info one{};
+      vef_status st = collect_status(*B.meshes[k], s, &one);
+      if (st != VEF_OK && worst == VEF_OK) worst = st;
+      info->coupled_groups += B.scheds[k]->coupled_groups;
+      info->lagged_face_points += B.scheds[k]->lagged_points;
+      info->levels = std::max(info->levels, B.scheds[k]->levels);
+      info->max_inner_iterations = std::max(info->max_inner_iterations, one.max_inner_iterations);
+      info->timed_out |= one.timed_out;
+    }
+    return worst;
+  }
+  return VEF_OK;
+}
+
+extern "C" vef_status vef_batch_tune(vef_batch batch, void* stream, int* tiles_out) {
+  if (!batch) { set_last_error("batch is NULL"); return VEF_ERR_INVALID_ARG; }
+  if (!batch->swept) { set_last_error("call vef_batch_sweep once before tuning"); return VEF_ERR_INVALID_ARG; }
+  cudaStream_t s = (cudaStream_t)stream;
+  static const int candidates[] = {204, 208, 404, 408, 804, 808, 1604};
+  cudaEvent_t e0, e1;
+  VEF_CUDA_TRY(cudaEventCreate(&e0));
+  VEF_CUDA_TRY(cudaEventCreate(&e1));
+  for (int p = 1; p <= kMaxP; ++p) {
+    BatchClass& C = batch->cls[p];
+    if (tiles_out) tiles_out[p - 1] = 0;
+    if (C.probs.empty()) continue;
+    float best = 1e30f;
+    int best_tile = kDefaultTile64;
+    for (int tile : candidates) {
+      vef_status st = batch_launch(*batch, p, tile, s);   // warm-up (also checks the shape launches)
+      if (st != VEF_OK) continue;
+      VEF_CUDA_TRY(cudaEventRecord(e0, s));
+      for (int r = 0; r < 3; ++r)
+        if ((st = batch_launch(*batch, p, tile, s)) != VEF_OK) break;
+      VEF_CUDA_TRY(cudaEventRecord(e1, s));
+      VEF_CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      VEF_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (st == VEF_OK && ms < best) {
+        best = ms;
+        best_tile = tile;
+      }
+    }
+    C.tile = best_tile;
+    if (tiles_out) tiles_out[p - 1] = best_tile;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return VEF_OK;
+}

@@ -1,0 +1,91 @@
+"""Batched sweeps, the autotuner and CUDA-graph capture (GPU, through the C ABI)."""
+import numpy as np
+import pytest
+import torch
+
+from _gpu import dev, host, rel
+from vef_inputs import level_symmetric, seeded_media
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [(9, 1, 4), (12, 2, 8), (7, 3, 6), (5, 4, 12), (16, 2, 16), (10, 1, 8)]   # (N, p, S_N)
+
+
+def _problems():
+    from paper_2301_04758_gb300.api import Mesh
+    probs = []
+    for k, (N, p, sn) in enumerate(SPECS):
+        mesh = Mesh(N, N, 3, p, 0.05)
+        om, w = level_symmetric(sn)
+        st, ss = seeded_media(N * N, 400 + k)
+        rng = np.random.default_rng(k)
+        phi = rng.uniform(0.5, 1.5, (N * N, (p + 1) ** 2))
+        q = np.ones((N * N, (p + 1) ** 2))
+        probs.append(dict(mesh=mesh, om=om, w=w, st=dev(st), ss=dev(ss), phi=dev(phi), q=dev(q)))
+    return probs
+
+
+def test_batch_matches_single_sweeps_and_tuning_keeps_results(lib):
+    from paper_2301_04758_gb300.api import Batch
+    probs = _problems()
+    single = [P["mesh"].sweep(P["st"], P["ss"], P["om"], P["w"], phi_in=P["phi"], source=P["q"]) for P in probs]
+    single = [host(x) for x in single]
+    batch = Batch([P["mesh"] for P in probs], [P["om"] for P in probs], [P["w"] for P in probs])
+    args = ([P["st"] for P in probs], [P["ss"] for P in probs])
+    kw = dict(phi_in=[P["phi"] for P in probs], source=[P["q"] for P in probs])
+    out, info = batch.sweep(*args, info=True, **kw)
+    assert info["timed_out"] == 0
+    for a, b in zip(out, single):
+        assert rel(host(a), b) < 1e-15
+    tiles = batch.tune()
+    assert set(tiles) == {1, 2, 3, 4}
+    out2 = batch.sweep(*args, **kw)
+    torch.cuda.synchronize()
+    for a, b in zip(out2, single):
+        assert rel(host(a), b) < 1e-15
+
+
+def test_batch_sweep_replays_from_a_cuda_graph(lib):
+    from paper_2301_04758_gb300.api import Batch
+    probs = _problems()
+    batch = Batch([P["mesh"] for P in probs], [P["om"] for P in probs], [P["w"] for P in probs])
+    args = ([P["st"] for P in probs], [P["ss"] for P in probs])
+    kw = dict(phi_in=[P["phi"] for P in probs], source=[P["q"] for P in probs])
+    psi = batch.sweep(*args, **kw)              # first call allocates
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        batch.sweep(*args, psi=psi, stream=s, **kw)
+    # new cross sections, replay, compare with a direct call
+    for P in probs:
+        P["st"].mul_(1.5)
+    g.replay()
+    torch.cuda.synchronize()
+    got = [host(x).copy() for x in psi]
+    ref = batch.sweep(*args, **kw)
+    torch.cuda.synchronize()
+    for a, b in zip(got, ref):
+        assert rel(a, host(b)) < 1e-15
+
+
+def test_source_iteration_replays_from_a_cuda_graph(lib):
+    from paper_2301_04758_gb300.api import Mesh
+    om, w = level_symmetric(8)
+    N, p = 24, 2
+    mesh = Mesh(N, N, 3, p, 0.05)
+    st, ss = seeded_media(N * N, 2)
+    st, ss = dev(st), dev(ss)
+    q = dev(np.ones((N * N, 9)))
+    phi, psi, dphi = mesh.source_iterate(st, ss, om, w, 4, source=q)
+    ref = host(phi).copy()
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        out = mesh.source_iterate(st, ss, om, w, 4, source=q, psi=psi, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert rel(host(out[0]), ref) < 1e-15
