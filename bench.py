@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--sweep-only", type=int, default=0, metavar="NX",
                     help="profiling driver: build an NX x NX mesh with the workload's recipe and run "
                          "--steps FP64 sweeps (no timing line)")
+    ap.add_argument("--suite", default="", choices=("", "precision", "batch", "adjoint"),
+                    help="other workloads (one JSON line each, not the headline): precision = 512x512 "
+                         "Q3 S12 FP64 vs mixed; batch = the 64-problem batch; adjoint = 128x128 Q2 S8 "
+                         "adjoint gradients with a central-difference check")
     ap.add_argument("--mixed-tol", type=float, default=1e-12,
                     help="relative residual target of the mixed-precision defect correction")
     return ap.parse_args()
@@ -410,6 +414,157 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+# ------------------------------------------------------------------ other workloads
+def _cuda_time(fn, reps=1):
+    import torch
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        out = fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def suite_precision(args):
+    """512 x 512 sine mesh (alpha 0.05, Q3 map), DG Q3, S12 (84 directions), seed-3 media,
+    q = 1, vacuum: one transport inversion + closures, FP64 against mixed precision
+    (FP32 factorisation and sweeps inside FP64 defect correction)."""
+    import torch
+    from paper_2301_04758_gb300.api import Mesh
+    from vef_inputs import config_workload
+    wl = config_workload("sine512_q3_s12")
+    om, w = wl["omega"], wl["weights"]
+    E, n, D = wl["E"], wl["n"], wl["D"]
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda").contiguous()
+    st, ss, q = T(wl["sigma_t"]), T(wl["sigma_s"]), T(wl["source"])
+    mesh = Mesh(512, 512, 3, 3, 0.05)
+    psi = torch.empty(D, E, n, dtype=torch.float64, device="cuda")
+    res = {}
+    outs = {}
+    for prec in ("fp64", "mixed"):
+        def step():
+            ps = mesh.sweep(st, ss, om, w, source=q, psi=psi, precision=prec,
+                            tol=args.mixed_tol if prec == "mixed" else 0.0)
+            return mesh.moments(ps, om, w, outputs=("phi", "J", "E", "Eb"))
+        step()
+        mesh.profile(True)
+        ms, out = _cuda_time(step, reps=max(1, args.steps))
+        prof = mesh.profile_read()
+        mesh.profile(False)
+        mesh.sync()
+        outs[prec] = {k: v.clone() for k, v in out.items()}
+        outs[prec]["psi"] = psi.clone() if prec == "fp64" else psi
+        res[prec] = {"ms_per_step": ms, "angular_dof_updates_per_s": E * n * D / (ms * 1e-3),
+                     "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items() if v[0]}}
+    err = {k: float(torch.linalg.norm((outs["mixed"][k] - outs["fp64"][k]).flatten())
+                    / torch.linalg.norm(outs["fp64"][k].flatten())) for k in ("psi", "phi", "J", "E", "Eb")}
+    _, info = mesh.sweep(st, ss, om, w, source=q, psi=psi, info=True)
+    return {"suite": "precision", "workload": "512x512 sine-curved Q3 mesh, DG Q3, S12 (84 dirs), seed-3 media, "
+            "q=1, vacuum; one sweep + closures", "fp64": res["fp64"], "mixed": res["mixed"],
+            "mixed_rel_err_vs_fp64": err, "mixed_speedup": res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"],
+            "defect_correction_rel_residual_target": args.mixed_tol,
+            "levels": info["levels"], "coupled_groups": info["coupled_groups"]}
+
+
+def suite_batch(args):
+    """The 64-problem batch: problem k (seed 400 + k) has N in {16,32,64,128,256} (k mod 5),
+    p = 1 + (k mod 4), S_N in {4,6,8,12,16} (k mod 5 shifted by k // 5), sine mesh alpha 0.05,
+    Q3 map, q = 1, vacuum.  One batched FP64 sweep (cluster shapes from the autotuner),
+    timed directly and as a CUDA-graph replay."""
+    import torch
+    from paper_2301_04758_gb300.api import Mesh, Batch
+    from vef_inputs.media import batch_problem
+    from vef_inputs import level_symmetric, seeded_media
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda").contiguous()
+    meshes, oms, ws, sts, sss, qs = [], [], [], [], [], []
+    updates = 0
+    for k in range(64):
+        spec = batch_problem(k)
+        N, p = spec["nx"], spec["p"]
+        meshes.append(Mesh(N, N, spec["mesh_order"], p, spec["alpha"]))
+        om, w = level_symmetric(spec["sn"])
+        oms.append(om)
+        ws.append(w)
+        st, ss = seeded_media(N * N, spec["media"][1])
+        sts.append(T(st))
+        sss.append(T(ss))
+        qs.append(torch.ones(N * N, (p + 1) ** 2, dtype=torch.float64, device="cuda"))
+        updates += N * N * (p + 1) ** 2 * len(w)
+    t0 = time.perf_counter()
+    batch = Batch(meshes, oms, ws)
+    build_s = time.perf_counter() - t0
+    psi = batch.sweep(sts, sss, source=qs)
+    tiles = batch.tune()
+    ms, _ = _cuda_time(lambda: batch.sweep(sts, sss, source=qs, psi=psi), reps=max(1, args.steps))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        batch.sweep(sts, sss, source=qs, psi=psi, stream=s)
+    ms_g, _ = _cuda_time(g.replay, reps=max(1, args.steps))
+    return {"suite": "batch", "workload": "64 problems, N 16..256, Q1..Q4, S4..S16, sine alpha 0.05, seeds 400+k",
+            "problems": 64, "angular_dof_updates_per_sweep": updates, "ms_per_sweep": ms,
+            "angular_dof_updates_per_s": updates / (ms * 1e-3), "graph_replay_ms": ms_g,
+            "graph_angular_dof_updates_per_s": updates / (ms_g * 1e-3), "tuned_tiles": tiles,
+            "schedule_build_s": build_s}
+
+
+def suite_adjoint(args):
+    """128 x 128 sine mesh, Q2, S8, seed-5 media: forward sweep, adjoint sweep and the
+    gradients of R = int_[0.6,0.8]^2 phi; central differences (relative step 1e-6) on 64
+    seeded elements per cross section."""
+    import numpy as np
+    import torch
+    from paper_2301_04758_gb300.api import Mesh
+    from vef_inputs import config_workload
+    wl = config_workload("sine128_q2_s8_adjoint")
+    om, w = wl["omega"], wl["weights"]
+    E, n = wl["E"], wl["n"]
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda").contiguous()
+    st_h, ss_h = wl["sigma_t"].copy(), wl["sigma_s"].copy()
+    rng = np.random.Generator(np.random.PCG64(5))
+    phi_in = T(rng.uniform(0.5, 1.5, (E, n)))
+    q = T(wl["source"])
+    mesh = Mesh(128, 128, 3, 2, 0.05)
+    g = mesh.region_weights((0.6, 0.6), (0.8, 0.8))
+    st, ss = T(st_h), T(ss_h)
+
+    def R_of(st_, ss_):
+        psi = mesh.sweep(st_, ss_, om, w, phi_in=phi_in, source=q)
+        return float((g * mesh.moments(psi, om, w, outputs=("phi",))["phi"]).sum())
+
+    psi = mesh.sweep(st, ss, om, w, phi_in=phi_in, source=q)
+    ms_f, _ = _cuda_time(lambda: mesh.sweep(st, ss, om, w, phi_in=phi_in, source=q, psi=psi), reps=3)
+    ms_a, (dst, dss, _) = _cuda_time(lambda: mesh.adjoint(st, ss, om, w, psi, g, phi_in=phi_in), reps=3)
+    worst, checked = {}, 0
+    for rel_step in (1e-6, 1e-4):
+        worst[rel_step] = 0.0
+        for arr_h, grad in ((st_h, dst), (ss_h, dss)):
+            gh = grad.cpu().numpy()
+            # seeded sample among elements whose gradient is not negligible (central
+            # differences of R resolve about 1e-10 R / h; tiny gradients are FD noise)
+            big = np.flatnonzero(np.abs(gh) >= 1e-2 * np.abs(gh).max())
+            sample = rng.choice(big, min(32, len(big)), replace=False)
+            checked += len(sample)
+            for e in sample:
+                h = rel_step * arr_h[e]
+                arr_h[e] += h
+                Rp = R_of(T(st_h), T(ss_h))
+                arr_h[e] -= 2 * h
+                Rm = R_of(T(st_h), T(ss_h))
+                arr_h[e] += h
+                fd = (Rp - Rm) / (2 * h)
+                worst[rel_step] = max(worst[rel_step], abs(fd - gh[e]) / abs(gh[e]))
+    return {"suite": "adjoint", "workload": "128x128 sine-curved Q3 mesh, DG Q2, S8, seed-5 media; "
+            "R = int over [0.6,0.8]^2 of phi", "forward_sweep_ms": ms_f, "adjoint_ms": ms_a,
+            "fd_samples": checked, "fd_max_rel_diff_step_1e-6": worst[1e-6],
+            "fd_max_rel_diff_step_1e-4": worst[1e-4],
+            "fd_note": "central differences, relative steps 1e-6 and 1e-4, elements with |dR/dsigma| >= 1e-2 max"}
+
+
 def sweep_only(args):
     """Small driver for ncu captures: NX x NX sine mesh (alpha 0.05, Q3 map), Q2, S8,
     seed-2 media, q = 1; runs --steps FP64 sweeps through the public API."""
@@ -436,6 +591,12 @@ def main():
     args = parse()
     if args.sweep_only:
         sweep_only(args)
+        return
+    if args.suite:
+        from paper_2301_04758_gb300 import build as vbuild
+        vbuild.build()
+        fn = {"precision": suite_precision, "batch": suite_batch, "adjoint": suite_adjoint}[args.suite]
+        print(json.dumps(fn(args)))
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -167,6 +167,13 @@ vef_status vef_source_iterate(vef_mesh mesh, const double* sigma_t, const double
                               int D, int K, const vef_opts* opts, double* phi_out, double* psi,
                               double* dphi_inf, vef_info* info, void* stream);
 
+/* g [device] [E][n] such that sum_{e,j} g[e][j] phi[e][j] = int over the box
+ * [x0,x1] x [y0,y1] of phi dx, for phi given by its DG nodal values; the box indicator
+ * is evaluated at the volume Gauss points (its integral is exact for elements inside or
+ * outside the box).  The right-hand side of vef_adjoint_sweep for a region functional. */
+vef_status vef_region_weights(vef_mesh mesh, double x0, double y0, double x1, double y1, double* g,
+                              void* stream);
+
 /* Adjoint sweep for R = sum_{e,j} g[e][j] phi[e][j] of one transport inversion with fixed
  * phi_in: solves L_d^T lambda_d = w_d g (directions reversed: downwind order), then
  *   dR_dsigma_t[e] = - sum_d lambda_{d,e}^T M_e psi_{d,e},

@@ -27,6 +27,7 @@ EXPORTS = ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sy
            "vef_moments", "vef_source_iterate", "vef_adjoint_sweep", "vef_profile",
            "vef_profile_read", "vef_measure_fma_peak", "vef_eddington_noalloc",
            "vef_batch_create", "vef_batch_destroy", "vef_batch_sweep", "vef_batch_tune",
+           "vef_region_weights",
            "vef_status_string", "vef_last_error")
 
 KERNEL_CLASSES = ("geometry", "factor", "sweep", "residual", "source", "moments", "adjoint")
@@ -91,11 +92,12 @@ def _declare(lib):
     lib.vef_batch_sweep.argtypes = [P, PP, PP, PP, PP, PP, PP, ctypes.POINTER(VefOpts),
                                     ctypes.POINTER(VefInfo), P]
     lib.vef_batch_tune.argtypes = [P, P, ctypes.POINTER(ctypes.c_int)]
+    lib.vef_region_weights.argtypes = [P, D, D, D, D, P, P]
     for name in ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sync",
                  "vef_sweep", "vef_moments", "vef_source_iterate", "vef_adjoint_sweep",
                  "vef_profile", "vef_profile_read", "vef_measure_fma_peak",
                  "vef_eddington_noalloc", "vef_batch_create", "vef_batch_destroy",
-                 "vef_batch_sweep", "vef_batch_tune"):
+                 "vef_batch_sweep", "vef_batch_tune", "vef_region_weights"):
         getattr(lib, name).restype = I
     lib.vef_status_string.argtypes = [I]
     lib.vef_status_string.restype = ctypes.c_char_p

@@ -154,6 +154,13 @@ class Mesh:
         _lib.check(st, "vef_source_iterate")
         return (phi, psi, dphi, inf.as_dict()) if info else (phi, psi, dphi)
 
+    def region_weights(self, lo=(0.6, 0.6), hi=(0.8, 0.8), stream=None):
+        """g [E][n] with sum g * phi = int over the box [lo, hi] of phi dx."""
+        g = self._empty(self.E, self.n)
+        _lib.check(self.lib.vef_region_weights(self.handle, float(lo[0]), float(lo[1]), float(hi[0]),
+                                               float(hi[1]), _ptr(g), _stream(stream)), "vef_region_weights")
+        return g
+
     def adjoint(self, sigma_t, sigma_s, omega, weights, psi, g, phi_in=None, want_lambda=False,
                 info=False, stream=None):
         """Gradients of R = sum g * phi: returns (dR/dsigma_t [E], dR/dsigma_s [E] or None, lambda)."""

@@ -110,6 +110,8 @@ struct Mesh {
   float* Gy32 = nullptr;
   float* nds32 = nullptr;
   std::vector<double> nds_host;  // host copy for schedule building
+  double* ctrl_dev = nullptr;    // [E][(m+1)^2][2] control points
+  std::shared_ptr<void> map_tab; // mesh-order Lagrange tables (MapTab, mesh.cu)
   // schedules keyed by direction set
   std::vector<std::unique_ptr<Schedule>> schedules;
   // scratch

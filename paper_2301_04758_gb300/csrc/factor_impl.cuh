@@ -124,6 +124,124 @@ factor_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t*
   *reinterpret_cast<uint4*>(out) = make_uint4((unsigned)e, (unsigned)bits, faces, 0u);
 }
 
+// Row-parallel factorisation (used for p >= 3, where a whole element matrix per thread
+// spills): N lanes per (element, direction), lane i holds row i of A in registers.
+// Gauss-Jordan step k broadcasts the unscaled pivot row r = A[k][:] and every lane
+// applies one FMA per entry, row[j] += beta * r[j], with beta = -A[i][k] / r[k] on the
+// other rows and beta = 1/r[k] - 1 on the pivot row itself (which turns it into r / r[k]);
+// column k is then set to -A[i][k] / r[k], or 1 / r[k] on the pivot row.  Same FP64
+// instruction count per task as the thread-per-task form, no local memory.
+template <int P, typename T>
+__global__ void __launch_bounds__(128)
+factor_rows_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t* __restrict__ finfo,
+                   const double* __restrict__ omega, const double* __restrict__ sigma_t,
+                   const T* __restrict__ Mm, const T* __restrict__ Gxm, const T* __restrict__ Gym,
+                   const T* __restrict__ nds, FaceTab<T> ft, int nx, int ny, long long E,
+                   T* __restrict__ rec, unsigned int* status) {
+  constexpr int Q = P + 1, N = Q * Q, NQ = P + 2;
+  constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
+  constexpr unsigned FULL = 0xffffffffu;
+  using L = Rec<P, T>;
+  const int lane = threadIdx.x & 31;
+  const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long m = gw * SPC + lane / N;
+  const int i = lane % N;
+  const int base = (lane / N) * N;
+  const bool valid = lane < SPC * N && m < nmem;
+  int d = 0, e = 0;
+  uint16_t bits = 0;
+  T mu = 0, eta = 0, st = 0;
+  if (valid) {
+    const uint32_t c = code[m];
+    d = (int)(c >> 22);
+    e = (int)(c & 0x3fffffu);
+    mu = (T)omega[2 * d];
+    eta = (T)omega[2 * d + 1];
+    st = (T)sigma_t[e];
+    bits = finfo[(size_t)d * E + e];
+  }
+  T row[N];
+  {
+    const size_t o = ((size_t)e * N + i) * N;
+#pragma unroll
+    for (int j = 0; j < N; ++j) row[j] = valid ? st * Mm[o + j] - mu * Gxm[o + j] - eta * Gym[o + j] : (T)(i == j);
+  }
+  // face terms: outflow part into A; row `pos` of each face's inflow coupling Cin_f
+  const int ia = i % Q, ib = i / Q;
+  T cin[4][Q];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    int pos = -1;
+    if (f == 0 && ib == 0) pos = ia;
+    if (f == 1 && ia == P) pos = ib;
+    if (f == 2 && ib == P) pos = ia;
+    if (f == 3 && ia == 0) pos = ib;
+#pragma unroll
+    for (int t = 0; t < Q; ++t) cin[f][t] = 0;
+    if (pos < 0 || !valid) continue;
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      const T* v = nds + (((size_t)e * 4 + f) * NQ + k) * 2;
+      const T s = ft.w[k] * (mu * v[0] + eta * v[1]);
+      const T la = ft.l[pos][k];
+#pragma unroll
+      for (int t = 0; t < Q; ++t) {
+        const T ll = la * ft.l[t][k];
+        if (s > (T)0) row[face_dof<P>(f, t)] += s * ll;
+        else cin[f][t] += s * ll;
+      }
+    }
+  }
+  // in-place Gauss-Jordan, row-parallel
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    T r[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) r[j] = __shfl_sync(FULL, row[j], (base + k) & 31);
+    if (valid && i == k && !(fabs(r[k]) > tiny_pivot<T>())) atomicOr(status, kDevSingular);
+    const T inv = (T)1 / r[k];
+    const T aik = row[k];
+    const T beta = (i == k) ? inv - (T)1 : -aik * inv;
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      if (j != k) row[j] = fma(beta, r[j], row[j]);
+    row[k] = (i == k) ? inv : -aik * inv;
+  }
+  // records: A^{-1} column-major (lane i writes entry i of every column), W slots
+  char* out = L::s_at(rec, valid ? m : 0);
+  char* outx = L::x_at((char*)rec + nmem * (long long)L::kStaged, valid ? m : 0);
+  if (valid) {
+    T* ai = L::ainv(outx);
+#pragma unroll
+    for (int j = 0; j < N; ++j) ai[j * N + i] = row[j];
+  }
+  unsigned faces = 0xffffffffu;
+  int slot = 0;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const bool use = (bits & (1u << f)) && nb_elem(nx, ny, e, f) >= 0;
+    // W_f[i][t] = sum_a Ainv[i][face_dof(f, a)] Cin_f[a][t]; Cin_f row a lives on the lane
+    // holding face node a
+    T w[Q];
+#pragma unroll
+    for (int t = 0; t < Q; ++t) w[t] = 0;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      const int src = base + face_dof<P>(f, a);
+#pragma unroll
+      for (int t = 0; t < Q; ++t) w[t] += row[face_dof<P>(f, a)] * __shfl_sync(FULL, cin[f][t], src & 31);
+    }
+    if (valid && use) {
+      T* W = L::slot(out, outx, slot);
+#pragma unroll
+      for (int t = 0; t < Q; ++t) W[t * N + i] = w[t];
+      if (i == 0) faces = (faces & ~(0xffu << (8 * slot))) | ((unsigned)f << (8 * slot));
+      ++slot;
+    }
+  }
+  if (valid && i == 0) *reinterpret_cast<uint4*>(out) = make_uint4((unsigned)e, (unsigned)bits, faces, 0u);
+}
+
 // FP64 element matrix and inflow couplings of every (element, direction), for the FP64
 // residual of the mixed-precision defect correction: per task [A (n x n, row-major)]
 // [Cin of W slots 0..3 ((p+1) x (p+1), row a = own face node, column t = neighbour's)].
@@ -208,9 +326,18 @@ static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, cud
         make_facetab<double>(M.tab), M.nx, M.ny, M.E, (double*)S.a64);
   }
   KTimer kt(&M, VEF_K_FACTOR, stream);
-  factor_kernel<P, T><<<nblk(S.members, 128), 128, 0, stream>>>(
-      S.members, S.member_code, S.faceinfo, S.omega_dev, sigma_t, Mm, Gx, Gy, nds,
-      make_facetab<T>(M.tab), M.nx, M.ny, M.E, (T*)*recp, M.dev_status);
+  if (P >= 3) {
+    constexpr int N = (P + 1) * (P + 1);
+    constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
+    const long long warps = (S.members + SPC - 1) / SPC;
+    factor_rows_kernel<P, T><<<nblk(warps * 32, 128), 128, 0, stream>>>(
+        S.members, S.member_code, S.faceinfo, S.omega_dev, sigma_t, Mm, Gx, Gy, nds,
+        make_facetab<T>(M.tab), M.nx, M.ny, M.E, (T*)*recp, M.dev_status);
+  } else {
+    factor_kernel<P, T><<<nblk(S.members, 128), 128, 0, stream>>>(
+        S.members, S.member_code, S.faceinfo, S.omega_dev, sigma_t, Mm, Gx, Gy, nds,
+        make_facetab<T>(M.tab), M.nx, M.ny, M.E, (T*)*recp, M.dev_status);
+  }
   VEF_CUDA_TRY(cudaGetLastError());
   return VEF_OK;
 }

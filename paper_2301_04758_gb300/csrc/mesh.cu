@@ -143,6 +143,36 @@ __global__ void geom_canon_kernel(int nx, int ny, int nq, double* __restrict__ n
   }
 }
 
+// g[e][j] = sum_q w_q J_q chi(x_q) l_j(x_q): weights of R = int_region phi dx over the DG
+// nodal values of phi, with the box indicator chi evaluated at the volume Gauss points.
+__global__ void region_weights_kernel(const double* __restrict__ ctrl, long long E, MapTab mt, Tab1D tab,
+                                      double x0, double y0, double x1, double y1, double* __restrict__ g) {
+  const int np1 = tab.np1, n = np1 * np1, nq = tab.nq;
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= E * n) return;
+  const long long e = t / n;
+  const int j = (int)(t % n), ja = j % np1, jb = j / np1;
+  const double* c = ctrl + e * 2 * (mt.m + 1) * (mt.m + 1);
+  const int q = mt.m + 1;
+  double acc = 0.0;
+  for (int k2 = 0; k2 < nq; ++k2)
+    for (int k1 = 0; k1 < nq; ++k1) {
+      double x = 0.0, y = 0.0;
+      for (int b = 0; b < q; ++b)
+        for (int a = 0; a < q; ++a) {
+          const double l = mt.lv[a][k1] * mt.lv[b][k2];
+          x += c[2 * (a + q * b)] * l;
+          y += c[2 * (a + q * b) + 1] * l;
+        }
+      if (x < x0 || x > x1 || y < y0 || y > y1) continue;
+      double F[2][2];
+      map_jac(c, mt, k1, k2, F);
+      const double J = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+      acc += tab.glw[k1] * tab.glw[k2] * J * tab.l[ja][k1] * tab.l[jb][k2];
+    }
+  g[t] = acc;
+}
+
 template <typename T>
 __global__ void to_float_kernel(const double* __restrict__ a, T* __restrict__ b, long long n) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -188,6 +218,7 @@ void destroy_events(Mesh& M);
 Mesh::~Mesh() {
   destroy_events(*this);
   schedules.clear();
+  cudaFree(ctrl_dev);
   cudaFree(Mmat);
   cudaFree(Gx);
   cudaFree(Gy);
@@ -286,7 +317,7 @@ extern "C" vef_status vef_mesh_create(int nx, int ny, int mesh_order, int p, dou
   double* dctrl = nullptr;
   double* g5 = nullptr;
   const long long nn = M.E * M.n * M.n;
-  auto cleanup = [&]() { cudaFree(dctrl); cudaFree(g5); };
+  auto cleanup = [&]() { cudaFree(g5); };
   cudaError_t err = cudaSuccess;
   if ((err = cudaMalloc(&dctrl, ctrl.size() * sizeof(double))) != cudaSuccess ||
       (err = cudaMalloc(&g5, (size_t)M.E * M.nq * M.nq * 5 * sizeof(double))) != cudaSuccess ||
@@ -311,6 +342,8 @@ extern "C" vef_status vef_mesh_create(int nx, int ny, int mesh_order, int p, dou
   err = cudaGetLastError();
   if (err == cudaSuccess) err = cudaDeviceSynchronize();
   if (err != cudaSuccess) { cleanup(); return cuda_fail(err, "geometry kernels"); }
+  M.ctrl_dev = dctrl;
+  M.map_tab = std::make_shared<MapTab>(mt);
   M.nds_host.resize((size_t)nf * 2);
   err = cudaMemcpy(M.nds_host.data(), M.nds, nf * 2 * sizeof(double), cudaMemcpyDeviceToHost);
   cleanup();
@@ -335,5 +368,16 @@ extern "C" vef_status vef_mesh_query(vef_mesh mesh, vef_mesh_desc* out) {
   const Mesh& M = mesh->impl;
   out->nx = M.nx; out->ny = M.ny; out->mesh_order = M.m; out->p = M.p;
   out->n = M.n; out->nq = M.nq; out->E = M.E; out->nbf = M.nbf;
+  return VEF_OK;
+}
+
+extern "C" vef_status vef_region_weights(vef_mesh mesh, double x0, double y0, double x1, double y1,
+                                         double* g, void* stream) {
+  if (!mesh || !g) { set_last_error("mesh and g are required"); return VEF_ERR_INVALID_ARG; }
+  const Mesh& M = mesh->impl;
+  const MapTab& mt = *std::static_pointer_cast<MapTab>(M.map_tab);
+  region_weights_kernel<<<blocks_for(M.E * M.n, 128), 128, 0, (cudaStream_t)stream>>>(
+      M.ctrl_dev, M.E, mt, M.tab, x0, y0, x1, y1, g);
+  VEF_CUDA_TRY(cudaGetLastError());
   return VEF_OK;
 }

@@ -67,3 +67,13 @@ def test_adjoint_with_coupled_groups(lib):
     assert info["coupled_groups"] > 0
     assert rel(host(glam), lam) < 1e-12, info
     assert rel(host(gdst), dst) < 1e-12
+
+
+def test_region_weights_match_oracle(lib):
+    from paper_2301_04758_gb300.api import Mesh
+    disc = Discretization(11, 7, 3, 0.06, 3)
+    mesh = Mesh(11, 7, 3, 3, 0.06)
+    for lo, hi in (((0.6, 0.6), (0.8, 0.8)), ((0.0, 0.0), (1.0, 1.0)), ((0.13, 0.21), (0.47, 0.83))):
+        ref = region_weights(disc, lo, hi)
+        got = host(mesh.region_weights(lo, hi))
+        assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max() + 1e-18
