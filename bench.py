@@ -93,7 +93,7 @@ def bytes_sweep(p, word=8, inflow_faces=2.0):
     return pad(16 + 2 * word * n * (p + 1)) + pad(word * n) + 8 * inflow_faces * (p + 1) + 8 * n
 
 
-SWEEP_REGION = ("// Coupled group, global-memory form",
+SWEEP_REGION = ("// upwind correction of row i for face f of member record r",
                 "// -------------------------------------------------------------- FP64 residual (mixed)")
 
 

@@ -32,7 +32,10 @@
  * ordering: the library orders elements per direction along the upwind dependency
  * graph (one thread-block cluster per direction walks its levels) and solves the rare
  * strongly coupled element groups (curved faces that are partly inflow and partly
- * outflow) by an inner block Gauss-Seidel iteration to a relative change below
+ * outflow) as units: directly, through the dense system for the face traces the
+ * group's elements exchange (its inverse is formed with the element factorisations;
+ * groups of up to 32 elements for p <= 2, 16 for p >= 3, and up to 128 trace values),
+ * else by an inner block Gauss-Seidel iteration to a relative change below
  * `vef_opts.tol`.
  *
  * Conventions
@@ -67,13 +70,16 @@ typedef enum {
   VEF_ERR_INVALID_ARG = 1,
   VEF_ERR_CUDA = 2,
   VEF_ERR_OOM = 3,
-  VEF_ERR_TIMEOUT = 4,            /* reserved: no kernel waits on another (cluster barriers only) */
+  VEF_ERR_TIMEOUT = 4,            /* a bounded device-side wait (staging copy) gave up */
   VEF_ERR_NOT_CONVERGED = 5,      /* an inner or defect-correction iteration hit its cap */
   VEF_ERR_NONPOSITIVE_DENOM = 6,  /* sum_d w_d psi_d <= 1e-300 at a closure point (NaN written) */
   VEF_ERR_NOT_IMPLEMENTED = 7
 } vef_status;
 
 enum { VEF_FP64 = 0, VEF_MIXED = 1 };
+
+/* vef_opts.flags */
+enum { VEF_GROUPS_ITERATIVE = 1 /* solve every coupled group by the inner iteration */ };
 
 typedef struct vef_mesh_s* vef_mesh;
 
@@ -88,6 +94,7 @@ typedef struct {
                         coupled-group iterations */
   int tile_override; /* 0 = library choice; else 100 * (CTAs per direction cluster, 1..16)
                         + (warps per CTA, 1..8) of the sweep kernel */
+  int flags;         /* bit set of VEF_GROUPS_ITERATIVE (default 0: direct group solves) */
 } vef_opts;
 
 /* Filled by calls given a non-NULL pointer (those calls synchronise `stream`). */
@@ -95,9 +102,10 @@ typedef struct {
   int passes;                 /* sweeps executed (1 for FP64; 1 + corrections for mixed) */
   double rel_residual;        /* mixed: final ||b - L psi||_2 / ||b||_2 (FP64 path: -1) */
   long long coupled_groups;   /* (element group, direction) tasks with more than one element */
-  long long lagged_face_points; /* face points inside coupled groups (solved iteratively) */
-  int max_inner_iterations;   /* largest inner Gauss-Seidel count used by a coupled group */
-  int timed_out;              /* reserved, always 0 (no device-side waits) */
+  long long lagged_face_points; /* inflow face points between elements of one coupled group */
+  int max_inner_iterations;   /* largest inner Gauss-Seidel count used by a coupled group
+                                 (0 when every group was solved directly) */
+  int timed_out;              /* 1 if a bounded device-side wait gave up */
   int levels;                 /* dependency levels of the schedule (critical path length) */
 } vef_info;
 

@@ -21,6 +21,7 @@ VEF_ERR_NOT_IMPLEMENTED = 7
 
 VEF_FP64 = 0
 VEF_MIXED = 1
+VEF_GROUPS_ITERATIVE = 1
 
 # every symbol include/vef.h declares
 EXPORTS = ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sync", "vef_sweep",
@@ -35,7 +36,8 @@ KERNEL_CLASSES = ("geometry", "factor", "sweep", "residual", "source", "moments"
 
 class VefOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double),
-                ("max_passes", ctypes.c_int), ("tile_override", ctypes.c_int)]
+                ("max_passes", ctypes.c_int), ("tile_override", ctypes.c_int),
+                ("flags", ctypes.c_int)]
 
 
 class VefInfo(ctypes.Structure):

@@ -32,12 +32,13 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _opts(precision="fp64", tol=0.0, max_passes=0, tile=0):
+def _opts(precision="fp64", tol=0.0, max_passes=0, tile=0, groups="direct"):
     o = _lib.VefOpts()
     o.precision = {"fp64": _lib.VEF_FP64, "mixed": _lib.VEF_MIXED}[precision]
     o.tol = float(tol)
     o.max_passes = int(max_passes)
     o.tile_override = int(tile)
+    o.flags = {"direct": 0, "iterative": _lib.VEF_GROUPS_ITERATIVE}[groups]
     return o
 
 
@@ -99,8 +100,12 @@ class Mesh:
 
     # ---------------------------------------------------------------- transport
     def sweep(self, sigma_t, sigma_s, omega, weights, phi_in=None, source=None, inflow=None,
-              precision="fp64", tol=0.0, max_passes=0, tile=0, psi=None, info=False, stream=None):
-        """psi [D][E][n] = L^{-1} b for every direction (see vef_sweep in include/vef.h)."""
+              precision="fp64", tol=0.0, max_passes=0, tile=0, groups="direct", psi=None, info=False,
+              stream=None):
+        """psi [D][E][n] = L^{-1} b for every direction (see vef_sweep in include/vef.h).
+
+        groups: "direct" (coupled element groups through their trace system) or
+        "iterative" (inner block Gauss-Seidel for every group)."""
         om, omp = _host(omega)
         w, wp = _host(weights)
         D = len(w)
@@ -108,7 +113,7 @@ class Mesh:
         if psi is None:
             psi = self._empty(D, self.E, self.n)
         inf = _lib.VefInfo() if info else None
-        o = _opts(precision, tol, max_passes, tile)
+        o = _opts(precision, tol, max_passes, tile, groups)
         st = self.lib.vef_sweep(self.handle, _ptr(sigma_t), _ptr(sigma_s), _ptr(phi_in), _ptr(source),
                                 aniso, _ptr(inflow), omp, wp, D, ctypes.byref(o), _ptr(psi),
                                 ctypes.byref(inf) if info else None, _stream(stream))

@@ -174,7 +174,7 @@ __device__ __forceinline__ void adj_group(const AdjArgs& a, int d, int s0) {
 }
 
 template <int P>
-__global__ void __launch_bounds__(256) adjoint_kernel(AdjArgs a) {
+__global__ void __maxnreg__(128) adjoint_kernel(AdjArgs a) {
   constexpr int Q = P + 1, N = Q * Q;
   constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
   (void)Q;

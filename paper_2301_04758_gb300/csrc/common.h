@@ -48,11 +48,18 @@ vef_status cuda_fail(cudaError_t err, const char* what);
 
 // device status word values written by kernels (bit flags)
 enum : unsigned int {
-  kDevTimeout = 1u,        // reserved: the current kernels never wait on each other
+  kDevTimeout = 1u,        // a bounded wait on a staging copy gave up
   kDevNotConverged = 2u,
   kDevNonpositive = 4u,
   kDevSingular = 8u,
 };
+
+// Coupled element groups are solved directly through a trace system precomputed by the
+// factorisation (schedule.cpp, factor_impl.cuh) when they have at most this many members
+// and trace unknowns; larger groups use the inner block Gauss-Seidel iteration.
+__host__ __device__ constexpr int group_direct_members(int p) { return p <= 2 ? 32 : 16; }
+constexpr int kGroupMaxTrace = 128;
+constexpr int kGroupSmemTrace = 32;   // the trace-system inverse sits in shared memory up to this size
 
 // Per-direction-set schedule: dependency levels, element groups and task chunks.
 struct Schedule {
@@ -74,6 +81,17 @@ struct Schedule {
   uint32_t* member_nbpos = nullptr;  // [members] per face: in-group position of the neighbour or 255
   int* slot_first = nullptr;   // [nslots] first member index (-1 = padding)
   int* slot_count = nullptr;   // [nslots] members in the group
+  // coupled groups solved directly: per slot its group index or -1; per group its slot,
+  // the number of trace unknowns nt and the offset of its nt x nt inverse in grec
+  int* slot_gid = nullptr;     // [nslots]
+  int* grp_slot = nullptr;     // [ngroups]
+  int* grp_nt = nullptr;       // [ngroups]
+  long long* grp_toff = nullptr;  // [ngroups + 1]
+  long long ngroups = 0;
+  long long grec_elems = 0;    // entries of all inverses (grp_toff[ngroups])
+  int max_nt = 0;
+  void* grec64 = nullptr;      // trace-system inverses (lazily allocated): FP64 and FP32
+  void* grec32 = nullptr;
   uint32_t* member_code = nullptr;  // [members] (d << 22) | e, in schedule order
   int* member_of = nullptr;    // [D][E] -> member index
   uint16_t* faceinfo = nullptr;  // [D][E] bits 0-3 inflow face, 4-7 intra-group face, 8-11 outflow to a neighbour

@@ -11,6 +11,7 @@
 //     [element, face bits, slot faces][W slots, column-major n x (p+1)][A^{-1} column-major]
 // (see Rec in device.cuh).
 #pragma once
+#include <algorithm>
 #include <type_traits>
 
 #include "device.cuh"
@@ -294,6 +295,149 @@ assemble64_kernel(long long nmem, const uint32_t* __restrict__ code, const uint1
   }
 }
 
+// Trace system of a coupled element group.  Member a of a group solves
+//     psi_a = z_a - sum_{(a,f)} W_{a,f} tau_{a,f},
+// where z_a = A_a^{-1} b_a minus the couplings to elements outside the group, and the
+// sum runs over the faces f of a that are inflow somewhere and shared with another
+// member b; tau_{a,f} holds b's values at the p+1 nodes of its face opposite f.  Taking
+// those traces of the member equations gives the closed system
+//     (I + R) tau = P z,   R[(a,f,s), (b,g,t)] = W_{b,g}[face_dof(opp f, s)][t],
+// which is the element block system of the group (the upwind weak form with the group's
+// internal upwind traces as unknowns) reduced to its interface.  One CTA per group forms
+// I + R in shared memory and inverts it in place (Gauss-Jordan with partial pivoting, in
+// FP64); the inverse is stored column-major.  Trace unknowns are numbered by member, then
+// face, then face node; the sweep numbers them the same way.
+template <int P, typename T>
+__global__ void __launch_bounds__(128)
+group_factor_kernel(const int* __restrict__ grp_slot, const int* __restrict__ grp_nt,
+                    const long long* __restrict__ grp_toff, const int* __restrict__ slot_first,
+                    const int* __restrict__ slot_count, const uint32_t* __restrict__ member_nbpos,
+                    const T* __restrict__ rec, long long nmem, T* __restrict__ grec,
+                    unsigned int* status) {
+  constexpr int Q = P + 1, N = Q * Q;
+  constexpr int GM = group_direct_members(P);
+  constexpr int NC = kGroupMaxTrace / Q + 1;
+  using L = Rec<P, T>;
+  extern __shared__ __align__(16) double gsm[];
+  __shared__ uint32_t cpl[NC];
+  __shared__ int perm[kGroupMaxTrace];
+  __shared__ double colk[kGroupMaxTrace];
+  __shared__ int piv_row, ncpl;
+  const int g = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+  const int sl = grp_slot[g], nt = grp_nt[g];
+  const int first = slot_first[sl], m = slot_count[sl];
+  const char* recx = (const char*)rec + nmem * (long long)L::kStaged;
+  double* Mx = gsm;   // nt x nt, row-major
+  if (tid == 0) {
+    int c = 0;
+    for (int a = 0; a < m && a < GM; ++a) {
+      const uint4 info = *reinterpret_cast<const uint4*>(L::s_at(rec, first + a));
+      const uint32_t nbp = member_nbpos[first + a];
+      for (int f = 0; f < 4; ++f) {
+        if (!((info.y >> f) & 1u) || !((info.y >> (4 + f)) & 1u)) continue;
+        const int s = rec_slot_of(info.z, f);
+        if (c < NC && s >= 0) cpl[c] = (uint32_t)a | ((uint32_t)f << 8) | (((nbp >> (8 * f)) & 0xffu) << 16) |
+                                       ((uint32_t)s << 24);
+        ++c;
+      }
+    }
+    ncpl = c;
+  }
+  __syncthreads();
+  if (ncpl * Q != nt) {   // schedule and records disagree: leave the group to the iteration
+    if (tid == 0) atomicOr(status, kDevSingular);
+    return;
+  }
+  for (int idx = tid; idx < nt * nt; idx += nth) {
+    const int r = idx / nt, col = idx % nt;
+    const uint32_t c1 = cpl[r / Q], c2 = cpl[col / Q];
+    const int b = (int)((c1 >> 16) & 0xffu), f = (int)((c1 >> 8) & 0xffu);
+    double v = r == col ? 1.0 : 0.0;
+    if ((int)(c2 & 0xffu) == b) {
+      const T* W = L::slot(L::s_at(rec, first + b), L::x_at(recx, first + b), (int)(c2 >> 24));
+      v += (double)W[(col % Q) * N + face_dof<P>((f + 2) & 3, r % Q)];
+    }
+    Mx[idx] = v;
+  }
+  for (int k = 0; k < nt; ++k) {
+    __syncthreads();
+    if (tid < 32) {   // pivot: largest |entry| of column k on or below the diagonal
+      double best = -1.0;
+      int bi = k;
+      for (int i = k + tid; i < nt; i += 32) {
+        const double v = fabs(Mx[i * nt + k]);
+        if (v > best) { best = v; bi = i; }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (tid == 0) {
+        piv_row = bi;
+        perm[k] = bi;
+        if (!(best > 1e-300)) atomicOr(status, kDevSingular);
+      }
+    }
+    __syncthreads();
+    const int pr = piv_row;
+    if (pr != k)
+      for (int j = tid; j < nt; j += nth) {
+        const double t = Mx[k * nt + j];
+        Mx[k * nt + j] = Mx[pr * nt + j];
+        Mx[pr * nt + j] = t;
+      }
+    __syncthreads();
+    const double inv = 1.0 / Mx[k * nt + k];
+    for (int i = tid; i < nt; i += nth) colk[i] = Mx[i * nt + k];
+    __syncthreads();
+    for (int j = tid; j < nt; j += nth) Mx[k * nt + j] = j == k ? inv : Mx[k * nt + j] * inv;
+    __syncthreads();
+    for (int idx = tid; idx < nt * nt; idx += nth) {
+      const int i = idx / nt, j = idx % nt;
+      if (i == k) continue;
+      Mx[idx] = j == k ? -colk[i] * inv : fma(-colk[i], Mx[k * nt + j], Mx[idx]);
+    }
+  }
+  // undo the row interchanges as column interchanges, last first
+  for (int k = nt - 1; k >= 0; --k) {
+    __syncthreads();
+    const int pr = perm[k];
+    if (pr != k)
+      for (int i = tid; i < nt; i += nth) {
+        const double t = Mx[i * nt + k];
+        Mx[i * nt + k] = Mx[i * nt + pr];
+        Mx[i * nt + pr] = t;
+      }
+  }
+  __syncthreads();
+  T* out = grec + grp_toff[g];
+  for (int idx = tid; idx < nt * nt; idx += nth) {
+    const int j = idx / nt, r = idx % nt;
+    out[idx] = (T)Mx[r * nt + j];
+  }
+}
+
+template <int P, typename T>
+static vef_status launch_group_factor(Schedule& S, const void* rec, cudaStream_t stream, unsigned int* status) {
+  if (S.ngroups == 0) return VEF_OK;
+  void** gp = std::is_same<T, double>::value ? &S.grec64 : &S.grec32;
+  if (!*gp) {
+    size_t cap = 0;
+    vef_status st = ensure_buffer(gp, &cap, (size_t)std::max(1LL, S.grec_elems) * sizeof(T));
+    if (st != VEF_OK) return st;
+  }
+  const size_t smem = (size_t)S.max_nt * S.max_nt * sizeof(double);
+  VEF_CUDA_TRY(cudaFuncSetAttribute(group_factor_kernel<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  group_factor_kernel<P, T><<<(unsigned)S.ngroups, 128, smem, stream>>>(
+      S.grp_slot, S.grp_nt, S.grp_toff, S.slot_first, S.slot_count, S.member_nbpos, (const T*)rec,
+      S.members, (T*)*gp, status);
+  VEF_CUDA_TRY(cudaGetLastError());
+  return VEF_OK;
+}
+
 template <int P, typename T>
 static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, cudaStream_t stream) {
   void** recp = std::is_same<T, double>::value ? &S.rec64 : &S.rec32;
@@ -339,7 +483,7 @@ static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, cud
         make_facetab<T>(M.tab), M.nx, M.ny, M.E, (T*)*recp, M.dev_status);
   }
   VEF_CUDA_TRY(cudaGetLastError());
-  return VEF_OK;
+  return launch_group_factor<P, T>(S, *recp, stream, M.dev_status);
 }
 
 

@@ -251,6 +251,12 @@ Schedule::~Schedule() {
   cudaFree(rec64);
   cudaFree(rec32);
   cudaFree(a64);
+  cudaFree(slot_gid);
+  cudaFree(grp_slot);
+  cudaFree(grp_nt);
+  cudaFree(grp_toff);
+  cudaFree(grec64);
+  cudaFree(grec32);
 }
 
 }  // namespace vef

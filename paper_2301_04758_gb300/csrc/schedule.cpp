@@ -8,8 +8,10 @@
 // follows the flow, and a face can be inflow at some points and outflow at others,
 // which couples the two elements both ways (the lagging situation the paper describes
 // for re-entrant faces in its thick-diffusion section).  The graph's strongly
-// connected components ("groups") are solved as units by an inner block Gauss-Seidel
-// iteration; everything else is a DAG processed level by level.  Within a group the
+// connected components ("groups") are solved as units; everything else is a DAG
+// processed level by level.  A group is solved directly from a small dense system for
+// the traces its members exchange (its inverse is formed by the factorisation), or,
+// beyond the direct size limits, by an inner block Gauss-Seidel iteration for which the
 // members are ordered along the net face flux so that only the minority points of
 // mixed faces are iterated.
 #include <algorithm>
@@ -351,6 +353,40 @@ Schedule* get_schedule(Mesh* mesh, const double* omega, const double* weights, i
       }
     }
     if ((*st = upload(&S->member_nbpos, nbpos)) != VEF_OK) return nullptr;
+  }
+  // Coupled groups solved directly.  For member a (in group order) and face f that is
+  // inflow somewhere and shared with another member b, the Q values of b's trace on that
+  // face are trace unknowns, numbered by member, then face, then face node.  Groups with
+  // more members or unknowns than the direct limits keep slot_gid = -1.
+  {
+    const int Q = M.p + 1;
+    std::vector<int> slot_gid(slot_first.size(), -1), grp_slot, grp_nt;
+    std::vector<long long> grp_toff(1, 0);
+    for (size_t sl = 0; sl < slot_first.size(); ++sl) {
+      const int cnt = slot_count[sl];
+      if (cnt == 1 || cnt > group_direct_members(M.p)) continue;
+      int couplings = 0;
+      for (int t = 0; t < cnt; ++t) {
+        const uint32_t code = member_code[slot_first[sl] + t];
+        const uint16_t bits = graphs[code >> 22].info[code & ((1u << 22) - 1)];
+        for (int f = 0; f < 4; ++f)
+          if ((bits & (1u << f)) && (bits & (1u << (4 + f)))) ++couplings;
+      }
+      const int nt = couplings * Q;
+      if (nt == 0 || nt > kGroupMaxTrace) continue;
+      slot_gid[sl] = (int)grp_slot.size();
+      grp_slot.push_back((int)sl);
+      grp_nt.push_back(nt);
+      // offsets rounded to 4 entries keep every inverse 16-byte aligned in both precisions
+      grp_toff.push_back(grp_toff.back() + ((long long)nt * nt + 3) / 4 * 4);
+      S->max_nt = std::max(S->max_nt, nt);
+    }
+    S->ngroups = (long long)grp_slot.size();
+    S->grec_elems = grp_toff.back();
+    if ((*st = upload(&S->slot_gid, slot_gid)) != VEF_OK) return nullptr;
+    if ((*st = upload(&S->grp_slot, grp_slot)) != VEF_OK) return nullptr;
+    if ((*st = upload(&S->grp_nt, grp_nt)) != VEF_OK) return nullptr;
+    if ((*st = upload(&S->grp_toff, grp_toff)) != VEF_OK) return nullptr;
   }
   if ((*st = upload(&S->slot_first, slot_first)) != VEF_OK) return nullptr;
   if ((*st = upload(&S->slot_count, slot_count)) != VEF_OK) return nullptr;

@@ -18,6 +18,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <map>
+#include <mutex>
 
 #include "device.cuh"
 
@@ -25,8 +27,7 @@ namespace vef {
 
 // sweep launch defaults, 100 * (CTAs per direction cluster) + (warps per CTA), measured
 // on the 256 x 256 Q2 S8 sine-mesh sweep (FP64: 4 x 8 warps, FP32: 8 x 8 warps)
-constexpr int kDefaultTile64 = 408;
-constexpr int kDefaultTile32 = 808;
+constexpr int kDefaultTile64 = 408;   // batches before tuning (their clusters outnumber the SMs)
 
 
 // ----------------------------------------------------------------- right-hand sides
@@ -61,6 +62,9 @@ struct SweepArgs {
   int cluster_size;
   const int* slot_first;
   const int* slot_count;
+  const int* slot_gid;       // group index of a directly solved group slot, or -1; null = none
+  const long long* grp_toff; // offset of each group's trace-system inverse in grec
+  const T* grec;
   const uint32_t* code;
   const int* member_of;
   const uint16_t* finfo;
@@ -167,7 +171,8 @@ __device__ __forceinline__ T face_term(const T* W, const T* un, int f, int i) {
   return acc;
 }
 
-// Coupled group, global-memory form (groups larger than the shared-memory capacity).
+// Coupled group by inner block Gauss-Seidel over its members, in global memory (groups
+// beyond the direct limits, or every group when the caller asks for the iteration).
 template <int P, typename T, int MODE>
 __device__ __forceinline__ void group_solve(const SweepArgs<T>& a, int d, int s0) {
   constexpr int Q = P + 1, N = Q * Q;
@@ -221,107 +226,132 @@ __device__ __forceinline__ void group_solve(const SweepArgs<T>& a, int d, int s0
   }
 }
 
-// Coupled group held in shared memory: members' y rows, current iterates and external
-// upwind traces are staged once, so each inner Gauss-Seidel step touches only shared
-// memory (and the L1-resident W rows).
-template <int P, typename T>
-__host__ __device__ constexpr int group_smem_max() { return P <= 2 ? 16 : 8; }
-
+// Coupled group solved directly (groups within the direct limits).  The trace-system
+// inverse T = (I + R)^{-1} of the group was formed by the factorisation; with it the
+// group costs two passes over its member rows and one dense product:
+//   z_a   = y_a - sum over faces of a fed from outside the group of W_{a,f} u_f
+//   tau   = T (P z)          (P z: the members' z at the internal upwind face nodes)
+//   psi_a = z_a - sum_{(a,f) internal} W_{a,f} tau_{a,f}
+// Everything that does not depend on earlier levels (member info, y rows, the coupling
+// list and, when small, T itself) is staged into shared memory ahead of the level.
 template <int P, typename T>
 struct GroupSmem {
-  T y[group_smem_max<P, T>() * (P + 1) * (P + 1)];
-  T psi[group_smem_max<P, T>() * (P + 1) * (P + 1)];
-  T ext[group_smem_max<P, T>() * 4 * (P + 1)];
-  uint4 info[group_smem_max<P, T>()];
-  uint32_t nbpos[group_smem_max<P, T>()];
+  static constexpr int Q = P + 1, N = Q * Q, GM = group_direct_members(P);
+  static constexpr int NC = kGroupMaxTrace / Q + 1;
+  T z[GM * N];                                     // member rows: y, then z
+  T rhs[kGroupMaxTrace];                           // P z
+  T tau[kGroupMaxTrace];                           // trace unknowns
+  T tinv[kGroupSmemTrace * kGroupSmemTrace];       // T (column-major) when nt <= kGroupSmemTrace
+  uint4 info[GM];                                  // member record info
+  uint32_t cpl[NC];                                // coupling: a | f << 8 | b << 16 | W slot << 24
+  int cbase[GM + 1];                               // first coupling of each member
+  int m, nt, gid;
 };
 
-// members' record info, in-group neighbour positions and y rows: none of it depends on
-// earlier levels, so a group warp stages it ahead of its level
 template <int P, typename T>
-__device__ __forceinline__ void group_stage_static(const SweepArgs<T>& a, int s0, GroupSmem<P, T>& g) {
-  constexpr int Q = P + 1, N = Q * Q;
-  using L = Rec<P, T>;
-  (void)Q;
-  const int lane = threadIdx.x & 31;
-  const int first = a.slot_first[s0];
-  const int cnt = a.slot_count[s0];
-  for (int mi = lane; mi < cnt; mi += 32) {
-    g.info[mi] = *reinterpret_cast<const uint4*>(L::s_at(a.rec, first + mi));
-    g.nbpos[mi] = a.member_nbpos[first + mi];
-  }
-  for (int t = lane; t < cnt * N; t += 32) g.y[t] = a.y[(size_t)(first + t / N) * L::kYStride + t % N];
-  __syncwarp();
-}
-
-template <int P, typename T, int MODE>
-__device__ __forceinline__ void group_solve_smem(const SweepArgs<T>& a, int d, int s0,
-                                                 GroupSmem<P, T>& g) {
+__device__ __forceinline__ void group_stage(const SweepArgs<T>& a, int s0, GroupSmem<P, T>& g) {
   constexpr int Q = P + 1, N = Q * Q;
   using L = Rec<P, T>;
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int first = a.slot_first[s0];
-  const int cnt = a.slot_count[s0];
-  const int i = lane;
-  const bool act = lane < N;
-  for (int mi = 0; mi < cnt; ++mi) {
-    const int e = (int)g.info[mi].x;
-    const unsigned bits = g.info[mi].y;
+  const int cnt = a.slot_count[s0];           // <= group_direct_members(P) <= 32
+  const int gid = a.slot_gid[s0];
+  uint4 info = make_uint4(0u, 0u, 0xffffffffu, 0u);
+  uint32_t nbp = 0xffffffffu;
+  if (lane < cnt) {
+    info = *reinterpret_cast<const uint4*>(L::s_at(a.rec, first + lane));
+    nbp = a.member_nbpos[first + lane];
+    g.info[lane] = info;
+  }
+  // couplings of this member (faces inflow somewhere and shared with another member),
+  // numbered by member then face: exclusive warp prefix sum of the counts
+  const unsigned mine = lane < cnt ? (unsigned)__popc(info.y & (info.y >> 4) & 0xfu) : 0u;
+  unsigned incl = mine;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned v = __shfl_up_sync(FULL, incl, off);
+    if (lane >= off) incl += v;
+  }
+  unsigned c = incl - mine;
+  if (lane < cnt) {
+    g.cbase[lane] = (int)c;
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-      if (!(bits & (1u << f)) || ((g.nbpos[mi] >> (8 * f)) & 0xffu) != 0xffu) continue;
-      const int nb = nb_elem(a.nx, a.ny, e, f);
-      if (nb < 0 || lane >= Q) continue;
-      g.ext[(mi * 4 + f) * Q + lane] = ldcg(a.out + ((size_t)d * a.E + nb) * N + face_dof<P>((f + 2) & 3, lane));
+      if (!((info.y >> f) & 1u) || !((info.y >> (4 + f)) & 1u)) continue;
+      g.cpl[c++] = (uint32_t)lane | ((uint32_t)f << 8) | (((nbp >> (8 * f)) & 0xffu) << 16) |
+                   ((uint32_t)rec_slot_of(info.z, f) << 24);
     }
+  }
+  const int total = (int)__shfl_sync(FULL, incl, 31);
+  if (lane == 0) {
+    g.cbase[cnt] = total;
+    g.m = cnt;
+    g.nt = total * Q;
+    g.gid = gid;
+  }
+  for (int t = lane; t < cnt * N; t += 32) g.z[t] = a.y[(size_t)(first + t / N) * L::kYStride + t % N];
+  const int nt = total * Q;
+  const T* Tg = a.grec + a.grp_toff[gid];
+  if (nt <= kGroupSmemTrace)
+    for (int t = lane; t < nt * nt; t += 32) g.tinv[t] = Tg[t];
+  __syncwarp();
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void group_solve_direct(const SweepArgs<T>& a, int d, int s0, GroupSmem<P, T>& g) {
+  constexpr int Q = P + 1, N = Q * Q;
+  using L = Rec<P, T>;
+  const int lane = threadIdx.x & 31;
+  const int first = a.slot_first[s0];
+  const int m = g.m, nt = g.nt;
+  // z: y minus the couplings to elements outside the group (earlier levels)
+  for (int idx = lane; idx < m * N; idx += 32) {
+    const int mi = idx / N, i = idx % N;
+    const uint4 info = g.info[mi];
+    const char* r = L::s_at(a.rec, first + mi);
+    const char* rx = L::x_at(a.recx, first + mi);
+    T z = g.z[idx];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const int sl = rec_slot_of(info.z, f);
+      if (sl < 0 || ((info.y >> (4 + f)) & 1u)) continue;
+      const int nb = nb_elem(a.nx, a.ny, (int)info.x, f);
+      z -= face_term<P, T>(L::slot(r, rx, sl), a.out + ((size_t)d * a.E + nb) * N, f, i);
+    }
+    g.z[idx] = z;
   }
   __syncwarp();
-  int it = 0;
-  bool conv = false;
-  for (; it < a.max_inner; ++it) {
-    T dmax = 0, amax = 0;
-    for (int mi = 0; mi < cnt; ++mi) {
-      const char* r = L::s_at(a.rec, first + mi);
-      const char* rx = L::x_at(a.recx, first + mi);
-      const unsigned faces = g.info[mi].z;
-      if (act) {
-        T y = g.y[mi * N + i];
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          const int sl = rec_slot_of(faces, f);
-          if (sl < 0) continue;
-          const T* W = L::slot(r, rx, sl);
-          const unsigned pos = (g.nbpos[mi] >> (8 * f)) & 0xffu;
-          if (pos != 0xffu) {
-            if (it == 0 && (int)pos >= mi) continue;  // not computed yet in the first sweep
-#pragma unroll
-            for (int t = 0; t < Q; ++t) y -= W[t * N + i] * g.psi[pos * N + face_dof<P>((f + 2) & 3, t)];
-          } else {
-#pragma unroll
-            for (int t = 0; t < Q; ++t) y -= W[t * N + i] * g.ext[(mi * 4 + f) * Q + t];
-          }
-        }
-        if (it > 0) dmax = fmax(dmax, fabs(y - g.psi[mi * N + i]));
-        amax = fmax(amax, fabs(y));
-        g.psi[mi * N + i] = y;
-      }
-      __syncwarp();
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      dmax = fmax(dmax, __shfl_xor_sync(FULL, dmax, off));
-      amax = fmax(amax, __shfl_xor_sync(FULL, amax, off));
-    }
-    if (it > 0 && dmax <= a.tol * amax) { conv = true; ++it; break; }
+  for (int j = lane; j < nt; j += 32) {
+    const uint32_t cp = g.cpl[j / Q];
+    const int b = (int)((cp >> 16) & 0xffu), f = (int)((cp >> 8) & 0xffu);
+    g.rhs[j] = g.z[b * N + face_dof<P>((f + 2) & 3, j % Q)];
   }
-  if (lane == 0) {
-    if (!conv) atomicOr(a.status, kDevNotConverged);
-    atomicMax(a.status + 2, (unsigned)it);
+  __syncwarp();
+  const T* Tm = nt <= kGroupSmemTrace ? g.tinv : a.grec + a.grp_toff[g.gid];
+  for (int r = lane; r < nt; r += 32) {
+    T acc0 = 0, acc1 = 0;
+    int j = 0;
+    for (; j + 1 < nt; j += 2) {
+      acc0 += Tm[j * nt + r] * g.rhs[j];
+      acc1 += Tm[(j + 1) * nt + r] * g.rhs[j + 1];
+    }
+    if (j < nt) acc0 += Tm[j * nt + r] * g.rhs[j];
+    g.tau[r] = acc0 + acc1;
   }
-  if (act)
-    for (int mi = 0; mi < cnt; ++mi)
-      a.out[((size_t)d * a.E + g.info[mi].x) * N + i] = g.psi[mi * N + i];
+  __syncwarp();
+  for (int idx = lane; idx < m * N; idx += 32) {
+    const int mi = idx / N, i = idx % N;
+    const char* r = L::s_at(a.rec, first + mi);
+    const char* rx = L::x_at(a.recx, first + mi);
+    T psi = g.z[idx];
+    for (int c = g.cbase[mi]; c < g.cbase[mi + 1]; ++c) {
+      const T* W = L::slot(r, rx, (int)(g.cpl[c] >> 24));
+#pragma unroll
+      for (int t = 0; t < Q; ++t) psi -= W[t * N + i] * g.tau[c * Q + t];
+    }
+    a.out[((size_t)d * a.E + g.info[mi].x) * N + i] = psi;
+  }
   __syncwarp();
 }
 
@@ -336,8 +366,18 @@ struct SweepSmem {
   alignas(16) unsigned char rec[2][kSweepRounds][SPC][Rec<P, T>::kStaged];
   alignas(16) unsigned char y[2][kSweepRounds][SPC][Rec<P, T>::kYBytes];
   uint64_t bar[2];
-  GroupSmem<P, T> group;
 };
+
+// dynamic shared memory of a sweep CTA: one SweepSmem per warp, then one GroupSmem per
+// group warp of the cluster (group warps are the cluster's last warps, all in its last CTA)
+__host__ __device__ constexpr int sweep_group_warps(int cluster_warps) {
+  return cluster_warps >= 16 ? cluster_warps / 16 : 1;
+}
+template <int P, typename T>
+__host__ __device__ constexpr size_t sweep_smem_bytes(int cta_warps, int cluster_warps) {
+  return sizeof(SweepSmem<P, T>) * (size_t)cta_warps +
+         sizeof(GroupSmem<P, T>) * (size_t)sweep_group_warps(cluster_warps);
+}
 
 constexpr uint32_t kStageWaitIters = 1u << 26;
 
@@ -355,11 +395,15 @@ __device__ __forceinline__ void sweep_direction(const SweepArgs<T>& a, int d) {
   const int cs = a.cluster_size;
   const int nw = cs * (blockDim.x >> 5);
   const int gw = (blockIdx.x % cs) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int ng = nw >= 16 ? nw / 16 : 1;
+  const int ng = sweep_group_warps(nw);
   const int nws = nw > ng ? nw - ng : nw;   // one-warp clusters do both kinds
   const bool singles = gw < nws;
   const bool groups = gw >= nws || nw == 1;
   const int gidx = nw == 1 ? 0 : gw - nws;
+  GroupSmem<P, T>* gsm = reinterpret_cast<GroupSmem<P, T>*>(
+      sweep_smem + sizeof(SweepSmem<P, T>) * (blockDim.x >> 5));
+  GroupSmem<P, T>& gs = gsm[groups ? gidx : 0];
+  auto direct = [&](int slot) { return a.slot_gid != nullptr && a.slot_gid[slot] >= 0; };
   const int k0 = a.dir_lev0[d], k1 = a.dir_lev0[d + 1];
   const int i = lane % N;
   const int s_lane = lane / N;              // task slot of this lane inside a round
@@ -371,11 +415,28 @@ __device__ __forceinline__ void sweep_direction(const SweepArgs<T>& a, int d) {
     mbar_fence_init();
   }
   __syncwarp();
+  // level table window in registers: lane j holds the table entries of levels kb + j and
+  // kb + 32 + j; a level's entries are read with a shuffle, so the tables never sit on
+  // the per-level critical path
+  constexpr unsigned FULL = 0xffffffffu;
+  int kb = k0;
+  int lb0, lg0, lm0, lb1, lg1, lm1;
+  auto load_win = [&](int base, int& lb, int& lg, int& lm) {
+    const int kk = base + lane;
+    lb = kk <= k1 ? a.lev_begin[kk] : 0;
+    lg = kk < k1 ? a.lev_gbegin[kk] : 0;
+    lm = kk < k1 ? a.lev_mbegin[kk] : 0;
+  };
+  load_win(k0, lb0, lg0, lm0);
+  load_win(k0 + 32, lb1, lg1, lm1);
+  auto lev_b = [&](int kk) { const int j = kk - kb; return __shfl_sync(FULL, j < 32 ? lb0 : lb1, j & 31); };
+  auto lev_g = [&](int kk) { const int j = kk - kb; return __shfl_sync(FULL, j < 32 ? lg0 : lg1, j & 31); };
+  auto lev_m = [&](int kk) { const int j = kk - kb; return __shfl_sync(FULL, j < 32 ? lm0 : lm1, j & 31); };
   unsigned phase[2] = {0u, 0u};
   bool pending[2] = {false, false};
   // stage level k into buffer b: up to kSweepRounds rounds of SPC consecutive members
   auto stage_level = [&](int k, int b) {
-    const int n = a.lev_gbegin[k] - a.lev_begin[k], mb = a.lev_mbegin[k];
+    const int n = lev_g(k) - lev_b(k), mb = lev_m(k);
     unsigned bytes = 0;
     int cnt[kSweepRounds];
 #pragma unroll
@@ -412,19 +473,24 @@ __device__ __forceinline__ void sweep_direction(const SweepArgs<T>& a, int d) {
     stage_level(k0, 0);
     if (k0 + 1 < k1) stage_level(k0 + 1, 1);
   }
-  int staged = -1;   // group slot whose static data sits in sm.group
+  int staged = -1;   // group slot whose static data sits in gs
   if (groups) {
-    const int g0 = a.lev_gbegin[k0] + gidx;
-    if (g0 < a.lev_begin[k0 + 1] && a.slot_count[g0] <= group_smem_max<P, T>()) {
-      group_stage_static<P, T>(a, g0, sm.group);
+    const int g0 = lev_g(k0) + gidx;
+    if (g0 < lev_b(k0 + 1) && direct(g0)) {
+      group_stage<P, T>(a, g0, gs);
       staged = g0;
     }
   }
   for (int k = k0; k < k1; ++k) {
     const int b = (k - k0) & 1;
-    const int sb = a.lev_begin[k], sg = a.lev_gbegin[k], se = a.lev_begin[k + 1];
+    if (k - kb >= 32) {   // advance the window; the new half is first read 32 levels on
+      kb += 32;
+      lb0 = lb1; lg0 = lg1; lm0 = lm1;
+      load_win(kb + 32, lb1, lg1, lm1);
+    }
+    const int sb = lev_b(k), sg = lev_g(k), se = lev_b(k + 1);
     if (singles) {
-      const int nsingle = sg - sb, mb = a.lev_mbegin[k];
+      const int nsingle = sg - sb, mb = lev_m(k);
       wait_level(b);
       // staged rounds: issue every upwind load first, then the FMAs
       T u[kSweepRounds][2][Q];
@@ -492,9 +558,9 @@ __device__ __forceinline__ void sweep_direction(const SweepArgs<T>& a, int d) {
     }
     if (groups) {
       for (int g = sg + gidx; g < se; g += ng) {
-        if (a.slot_count[g] <= group_smem_max<P, T>()) {
-          if (staged != g) group_stage_static<P, T>(a, g, sm.group);
-          group_solve_smem<P, T, MODE>(a, d, g, sm.group);
+        if (direct(g)) {
+          if (staged != g) group_stage<P, T>(a, g, gs);
+          group_solve_direct<P, T>(a, d, g, gs);
         } else {
           group_solve<P, T, MODE>(a, d, g);
         }
@@ -505,9 +571,9 @@ __device__ __forceinline__ void sweep_direction(const SweepArgs<T>& a, int d) {
     cluster_arrive();
     if (singles && k + 2 < k1) stage_level(k + 2, b);
     if (groups && k + 1 < k1) {
-      const int g1 = a.lev_gbegin[k + 1] + gidx;
-      if (g1 < a.lev_begin[k + 2] && a.slot_count[g1] <= group_smem_max<P, T>()) {
-        group_stage_static<P, T>(a, g1, sm.group);
+      const int g1 = lev_g(k + 1) + gidx;
+      if (g1 < lev_b(k + 2) && direct(g1)) {
+        group_stage<P, T>(a, g1, gs);
         staged = g1;
       }
     }
@@ -520,14 +586,14 @@ __device__ __forceinline__ void sweep_direction(const SweepArgs<T>& a, int d) {
 
 // one cluster per direction of one problem
 template <int P, typename T, int MODE>
-__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs<T> a) {
+__global__ void __maxnreg__(128) sweep_kernel(SweepArgs<T> a) {
   sweep_direction<P, T, MODE>(a, blockIdx.x / a.cluster_size);
 }
 
 // batch of independent problems of one DG order: cluster c runs direction cmap[c].y of
 // problem cmap[c].x, whose arguments sit in tab
 template <int P, typename T, int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __maxnreg__(128)
 sweep_batch_kernel(const SweepArgs<T>* __restrict__ tab, const int2* __restrict__ cmap, int cluster_size) {
   const int2 pd = cmap[blockIdx.x / cluster_size];
   sweep_direction<P, T, MODE>(tab[pd.x], pd.y);
@@ -672,6 +738,7 @@ struct SweepCall {
   int precision;
   int cluster_size;  // CTAs per direction cluster
   int cta_warps;     // warps per CTA
+  bool group_iterative;  // solve every coupled group by the inner iteration
 };
 
 // Host-side arguments of one problem's sweep (also the batch table entries).
@@ -688,6 +755,12 @@ static vef_status make_sweep_args(const SweepCall& c, const double* rhs, T* out,
   a.member_nbpos = S.member_nbpos;
   a.slot_first = S.slot_first;
   a.slot_count = S.slot_count;
+  const void* grec = std::is_same<T, double>::value ? S.grec64 : S.grec32;
+  if (!c.group_iterative && S.ngroups > 0 && grec) {
+    a.slot_gid = S.slot_gid;
+    a.grp_toff = S.grp_toff;
+    a.grec = (const T*)grec;
+  }
   a.code = S.member_code;
   a.member_of = S.member_of;
   a.finfo = S.faceinfo;
@@ -742,15 +815,50 @@ static vef_status cluster_config(K kernel, long long clusters, int cs, int warps
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cfg.dynamicSmemBytes = sizeof(SweepSmem<P, T>) * (size_t)warps;
+  cfg.dynamicSmemBytes = sweep_smem_bytes<P, T>(warps, cs * warps);
   VEF_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)cfg.dynamicSmemBytes));
   if (cs > 8) VEF_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   return VEF_OK;
 }
 
+// Cluster shape of a sweep when the caller gives none: 8-warp CTAs and the largest
+// cluster (at most 8 CTAs, the portable limit) for which the occupancy calculator
+// reports room for all D direction clusters at once.  Directions never wait on each
+// other, but a cluster that does not fit starts only when another has finished, which
+// doubles the critical path.
 template <int P, typename T, int MODE>
-static vef_status launch_sweep(const SweepCall& c, const double* rhs, T* out) {
+static vef_status auto_tile(int D, int& cs_out, int& warps_out) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> cache;   // (device, D) -> CTAs per cluster
+  int dev = 0;
+  VEF_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  warps_out = 8;
+  auto it = cache.find({dev, D});
+  if (it != cache.end()) { cs_out = it->second; return VEF_OK; }
+  int best = 1;
+  for (int cs = 8; cs >= 1; --cs) {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    vef_status st = cluster_config<P, T>(sweep_kernel<P, T, MODE>, 1, cs, warps_out, nullptr, cfg, attr);
+    if (st != VEF_OK) return st;
+    int fit = 0;
+    VEF_CUDA_TRY(cudaOccupancyMaxActiveClusters(&fit, sweep_kernel<P, T, MODE>, &cfg));
+    if (fit >= D) { best = cs; break; }
+  }
+  cache[{dev, D}] = best;
+  cs_out = best;
+  return VEF_OK;
+}
+
+template <int P, typename T, int MODE>
+static vef_status launch_sweep(const SweepCall& c0, const double* rhs, T* out) {
+  SweepCall c = c0;
+  if (c.cluster_size == 0) {
+    vef_status st = auto_tile<P, T, MODE>(c.S->D, c.cluster_size, c.cta_warps);
+    if (st != VEF_OK) return st;
+  }
   SweepArgs<T> a;
   vef_status st = make_sweep_args<P, T>(c, rhs, out, a);
   if (st != VEF_OK) return st;
@@ -906,11 +1014,11 @@ static void fill_opts(const vef_opts* o, SweepCall& c) {
   const double deftol = c.precision == VEF_FP64 ? 1e-15 : 1e-13;
   c.tol = (o && o->tol > 0.0) ? o->tol : deftol;
   c.max_passes = (o && o->max_passes > 0) ? o->max_passes : 8;
-  // tile_override = 100 * (CTAs per direction cluster) + (warps per CTA)
-  const int t = (o && o->tile_override > 0) ? o->tile_override
-                                             : (c.precision == VEF_FP64 ? kDefaultTile64 : kDefaultTile32);
-  c.cluster_size = std::min(16, std::max(1, t / 100));
-  c.cta_warps = std::min(8, std::max(1, t % 100));
+  // tile_override = 100 * (CTAs per direction cluster) + (warps per CTA); 0 = automatic
+  const int t = (o && o->tile_override > 0) ? o->tile_override : 0;
+  c.cluster_size = t ? std::min(16, std::max(1, t / 100)) : 0;
+  c.cta_warps = t ? std::min(8, std::max(1, t % 100)) : 0;
+  c.group_iterative = o && (o->flags & VEF_GROUPS_ITERATIVE);
 }
 
 static void schedule_info(const Schedule& S, vef_info* info) {

@@ -11,14 +11,14 @@ from oracle.transport import Discretization, sweep as o_sweep, residual as o_res
 pytestmark = pytest.mark.gpu
 
 
-def _run(prob, precision="fp64", info=True):
+def _run(prob, precision="fp64", info=True, **kw):
     from paper_2301_04758_gb300.api import Mesh
     mesh = Mesh(prob["nx"], prob["ny"], prob["m"], prob["p"], prob["alpha"])
     src = prob["source"]
     out = mesh.sweep(dev(prob["sigma_t"]), dev(prob["sigma_s"]), prob["omega"], prob["weights"],
                      phi_in=None if prob["phi_in"] is None else dev(prob["phi_in"]),
                      source=dev(src), inflow=None if prob["inflow"] is None else dev(prob["inflow"]),
-                     precision=precision, info=info)
+                     precision=precision, info=info, **kw)
     return mesh, out
 
 
@@ -51,15 +51,36 @@ def test_curved_heterogeneous_all_orders(lib, p):
     assert rel(host(psi), ref) < 1e-12, info
 
 
+@pytest.mark.parametrize("groups", ["direct", "iterative"])
 @pytest.mark.parametrize("sn", [8, 12])
-def test_curved_with_coupled_groups(lib, sn):
+def test_curved_with_coupled_groups(lib, sn, groups):
     """Strong distortion gives faces that are part inflow, part outflow: the coupled
-    element groups must be solved to round-off, not lagged."""
+    element groups must be solved to round-off, not lagged.  At S12 the largest groups
+    have 8 elements and 42 trace values, so both the shared-memory and the global-memory
+    form of the direct solve run; "iterative" forces the inner Gauss-Seidel for all."""
     prob = random_problem(20, 20, 3, 0.1, 2, sn, seed=3, sigma_range=(-1.0, 0.5))
-    _, (psi, info) = _run(prob)
+    _, (psi, info) = _run(prob, groups=groups)
     disc, ref = _oracle(prob)
     assert info["coupled_groups"] > 0, info
     assert rel(host(psi), ref) < 1e-12, info
+    if groups == "direct":
+        assert info["max_inner_iterations"] == 0, info
+    else:
+        assert info["max_inner_iterations"] >= 2, info
+
+
+def test_large_groups_mix_direct_and_iterative(lib):
+    """alpha = 0.15 on a 16x16 mesh at S16 gives groups of up to ~36 elements whose trace
+    systems exceed 128 values: those fall back to the inner iteration while the smaller
+    groups of the same sweep are solved directly."""
+    prob = random_problem(16, 16, 3, 0.15, 2, 16, seed=21, sigma_range=(-1.0, 0.5))
+    _, (psi, info) = _run(prob)
+    disc, ref = _oracle(prob)
+    assert info["coupled_groups"] > 0, info
+    assert info["max_inner_iterations"] >= 2, info
+    assert rel(host(psi), ref) < 1e-12, info
+    _, (psi_it, _) = _run(prob, groups="iterative")
+    assert rel(host(psi), host(psi_it)) < 1e-12
 
 
 def test_anisotropic_source_and_inflow(lib):
