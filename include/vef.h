@@ -93,7 +93,7 @@ typedef struct {
   int max_passes;    /* cap on defect-correction passes (default 8) and, x4, on inner
                         coupled-group iterations */
   int tile_override; /* 0 = library choice; else 100 * (CTAs per direction cluster, 1..16)
-                        + (warps per CTA, 1..8) of the sweep kernel */
+                        + (warps per CTA, 1..16) of the sweep kernel */
   int flags;         /* bit set of VEF_GROUPS_ITERATIVE (default 0: direct group solves) */
 } vef_opts;
 

@@ -309,7 +309,7 @@ assemble64_kernel(long long nmem, const uint32_t* __restrict__ code, const uint1
 // face, then face node; the sweep numbers them the same way.
 template <int P, typename T>
 __global__ void __launch_bounds__(128)
-group_factor_kernel(const int* __restrict__ grp_slot, const int* __restrict__ grp_nt,
+group_factor_kernel(int g0, const int* __restrict__ grp_slot, const int* __restrict__ grp_nt,
                     const long long* __restrict__ grp_toff, const int* __restrict__ slot_first,
                     const int* __restrict__ slot_count, const uint32_t* __restrict__ member_nbpos,
                     const T* __restrict__ rec, long long nmem, T* __restrict__ grec,
@@ -323,7 +323,7 @@ group_factor_kernel(const int* __restrict__ grp_slot, const int* __restrict__ gr
   __shared__ int perm[kGroupMaxTrace];
   __shared__ double colk[kGroupMaxTrace];
   __shared__ int piv_row, ncpl;
-  const int g = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+  const int g = g0 + (int)blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
   const int sl = grp_slot[g], nt = grp_nt[g];
   const int first = slot_first[sl], m = slot_count[sl];
   const char* recx = (const char*)rec + nmem * (long long)L::kStaged;
@@ -428,13 +428,20 @@ static vef_status launch_group_factor(Schedule& S, const void* rec, cudaStream_t
     vef_status st = ensure_buffer(gp, &cap, (size_t)std::max(1LL, S.grec_elems) * sizeof(T));
     if (st != VEF_OK) return st;
   }
-  const size_t smem = (size_t)S.max_nt * S.max_nt * sizeof(double);
-  VEF_CUDA_TRY(cudaFuncSetAttribute(group_factor_kernel<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-  group_factor_kernel<P, T><<<(unsigned)S.ngroups, 128, smem, stream>>>(
-      S.grp_slot, S.grp_nt, S.grp_toff, S.slot_first, S.slot_count, S.member_nbpos, (const T*)rec,
-      S.members, (T*)*gp, status);
-  VEF_CUDA_TRY(cudaGetLastError());
+  // groups are numbered by trace-system size: the small ones get a launch with 8 KB of
+  // shared memory per CTA, the rest one sized for the largest
+  const long long parts[3] = {0, S.ngroups_small, S.ngroups};
+  const int nts[2] = {std::min(S.max_nt, kGroupSmemTrace), S.max_nt};
+  for (int k = 0; k < 2; ++k) {
+    if (parts[k + 1] == parts[k]) continue;
+    const size_t smem = (size_t)nts[k] * nts[k] * sizeof(double);
+    VEF_CUDA_TRY(cudaFuncSetAttribute(group_factor_kernel<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    group_factor_kernel<P, T><<<(unsigned)(parts[k + 1] - parts[k]), 128, smem, stream>>>(
+        (int)parts[k], S.grp_slot, S.grp_nt, S.grp_toff, S.slot_first, S.slot_count, S.member_nbpos,
+        (const T*)rec, S.members, (T*)*gp, status);
+    VEF_CUDA_TRY(cudaGetLastError());
+  }
   return VEF_OK;
 }
 

@@ -362,6 +362,7 @@ Schedule* get_schedule(Mesh* mesh, const double* omega, const double* weights, i
     const int Q = M.p + 1;
     std::vector<int> slot_gid(slot_first.size(), -1), grp_slot, grp_nt;
     std::vector<long long> grp_toff(1, 0);
+    std::vector<std::pair<int, int>> direct;   // (nt, slot)
     for (size_t sl = 0; sl < slot_first.size(); ++sl) {
       const int cnt = slot_count[sl];
       if (cnt == 1 || cnt > group_direct_members(M.p)) continue;
@@ -374,12 +375,20 @@ Schedule* get_schedule(Mesh* mesh, const double* omega, const double* weights, i
       }
       const int nt = couplings * Q;
       if (nt == 0 || nt > kGroupMaxTrace) continue;
-      slot_gid[sl] = (int)grp_slot.size();
-      grp_slot.push_back((int)sl);
-      grp_nt.push_back(nt);
+      direct.push_back({nt, (int)sl});
+    }
+    // groups numbered by size, so the factorisation can give the small trace systems
+    // (the great majority) a launch with little shared memory per CTA
+    std::stable_sort(direct.begin(), direct.end(),
+                     [](const std::pair<int, int>& x, const std::pair<int, int>& y) { return x.first < y.first; });
+    for (const auto& g : direct) {
+      slot_gid[g.second] = (int)grp_slot.size();
+      grp_slot.push_back(g.second);
+      grp_nt.push_back(g.first);
       // offsets rounded to 4 entries keep every inverse 16-byte aligned in both precisions
-      grp_toff.push_back(grp_toff.back() + ((long long)nt * nt + 3) / 4 * 4);
-      S->max_nt = std::max(S->max_nt, nt);
+      grp_toff.push_back(grp_toff.back() + ((long long)g.first * g.first + 3) / 4 * 4);
+      S->max_nt = std::max(S->max_nt, g.first);
+      if (g.first <= kGroupSmemTrace) ++S->ngroups_small;
     }
     S->ngroups = (long long)grp_slot.size();
     S->grec_elems = grp_toff.back();

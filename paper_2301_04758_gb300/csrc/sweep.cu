@@ -408,6 +408,10 @@ __device__ __forceinline__ void sweep_direction(const SweepArgs<T>& a, int d) {
   const int i = lane % N;
   const int s_lane = lane / N;              // task slot of this lane inside a round
   const int stride = nws * SPC;
+  // task offset of this warp at level k: the warps' order rotates from level to level, so
+  // the warps that take a level's extra round are not the ones that took the previous
+  // level's (those finish their staging last and would start every level late)
+  auto wbase = [&](int k) { return ((gw + (k - k0) * 17) % nws) * SPC; };
   const bool lane_ok = singles && lane < SPC * N;
   if (lane == 0) {
     mbar_init(&sm.bar[0], 1);
@@ -441,7 +445,7 @@ __device__ __forceinline__ void sweep_direction(const SweepArgs<T>& a, int d) {
     int cnt[kSweepRounds];
 #pragma unroll
     for (int r = 0; r < kSweepRounds; ++r) {
-      const int t0 = gw * SPC + r * stride;
+      const int t0 = wbase(k) + r * stride;
       cnt[r] = singles ? max(0, min(SPC, n - t0)) : 0;
       bytes += (unsigned)cnt[r] * (L::kStaged + L::kYBytes);
     }
@@ -454,7 +458,7 @@ __device__ __forceinline__ void sweep_direction(const SweepArgs<T>& a, int d) {
 #pragma unroll
       for (int r = 0; r < kSweepRounds; ++r) {
         if (!cnt[r]) continue;
-        const long long m0 = mb + gw * SPC + r * stride;
+        const long long m0 = mb + wbase(k) + r * stride;
         bulk_g2s(sm.rec[b][r][0], L::s_at(a.rec, m0), (unsigned)cnt[r] * L::kStaged, &sm.bar[b]);
         bulk_g2s(sm.y[b][r][0], a.y + m0 * L::kYStride, (unsigned)cnt[r] * L::kYBytes, &sm.bar[b]);
       }
@@ -490,14 +494,14 @@ __device__ __forceinline__ void sweep_direction(const SweepArgs<T>& a, int d) {
     }
     const int sb = lev_b(k), sg = lev_g(k), se = lev_b(k + 1);
     if (singles) {
-      const int nsingle = sg - sb, mb = lev_m(k);
+      const int nsingle = sg - sb, mb = lev_m(k), wb = wbase(k);
       wait_level(b);
       // staged rounds: issue every upwind load first, then the FMAs
       T u[kSweepRounds][2][Q];
       bool has[kSweepRounds];
 #pragma unroll
       for (int r = 0; r < kSweepRounds; ++r) {
-        has[r] = lane_ok && gw * SPC + r * stride + s_lane < nsingle;
+        has[r] = lane_ok && wb + r * stride + s_lane < nsingle;
         if (!has[r]) continue;
         const uint4 info = *reinterpret_cast<const uint4*>(sm.rec[b][r][s_lane]);
 #pragma unroll
@@ -514,19 +518,22 @@ __device__ __forceinline__ void sweep_direction(const SweepArgs<T>& a, int d) {
         if (!has[r]) continue;
         const char* rs = (const char*)sm.rec[b][r][s_lane];
         const uint4 info = *reinterpret_cast<const uint4*>(rs);
+        // two independent FMA chains (one per slot) joined by one add: 2(p+1) + 1 FP64
+        // instructions on the critical path of the level
         T y0 = reinterpret_cast<const T*>(sm.y[b][r][s_lane])[i], y1 = 0;
 #pragma unroll
         for (int sl = 0; sl < 2; ++sl) {
           if (((info.z >> (8 * sl)) & 0xffu) == 0xffu) continue;
           const T* W = L::slot(rs, nullptr, sl);
-          T acc = 0;
 #pragma unroll
-          for (int t = 0; t < Q; ++t) acc += W[t * N + i] * u[r][sl][t];
-          if (sl == 0) y0 -= acc; else y1 -= acc;
+          for (int t = 0; t < Q; ++t) {
+            if (sl == 0) y0 = fma(-W[t * N + i], u[r][sl][t], y0);
+            else y1 = fma(-W[t * N + i], u[r][sl][t], y1);
+          }
         }
         T y = y0 + y1;
         if (((info.z >> 16) & 0xffu) != 0xffu) {   // rare: more than two interior inflow faces
-          const char* rg = L::x_at(a.recx, mb + gw * SPC + r * stride + s_lane);
+          const char* rg = L::x_at(a.recx, mb + wb + r * stride + s_lane);
           for (int sl = 2; sl < 4; ++sl) {
             const unsigned f = (info.z >> (8 * sl)) & 0xffu;
             if (f == 0xffu) continue;
@@ -538,8 +545,8 @@ __device__ __forceinline__ void sweep_direction(const SweepArgs<T>& a, int d) {
         a.out[((size_t)d * a.E + info.x) * N + i] = y;
       }
       // rounds beyond the staged ones (levels wider than kSweepRounds * stride)
-      for (int r = kSweepRounds; gw * SPC + r * stride < nsingle; ++r) {
-        const int tl = gw * SPC + r * stride + s_lane;
+      for (int r = kSweepRounds; wb + r * stride < nsingle; ++r) {
+        const int tl = wb + r * stride + s_lane;
         if (lane_ok && tl < nsingle) {
           const char* rg = L::s_at(a.rec, mb + tl);
           const char* rgx = L::x_at(a.recx, mb + tl);
@@ -1017,7 +1024,7 @@ static void fill_opts(const vef_opts* o, SweepCall& c) {
   // tile_override = 100 * (CTAs per direction cluster) + (warps per CTA); 0 = automatic
   const int t = (o && o->tile_override > 0) ? o->tile_override : 0;
   c.cluster_size = t ? std::min(16, std::max(1, t / 100)) : 0;
-  c.cta_warps = t ? std::min(8, std::max(1, t % 100)) : 0;
+  c.cta_warps = t ? std::min(16, std::max(1, t % 100)) : 0;
   c.group_iterative = o && (o->flags & VEF_GROUPS_ITERATIVE);
 }
 
@@ -1180,7 +1187,7 @@ namespace vef {
 
 template <int P>
 static vef_status batch_launch_class(vef_batch_s& B, BatchClass& C, int tile, cudaStream_t s) {
-  const int cs = std::min(16, std::max(1, tile / 100)), warps = std::min(8, std::max(1, tile % 100));
+  const int cs = std::min(16, std::max(1, tile / 100)), warps = std::min(16, std::max(1, tile % 100));
   for (size_t j = 0; j < C.probs.size(); ++j) C.tab_host[j].cluster_size = cs;
   VEF_CUDA_TRY(cudaMemcpyAsync(C.tab_dev, C.tab_host, C.probs.size() * sizeof(SweepArgs<double>),
                                cudaMemcpyHostToDevice, s));
