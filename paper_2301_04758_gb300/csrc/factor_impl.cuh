@@ -125,173 +125,273 @@ factor_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t*
   *reinterpret_cast<uint4*>(out) = make_uint4((unsigned)e, (unsigned)bits, faces, 0u);
 }
 
-// Row-parallel factorisation (used for p >= 3, where a whole element matrix per thread
-// spills): N lanes per (element, direction), lane i holds row i of A in registers.
-// Gauss-Jordan step k broadcasts the unscaled pivot row r = A[k][:] and every lane
-// applies one FMA per entry, row[j] += beta * r[j], with beta = -A[i][k] / r[k] on the
-// other rows and beta = 1/r[k] - 1 on the pivot row itself (which turns it into r / r[k]);
-// column k is then set to -A[i][k] / r[k], or 1 / r[k] on the pivot row.  Same FP64
-// instruction count per task as the thread-per-task form, no local memory.
+// Element-major factorisation (used for p >= 3, where a whole element matrix per thread
+// spills).  One CTA per element stages M, Gx, Gy and the face normals in shared memory
+// once and walks the element's directions, so the direction-independent element data is
+// read from memory once instead of D times.  A task (one direction) is held by LPU lanes,
+// each owning RPL rows of A (row i on lane i mod LPU, slot i / LPU).  Gauss-Jordan step k
+// broadcasts the unscaled pivot row r = A[k][:] from its owner lane, and every row
+// applies one FMA per entry, row[j] += beta r[j], with beta = -A[i][k] / r[k] on the other
+// rows and beta = 1/r[k] - 1 on the pivot row itself (which turns it into r / r[k]);
+// column k then becomes -A[i][k] / r[k], or 1 / r[k] on the pivot row.  With several rows
+// per lane the reciprocal and the broadcast are shared by RPL rows' FMAs.
+template <int P> struct ElemShape;
+template <> struct ElemShape<3> { static constexpr int RPL = 4, LPU = 4; };
+template <> struct ElemShape<4> { static constexpr int RPL = 2, LPU = 13; };
+
 template <int P, typename T>
 __global__ void __launch_bounds__(128)
-factor_rows_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t* __restrict__ finfo,
+factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const uint16_t* __restrict__ finfo,
                    const double* __restrict__ omega, const double* __restrict__ sigma_t,
                    const T* __restrict__ Mm, const T* __restrict__ Gxm, const T* __restrict__ Gym,
-                   const T* __restrict__ nds, FaceTab<T> ft, int nx, int ny, long long E,
+                   const T* __restrict__ nds, FaceTab<T> ft, int nx, int ny, long long nmem,
                    T* __restrict__ rec, unsigned int* status) {
   constexpr int Q = P + 1, N = Q * Q, NQ = P + 2;
-  constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
+  constexpr int RPL = ElemShape<P>::RPL, LPU = ElemShape<P>::LPU, UPW = 32 / LPU;
+  constexpr int LD = N + 1;                  // padded shared-memory row stride
+  constexpr int CPL = (Q * Q + LPU - 1) / LPU;   // inflow-coupling entries computed per lane
   constexpr unsigned FULL = 0xffffffffu;
   using L = Rec<P, T>;
-  const int lane = threadIdx.x & 31;
-  const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const long long m = gw * SPC + lane / N;
-  const int i = lane % N;
-  const int base = (lane / N) * N;
-  const bool valid = lane < SPC * N && m < nmem;
-  int d = 0, e = 0;
-  uint16_t bits = 0;
-  T mu = 0, eta = 0, st = 0;
-  if (valid) {
-    const uint32_t c = code[m];
-    d = (int)(c >> 22);
-    e = (int)(c & 0x3fffffu);
-    mu = (T)omega[2 * d];
-    eta = (T)omega[2 * d + 1];
-    st = (T)sigma_t[e];
-    bits = finfo[(size_t)d * E + e];
+  __shared__ T sM[N * LD], sX[N * LD], sY[N * LD];
+  __shared__ T sN[4 * NQ * 2];
+  __shared__ T sL[Q][NQ];   // face Lagrange table: lanes index it by their own face node
+  const long long e = blockIdx.x;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < N * N; idx += blockDim.x) {
+    const int r = idx / N, j = idx % N;
+    const size_t g = (size_t)e * N * N + idx;
+    sM[r * LD + j] = Mm[g];
+    sX[r * LD + j] = Gxm[g];
+    sY[r * LD + j] = Gym[g];
   }
-  T row[N];
-  {
-    const size_t o = ((size_t)e * N + i) * N;
+  for (int idx = tid; idx < 4 * NQ * 2; idx += blockDim.x) sN[idx] = nds[(size_t)e * 4 * NQ * 2 + idx];
+  if (tid < Q * NQ) sL[tid / NQ][tid % NQ] = ft.l[tid / NQ][tid % NQ];
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int u = lane / LPU, li = lane % LPU, base = u * LPU;
+  const T st = (T)sigma_t[e];
+  char* recx = (char*)rec + nmem * (long long)L::kStaged;
+  for (int d0 = warp * UPW; d0 < D; d0 += nwarps * UPW) {
+    const int d = d0 + u;
+    const bool valid = u < UPW && d < D;
+    const int dd = valid ? d : 0;
+    const T mu = (T)omega[2 * dd], eta = (T)omega[2 * dd + 1];
+    const uint16_t bits = finfo[(size_t)dd * E + e];
+    // assemble the owned rows: sigma_t M - mu Gx - eta Gy plus the outflow face terms
+    T row[RPL][N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) row[j] = valid ? st * Mm[o + j] - mu * Gxm[o + j] - eta * Gym[o + j] : (T)(i == j);
-  }
-  // face terms: outflow part into A; row `pos` of each face's inflow coupling Cin_f
-  const int ia = i % Q, ib = i / Q;
-  T cin[4][Q];
+    for (int r = 0; r < RPL; ++r) {
+      const int i = li + LPU * r;
 #pragma unroll
-  for (int f = 0; f < 4; ++f) {
-    int pos = -1;
-    if (f == 0 && ib == 0) pos = ia;
-    if (f == 1 && ia == P) pos = ib;
-    if (f == 2 && ib == P) pos = ia;
-    if (f == 3 && ia == 0) pos = ib;
+      for (int j = 0; j < N; ++j)
+        row[r][j] = i < N ? st * sM[i * LD + j] - mu * sX[i * LD + j] - eta * sY[i * LD + j] : (T)0;
+      if (i >= N) continue;
+      const int ia = i % Q, ib = i / Q;
 #pragma unroll
-    for (int t = 0; t < Q; ++t) cin[f][t] = 0;
-    if (pos < 0 || !valid) continue;
+      for (int f = 0; f < 4; ++f) {
+        int pos = -1;
+        if (f == 0 && ib == 0) pos = ia;
+        if (f == 1 && ia == P) pos = ib;
+        if (f == 2 && ib == P) pos = ia;
+        if (f == 3 && ia == 0) pos = ib;
+        if (pos < 0) continue;
 #pragma unroll
-    for (int k = 0; k < NQ; ++k) {
-      const T* v = nds + (((size_t)e * 4 + f) * NQ + k) * 2;
-      const T s = ft.w[k] * (mu * v[0] + eta * v[1]);
-      const T la = ft.l[pos][k];
+        for (int k = 0; k < NQ; ++k) {
+          const T s = ft.w[k] * (mu * sN[(f * NQ + k) * 2] + eta * sN[(f * NQ + k) * 2 + 1]);
+          if (!(s > (T)0)) continue;
+          const T sl = s * sL[pos][k];
 #pragma unroll
-      for (int t = 0; t < Q; ++t) {
-        const T ll = la * ft.l[t][k];
-        if (s > (T)0) row[face_dof<P>(f, t)] += s * ll;
-        else cin[f][t] += s * ll;
+          for (int t = 0; t < Q; ++t) row[r][face_dof<P>(f, t)] += sl * sL[t][k];
+        }
       }
     }
-  }
-  // in-place Gauss-Jordan, row-parallel
+    // in-place Gauss-Jordan over the task's LPU lanes
 #pragma unroll
-  for (int k = 0; k < N; ++k) {
-    T r[N];
+    for (int k = 0; k < N; ++k) {
+      const int owner = k % LPU, slot = k / LPU;
+      T pr[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) r[j] = __shfl_sync(FULL, row[j], (base + k) & 31);
-    if (valid && i == k && !(fabs(r[k]) > tiny_pivot<T>())) atomicOr(status, kDevSingular);
-    const T inv = (T)1 / r[k];
-    const T aik = row[k];
-    const T beta = (i == k) ? inv - (T)1 : -aik * inv;
+      for (int j = 0; j < N; ++j) pr[j] = __shfl_sync(FULL, row[slot][j], (base + owner) & 31);
+      if (valid && li == 0 && !(fabs(pr[k]) > tiny_pivot<T>())) atomicOr(status, kDevSingular);
+      const T inv = (T)1 / pr[k];
 #pragma unroll
-    for (int j = 0; j < N; ++j)
-      if (j != k) row[j] = fma(beta, r[j], row[j]);
-    row[k] = (i == k) ? inv : -aik * inv;
-  }
-  // records: A^{-1} column-major (lane i writes entry i of every column), W slots
-  char* out = L::s_at(rec, valid ? m : 0);
-  char* outx = L::x_at((char*)rec + nmem * (long long)L::kStaged, valid ? m : 0);
-  if (valid) {
-    T* ai = L::ainv(outx);
+      for (int r = 0; r < RPL; ++r) {
+        const int i = li + LPU * r;
+        const T aik = row[r][k];
+        const T beta = (i == k) ? inv - (T)1 : -aik * inv;
 #pragma unroll
-    for (int j = 0; j < N; ++j) ai[j * N + i] = row[j];
-  }
-  unsigned faces = 0xffffffffu;
-  int slot = 0;
-#pragma unroll
-  for (int f = 0; f < 4; ++f) {
-    const bool use = (bits & (1u << f)) && nb_elem(nx, ny, e, f) >= 0;
-    // W_f[i][t] = sum_a Ainv[i][face_dof(f, a)] Cin_f[a][t]; Cin_f row a lives on the lane
-    // holding face node a
-    T w[Q];
-#pragma unroll
-    for (int t = 0; t < Q; ++t) w[t] = 0;
-#pragma unroll
-    for (int a = 0; a < Q; ++a) {
-      const int src = base + face_dof<P>(f, a);
-#pragma unroll
-      for (int t = 0; t < Q; ++t) w[t] += row[face_dof<P>(f, a)] * __shfl_sync(FULL, cin[f][t], src & 31);
+        for (int j = 0; j < N; ++j)
+          if (j != k) row[r][j] = fma(beta, pr[j], row[r][j]);
+        row[r][k] = (i == k) ? inv : -aik * inv;
+      }
     }
-    if (valid && use) {
-      T* W = L::slot(out, outx, slot);
+    // records: A^{-1} column-major, then the W slots of the interior inflow faces
+    const long long m = valid ? (long long)member_of[(size_t)dd * E + e] : 0;
+    char* out = L::s_at(rec, m);
+    char* outx = L::x_at(recx, m);
+    if (valid) {
+      T* ai = L::ainv(outx);
 #pragma unroll
-      for (int t = 0; t < Q; ++t) W[t * N + i] = w[t];
-      if (i == 0) faces = (faces & ~(0xffu << (8 * slot))) | ((unsigned)f << (8 * slot));
-      ++slot;
+      for (int r = 0; r < RPL; ++r) {
+        const int i = li + LPU * r;
+        if (i >= N) continue;
+#pragma unroll
+        for (int j = 0; j < N; ++j) ai[j * N + i] = row[r][j];
+      }
     }
+    unsigned faces = 0xffffffffu;
+    int nslot = 0;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const bool use = valid && (bits & (1u << f)) && nb_elem(nx, ny, (int)e, f) >= 0;
+      if (!__any_sync(FULL, use)) continue;
+      // Cin_f[a][t] = sum_k min(c_k, 0) l_a(s_k) l_t(s_k), entries q = a Q + t spread over
+      // the task's lanes, then gathered
+      T cmine[CPL];
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        const int q = li + LPU * c;
+        T v = 0;
+        if (q < Q * Q) {
+          const int qa = q / Q, qt = q % Q;
+#pragma unroll
+          for (int k = 0; k < NQ; ++k) {
+            const T s = ft.w[k] * (mu * sN[(f * NQ + k) * 2] + eta * sN[(f * NQ + k) * 2 + 1]);
+            if (s < (T)0) v += s * sL[qa][k] * sL[qt][k];
+          }
+        }
+        cmine[c] = v;
+      }
+      T W[RPL][Q];
+#pragma unroll
+      for (int r = 0; r < RPL; ++r)
+#pragma unroll
+        for (int t = 0; t < Q; ++t) W[r][t] = 0;
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+#pragma unroll
+        for (int t = 0; t < Q; ++t) {
+          const int q = a * Q + t;
+          const T cat = __shfl_sync(FULL, cmine[q / LPU], (base + q % LPU) & 31);
+#pragma unroll
+          for (int r = 0; r < RPL; ++r) W[r][t] = fma(row[r][face_dof<P>(f, a)], cat, W[r][t]);
+        }
+      }
+      if (use) {
+        T* Wo = L::slot(out, outx, nslot);
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+          const int i = li + LPU * r;
+          if (i >= N) continue;
+#pragma unroll
+          for (int t = 0; t < Q; ++t) Wo[t * N + i] = W[r][t];
+        }
+        faces = (faces & ~(0xffu << (8 * nslot))) | ((unsigned)f << (8 * nslot));
+        ++nslot;
+      }
+    }
+    if (valid && li == 0) *reinterpret_cast<uint4*>(out) = make_uint4((unsigned)e, (unsigned)bits, faces, 0u);
   }
-  if (valid && i == 0) *reinterpret_cast<uint4*>(out) = make_uint4((unsigned)e, (unsigned)bits, faces, 0u);
 }
 
 // FP64 element matrix and inflow couplings of every (element, direction), for the FP64
-// residual of the mixed-precision defect correction: per task [A (n x n, row-major)]
+// residual of the mixed-precision defect correction: per task [A (n x n, column-major)]
 // [Cin of W slots 0..3 ((p+1) x (p+1), row a = own face node, column t = neighbour's)].
+// Element-major like factor_elem_kernel: one CTA per element holds M, Gx, Gy, the
+// normals and the face products l_a(s_k) l_t(s_k) in shared memory.  A task takes
+// LPU = max(n, 4(p+1)) lanes: lane i < n assembles row i of the volume part, lane
+// f (p+1) + a < 4 (p+1) forms row a of face f's outflow and inflow matrices, and the
+// outflow rows are shuffled to the lanes owning those matrix rows.  Every lane does
+// useful FP64 work and every store of A is coalesced.
 template <int P>
 __global__ void __launch_bounds__(128)
-assemble64_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t* __restrict__ finfo,
+assemble64_kernel(int D, long long E, const int* __restrict__ member_of, const uint16_t* __restrict__ finfo,
                   const double* __restrict__ omega, const double* __restrict__ sigma_t,
                   const double* __restrict__ Mm, const double* __restrict__ Gxm,
                   const double* __restrict__ Gym, const double* __restrict__ nds, FaceTab<double> ft,
-                  int nx, int ny, long long E, double* __restrict__ out) {
+                  int nx, int ny, double* __restrict__ out) {
   constexpr int Q = P + 1, N = Q * Q, NQ = P + 2, B = N * N + 4 * Q * Q;
-  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (m >= nmem) return;
-  const uint32_t c = code[m];
-  const int d = (int)(c >> 22), e = (int)(c & 0x3fffffu);
-  const double mu = omega[2 * d], eta = omega[2 * d + 1], st = sigma_t[e];
-  const uint16_t bits = finfo[(size_t)d * E + e];
-  double* A = out + m * (long long)B;
-  const double* Me = Mm + (size_t)e * N * N;
-  const double* Xe = Gxm + (size_t)e * N * N;
-  const double* Ye = Gym + (size_t)e * N * N;
-  for (int ij = 0; ij < N * N; ++ij) A[ij] = st * Me[ij] - mu * Xe[ij] - eta * Ye[ij];
-  int slot = 0;
-  for (int f = 0; f < 4; ++f) {
-    double cp[NQ], cm[NQ];
+  constexpr int LPU = N > 4 * Q ? N : 4 * Q;
+  constexpr int UPW = 32 / LPU;
+  constexpr int LD = N + 1;
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ double sM[N * LD], sX[N * LD], sY[N * LD];
+  __shared__ double sN[4 * NQ * 2];
+  __shared__ double sLL[Q][Q][NQ];
+  const long long e = blockIdx.x;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < N * N; idx += blockDim.x) {
+    const int r = idx / N, j = idx % N;
+    const size_t g = (size_t)e * N * N + idx;
+    sM[r * LD + j] = Mm[g];
+    sX[r * LD + j] = Gxm[g];
+    sY[r * LD + j] = Gym[g];
+  }
+  for (int idx = tid; idx < 4 * NQ * 2; idx += blockDim.x) sN[idx] = nds[(size_t)e * 4 * NQ * 2 + idx];
+  for (int idx = tid; idx < Q * Q * NQ; idx += blockDim.x) {
+    const int qa = idx / (Q * NQ), qt = (idx / NQ) % Q, k = idx % NQ;
+    sLL[qa][qt][k] = ft.l[qa][k] * ft.l[qt][k];
+  }
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int u = lane / LPU, li = lane % LPU, base = u * LPU;
+  const double st = sigma_t[e];
+  const int ia = li % Q, ib = li / Q;                 // node of row li (li < n)
+  const int ff = li / Q, fa = li % Q;                 // face row of lane li (li < 4 (p+1))
+  for (int d0 = warp * UPW; d0 < D; d0 += nwarps * UPW) {
+    const int d = d0 + u;
+    const bool valid = u < UPW && d < D;
+    const int dd = valid ? d : 0;
+    const double mu = omega[2 * dd], eta = omega[2 * dd + 1];
+    const uint16_t bits = finfo[(size_t)dd * E + e];
+    double row[N];
 #pragma unroll
-    for (int k = 0; k < NQ; ++k) {
-      const double* v = nds + (((size_t)e * 4 + f) * NQ + k) * 2;
-      const double sv = ft.w[k] * (mu * v[0] + eta * v[1]);
-      cp[k] = sv > 0.0 ? sv : 0.0;
-      cm[k] = sv < 0.0 ? sv : 0.0;
-    }
-    const bool inflow_nb = (bits & (1u << f)) && nb_elem(nx, ny, e, f) >= 0;
-    double* C = A + N * N + slot * Q * Q;
+    for (int j = 0; j < N; ++j)
+      row[j] = li < N ? st * sM[li * LD + j] - mu * sX[li * LD + j] - eta * sY[li * LD + j] : 0.0;
+    double fo[Q], ci[Q];
 #pragma unroll
-    for (int a = 0; a < Q; ++a)
+    for (int t = 0; t < Q; ++t) fo[t] = ci[t] = 0.0;
+    if (li < 4 * Q) {
 #pragma unroll
-      for (int b = 0; b < Q; ++b) {
-        double vo = 0, vi = 0;
+      for (int k = 0; k < NQ; ++k) {
+        const double c = ft.w[k] * (mu * sN[(ff * NQ + k) * 2] + eta * sN[(ff * NQ + k) * 2 + 1]);
+        const double cp = c > 0.0 ? c : 0.0, cm = c < 0.0 ? c : 0.0;
 #pragma unroll
-        for (int k = 0; k < NQ; ++k) {
-          const double ll = ft.l[a][k] * ft.l[b][k];
-          vo += cp[k] * ll;
-          vi += cm[k] * ll;
+        for (int t = 0; t < Q; ++t) {
+          fo[t] = fma(cp, sLL[fa][t][k], fo[t]);
+          ci[t] = fma(cm, sLL[fa][t][k], ci[t]);
         }
-        A[face_dof<P>(f, a) * N + face_dof<P>(f, b)] += vo;
-        if (inflow_nb) C[a * Q + b] = vi;
       }
-    if (inflow_nb) ++slot;
+    }
+    // outflow face rows onto the matrix rows they belong to
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      int pos = -1;
+      if (f == 0 && ib == 0) pos = ia;
+      if (f == 1 && ia == P) pos = ib;
+      if (f == 2 && ib == P) pos = ia;
+      if (f == 3 && ia == 0) pos = ib;
+      const int src = (base + f * Q + (pos > 0 ? pos : 0)) & 31;
+#pragma unroll
+      for (int t = 0; t < Q; ++t) {
+        const double v = __shfl_sync(FULL, fo[t], src);
+        if (li < N && pos >= 0) row[face_dof<P>(f, t)] += v;
+      }
+    }
+    if (!valid) continue;
+    double* blk = out + (long long)member_of[(size_t)d * E + e] * B;
+    if (li < N) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) blk[j * N + li] = row[j];
+    }
+    if (li < 4 * Q && (bits & (1u << ff)) && nb_elem(nx, ny, (int)e, ff) >= 0) {
+      int slot = 0;
+      for (int g = 0; g < ff; ++g)
+        if ((bits & (1u << g)) && nb_elem(nx, ny, (int)e, g) >= 0) ++slot;
+      double* C = blk + N * N + slot * Q * Q + fa * Q;
+#pragma unroll
+      for (int t = 0; t < Q; ++t) C[t] = ci[t];
+    }
   }
 }
 
@@ -472,18 +572,19 @@ static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, cud
       if (st != VEF_OK) return st;
     }
     KTimer kt(&M, VEF_K_FACTOR, stream);
-    assemble64_kernel<P><<<nblk(S.members, 128), 128, 0, stream>>>(
-        S.members, S.member_code, S.faceinfo, S.omega_dev, sigma_t, M.Mmat, M.Gx, M.Gy, M.nds,
-        make_facetab<double>(M.tab), M.nx, M.ny, M.E, (double*)S.a64);
+    constexpr int UPW = 32 / (N > 4 * Q ? N : 4 * Q);
+    const int warps = std::max(1, std::min(4, (S.D + UPW - 1) / UPW));
+    assemble64_kernel<P><<<(unsigned)M.E, 32 * warps, 0, stream>>>(
+        S.D, M.E, S.member_of, S.faceinfo, S.omega_dev, sigma_t, M.Mmat, M.Gx, M.Gy, M.nds,
+        make_facetab<double>(M.tab), M.nx, M.ny, (double*)S.a64);
   }
   KTimer kt(&M, VEF_K_FACTOR, stream);
-  if (P >= 3) {
-    constexpr int N = (P + 1) * (P + 1);
-    constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
-    const long long warps = (S.members + SPC - 1) / SPC;
-    factor_rows_kernel<P, T><<<nblk(warps * 32, 128), 128, 0, stream>>>(
-        S.members, S.member_code, S.faceinfo, S.omega_dev, sigma_t, Mm, Gx, Gy, nds,
-        make_facetab<T>(M.tab), M.nx, M.ny, M.E, (T*)*recp, M.dev_status);
+  if constexpr (P >= 3) {
+    constexpr int UPW = 32 / ElemShape<P>::LPU;
+    const int warps = std::max(1, std::min(4, (S.D + UPW - 1) / UPW));
+    factor_elem_kernel<P, T><<<(unsigned)M.E, 32 * warps, 0, stream>>>(
+        S.D, M.E, S.member_of, S.faceinfo, S.omega_dev, sigma_t, Mm, Gx, Gy, nds, make_facetab<T>(M.tab),
+        M.nx, M.ny, S.members, (T*)*recp, M.dev_status);
   } else {
     factor_kernel<P, T><<<nblk(S.members, 128), 128, 0, stream>>>(
         S.members, S.member_code, S.faceinfo, S.omega_dev, sigma_t, Mm, Gx, Gy, nds,

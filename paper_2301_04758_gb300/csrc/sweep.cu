@@ -644,7 +644,7 @@ residual_kernel(long long nmem, long long E, int nx, int ny, long long nbf,
     }
     double Apsi = 0.0;
 #pragma unroll
-    for (int j = 0; j < N; ++j) Apsi += blk[i * N + j] * pe[j];
+    for (int j = 0; j < N; ++j) Apsi += blk[j * N + i] * pe[j];   // A column-major
     const int ia = i % Q, ib = i / Q;
 #pragma unroll
     for (int f = 0; f < 4; ++f) {

@@ -77,3 +77,30 @@ def test_region_weights_match_oracle(lib):
         ref = region_weights(disc, lo, hi)
         got = host(mesh.region_weights(lo, hi))
         assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max() + 1e-18
+
+
+def test_autograd_transport_phi(lib):
+    """phi from transport_phi is differentiable: backward through the adjoint sweep gives
+    the oracle's gradients of R = int_region phi."""
+    from paper_2301_04758_gb300.api import Mesh
+    from paper_2301_04758_gb300.autograd import transport_phi
+    nx, m, alpha, p = 9, 3, 0.08, 2
+    om, w = level_symmetric(8)
+    E, n = nx * nx, (p + 1) ** 2
+    st, ss = seeded_media(E, 5, log10_range=(-1.0, 1.0))
+    rng = np.random.default_rng(9)
+    phi_in = rng.uniform(0.5, 1.5, (E, n))
+    q = np.ones((E, n))
+    disc = Discretization(nx, nx, m, alpha, p)
+    g = region_weights(disc)
+    psi = o_sweep(disc, om, w, st, ss, phi_in=phi_in, source=q)
+    _, dst, dss = o_adjoint(disc, om, w, st, ss, psi, g, phi_in=phi_in)
+    mesh = Mesh(nx, nx, m, p, alpha)
+    st_t = dev(st).requires_grad_()
+    ss_t = dev(ss).requires_grad_()
+    phi = transport_phi(mesh, st_t, ss_t, om, w, phi_in=dev(phi_in), source=dev(q))
+    assert rel(host(phi), np.einsum("d,den->en", w, psi)) < 1e-12
+    R = (dev(g) * phi).sum()
+    R.backward()
+    assert rel(host(st_t.grad), dst) < 1e-12
+    assert rel(host(ss_t.grad), dss) < 1e-12
