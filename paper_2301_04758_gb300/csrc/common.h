@@ -88,7 +88,7 @@ struct Schedule {
   int* grp_nt = nullptr;       // [ngroups]
   long long* grp_toff = nullptr;  // [ngroups + 1]
   long long ngroups = 0;
-  long long ngroups_small = 0; // groups [0, ngroups_small) have nt <= kGroupSmemTrace (ordered by nt)
+  long long ngroups_upto[3] = {0, 0, 0};  // groups (ordered by nt) with nt <= 8, 16, 32
   long long grec_elems = 0;    // entries of all inverses (grp_toff[ngroups])
   int max_nt = 0;
   void* grec64 = nullptr;      // trace-system inverses (lazily allocated): FP64 and FP32

@@ -395,6 +395,65 @@ assemble64_kernel(int D, long long E, const int* __restrict__ member_of, const u
   }
 }
 
+// Thread-per-task form of the FP64 assembly for p <= 2, where a whole element system
+// fits in one thread's registers and every FP64 instruction is useful on all lanes (the
+// element-major form wastes lanes on the face rows at these sizes).  Same output layout.
+template <int P>
+__global__ void __launch_bounds__(128)
+assemble64_thread_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t* __restrict__ finfo,
+                         const double* __restrict__ omega, const double* __restrict__ sigma_t,
+                         const double* __restrict__ Mm, const double* __restrict__ Gxm,
+                         const double* __restrict__ Gym, const double* __restrict__ nds, FaceTab<double> ft,
+                         int nx, int ny, long long E, double* __restrict__ out) {
+  constexpr int Q = P + 1, N = Q * Q, NQ = P + 2, B = N * N + 4 * Q * Q;
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (m >= nmem) return;
+  const uint32_t c = code[m];
+  const int d = (int)(c >> 22), e = (int)(c & 0x3fffffu);
+  const double mu = omega[2 * d], eta = omega[2 * d + 1], st = sigma_t[e];
+  const uint16_t bits = finfo[(size_t)d * E + e];
+  double* blk = out + m * (long long)B;
+  const double* Me = Mm + (size_t)e * N * N;
+  const double* Xe = Gxm + (size_t)e * N * N;
+  const double* Ye = Gym + (size_t)e * N * N;
+  double A[N * N];   // column-major
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) A[j * N + i] = st * Me[i * N + j] - mu * Xe[i * N + j] - eta * Ye[i * N + j];
+  int slot = 0;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    double cp[NQ], cm[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      const double* v = nds + (((size_t)e * 4 + f) * NQ + k) * 2;
+      const double sv = ft.w[k] * (mu * v[0] + eta * v[1]);
+      cp[k] = sv > 0.0 ? sv : 0.0;
+      cm[k] = sv < 0.0 ? sv : 0.0;
+    }
+    const bool inflow_nb = (bits & (1u << f)) && nb_elem(nx, ny, e, f) >= 0;
+    double* C = blk + N * N + slot * Q * Q;
+#pragma unroll
+    for (int a = 0; a < Q; ++a)
+#pragma unroll
+      for (int b = 0; b < Q; ++b) {
+        double vo = 0, vi = 0;
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+          const double ll = ft.l[a][k] * ft.l[b][k];
+          vo += cp[k] * ll;
+          vi += cm[k] * ll;
+        }
+        A[face_dof<P>(f, b) * N + face_dof<P>(f, a)] += vo;
+        if (inflow_nb) C[a * Q + b] = vi;
+      }
+    if (inflow_nb) ++slot;
+  }
+#pragma unroll
+  for (int q = 0; q < N * N; ++q) blk[q] = A[q];
+}
+
 // Trace system of a coupled element group.  Member a of a group solves
 //     psi_a = z_a - sum_{(a,f)} W_{a,f} tau_{a,f},
 // where z_a = A_a^{-1} b_a minus the couplings to elements outside the group, and the
@@ -448,16 +507,20 @@ group_factor_kernel(int g0, const int* __restrict__ grp_slot, const int* __restr
     if (tid == 0) atomicOr(status, kDevSingular);
     return;
   }
-  for (int idx = tid; idx < nt * nt; idx += nth) {
-    const int r = idx / nt, col = idx % nt;
-    const uint32_t c1 = cpl[r / Q], c2 = cpl[col / Q];
+  // rows by warp, columns by lane (no integer division by the runtime size)
+  const int lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
+  for (int r = wid; r < nt; r += nw) {
+    const uint32_t c1 = cpl[r / Q];
     const int b = (int)((c1 >> 16) & 0xffu), f = (int)((c1 >> 8) & 0xffu);
-    double v = r == col ? 1.0 : 0.0;
-    if ((int)(c2 & 0xffu) == b) {
-      const T* W = L::slot(L::s_at(rec, first + b), L::x_at(recx, first + b), (int)(c2 >> 24));
-      v += (double)W[(col % Q) * N + face_dof<P>((f + 2) & 3, r % Q)];
+    for (int col = lane; col < nt; col += 32) {
+      const uint32_t c2 = cpl[col / Q];
+      double v = r == col ? 1.0 : 0.0;
+      if ((int)(c2 & 0xffu) == b) {
+        const T* W = L::slot(L::s_at(rec, first + b), L::x_at(recx, first + b), (int)(c2 >> 24));
+        v += (double)W[(col % Q) * N + face_dof<P>((f + 2) & 3, r % Q)];
+      }
+      Mx[r * nt + col] = v;
     }
-    Mx[idx] = v;
   }
   for (int k = 0; k < nt; ++k) {
     __syncthreads();
@@ -494,10 +557,11 @@ group_factor_kernel(int g0, const int* __restrict__ grp_slot, const int* __restr
     __syncthreads();
     for (int j = tid; j < nt; j += nth) Mx[k * nt + j] = j == k ? inv : Mx[k * nt + j] * inv;
     __syncthreads();
-    for (int idx = tid; idx < nt * nt; idx += nth) {
-      const int i = idx / nt, j = idx % nt;
+    for (int i = wid; i < nt; i += nw) {
       if (i == k) continue;
-      Mx[idx] = j == k ? -colk[i] * inv : fma(-colk[i], Mx[k * nt + j], Mx[idx]);
+      const double ci = colk[i];
+      for (int j = lane; j < nt; j += 32)
+        Mx[i * nt + j] = j == k ? -ci * inv : fma(-ci, Mx[k * nt + j], Mx[i * nt + j]);
     }
   }
   // undo the row interchanges as column interchanges, last first
@@ -513,9 +577,128 @@ group_factor_kernel(int g0, const int* __restrict__ grp_slot, const int* __restr
   }
   __syncthreads();
   T* out = grec + grp_toff[g];
-  for (int idx = tid; idx < nt * nt; idx += nth) {
-    const int j = idx / nt, r = idx % nt;
-    out[idx] = (T)Mx[r * nt + j];
+  for (int j = wid; j < nt; j += nw)
+    for (int r = lane; r < nt; r += 32) out[j * nt + r] = (T)Mx[r * nt + j];
+}
+
+// Small trace systems (nt <= NTB <= 32): one warp per group, lane r holds row r of
+// I + R in registers; the pivot search is a warp argmax, row interchanges and the
+// pivot-row broadcast are shuffles.  Same algorithm as group_factor_kernel.
+template <int P, typename T, int NTB>
+__global__ void __launch_bounds__(128)
+group_factor_warp_kernel(int g0, int g1, const int* __restrict__ grp_slot, const int* __restrict__ grp_nt,
+                         const long long* __restrict__ grp_toff, const int* __restrict__ slot_first,
+                         const int* __restrict__ slot_count, const uint32_t* __restrict__ member_nbpos,
+                         const T* __restrict__ rec, long long nmem, T* __restrict__ grec,
+                         unsigned int* status) {
+  constexpr int Q = P + 1, N = Q * Q;
+  constexpr int NCW = NTB / Q + 1;
+  constexpr unsigned FULL = 0xffffffffu;
+  using L = Rec<P, T>;
+  __shared__ uint32_t cpl_s[4][NCW];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int g = g0 + (int)blockIdx.x * (int)(blockDim.x >> 5) + wib;
+  if (g >= g1) return;   // the whole warp
+  const int sl = grp_slot[g], nt = grp_nt[g];
+  const int first = slot_first[sl], m = slot_count[sl];   // m <= 32 for a direct group
+  const char* recx = (const char*)rec + nmem * (long long)L::kStaged;
+  uint32_t* cpl = cpl_s[wib];
+  uint4 info = make_uint4(0u, 0u, 0xffffffffu, 0u);
+  uint32_t nbp = 0xffffffffu;
+  if (lane < m) {
+    info = *reinterpret_cast<const uint4*>(L::s_at(rec, first + lane));
+    nbp = member_nbpos[first + lane];
+  }
+  const unsigned mine = lane < m ? (unsigned)__popc(info.y & (info.y >> 4) & 0xfu) : 0u;
+  unsigned incl = mine;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned v = __shfl_up_sync(FULL, incl, off);
+    if (lane >= off) incl += v;
+  }
+  const int total = (int)__shfl_sync(FULL, incl, 31);
+  if (total * Q != nt || nt > NTB) {   // schedule and records disagree
+    if (lane == 0) atomicOr(status, kDevSingular);
+    return;
+  }
+  if (lane < m) {
+    unsigned c = incl - mine;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      if (!((info.y >> f) & 1u) || !((info.y >> (4 + f)) & 1u)) continue;
+      cpl[c++] = (uint32_t)lane | ((uint32_t)f << 8) | (((nbp >> (8 * f)) & 0xffu) << 16) |
+                 ((uint32_t)rec_slot_of(info.z, f) << 24);
+    }
+  }
+  __syncwarp();
+  double row[NTB];
+  {
+    const uint32_t c1 = cpl[(lane < nt ? lane : 0) / Q];
+    const int b = (int)((c1 >> 16) & 0xffu), f = (int)((c1 >> 8) & 0xffu), s = lane % Q;
+#pragma unroll
+    for (int j = 0; j < NTB; ++j) {
+      double v = (lane == j && lane < nt) ? 1.0 : 0.0;
+      if (lane < nt && j < nt) {
+        const uint32_t c2 = cpl[j / Q];
+        if ((int)(c2 & 0xffu) == b) {
+          const T* W = L::slot(L::s_at(rec, first + b), L::x_at(recx, first + b), (int)(c2 >> 24));
+          v += (double)W[(j % Q) * N + face_dof<P>((f + 2) & 3, s)];
+        }
+      }
+      row[j] = v;
+    }
+  }
+  int myperm = lane;
+#pragma unroll
+  for (int k = 0; k < NTB; ++k) {
+    if (k >= nt) break;
+    double best = (lane >= k && lane < nt) ? fabs(row[k]) : -1.0;
+    int bi = lane;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double ob = __shfl_xor_sync(FULL, best, off);
+      const int oi = __shfl_xor_sync(FULL, bi, off);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0 && !(best > 1e-300)) atomicOr(status, kDevSingular);
+    if (lane == k) myperm = bi;
+    if (bi != k) {
+      const int src = lane == k ? bi : (lane == bi ? k : lane);
+#pragma unroll
+      for (int j = 0; j < NTB; ++j) row[j] = __shfl_sync(FULL, row[j], src);
+    }
+    double pr[NTB];
+#pragma unroll
+    for (int j = 0; j < NTB; ++j) pr[j] = __shfl_sync(FULL, row[j], k);
+    const double inv = 1.0 / pr[k];
+    const double aik = row[k];
+    const double beta = lane == k ? inv - 1.0 : -aik * inv;
+#pragma unroll
+    for (int j = 0; j < NTB; ++j)
+      if (j != k) row[j] = fma(beta, pr[j], row[j]);
+    row[k] = lane == k ? inv : -aik * inv;
+  }
+  // undo the row interchanges as column interchanges, last first
+#pragma unroll
+  for (int k = NTB - 1; k >= 0; --k) {
+    if (k >= nt) continue;
+    const int pk = __shfl_sync(FULL, myperm, k);
+    if (pk == k) continue;
+    const double vk = row[k];
+    double vp = 0.0;
+#pragma unroll
+    for (int j = 0; j < NTB; ++j)
+      if (j == pk) vp = row[j];
+#pragma unroll
+    for (int j = 0; j < NTB; ++j)
+      if (j == pk) row[j] = vk;
+    row[k] = vp;
+  }
+  if (lane < nt) {
+    T* out = grec + grp_toff[g];
+#pragma unroll
+    for (int j = 0; j < NTB; ++j)
+      if (j < nt) out[j * nt + lane] = (T)row[j];
   }
 }
 
@@ -528,17 +711,28 @@ static vef_status launch_group_factor(Schedule& S, const void* rec, cudaStream_t
     vef_status st = ensure_buffer(gp, &cap, (size_t)std::max(1LL, S.grec_elems) * sizeof(T));
     if (st != VEF_OK) return st;
   }
-  // groups are numbered by trace-system size: the small ones get a launch with 8 KB of
-  // shared memory per CTA, the rest one sized for the largest
-  const long long parts[3] = {0, S.ngroups_small, S.ngroups};
-  const int nts[2] = {std::min(S.max_nt, kGroupSmemTrace), S.max_nt};
-  for (int k = 0; k < 2; ++k) {
-    if (parts[k + 1] == parts[k]) continue;
-    const size_t smem = (size_t)nts[k] * nts[k] * sizeof(double);
+  // groups are numbered by trace-system size: warps for nt <= 8, 16, 32, one CTA with
+  // shared memory sized for the largest for the rest
+  const long long* up = S.ngroups_upto;
+  const long long lo[3] = {0, up[0], up[1]};
+  auto warp_launch = [&](auto kernel, long long a, long long b) -> vef_status {
+    if (b <= a) return VEF_OK;
+    kernel<<<(unsigned)((b - a + 3) / 4), 128, 0, stream>>>((int)a, (int)b, S.grp_slot, S.grp_nt, S.grp_toff,
+                                                           S.slot_first, S.slot_count, S.member_nbpos,
+                                                           (const T*)rec, S.members, (T*)*gp, status);
+    VEF_CUDA_TRY(cudaGetLastError());
+    return VEF_OK;
+  };
+  vef_status st;
+  if ((st = warp_launch(group_factor_warp_kernel<P, T, 8>, lo[0], up[0])) != VEF_OK) return st;
+  if ((st = warp_launch(group_factor_warp_kernel<P, T, 16>, lo[1], up[1])) != VEF_OK) return st;
+  if ((st = warp_launch(group_factor_warp_kernel<P, T, 32>, lo[2], up[2])) != VEF_OK) return st;
+  if (S.ngroups > up[2]) {
+    const size_t smem = (size_t)S.max_nt * S.max_nt * sizeof(double);
     VEF_CUDA_TRY(cudaFuncSetAttribute(group_factor_kernel<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-    group_factor_kernel<P, T><<<(unsigned)(parts[k + 1] - parts[k]), 128, smem, stream>>>(
-        (int)parts[k], S.grp_slot, S.grp_nt, S.grp_toff, S.slot_first, S.slot_count, S.member_nbpos,
+    group_factor_kernel<P, T><<<(unsigned)(S.ngroups - up[2]), 128, smem, stream>>>(
+        (int)up[2], S.grp_slot, S.grp_nt, S.grp_toff, S.slot_first, S.slot_count, S.member_nbpos,
         (const T*)rec, S.members, (T*)*gp, status);
     VEF_CUDA_TRY(cudaGetLastError());
   }
@@ -572,11 +766,17 @@ static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, cud
       if (st != VEF_OK) return st;
     }
     KTimer kt(&M, VEF_K_FACTOR, stream);
-    constexpr int UPW = 32 / (N > 4 * Q ? N : 4 * Q);
-    const int warps = std::max(1, std::min(4, (S.D + UPW - 1) / UPW));
-    assemble64_kernel<P><<<(unsigned)M.E, 32 * warps, 0, stream>>>(
-        S.D, M.E, S.member_of, S.faceinfo, S.omega_dev, sigma_t, M.Mmat, M.Gx, M.Gy, M.nds,
-        make_facetab<double>(M.tab), M.nx, M.ny, (double*)S.a64);
+    if constexpr (P >= 3) {
+      constexpr int UPW = 32 / (N > 4 * Q ? N : 4 * Q);
+      const int warps = std::max(1, std::min(4, (S.D + UPW - 1) / UPW));
+      assemble64_kernel<P><<<(unsigned)M.E, 32 * warps, 0, stream>>>(
+          S.D, M.E, S.member_of, S.faceinfo, S.omega_dev, sigma_t, M.Mmat, M.Gx, M.Gy, M.nds,
+          make_facetab<double>(M.tab), M.nx, M.ny, (double*)S.a64);
+    } else {
+      assemble64_thread_kernel<P><<<nblk(S.members, 128), 128, 0, stream>>>(
+          S.members, S.member_code, S.faceinfo, S.omega_dev, sigma_t, M.Mmat, M.Gx, M.Gy, M.nds,
+          make_facetab<double>(M.tab), M.nx, M.ny, M.E, (double*)S.a64);
+    }
   }
   KTimer kt(&M, VEF_K_FACTOR, stream);
   if constexpr (P >= 3) {

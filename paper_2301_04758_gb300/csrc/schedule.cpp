@@ -319,6 +319,7 @@ Schedule* get_schedule(Mesh* mesh, const double* omega, const double* weights, i
       }
     }
   S->nslots = (long long)slot_first.size();
+
   std::vector<uint16_t> faceinfo((size_t)D * E);
   for (int d = 0; d < D; ++d)
     std::copy(graphs[d].info.begin(), graphs[d].info.end(), faceinfo.begin() + (size_t)d * E);
@@ -388,7 +389,8 @@ Schedule* get_schedule(Mesh* mesh, const double* omega, const double* weights, i
       // offsets rounded to 4 entries keep every inverse 16-byte aligned in both precisions
       grp_toff.push_back(grp_toff.back() + ((long long)g.first * g.first + 3) / 4 * 4);
       S->max_nt = std::max(S->max_nt, g.first);
-      if (g.first <= kGroupSmemTrace) ++S->ngroups_small;
+      for (int b = 0; b < 3; ++b)
+        if (g.first <= (8 << b)) ++S->ngroups_upto[b];
     }
     S->ngroups = (long long)grp_slot.size();
     S->grec_elems = grp_toff.back();
