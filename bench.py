@@ -42,7 +42,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep-only", type=int, default=0, metavar="NX",
                     help="profiling driver: build an NX x NX mesh with the workload's recipe and run "
-                         "--steps FP64 sweeps (no timing line)")
+                         "--steps sweeps (factorisation included; no timing line)")
+    ap.add_argument("--order", type=int, default=2, help="--sweep-only: DG order p")
+    ap.add_argument("--sn", type=int, default=8, help="--sweep-only: level-symmetric order N")
+    ap.add_argument("--precision", default="fp64", choices=("fp64", "mixed"), help="--sweep-only: precision")
     ap.add_argument("--suite", default="", choices=("", "precision", "batch", "adjoint"),
                     help="other workloads (one JSON line each, not the headline): precision = 512x512 "
                          "Q3 S12 FP64 vs mixed; batch = the 64-problem batch; adjoint = 128x128 Q2 S8 "
@@ -566,23 +569,25 @@ def suite_adjoint(args):
 
 
 def sweep_only(args):
-    """Small driver for ncu captures: NX x NX sine mesh (alpha 0.05, Q3 map), Q2, S8,
-    seed-2 media, q = 1; runs --steps FP64 sweeps through the public API."""
+    """Small driver for ncu captures: NX x NX sine mesh (alpha 0.05, Q3 map), DG order
+    --order (default 2), S_N --sn (default 8), seed-2 media, q = 1; runs --steps sweeps
+    (each with its factorisation) in --precision through the public API."""
     import torch
 
     from paper_2301_04758_gb300 import build as vbuild
     vbuild.build()
     from paper_2301_04758_gb300.api import Mesh
     from vef_inputs import level_symmetric, seeded_media
-    N = args.sweep_only
-    om, w = level_symmetric(8)
+    N, p = args.sweep_only, args.order
+    n = (p + 1) ** 2
+    om, w = level_symmetric(args.sn)
     st, ss = seeded_media(N * N, 2)
     T = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda").contiguous()
-    mesh = Mesh(N, N, 3, 2, 0.05)
-    q = torch.ones(N * N, 9, dtype=torch.float64, device="cuda")
-    psi = torch.empty(len(w), N * N, 9, dtype=torch.float64, device="cuda")
+    mesh = Mesh(N, N, 3, p, 0.05)
+    q = torch.ones(N * N, n, dtype=torch.float64, device="cuda")
+    psi = torch.empty(len(w), N * N, n, dtype=torch.float64, device="cuda")
     for _ in range(args.steps):
-        mesh.sweep(T(st), T(ss), om, w, source=q, psi=psi)
+        mesh.sweep(T(st), T(ss), om, w, source=q, psi=psi, precision=args.precision)
     torch.cuda.synchronize()
     mesh.sync()
 

@@ -154,7 +154,9 @@ factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const 
   using L = Rec<P, T>;
   __shared__ T sM[N * LD], sX[N * LD], sY[N * LD];
   __shared__ T sN[4 * NQ * 2];
-  __shared__ T sL[Q][NQ];   // face Lagrange table: lanes index it by their own face node
+  __shared__ T sLL[Q][Q][NQ];          // l_a(s_k) l_t(s_k): face basis products
+  __shared__ T sW[NQ];                 // face Gauss weights
+  __shared__ T sC[4][UPW][4][NQ];      // per warp and task: w_k Omega . (n ds)_k of each face
   const long long e = blockIdx.x;
   const int tid = threadIdx.x;
   for (int idx = tid; idx < N * N; idx += blockDim.x) {
@@ -165,10 +167,15 @@ factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const 
     sY[r * LD + j] = Gym[g];
   }
   for (int idx = tid; idx < 4 * NQ * 2; idx += blockDim.x) sN[idx] = nds[(size_t)e * 4 * NQ * 2 + idx];
-  if (tid < Q * NQ) sL[tid / NQ][tid % NQ] = ft.l[tid / NQ][tid % NQ];
+  for (int idx = tid; idx < Q * Q * NQ; idx += blockDim.x) {
+    const int qa = idx / (Q * NQ), qt = (idx / NQ) % Q, kk = idx % NQ;
+    sLL[qa][qt][kk] = ft.l[qa][kk] * ft.l[qt][kk];
+  }
+  if (tid < NQ) sW[tid] = ft.w[tid];
   __syncthreads();
   const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int u = lane / LPU, li = lane % LPU, base = u * LPU;
+  const int uc = u < UPW ? u : UPW - 1;   // lanes past the last task read a valid slot
   const T st = (T)sigma_t[e];
   char* recx = (char*)rec + nmem * (long long)L::kStaged;
   for (int d0 = warp * UPW; d0 < D; d0 += nwarps * UPW) {
@@ -177,6 +184,13 @@ factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const 
     const int dd = valid ? d : 0;
     const T mu = (T)omega[2 * dd], eta = (T)omega[2 * dd + 1];
     const uint16_t bits = finfo[(size_t)dd * E + e];
+    // face coefficients of this task, once: its LPU lanes share the 4 NQ entries
+    __syncwarp();
+    for (int q = li; u < UPW && q < 4 * NQ; q += LPU) {
+      const int f = q / NQ, kk = q % NQ;
+      sC[warp][u][f][kk] = sW[kk] * (mu * sN[(f * NQ + kk) * 2] + eta * sN[(f * NQ + kk) * 2 + 1]);
+    }
+    __syncwarp();
     // assemble the owned rows: sigma_t M - mu Gx - eta Gy plus the outflow face terms
     T row[RPL][N];
 #pragma unroll
@@ -197,11 +211,10 @@ factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const 
         if (pos < 0) continue;
 #pragma unroll
         for (int k = 0; k < NQ; ++k) {
-          const T s = ft.w[k] * (mu * sN[(f * NQ + k) * 2] + eta * sN[(f * NQ + k) * 2 + 1]);
+          const T s = sC[warp][uc][f][k];
           if (!(s > (T)0)) continue;
-          const T sl = s * sL[pos][k];
 #pragma unroll
-          for (int t = 0; t < Q; ++t) row[r][face_dof<P>(f, t)] += sl * sL[t][k];
+          for (int t = 0; t < Q; ++t) row[r][face_dof<P>(f, t)] = fma(s, sLL[pos][t][k], row[r][face_dof<P>(f, t)]);
         }
       }
     }
@@ -256,8 +269,8 @@ factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const 
           const int qa = q / Q, qt = q % Q;
 #pragma unroll
           for (int k = 0; k < NQ; ++k) {
-            const T s = ft.w[k] * (mu * sN[(f * NQ + k) * 2] + eta * sN[(f * NQ + k) * 2 + 1]);
-            if (s < (T)0) v += s * sL[qa][k] * sL[qt][k];
+            const T s = sC[warp][uc][f][k];
+            v = fma(s < (T)0 ? s : (T)0, sLL[qa][qt][k], v);
           }
         }
         cmine[c] = v;
