@@ -25,13 +25,28 @@ namespace {
 
 static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// products of the face Lagrange values at the face Gauss points, l_a(s_k) l_b(s_k)
+template <typename T>
+struct FaceLL {
+  T ll[kMaxP + 1][kMaxP + 1][kMaxNq];
+};
+
+template <typename T>
+inline FaceLL<T> make_facell(const Tab1D& t) {
+  FaceLL<T> f{};
+  for (int a = 0; a <= t.p; ++a)
+    for (int b = 0; b <= t.p; ++b)
+      for (int k = 0; k < t.nq; ++k) f.ll[a][b][k] = (T)(t.l[a][k] * t.l[b][k]);
+  return f;
+}
+
 // ------------------------------------------------------------------- factorisation
 template <int P, typename T>
 __global__ void __launch_bounds__(128)
 factor_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t* __restrict__ finfo,
               const double* __restrict__ omega, const double* __restrict__ sigma_t,
               const T* __restrict__ Mm, const T* __restrict__ Gxm, const T* __restrict__ Gym,
-              const T* __restrict__ nds, FaceTab<T> ft, int nx, int ny, long long E,
+              const T* __restrict__ nds, FaceTab<T> ft, FaceLL<T> fll, int nx, int ny, long long E,
               T* __restrict__ rec, unsigned int* status) {
   constexpr int Q = P + 1, N = Q * Q, NQ = P + 2;
   using L = Rec<P, T>;
@@ -48,32 +63,44 @@ factor_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t*
   const T* Ye = Gym + (size_t)e * N * N;
 #pragma unroll
   for (int ij = 0; ij < N * N; ++ij) A[ij] = st * Me[ij] - mu * Xe[ij] - eta * Ye[ij];
+  // face terms: the outflow part only where some point is outflow, the inflow coupling
+  // only for the faces that get a W slot (interior neighbour, some point inflow)
   T Cin[4][Q][Q];
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
     T cp[NQ], cm[NQ];
+    bool anyout = false;
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
       const T* v = nds + (((size_t)e * 4 + f) * NQ + k) * 2;
       const T s = ft.w[k] * (mu * v[0] + eta * v[1]);
       cp[k] = s > (T)0 ? s : (T)0;
       cm[k] = s < (T)0 ? s : (T)0;
+      anyout = anyout || s > (T)0;
+    }
+    const bool need_in = (bits & (1u << f)) && nb_elem(nx, ny, e, f) >= 0;
+    if (anyout) {
+#pragma unroll
+      for (int a = 0; a < Q; ++a)
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+          T vo = 0;
+#pragma unroll
+          for (int k = 0; k < NQ; ++k) vo = fma(cp[k], fll.ll[a][b][k], vo);
+          A[face_dof<P>(f, a) * N + face_dof<P>(f, b)] += vo;
+        }
     }
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
+    for (int a = 0; a < Q; ++a)
 #pragma unroll
       for (int b = 0; b < Q; ++b) {
-        T vo = 0, vi = 0;
+        T vi = 0;
+        if (need_in) {
 #pragma unroll
-        for (int k = 0; k < NQ; ++k) {
-          const T ll = ft.l[a][k] * ft.l[b][k];
-          vo += cp[k] * ll;
-          vi += cm[k] * ll;
+          for (int k = 0; k < NQ; ++k) vi = fma(cm[k], fll.ll[a][b][k], vi);
         }
-        A[face_dof<P>(f, a) * N + face_dof<P>(f, b)] += vo;
         Cin[f][a][b] = vi;
       }
-    }
   }
   // in-place Gauss-Jordan inversion (no pivoting: the upwind element matrix has a
   // positive definite symmetric part, sigma_t M + (1/2) sum |Omega.n| face mass)
@@ -801,7 +828,7 @@ static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, cud
   } else {
     factor_kernel<P, T><<<nblk(S.members, 128), 128, 0, stream>>>(
         S.members, S.member_code, S.faceinfo, S.omega_dev, sigma_t, Mm, Gx, Gy, nds,
-        make_facetab<T>(M.tab), M.nx, M.ny, M.E, (T*)*recp, M.dev_status);
+        make_facetab<T>(M.tab), make_facell<T>(M.tab), M.nx, M.ny, M.E, (T*)*recp, M.dev_status);
   }
   VEF_CUDA_TRY(cudaGetLastError());
   return launch_group_factor<P, T>(S, *recp, stream, M.dev_status);
