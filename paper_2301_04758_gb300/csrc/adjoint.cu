@@ -165,12 +165,6 @@ __device__ __forceinline__ void adj_group(const AdjArgs& a, int d, int s0) {
     if (!conv) atomicOr(a.status, kDevNotConverged);
     atomicMax(a.status + 2, (unsigned)it);
   }
-  for (int mi = 0; mi < cnt; ++mi) {
-    const long long m = first + mi;
-    const int e = (int)(a.code[m] & 0x3fffffu);
-    const double r = act ? __ldcg(a.radj + ((size_t)d * a.E + e) * N + i) : 0.0;
-    adj_finish<P>(a, m, d, e, i, act, r);
-  }
 }
 
 template <int P>
@@ -200,11 +194,29 @@ __global__ void __maxnreg__(128) adjoint_kernel(AdjArgs a) {
         r = adj_rhs<P>(a, d, e, i, bits, 0, 0, 1, 1, false);
         a.radj[((size_t)d * a.E + e) * N + i] = r;
       }
-      adj_finish<P>(a, m, d, e, i, valid, r);
     }
     for (int gs = sg + gw; gs < se; gs += nw) adj_group<P>(a, d, gs);
     cluster_barrier();
   }
+}
+
+// lambda = A^{-T} r and the gradient sums for every (element, direction) once the
+// backward sweep has produced all r: nothing downstream needs them, so they stay off the
+// sweep's level-by-level critical path.  One lane per dof row, SPC tasks per warp.
+template <int P>
+__global__ void __launch_bounds__(128) adj_finish_kernel(AdjArgs a) {
+  constexpr int N = (P + 1) * (P + 1);
+  constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
+  const int lane = threadIdx.x & 31;
+  const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long mm = gw * SPC + lane / N;
+  const int i = lane % N;
+  const bool valid = lane < SPC * N && mm < a.nmem;
+  const long long m = valid ? mm : 0;
+  const uint32_t c = a.code[m];
+  const int d = (int)(c >> 22), e = (int)(c & 0x3fffffu);
+  const double r = valid ? a.radj[((size_t)d * a.E + e) * N + i] : 0.0;
+  adj_finish<P>(a, m, d, e, i, valid, r);
 }
 
 __global__ void mvec_kernel(long long E, int n, const double* __restrict__ M,
@@ -243,6 +255,11 @@ static vef_status launch_adjoint(Mesh& M, AdjArgs a, int D, int cs, int warps, c
   a.recx = (const double*)((const char*)a.rec + a.nmem * (long long)Rec<P, double>::kStaged);
   KTimer kt(&M, VEF_K_ADJOINT, s);
   VEF_CUDA_TRY(cudaLaunchKernelEx(&cfg, adjoint_kernel<P>, a));
+  constexpr int N = (P + 1) * (P + 1);
+  constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
+  const long long nwarp = (a.nmem + SPC - 1) / SPC;
+  adj_finish_kernel<P><<<nblk(nwarp * 32, 128), 128, 0, s>>>(a);
+  VEF_CUDA_TRY(cudaGetLastError());
   return VEF_OK;
 }
 
