@@ -36,6 +36,7 @@ struct AdjArgs {
   const double* psi;      // [D][E][n] forward checkpoint
   const double* Mm;       // [E][n][n]
   const double* mphi;     // [E][n] M phi_in or null
+  const uint32_t* link;   // [members][4] receiver member and W slot across each face
   double* radj;           // [D][E][n] adjoint right-hand sides r
   double* lambda;         // [D][E][n]
   double* dst;            // [E]
@@ -49,7 +50,7 @@ struct AdjArgs {
 
 // r_i of element e (lane = dof row i): w_d g_i minus the downstream couplings on e's faces
 template <int P>
-__device__ __forceinline__ double adj_rhs(const AdjArgs& a, int d, int e, int i, uint16_t bits,
+__device__ __forceinline__ double adj_rhs(const AdjArgs& a, int d, int e, long long m, int i, uint16_t bits,
                                           int first, int pos_self, int cnt, int it, bool in_group) {
   constexpr int Q = P + 1, N = Q * Q;
   using L = Rec<P, double>;
@@ -69,12 +70,10 @@ __device__ __forceinline__ double adj_rhs(const AdjArgs& a, int d, int e, int i,
       const int pos = a.member_of[(size_t)d * a.E + nb] - first;
       if (pos <= pos_self) continue;  // processed later in the first backward pass
     }
-    const int fn = (f + 2) & 3;      // receiver's face toward e
-    const long long mn = a.member_of[(size_t)d * a.E + nb];
-    const char* rr = L::s_at(a.rec, mn);
-    const int sl = rec_slot_of(reinterpret_cast<const uint4*>(rr)->z, fn);
-    if (sl < 0) continue;
-    const double* W = L::slot(rr, L::x_at(a.recx, mn), sl) + t * N;
+    const uint32_t lk = a.link[m * 4 + f];   // receiver and its W slot for the face toward e
+    if (lk == ~0u) continue;
+    const long long mn = (long long)(lk >> 2);
+    const double* W = L::slot(L::s_at(a.rec, mn), L::x_at(a.recx, mn), (int)(lk & 3u)) + t * N;
     const double* rn = a.radj + ((size_t)d * a.E + nb) * N;
     double s = 0.0;
 #pragma unroll
@@ -146,7 +145,7 @@ __device__ __forceinline__ void adj_group(const AdjArgs& a, int d, int s0) {
       const int e = (int)(a.code[first + mi] & 0x3fffffu);
       const uint16_t bits = a.finfo[(size_t)d * a.E + e];
       if (act) {
-        const double r = adj_rhs<P>(a, d, e, i, bits, first, mi, cnt, it, true);
+        const double r = adj_rhs<P>(a, d, e, first + mi, i, bits, first, mi, cnt, it, true);
         double* o = a.radj + ((size_t)d * a.E + e) * N + i;
         if (it > 0) dmax = fmax(dmax, fabs(r - __ldcg(o)));
         amax = fmax(amax, fabs(r));
@@ -191,7 +190,7 @@ __global__ void __maxnreg__(128) adjoint_kernel(AdjArgs a) {
         m = a.slot_first[slot];
         e = (int)(a.code[m] & 0x3fffffu);
         const uint16_t bits = a.finfo[(size_t)d * a.E + e];
-        r = adj_rhs<P>(a, d, e, i, bits, 0, 0, 1, 1, false);
+        r = adj_rhs<P>(a, d, e, m, i, bits, 0, 0, 1, 1, false);
         a.radj[((size_t)d * a.E + e) * N + i] = r;
       }
     }
@@ -217,6 +216,32 @@ __global__ void __launch_bounds__(128) adj_finish_kernel(AdjArgs a) {
   const int d = (int)(c >> 22), e = (int)(c & 0x3fffffu);
   const double r = valid ? a.radj[((size_t)d * a.E + e) * N + i] : 0.0;
   adj_finish<P>(a, m, d, e, i, valid, r);
+}
+
+// Receiver links of the backward sweep: for member m = (d, e) and a face f across which
+// e feeds its neighbour, the neighbour's member index and the W slot it holds for the
+// face toward e (its slots are its interior inflow faces in face order).
+__global__ void adj_link_kernel(long long nmem, long long E, int nx, int ny, const uint32_t* __restrict__ code,
+                                const uint16_t* __restrict__ finfo, const int* __restrict__ member_of,
+                                uint32_t* __restrict__ link) {
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (m >= nmem) return;
+  const uint32_t c = code[m];
+  const int d = (int)(c >> 22), e = (int)(c & 0x3fffffu);
+  const uint16_t bits = finfo[(size_t)d * E + e];
+  for (int f = 0; f < 4; ++f) {
+    uint32_t lk = ~0u;
+    const int nb = nb_elem(nx, ny, e, f);
+    if ((bits & (1u << (8 + f))) && nb >= 0) {
+      const uint16_t nbits = finfo[(size_t)d * E + nb];
+      const int fn = (f + 2) & 3;
+      int slot = 0;
+      for (int g = 0; g < fn; ++g)
+        if ((nbits & (1u << g)) && nb_elem(nx, ny, nb, g) >= 0) ++slot;
+      if (nbits & (1u << fn)) lk = ((uint32_t)member_of[(size_t)d * E + nb] << 2) | (uint32_t)slot;
+    }
+    link[m * 4 + f] = lk;
+  }
 }
 
 __global__ void mvec_kernel(long long E, int n, const double* __restrict__ M,
@@ -291,6 +316,18 @@ extern "C" vef_status vef_adjoint_sweep(vef_mesh mesh, const double* sigma_t, co
   Schedule* S = get_schedule(&M, omega, weights, D, s, &st);
   if (!S) return st;
   if ((st = factor_fp64(&M, S, sigma_t, s)) != VEF_OK) return st;
+  if (!S->adj_link) {
+    if (S->members >= (1LL << 30)) {
+      set_last_error("adjoint sweep supports at most 2^30 (element, direction) pairs");
+      return VEF_ERR_INVALID_ARG;
+    }
+    size_t cap = 0;
+    if ((st = ensure_buffer((void**)&S->adj_link, &cap, (size_t)S->members * 4 * sizeof(uint32_t))) != VEF_OK)
+      return st;
+    adj_link_kernel<<<nblk(S->members, 256), 256, 0, s>>>(S->members, M.E, M.nx, M.ny, S->member_code,
+                                                          S->faceinfo, S->member_of, S->adj_link);
+    VEF_CUDA_TRY(cudaGetLastError());
+  }
   const long long tot = (long long)D * M.E * M.n;
   const size_t need = (size_t)tot * sizeof(double) * (lambda ? 1 : 2) + (size_t)M.E * M.n * sizeof(double);
   if ((st = ensure_buffer((void**)&M.work2, &M.work2_cap, need)) != VEF_OK) return st;
@@ -314,6 +351,7 @@ extern "C" vef_status vef_adjoint_sweep(vef_mesh mesh, const double* sigma_t, co
   a.lambda = lambda ? lambda : M.work2 + tot;
   double* mphi = M.work2 + tot * (lambda ? 1 : 2);
   a.mphi = phi_in ? mphi : nullptr;
+  a.link = S->adj_link;
   a.dst = dR_dsigma_t;
   a.dss = dR_dsigma_s;
   a.status = M.dev_status;

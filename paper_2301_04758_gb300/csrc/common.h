@@ -102,6 +102,8 @@ struct Schedule {
   void* rec64 = nullptr;
   void* rec32 = nullptr;
   void* a64 = nullptr;         // FP64 element matrices + inflow couplings (mixed residual)
+  uint32_t* adj_link = nullptr;  // [members][4] downstream receiver across each face:
+                                 // (receiver member << 2) | its W slot, or ~0 (adjoint)
   ~Schedule();
 };
 

@@ -251,6 +251,7 @@ Schedule::~Schedule() {
   cudaFree(rec64);
   cudaFree(rec32);
   cudaFree(a64);
+  cudaFree(adj_link);
   cudaFree(slot_gid);
   cudaFree(grp_slot);
   cudaFree(grp_nt);
