@@ -79,7 +79,11 @@ typedef enum {
 enum { VEF_FP64 = 0, VEF_MIXED = 1 };
 
 /* vef_opts.flags */
-enum { VEF_GROUPS_ITERATIVE = 1 /* solve every coupled group by the inner iteration */ };
+enum {
+  VEF_GROUPS_ITERATIVE = 1, /* solve every coupled group by the inner iteration */
+  VEF_SWEEP_CLUSTER = 2     /* sweep each direction with a thread-block cluster (as the
+                               batched and adjoint sweeps do) instead of one CTA */
+};
 
 typedef struct vef_mesh_s* vef_mesh;
 
@@ -93,8 +97,10 @@ typedef struct {
   int max_passes;    /* cap on defect-correction passes (default 8) and, x4, on inner
                         coupled-group iterations */
   int tile_override; /* 0 = library choice; else 100 * (CTAs per direction cluster, 1..16)
-                        + (warps per CTA, 1..16) of the sweep kernel */
-  int flags;         /* bit set of VEF_GROUPS_ITERATIVE (default 0: direct group solves) */
+                        + (warps per CTA, 1..16) of the cluster sweep kernel (implies
+                        VEF_SWEEP_CLUSTER) */
+  int flags;         /* bit set of VEF_GROUPS_ITERATIVE, VEF_SWEEP_CLUSTER (default 0:
+                        direct group solves, one CTA per direction) */
 } vef_opts;
 
 /* Filled by calls given a non-NULL pointer (those calls synchronise `stream`). */

@@ -32,13 +32,14 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _opts(precision="fp64", tol=0.0, max_passes=0, tile=0, groups="direct"):
+def _opts(precision="fp64", tol=0.0, max_passes=0, tile=0, groups="direct", kernel="cta"):
     o = _lib.VefOpts()
     o.precision = {"fp64": _lib.VEF_FP64, "mixed": _lib.VEF_MIXED}[precision]
     o.tol = float(tol)
     o.max_passes = int(max_passes)
     o.tile_override = int(tile)
     o.flags = {"direct": 0, "iterative": _lib.VEF_GROUPS_ITERATIVE}[groups]
+    o.flags |= {"cta": 0, "cluster": _lib.VEF_SWEEP_CLUSTER}[kernel]
     return o
 
 
@@ -101,11 +102,13 @@ class Mesh:
     # ---------------------------------------------------------------- transport
     def sweep(self, sigma_t, sigma_s, omega, weights, phi_in=None, source=None, inflow=None,
               precision="fp64", tol=0.0, max_passes=0, tile=0, groups="direct", psi=None, info=False,
-              stream=None):
+              stream=None, kernel="cta"):
         """psi [D][E][n] = L^{-1} b for every direction (see vef_sweep in include/vef.h).
 
         groups: "direct" (coupled element groups through their trace system) or
-        "iterative" (inner block Gauss-Seidel for every group)."""
+        "iterative" (inner block Gauss-Seidel for every group).
+        kernel: "cta" (one CTA per direction, the default) or "cluster" (a thread-block
+        cluster per direction; a nonzero tile also selects it)."""
         om, omp = _host(omega)
         w, wp = _host(weights)
         D = len(w)
@@ -113,7 +116,7 @@ class Mesh:
         if psi is None:
             psi = self._empty(D, self.E, self.n)
         inf = _lib.VefInfo() if info else None
-        o = _opts(precision, tol, max_passes, tile, groups)
+        o = _opts(precision, tol, max_passes, tile, groups, kernel)
         st = self.lib.vef_sweep(self.handle, _ptr(sigma_t), _ptr(sigma_s), _ptr(phi_in), _ptr(source),
                                 aniso, _ptr(inflow), omp, wp, D, ctypes.byref(o), _ptr(psi),
                                 ctypes.byref(inf) if info else None, _stream(stream))
@@ -140,7 +143,8 @@ class Mesh:
         return out
 
     def source_iterate(self, sigma_t, sigma_s, omega, weights, K, source=None, inflow=None, phi0=None,
-                       precision="fp64", tol=0.0, max_passes=0, psi=None, info=False, stream=None):
+                       precision="fp64", tol=0.0, max_passes=0, psi=None, info=False, stream=None,
+                       kernel="cta"):
         """K source iterations: returns (phi^K, psi of the last sweep, dphi_inf [K])."""
         om, omp = _host(omega)
         w, wp = _host(weights)
@@ -151,7 +155,7 @@ class Mesh:
         phi = self._empty(self.E, self.n)
         dphi = self._empty(K)
         inf = _lib.VefInfo() if info else None
-        o = _opts(precision, tol, max_passes)
+        o = _opts(precision, tol, max_passes, kernel=kernel)
         st = self.lib.vef_source_iterate(self.handle, _ptr(sigma_t), _ptr(sigma_s), _ptr(phi0),
                                          _ptr(source), aniso, _ptr(inflow), omp, wp, D, int(K),
                                          ctypes.byref(o), _ptr(phi), _ptr(psi), _ptr(dphi),

@@ -61,6 +61,12 @@ __host__ __device__ constexpr int group_direct_members(int p) { return p <= 2 ? 
 constexpr int kGroupMaxTrace = 128;
 constexpr int kGroupSmemTrace = 32;   // the trace-system inverse sits in shared memory up to this size
 
+// Shared-memory trace slots one single-CTA sweep of DG order p can hold (sweep.cu).  Slot
+// kTraceZero holds zeros and is never written, slot kTraceSink is written and never read;
+// the schedule assigns the others.
+int cta_trace_capacity(int p);
+constexpr unsigned kTraceZero = 0, kTraceSink = 1, kTraceFirst = 2;
+
 // Per-direction-set schedule: dependency levels, element groups and task chunks.
 struct Schedule {
   std::vector<double> omega;   // [D][2] host copy (key)
@@ -104,6 +110,15 @@ struct Schedule {
   void* a64 = nullptr;         // FP64 element matrices + inflow couplings (mixed residual)
   uint32_t* adj_link = nullptr;  // [members][4] downstream receiver across each face:
                                  // (receiver member << 2) | its W slot, or ~0 (adjoint)
+  // Shared-memory trace slots of the single-CTA sweep, per member four 16-bit slot ids:
+  // x = the slots to read for the record's W slots 0 and 1 (the donors' face-node values;
+  // kTraceZero when the slot is absent or its donor is read from global memory), y / z =
+  // the slots the member's own face-node values go to, for faces 0, 1 / 2, 3 (kTraceSink
+  // when no later single-element task reads them); w = 1 when some upwind coupling of the
+  // member is read from global memory instead (see cta_trace_capacity).
+  uint4* tslot = nullptr;
+  int trace_slots = 0;          // slots in use at once (max over directions)
+  long long trace_global = 0;   // single-to-single face couplings left to global memory
   ~Schedule();
 };
 

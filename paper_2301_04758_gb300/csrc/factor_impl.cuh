@@ -783,9 +783,13 @@ template <int P, typename T>
 static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, cudaStream_t stream) {
   void** recp = std::is_same<T, double>::value ? &S.rec64 : &S.rec32;
   if (!*recp) {
+    // zero-filled once: the W slots of faces without interior inflow are never written
+    // and stay zero (the single-CTA sweep multiplies them by a zero trace)
     size_t cap = 0;
-    vef_status st = ensure_buffer(recp, &cap, (size_t)S.members * (Rec<P, T>::kStaged + Rec<P, T>::kX));
+    const size_t bytes = (size_t)S.members * (Rec<P, T>::kStaged + Rec<P, T>::kX);
+    vef_status st = ensure_buffer(recp, &cap, bytes);
     if (st != VEF_OK) return st;
+    VEF_CUDA_TRY(cudaMemsetAsync(*recp, 0, bytes, stream));
   }
   const T* Mm;
   const T* Gx;

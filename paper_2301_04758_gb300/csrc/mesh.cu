@@ -252,6 +252,7 @@ Schedule::~Schedule() {
   cudaFree(rec32);
   cudaFree(a64);
   cudaFree(adj_link);
+  cudaFree(tslot);
   cudaFree(slot_gid);
   cudaFree(grp_slot);
   cudaFree(grp_nt);

@@ -16,6 +16,7 @@
 // mixed faces are iterated.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <thread>
@@ -398,6 +399,99 @@ Schedule* get_schedule(Mesh* mesh, const double* omega, const double* weights, i
     if ((*st = upload(&S->grp_slot, grp_slot)) != VEF_OK) return nullptr;
     if ((*st = upload(&S->grp_nt, grp_nt)) != VEF_OK) return nullptr;
     if ((*st = upload(&S->grp_toff, grp_toff)) != VEF_OK) return nullptr;
+  }
+  // Shared-memory trace slots of the single-CTA sweep (two reserved, see kTraceZero).
+  // Per direction, levels in order: a
+  // single-element task that feeds a later single-element task across a face takes a free
+  // slot for that face's node values, released once the receiver's level is done, so a
+  // slot freed at level L is reused from level L + 1 on (reads and writes of one level
+  // never share a slot).  Receivers whose face is not one of their two staged W slots,
+  // coupled-group members and couplings beyond the capacity keep 0xffff: the receiver
+  // reads the donor's psi from global memory instead.
+  {
+    int cap = cta_trace_capacity(M.p);
+    if (const char* env = std::getenv("VEF_TRACE_SLOTS")) cap = std::max(0, std::min(cap, std::atoi(env)));
+    const unsigned zz = kTraceZero | (kTraceZero << 16), ss = kTraceSink | (kTraceSink << 16);
+    std::vector<uint4> tslot(member_code.size(), make_uint4(zz, ss, ss, 0u));
+    std::vector<int> dir_live(D, 0);
+    std::vector<long long> dir_global(D, 0);
+    auto set16 = [](unsigned& w, int half, unsigned id) {
+      w = (w & ~(0xffffu << (16 * half))) | (id << (16 * half));
+    };
+    auto interior_inflow_rank = [&](int d, int e, int g) {
+      const uint16_t bits = graphs[d].info[e];
+      int r = 0;
+      for (int f = 0; f < g; ++f)
+        if ((bits & (1u << f)) && nb_of(M.nx, M.ny, e, f) >= 0) ++r;
+      return r;
+    };
+    auto run = [&](int d) {
+      const DirGraph& g = graphs[d];
+      std::vector<unsigned> free_ids;
+      free_ids.reserve(cap);
+      for (int id = cap - 1; id >= (int)kTraceFirst; --id) free_ids.push_back((unsigned)id);
+      std::vector<std::vector<unsigned>> release(g.levels);
+      int live = (int)kTraceFirst;
+      dir_live[d] = live;
+      for (int L = 0; L < g.levels; ++L) {
+        const int k = dir_lev0[d] + L;
+        const int m0 = lev_mbegin[k];
+        const int nsingle = lev_gbegin[k] - lev_begin[k];
+        for (int m = m0; m < m0 + nsingle; ++m) {
+          const int e = (int)(member_code[m] & ((1u << 22) - 1));
+          const uint16_t bits = g.info[e];
+          for (int f = 0; f < 4; ++f) {
+            if (!(bits & (1u << (8 + f)))) continue;
+            const int w = nb_of(M.nx, M.ny, e, f);
+            const int wm = member_of[(size_t)d * E + w];
+            const int Lw = level_of[(size_t)d * E + w];
+            const int kw = dir_lev0[d] + Lw;
+            if (wm >= lev_mbegin[kw] + (lev_gbegin[kw] - lev_begin[kw])) continue;  // group member
+            const int rank = interior_inflow_rank(d, w, kOpp[f]);
+            if (rank >= 2) continue;
+            if (free_ids.empty()) { ++dir_global[d]; continue; }
+            const unsigned id = free_ids.back();
+            free_ids.pop_back();
+            set16(f < 2 ? tslot[m].y : tslot[m].z, f & 1, id);
+            set16(tslot[wm].x, rank, id);
+            release[Lw].push_back(id);
+            dir_live[d] = std::max(dir_live[d], ++live);
+          }
+        }
+        for (unsigned id : release[L]) free_ids.push_back(id);
+        live -= (int)release[L].size();
+        std::vector<unsigned>().swap(release[L]);
+      }
+      // members whose upwind couplings are not all in shared memory: an interior inflow
+      // face beyond the two staged W slots, or a staged one left without a slot
+      for (int L = 0; L < g.levels; ++L) {
+        const int k = dir_lev0[d] + L;
+        const int m0 = lev_mbegin[k];
+        const int nsingle = lev_gbegin[k] - lev_begin[k];
+        for (int m = m0; m < m0 + nsingle; ++m) {
+          const int e = (int)(member_code[m] & ((1u << 22) - 1));
+          int rank = 0;
+          for (int f = 0; f < 4; ++f) {
+            if (!(g.info[e] & (1u << f)) || nb_of(M.nx, M.ny, e, f) < 0) continue;
+            if (rank >= 2 || ((tslot[m].x >> (16 * rank)) & 0xffffu) == kTraceZero) tslot[m].w = 1u;
+            ++rank;
+          }
+        }
+      }
+    };
+    unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 32));
+    nt = std::min<unsigned>(nt, (unsigned)D);
+    std::vector<std::thread> pool;
+    for (unsigned t = 0; t < nt; ++t)
+      pool.emplace_back([&, t]() {
+        for (int d = (int)t; d < D; d += (int)nt) run(d);
+      });
+    for (auto& th : pool) th.join();
+    for (int d = 0; d < D; ++d) {
+      S->trace_slots = std::max(S->trace_slots, dir_live[d]);
+      S->trace_global += dir_global[d];
+    }
+    if ((*st = upload(&S->tslot, tslot)) != VEF_OK) return nullptr;
   }
   if ((*st = upload(&S->slot_first, slot_first)) != VEF_OK) return nullptr;
   if ((*st = upload(&S->slot_count, slot_count)) != VEF_OK) return nullptr;

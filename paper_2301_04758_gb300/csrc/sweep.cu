@@ -80,6 +80,9 @@ struct SweepArgs {
   T* out;                  // [D][E][n]
   T* y;                    // [D][E][n] A^{-1} b (apply_kernel)
   unsigned int* status;    // [0] status bits, [2] max inner iterations
+  const uint4* tslot;      // single-CTA sweep: trace slot ids per member (Schedule::tslot)
+  int ring;                // single-CTA sweep: round buffers in the ring
+  int tr_bytes;            // single-CTA sweep: bytes of the trace slots
   int nx, ny;
   long long E, nbf;
   T tol;
@@ -162,18 +165,23 @@ __global__ void __launch_bounds__(128) apply_kernel(SweepArgs<T> a, long long nm
 }
 
 // upwind correction of row i for face f of member record r: sum_t W_f[t][i] u_t
-template <int P, typename T>
+// (CG: the neighbour's values are read at L2, as a cluster's other CTAs wrote them; the
+// single-CTA sweep reads them with ordinary loads)
+template <int P, typename T, bool CG = true>
 __device__ __forceinline__ T face_term(const T* W, const T* un, int f, int i) {
   constexpr int Q = P + 1, N = Q * Q;
   T acc = 0;
 #pragma unroll
-  for (int t = 0; t < Q; ++t) acc += W[t * N + i] * ldcg(un + face_dof<P>((f + 2) & 3, t));
+  for (int t = 0; t < Q; ++t) {
+    const T* up = un + face_dof<P>((f + 2) & 3, t);
+    acc += W[t * N + i] * (CG ? ldcg(up) : *up);
+  }
   return acc;
 }
 
 // Coupled group by inner block Gauss-Seidel over its members, in global memory (groups
 // beyond the direct limits, or every group when the caller asks for the iteration).
-template <int P, typename T, int MODE>
+template <int P, typename T, int MODE, bool CG = true>
 __device__ __forceinline__ void group_solve(const SweepArgs<T>& a, int d, int s0) {
   constexpr int Q = P + 1, N = Q * Q;
   using L = Rec<P, T>;
@@ -204,7 +212,7 @@ __device__ __forceinline__ void group_solve(const SweepArgs<T>& a, int d, int s0
             const int pos = a.member_of[(size_t)d * a.E + nb] - first;
             if (pos >= mi) continue;  // not computed yet in the first sweep
           }
-          y -= face_term<P, T>(L::slot(r, rx, sl), a.out + ((size_t)d * a.E + nb) * N, f, i);
+          y -= face_term<P, T, CG>(L::slot(r, rx, sl), a.out + ((size_t)d * a.E + nb) * N, f, i);
         }
         T* o = a.out + ((size_t)d * a.E + e) * N + i;
         if (it > 0) dmax = fmax(dmax, fabs(y - ldcg(o)));
@@ -298,7 +306,7 @@ __device__ __forceinline__ void group_stage(const SweepArgs<T>& a, int s0, Group
   __syncwarp();
 }
 
-template <int P, typename T>
+template <int P, typename T, bool CG = true>
 __device__ __forceinline__ void group_solve_direct(const SweepArgs<T>& a, int d, int s0, GroupSmem<P, T>& g) {
   constexpr int Q = P + 1, N = Q * Q;
   using L = Rec<P, T>;
@@ -317,7 +325,7 @@ __device__ __forceinline__ void group_solve_direct(const SweepArgs<T>& a, int d,
       const int sl = rec_slot_of(info.z, f);
       if (sl < 0 || ((info.y >> (4 + f)) & 1u)) continue;
       const int nb = nb_elem(a.nx, a.ny, (int)info.x, f);
-      z -= face_term<P, T>(L::slot(r, rx, sl), a.out + ((size_t)d * a.E + nb) * N, f, i);
+      z -= face_term<P, T, CG>(L::slot(r, rx, sl), a.out + ((size_t)d * a.E + nb) * N, f, i);
     }
     g.z[idx] = z;
   }
@@ -606,6 +614,218 @@ sweep_batch_kernel(const SweepArgs<T>* __restrict__ tab, const int2* __restrict_
   sweep_direction<P, T, MODE>(tab[pd.x], pd.y);
 }
 
+// ------------------------------------------------------------- single-CTA sweep
+// One CTA of 16 warps per direction.  Warp 15 streams the records of the direction's
+// single-element tasks (staged prefix, y row, trace slot ids) through a ring of round
+// buffers with bulk copies, as far ahead as the ring allows; warps 0..11 compute them, a
+// round being 12 * SPC consecutive tasks of one level with one lane per dof row; warps
+// 12..14 solve the level's coupled groups, one group per warp at a time, each staging its
+// first group of the next level while the level finishes.  The upwind face values passed from one single-element task
+// to a later one go through shared-memory trace slots whose ids the schedule assigned,
+// so a level costs shared-memory latency and a named barrier over the 15 computing warps
+// instead of an L2 round trip and a cluster barrier.  Other couplings (from group
+// members, into a receiver's extra W slots, beyond the slot capacity) read the donor's
+// psi from global memory, which every task writes.
+template <int P, typename T>
+struct CtaShape {
+  static constexpr int Q = P + 1, N = Q * Q;
+  using L = Rec<P, T>;
+  static constexpr int kCompute = 12, kGroupWarps = 3, kProducer = 15, kThreads = 512;
+  static constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
+  static constexpr int CH = kCompute * SPC;                     // tasks per round
+  // round buffer: CH staged record prefixes, CH y rows, CH slot-id quadruples
+  static constexpr int kYOff = CH * L::kStaged;
+  static constexpr int kTsOff = kYOff + CH * L::kYBytes;
+  static constexpr int kRound = kTsOff + CH * 16;
+  static constexpr int kGroup = kGroupWarps * (((int)sizeof(GroupSmem<P, T>) + 15) / 16 * 16);
+  static constexpr int kMaxRing = 16;
+  static constexpr int kBars = 2 * kMaxRing * 8;
+  static constexpr int kSmemMax = 227 * 1024;
+  // bytes of shared memory for the trace slots when the ring keeps `rounds` buffers
+  static constexpr int trace_budget(int rounds) { return kSmemMax - kGroup - kBars - rounds * kRound; }
+};
+
+template <int P, typename T, int MODE>
+__global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
+  using Sh = CtaShape<P, T>;
+  using L = Rec<P, T>;
+  constexpr int Q = P + 1, N = Q * Q, SPC = Sh::SPC, CH = Sh::CH;
+  constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char cta_smem[];
+  constexpr int kGs = ((int)sizeof(GroupSmem<P, T>) + 15) / 16 * 16;
+  uint64_t* full = reinterpret_cast<uint64_t*>(cta_smem + Sh::kGroup);
+  uint64_t* empty = full + Sh::kMaxRing;
+  T* tr = reinterpret_cast<T*>(cta_smem + Sh::kGroup + Sh::kBars);
+  unsigned char* ring = cta_smem + Sh::kGroup + Sh::kBars + a.tr_bytes;
+  const unsigned NB = (unsigned)a.ring;
+  const int d = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (unsigned b = 0; b < NB; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&empty[b], Sh::kCompute);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const int k0 = a.dir_lev0[d], k1 = a.dir_lev0[d + 1];
+  // level tables in a register window of 64 levels, read with shuffles
+  int kb = k0;
+  int lb0, lg0, lm0, lb1, lg1, lm1;
+  auto load_win = [&](int base, int& lb, int& lg, int& lm) {
+    const int kk = base + lane;
+    lb = kk <= k1 ? a.lev_begin[kk] : 0;
+    lg = kk < k1 ? a.lev_gbegin[kk] : 0;
+    lm = kk < k1 ? a.lev_mbegin[kk] : 0;
+  };
+  load_win(k0, lb0, lg0, lm0);
+  load_win(k0 + 32, lb1, lg1, lm1);
+  auto lev_b = [&](int kk) { const int j = kk - kb; return __shfl_sync(FULL, j < 32 ? lb0 : lb1, j & 31); };
+  auto lev_g = [&](int kk) { const int j = kk - kb; return __shfl_sync(FULL, j < 32 ? lg0 : lg1, j & 31); };
+  auto lev_m = [&](int kk) { const int j = kk - kb; return __shfl_sync(FULL, j < 32 ? lm0 : lm1, j & 31); };
+  auto advance = [&](int k) {
+    if (k - kb >= 32) {
+      kb += 32;
+      lb0 = lb1; lg0 = lg1; lm0 = lm1;
+      load_win(kb + 32, lb1, lg1, lm1);
+    }
+  };
+  auto bounded_wait = [&](uint64_t* bar, unsigned parity) {
+    uint32_t n = 0;
+    while (!mbar_try_wait(bar, parity) && ++n < kStageWaitIters) {
+    }
+    if (n >= kStageWaitIters) atomicOr(a.status, kDevTimeout);
+  };
+  // ring position and phase parity of the next round
+  auto next = [&](unsigned& b, unsigned& par) {
+    if (++b == NB) { b = 0; par ^= 1u; }
+  };
+
+  if (warp == Sh::kProducer) {
+    unsigned rc = 0, b = 0, par = 0;
+    for (int k = k0; k < k1; ++k) {
+      advance(k);
+      const int nsingle = lev_g(k) - lev_b(k), mb = lev_m(k);
+      for (int r0 = 0; r0 < nsingle; r0 += CH, ++rc, next(b, par)) {
+        if (lane != 0) continue;
+        if (rc >= NB) bounded_wait(&empty[b], par ^ 1u);   // the buffer's previous use was released
+        const int cnt = min(CH, nsingle - r0);
+        const long long m0 = (long long)mb + r0;
+        unsigned char* rb = ring + (size_t)b * Sh::kRound;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&full[b], (unsigned)(cnt * (L::kStaged + L::kYBytes + 16)));
+        bulk_g2s(rb, L::s_at(a.rec, m0), (unsigned)(cnt * L::kStaged), &full[b]);
+        bulk_g2s(rb + Sh::kYOff, a.y + m0 * L::kYStride, (unsigned)(cnt * L::kYBytes), &full[b]);
+        bulk_g2s(rb + Sh::kTsOff, a.tslot + m0, (unsigned)(cnt * 16), &full[b]);
+      }
+    }
+    // no copy may be in flight when the CTA exits (the consumers wait for every round;
+    // this only matters after a timed-out wait)
+    if (lane == 0)
+      for (unsigned j = rc > NB ? rc - NB : 0u; j < rc; ++j) bounded_wait(&full[j % NB], (j / NB) & 1u);
+    return;
+  }
+
+  const bool compute = warp < Sh::kCompute;
+  const int i = lane % N, s_lane = lane / N;
+  const int task = warp * SPC + s_lane;
+  const bool lane_ok = compute && lane < SPC * N;
+  // the faces dof row i lies on (two at a corner) and its node position on each; the
+  // write slot of a face is 16-bit half `sh` of word y (faces 0, 1) or z (faces 2, 3)
+  // of the task's slot ids; rows on no face write to the sink slot
+  const int ia = i % Q, ib = i / Q;
+  int fA = -1, pA = 0, fB = -1, pB = 0;
+  auto on_face = [&](int f, int pos) {
+    if (fA < 0) { fA = f; pA = pos; } else { fB = f; pB = pos; }
+  };
+  if (ib == 0) on_face(0, ia);
+  if (ia == P) on_face(1, ib);
+  if (ib == P) on_face(2, ia);
+  if (ia == 0) on_face(3, ib);
+  const bool zA = fA >= 2, zB = fB >= 2;
+  const unsigned shA = 16u * (unsigned)(fA & 1), shB = 16u * (unsigned)(fB & 1);
+  const unsigned keepA = fA >= 0 ? 0xffffu : 0u, keepB = fB >= 0 ? 0xffffu : 0u;
+  const unsigned sinkA = fA >= 0 ? 0u : kTraceSink, sinkB = fB >= 0 ? 0u : kTraceSink;
+  T* outd = a.out + (size_t)d * a.E * N;
+  if (threadIdx.x < Q) tr[kTraceZero * Q + threadIdx.x] = (T)0;
+  auto direct = [&](int slot) { return a.slot_gid != nullptr && a.slot_gid[slot] >= 0; };
+  const int gidx = warp - Sh::kCompute;   // group warp index (group warps only)
+  GroupSmem<P, T>& gs = *reinterpret_cast<GroupSmem<P, T>*>(cta_smem + (compute ? 0 : gidx) * kGs);
+  unsigned rb_i = 0, rpar = 0;
+  int staged = -1;
+  if (!compute) {
+    const int g0 = lev_g(k0) + gidx;
+    if (g0 < lev_b(k0 + 1) && direct(g0)) {
+      group_stage<P, T>(a, g0, gs);
+      staged = g0;
+    }
+  }
+  named_barrier(1, (Sh::kCompute + Sh::kGroupWarps) * 32);   // the zero trace is in place
+  for (int k = k0; k < k1; ++k) {
+    advance(k);
+    const int sb = lev_b(k), sg = lev_g(k), se = lev_b(k + 1);
+    if (compute) {
+      const int nsingle = sg - sb, mb = lev_m(k);
+      for (int r0 = 0; r0 < nsingle; r0 += CH) {
+        const unsigned char* rb = ring + (size_t)rb_i * Sh::kRound;
+        bounded_wait(&full[rb_i], rpar);
+        if (lane_ok && task < nsingle - r0) {
+          const char* rs = (const char*)rb + task * L::kStaged;
+          const uint4 info = *reinterpret_cast<const uint4*>(rs);
+          const uint4 ts = *reinterpret_cast<const uint4*>(rb + Sh::kTsOff + task * 16);
+          const T* W = L::slot(rs, nullptr, 0);   // slots 0, 1 back to back; absent ones are zero
+          const T* u0 = tr + (ts.x & 0xffffu) * Q;
+          const T* u1 = tr + (ts.x >> 16) * Q;
+          // two independent FMA chains (one per W slot) joined by one add
+          T ya = reinterpret_cast<const T*>(rb + Sh::kYOff + task * L::kYBytes)[i], yb = 0;
+#pragma unroll
+          for (int t = 0; t < Q; ++t) {
+            ya = fma(-W[t * N + i], u0[t], ya);
+            yb = fma(-W[L::kSlot + t * N + i], u1[t], yb);
+          }
+          T y = ya + yb;
+          const int e = (int)info.x;
+          if (ts.w) {   // rare: couplings read from global memory
+#pragma unroll 1
+            for (int sl = 0; sl < 4; ++sl) {
+              const unsigned f = (info.z >> (8 * sl)) & 0xffu;
+              if (f == 0xffu || (sl < 2 && ((ts.x >> (16 * sl)) & 0xffffu) != kTraceZero)) continue;
+              const T* Ws = sl < 2 ? W + sl * L::kSlot
+                                   : L::slot(nullptr, L::x_at(a.recx, (long long)mb + r0 + task), sl);
+              y -= face_term<P, T, false>(Ws, outd + (size_t)nb_elem(a.nx, a.ny, e, (int)f) * N, (int)f, i);
+            }
+          }
+          outd[(size_t)(e * N + i)] = y;
+          // this row's face-node values for later single-element receivers
+          tr[((((zA ? ts.z : ts.y) >> shA) & keepA) | sinkA) * Q + pA] = y;
+          tr[((((zB ? ts.z : ts.y) >> shB) & keepB) | sinkB) * Q + pB] = y;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[rb_i]);
+        next(rb_i, rpar);
+      }
+    } else {
+      for (int g = sg + gidx; g < se; g += Sh::kGroupWarps) {
+        if (direct(g)) {
+          if (staged != g) group_stage<P, T>(a, g, gs);
+          group_solve_direct<P, T, false>(a, d, g, gs);
+        } else {
+          group_solve<P, T, MODE, false>(a, d, g);
+        }
+        staged = -1;
+      }
+      if (k + 1 < k1) {
+        const int g1 = lev_g(k + 1) + gidx;
+        if (g1 < lev_b(k + 2) && direct(g1)) {
+          group_stage<P, T>(a, g1, gs);
+          staged = g1;
+        }
+      }
+    }
+    named_barrier(1, (Sh::kCompute + Sh::kGroupWarps) * 32);
+  }
+}
+
 // -------------------------------------------------------------- FP64 residual (mixed)
 // r = b - L psi for every (element, direction) in schedule order, one lane per dof row,
 // from the stored FP64 element matrix and inflow couplings; accumulates ||r||^2, ||b||^2.
@@ -746,6 +966,7 @@ struct SweepCall {
   int cluster_size;  // CTAs per direction cluster
   int cta_warps;     // warps per CTA
   bool group_iterative;  // solve every coupled group by the inner iteration
+  bool cluster;      // cluster sweep kernel instead of the single-CTA one
 };
 
 // Host-side arguments of one problem's sweep (also the batch table entries).
@@ -859,9 +1080,55 @@ static vef_status auto_tile(int D, int& cs_out, int& warps_out) {
   return VEF_OK;
 }
 
+// Single-CTA sweep: one 16-warp CTA per direction; the trace slots take what the schedule
+// needs and the ring of round buffers the rest of the shared memory (at most 16 rounds).
+template <int P, typename T, int MODE>
+static vef_status launch_sweep_cta(const SweepCall& c, SweepArgs<T>& a) {
+  using Sh = CtaShape<P, T>;
+  const Schedule& S = *c.S;
+  const int tr = (S.trace_slots * (P + 1) * (int)sizeof(T) + 15) / 16 * 16;
+  const int rounds = std::min(Sh::kMaxRing, (Sh::trace_budget(0) - tr) / Sh::kRound);
+  if (rounds < 2) {
+    set_last_error("internal error: single-CTA sweep ring does not fit in shared memory");
+    return VEF_ERR_INVALID_ARG;
+  }
+  a.tslot = S.tslot;
+  a.ring = rounds;
+  a.tr_bytes = tr;
+  const size_t smem = (size_t)Sh::kGroup + Sh::kBars + tr + (size_t)rounds * Sh::kRound;
+  VEF_CUDA_TRY(cudaFuncSetAttribute(sweep_cta_kernel<P, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  KTimer kt(c.mesh, VEF_K_SWEEP, c.stream);
+  sweep_cta_kernel<P, T, MODE><<<(unsigned)S.D, Sh::kThreads, smem, c.stream>>>(a);
+  VEF_CUDA_TRY(cudaGetLastError());
+  return VEF_OK;
+}
+
+template <int P>
+static int cta_capacity_p() {
+  using Sh = CtaShape<P, double>;   // FP64 layout: the larger records, at least 3 rounds
+  return std::max(0, std::min(0xfffe, Sh::trace_budget(3) / ((P + 1) * (int)sizeof(double))));
+}
+
+int cta_trace_capacity(int p) {
+  switch (p) {
+    case 1: return cta_capacity_p<1>();
+    case 2: return cta_capacity_p<2>();
+    case 3: return cta_capacity_p<3>();
+    default: return cta_capacity_p<4>();
+  }
+}
+
 template <int P, typename T, int MODE>
 static vef_status launch_sweep(const SweepCall& c0, const double* rhs, T* out) {
   SweepCall c = c0;
+  if (!c.cluster) {
+    SweepArgs<T> a;
+    vef_status st = make_sweep_args<P, T>(c, rhs, out, a);
+    if (st != VEF_OK) return st;
+    if ((st = launch_apply<P, T, MODE>(c, a)) != VEF_OK) return st;
+    return launch_sweep_cta<P, T, MODE>(c, a);
+  }
   if (c.cluster_size == 0) {
     vef_status st = auto_tile<P, T, MODE>(c.S->D, c.cluster_size, c.cta_warps);
     if (st != VEF_OK) return st;
@@ -1026,6 +1293,7 @@ static void fill_opts(const vef_opts* o, SweepCall& c) {
   c.cluster_size = t ? std::min(16, std::max(1, t / 100)) : 0;
   c.cta_warps = t ? std::min(16, std::max(1, t % 100)) : 0;
   c.group_iterative = o && (o->flags & VEF_GROUPS_ITERATIVE);
+  c.cluster = t != 0 || (o && (o->flags & VEF_SWEEP_CLUSTER));
 }
 
 static void schedule_info(const Schedule& S, vef_info* info) {

@@ -83,6 +83,43 @@ def test_large_groups_mix_direct_and_iterative(lib):
     assert rel(host(psi), host(psi_it)) < 1e-12
 
 
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_cta_and_cluster_kernels_agree(lib, p):
+    """The default sweep (one CTA per direction, upwind traces in shared-memory slots) and
+    the cluster sweep both reproduce the oracle on a strongly curved mesh with coupled
+    groups, anisotropic source and inflow."""
+    prob = random_problem(11, 9, 3, 0.1, p, 8, seed=40 + p, aniso=True, sigma_range=(-1.0, 0.5))
+    _, (psi_cta, info) = _run(prob)
+    _, (psi_cl, info_cl) = _run(prob, kernel="cluster")
+    _, ref = _oracle(prob)
+    assert info["coupled_groups"] > 0 and info["timed_out"] == 0 and info_cl["timed_out"] == 0
+    assert rel(host(psi_cta), ref) < 1e-12, info
+    assert rel(host(psi_cl), ref) < 1e-12, info_cl
+
+
+@pytest.mark.parametrize("slots", ["0", "3"])
+def test_trace_slot_capacity_fallback(lib, monkeypatch, slots):
+    """With the shared-memory trace slots capped (none, or three live at a time) the
+    couplings left over read the donor's psi from global memory; results are unchanged."""
+    monkeypatch.setenv("VEF_TRACE_SLOTS", slots)
+    prob = random_problem(10, 12, 3, 0.08, 2, 8, seed=50, aniso=True)
+    _, (psi, info) = _run(prob)
+    _, ref = _oracle(prob)
+    assert rel(host(psi), ref) < 1e-12, info
+
+
+@pytest.mark.parametrize("nx,p,sn", [(30, 4, 4), (120, 1, 4)])
+def test_levels_wider_than_a_round(lib, nx, p, sn):
+    """Levels of up to nx single-element tasks span several rounds of the CTA sweep
+    (14 tasks per round at p = 4, 112 at p = 1), so the ring of round buffers wraps
+    inside a level and across levels."""
+    prob = random_problem(nx, nx, 3, 0.03, p, sn, seed=60 + p)
+    _, (psi, info) = _run(prob)
+    _, ref = _oracle(prob)
+    assert info["timed_out"] == 0
+    assert rel(host(psi), ref) < 1e-12, info
+
+
 def test_anisotropic_source_and_inflow(lib):
     prob = random_problem(6, 9, 2, 0.05, 2, 8, seed=4, aniso=True)
     _, (psi, _) = _run(prob)
