@@ -616,9 +616,11 @@ sweep_batch_kernel(const SweepArgs<T>* __restrict__ tab, const int2* __restrict_
 
 // ------------------------------------------------------------- single-CTA sweep
 // One CTA of 16 warps per direction.  Warp 15 streams the records of the direction's
-// single-element tasks (staged prefix, y row, trace slot ids) through a ring of round
-// buffers with bulk copies, as far ahead as the ring allows; warps 0..11 compute them, a
-// round being 12 * SPC consecutive tasks of one level with one lane per dof row; warps
+// single-element tasks (staged prefix, y row, trace slot ids) through a ring of chunk
+// buffers with bulk copies, as far ahead as the ring allows (a bulk copy request costs
+// ~150 issue cycles whatever its size, so a chunk holds several rounds of one level);
+// warps 0..11 compute them, a round being 12 * SPC consecutive tasks of one level with
+// one lane per dof row; warps
 // 12..14 solve the level's coupled groups, one group per warp at a time, each staging its
 // first group of the next level while the level finishes.  The upwind face values passed from one single-element task
 // to a later one go through shared-memory trace slots whose ids the schedule assigned,
@@ -633,10 +635,15 @@ struct CtaShape {
   static constexpr int kCompute = 12, kGroupWarps = 3, kProducer = 15, kThreads = 512;
   static constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
   static constexpr int CH = kCompute * SPC;                     // tasks per round
-  // round buffer: CH staged record prefixes, CH y rows, CH slot-id quadruples
-  static constexpr int kYOff = CH * L::kStaged;
-  static constexpr int kTsOff = kYOff + CH * L::kYBytes;
-  static constexpr int kRound = kTsOff + CH * 16;
+  static constexpr int kTaskBytes = L::kStaged + L::kYBytes + 16;
+  // rounds per chunk: about 48 KB of records per chunk
+  static constexpr int RC = (48 * 1024) / (CH * kTaskBytes) > 8 ? 8
+                          : ((48 * 1024) / (CH * kTaskBytes) < 1 ? 1 : (48 * 1024) / (CH * kTaskBytes));
+  static constexpr int CK = RC * CH;                             // tasks per chunk
+  // chunk buffer: CK staged record prefixes, CK y rows, CK slot-id quadruples
+  static constexpr int kYOff = CK * L::kStaged;
+  static constexpr int kTsOff = kYOff + CK * L::kYBytes;
+  static constexpr int kRound = kTsOff + CK * 16;                // bytes of one chunk buffer
   static constexpr int kGroup = kGroupWarps * (((int)sizeof(GroupSmem<P, T>) + 15) / 16 * 16);
   static constexpr int kMaxRing = 16;
   static constexpr int kBars = 2 * kMaxRing * 8;
@@ -649,7 +656,7 @@ template <int P, typename T, int MODE>
 __global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
   using Sh = CtaShape<P, T>;
   using L = Rec<P, T>;
-  constexpr int Q = P + 1, N = Q * Q, SPC = Sh::SPC, CH = Sh::CH;
+  constexpr int Q = P + 1, N = Q * Q, SPC = Sh::SPC, CH = Sh::CH, CK = Sh::CK;
   constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char cta_smem[];
   constexpr int kGs = ((int)sizeof(GroupSmem<P, T>) + 15) / 16 * 16;
@@ -706,10 +713,10 @@ __global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
     for (int k = k0; k < k1; ++k) {
       advance(k);
       const int nsingle = lev_g(k) - lev_b(k), mb = lev_m(k);
-      for (int r0 = 0; r0 < nsingle; r0 += CH, ++rc, next(b, par)) {
+      for (int r0 = 0; r0 < nsingle; r0 += CK, ++rc, next(b, par)) {
         if (lane != 0) continue;
         if (rc >= NB) bounded_wait(&empty[b], par ^ 1u);   // the buffer's previous use was released
-        const int cnt = min(CH, nsingle - r0);
+        const int cnt = min(CK, nsingle - r0);
         const long long m0 = (long long)mb + r0;
         unsigned char* rb = ring + (size_t)b * Sh::kRound;
         fence_proxy_async_smem();
@@ -766,39 +773,43 @@ __global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
     const int sb = lev_b(k), sg = lev_g(k), se = lev_b(k + 1);
     if (compute) {
       const int nsingle = sg - sb, mb = lev_m(k);
-      for (int r0 = 0; r0 < nsingle; r0 += CH) {
+      for (int c0 = 0; c0 < nsingle; c0 += CK) {
         const unsigned char* rb = ring + (size_t)rb_i * Sh::kRound;
         bounded_wait(&full[rb_i], rpar);
-        if (lane_ok && task < nsingle - r0) {
-          const char* rs = (const char*)rb + task * L::kStaged;
-          const uint4 info = *reinterpret_cast<const uint4*>(rs);
-          const uint4 ts = *reinterpret_cast<const uint4*>(rb + Sh::kTsOff + task * 16);
-          const T* W = L::slot(rs, nullptr, 0);   // slots 0, 1 back to back; absent ones are zero
-          const T* u0 = tr + (ts.x & 0xffffu) * Q;
-          const T* u1 = tr + (ts.x >> 16) * Q;
-          // two independent FMA chains (one per W slot) joined by one add
-          T ya = reinterpret_cast<const T*>(rb + Sh::kYOff + task * L::kYBytes)[i], yb = 0;
+        const int cend = min(CK, nsingle - c0);
+        for (int tk = task; tk - task < cend; tk += CH) {   // the chunk's rounds
+          const int r0 = c0 + tk - task;
+          if (lane_ok && tk < cend) {
+            const char* rs = (const char*)rb + tk * L::kStaged;
+            const uint4 info = *reinterpret_cast<const uint4*>(rs);
+            const uint4 ts = *reinterpret_cast<const uint4*>(rb + Sh::kTsOff + tk * 16);
+            const T* W = L::slot(rs, nullptr, 0);   // slots 0, 1 back to back; absent ones are zero
+            const T* u0 = tr + (ts.x & 0xffffu) * Q;
+            const T* u1 = tr + (ts.x >> 16) * Q;
+            // two independent FMA chains (one per W slot) joined by one add
+            T ya = reinterpret_cast<const T*>(rb + Sh::kYOff + tk * L::kYBytes)[i], yb = 0;
 #pragma unroll
-          for (int t = 0; t < Q; ++t) {
-            ya = fma(-W[t * N + i], u0[t], ya);
-            yb = fma(-W[L::kSlot + t * N + i], u1[t], yb);
-          }
-          T y = ya + yb;
-          const int e = (int)info.x;
-          if (ts.w) {   // rare: couplings read from global memory
-#pragma unroll 1
-            for (int sl = 0; sl < 4; ++sl) {
-              const unsigned f = (info.z >> (8 * sl)) & 0xffu;
-              if (f == 0xffu || (sl < 2 && ((ts.x >> (16 * sl)) & 0xffffu) != kTraceZero)) continue;
-              const T* Ws = sl < 2 ? W + sl * L::kSlot
-                                   : L::slot(nullptr, L::x_at(a.recx, (long long)mb + r0 + task), sl);
-              y -= face_term<P, T, false>(Ws, outd + (size_t)nb_elem(a.nx, a.ny, e, (int)f) * N, (int)f, i);
+            for (int t = 0; t < Q; ++t) {
+              ya = fma(-W[t * N + i], u0[t], ya);
+              yb = fma(-W[L::kSlot + t * N + i], u1[t], yb);
             }
+            T y = ya + yb;
+            const int e = (int)info.x;
+            if (ts.w) {   // rare: couplings read from global memory
+#pragma unroll 1
+              for (int sl = 0; sl < 4; ++sl) {
+                const unsigned f = (info.z >> (8 * sl)) & 0xffu;
+                if (f == 0xffu || (sl < 2 && ((ts.x >> (16 * sl)) & 0xffffu) != kTraceZero)) continue;
+                const T* Ws = sl < 2 ? W + sl * L::kSlot
+                                     : L::slot(nullptr, L::x_at(a.recx, (long long)mb + r0 + task), sl);
+                y -= face_term<P, T, false>(Ws, outd + (size_t)nb_elem(a.nx, a.ny, e, (int)f) * N, (int)f, i);
+              }
+            }
+            outd[(size_t)(e * N + i)] = y;
+            // this row's face-node values for later single-element receivers
+            tr[((((zA ? ts.z : ts.y) >> shA) & keepA) | sinkA) * Q + pA] = y;
+            tr[((((zB ? ts.z : ts.y) >> shB) & keepB) | sinkB) * Q + pB] = y;
           }
-          outd[(size_t)(e * N + i)] = y;
-          // this row's face-node values for later single-element receivers
-          tr[((((zA ? ts.z : ts.y) >> shA) & keepA) | sinkA) * Q + pA] = y;
-          tr[((((zB ? ts.z : ts.y) >> shB) & keepB) | sinkB) * Q + pB] = y;
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[rb_i]);
