@@ -786,14 +786,23 @@ __global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
             const T* W = L::slot(rs, nullptr, 0);   // slots 0, 1 back to back; absent ones are zero
             const T* u0 = tr + (ts.x & 0xffffu) * Q;
             const T* u1 = tr + (ts.x >> 16) * Q;
-            // two independent FMA chains (one per W slot) joined by one add
-            T ya = reinterpret_cast<const T*>(rb + Sh::kYOff + tk * L::kYBytes)[i], yb = 0;
+            T y = reinterpret_cast<const T*>(rb + Sh::kYOff + tk * L::kYBytes)[i];
+            if constexpr (sizeof(T) == 8) {
+              // FP64 issue is the limit: one chain of 2(p+1) FMAs
 #pragma unroll
-            for (int t = 0; t < Q; ++t) {
-              ya = fma(-W[t * N + i], u0[t], ya);
-              yb = fma(-W[L::kSlot + t * N + i], u1[t], yb);
+              for (int t = 0; t < Q; ++t) y = fma(-W[t * N + i], u0[t], y);
+#pragma unroll
+              for (int t = 0; t < Q; ++t) y = fma(-W[L::kSlot + t * N + i], u1[t], y);
+            } else {
+              // latency is the limit: two independent chains joined by one add
+              T yb = 0;
+#pragma unroll
+              for (int t = 0; t < Q; ++t) {
+                y = fma(-W[t * N + i], u0[t], y);
+                yb = fma(-W[L::kSlot + t * N + i], u1[t], yb);
+              }
+              y += yb;
             }
-            T y = ya + yb;
             const int e = (int)info.x;
             if (ts.w) {   // rare: couplings read from global memory
 #pragma unroll 1
