@@ -88,12 +88,13 @@ def flops_sweep(p, inflow_faces=2.0):
 
 
 def bytes_sweep(p, word=8, inflow_faces=2.0):
-    """Per (element, direction) sweep DRAM bytes: the staged record prefix (16 bytes of
-    element info + two W slots), the padded y row, the upwind face traces read and psi
-    written."""
+    """Per (element, direction) sweep DRAM bytes of the single-CTA sweep: the staged record
+    prefix (16 bytes of element info + two W slots), the padded y row, the 16 bytes of
+    trace-slot ids, and psi written (the upwind face values pass through shared memory;
+    inflow_faces is kept for the flop count's signature)."""
     n = (p + 1) ** 2
     pad = lambda b: (b + 15) // 16 * 16
-    return pad(16 + 2 * word * n * (p + 1)) + pad(word * n) + 8 * inflow_faces * (p + 1) + 8 * n
+    return pad(16 + 2 * word * n * (p + 1)) + pad(word * n) + 16 + 8 * n
 
 
 SWEEP_REGION = ("// upwind correction of row i for face f of member record r",
