@@ -69,6 +69,28 @@ def test_adjoint_with_coupled_groups(lib):
     assert rel(host(gdst), dst) < 1e-12
 
 
+@pytest.mark.parametrize("p", [1, 3, 4])
+def test_adjoint_other_orders(lib, p):
+    """Adjoint sweep against the oracle's adjoint at the other DG orders (curved mesh,
+    heterogeneous media, phi_in given)."""
+    from paper_2301_04758_gb300.api import Mesh
+    prob = random_problem(7, 6, 3, 0.06, p, 4, seed=80 + p, with_inflow=False)
+    disc = Discretization(7, 6, 3, 0.06, p)
+    g = region_weights(disc, (0.2, 0.2), (0.8, 0.7))
+    psi = o_sweep(disc, prob["omega"], prob["weights"], prob["sigma_t"], prob["sigma_s"],
+                  phi_in=prob["phi_in"], source=prob["source"])
+    lam, dst, dss = o_adjoint(disc, prob["omega"], prob["weights"], prob["sigma_t"], prob["sigma_s"],
+                              psi, g, phi_in=prob["phi_in"])
+    mesh = Mesh(7, 6, 3, p, 0.06)
+    gdst, gdss, glam, info = mesh.adjoint(dev(prob["sigma_t"]), dev(prob["sigma_s"]), prob["omega"],
+                                          prob["weights"], dev(psi), dev(g),
+                                          phi_in=dev(prob["phi_in"]), want_lambda=True, info=True)
+    assert info["timed_out"] == 0
+    assert rel(host(glam), lam) < 1e-12, info
+    assert rel(host(gdst), dst) < 1e-12
+    assert rel(host(gdss), dss) < 1e-12
+
+
 def test_region_weights_match_oracle(lib):
     from paper_2301_04758_gb300.api import Mesh
     disc = Discretization(11, 7, 3, 0.06, 3)
