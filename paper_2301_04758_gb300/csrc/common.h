@@ -62,8 +62,8 @@ constexpr int kGroupMaxTrace = 128;
 constexpr int kGroupSmemTrace = 32;   // the trace-system inverse sits in shared memory up to this size
 
 // Shared-memory trace slots one single-CTA sweep of DG order p can hold (sweep.cu).  Slot
-// kTraceZero holds zeros and is never written, slot kTraceSink is written and never read;
-// the schedule assigns the others.
+// kTraceZero holds zeros and is never written; id kTraceSink marks a face whose values no
+// later single-element task reads (nothing is stored); the schedule assigns the others.
 int cta_trace_capacity(int p);
 constexpr unsigned kTraceZero = 0, kTraceSink = 1, kTraceFirst = 2;
 

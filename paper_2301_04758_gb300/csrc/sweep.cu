@@ -739,7 +739,7 @@ __global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
   const bool lane_ok = compute && lane < SPC * N;
   // the faces dof row i lies on (two at a corner) and its node position on each; the
   // write slot of a face is 16-bit half `sh` of word y (faces 0, 1) or z (faces 2, 3)
-  // of the task's slot ids; rows on no face write to the sink slot
+  // of the task's slot ids; rows on no face get the sink id (no store)
   const int ia = i % Q, ib = i / Q;
   int fA = -1, pA = 0, fB = -1, pB = 0;
   auto on_face = [&](int f, int pos) {
@@ -815,9 +815,12 @@ __global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
               }
             }
             outd[(size_t)(e * N + i)] = y;
-            // this row's face-node values for later single-element receivers
-            tr[((((zA ? ts.z : ts.y) >> shA) & keepA) | sinkA) * Q + pA] = y;
-            tr[((((zB ? ts.z : ts.y) >> shB) & keepB) | sinkB) * Q + pB] = y;
+            // this row's face-node values for later single-element receivers (no store for
+            // faces nobody reads: id kTraceSink)
+            const unsigned idA = (((zA ? ts.z : ts.y) >> shA) & keepA) | sinkA;
+            const unsigned idB = (((zB ? ts.z : ts.y) >> shB) & keepB) | sinkB;
+            if (idA != kTraceSink) tr[idA * Q + pA] = y;
+            if (idB != kTraceSink) tr[idB * Q + pB] = y;
           }
         }
         __syncwarp();
