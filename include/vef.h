@@ -213,7 +213,11 @@ vef_status vef_batch_create(const vef_mesh* meshes, int nprob, const double* con
                             const double* const* weights, const int* D, vef_batch* out);
 vef_status vef_batch_destroy(vef_batch batch);
 /* Per-problem arrays of [device] pointers, layouts as in vef_sweep (isotropic source,
- * entries of phi_in / source / inflow may be NULL, and so may these arrays). */
+ * entries of phi_in / source / inflow may be NULL, and so may these arrays).  The
+ * per-problem kernel arguments live in a pinned host table that each call rewrites and
+ * copies to the device asynchronously; a call first waits (host side) for the previous
+ * call's copy.  A captured call copies the table when the graph is replayed, so new
+ * calls on the same batch must not overlap replays still in flight. */
 vef_status vef_batch_sweep(vef_batch batch, const double* const* sigma_t, const double* const* sigma_s,
                            const double* const* phi_in, const double* const* source,
                            const double* const* inflow, double* const* psi, const vef_opts* opts,

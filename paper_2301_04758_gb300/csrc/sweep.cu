@@ -393,14 +393,13 @@ constexpr uint32_t kStageWaitIters = 1u << 26;
 // coupled groups, so a group's inner iteration never delays a warp's singles and its
 // static data is staged while the previous level finishes.
 template <int P, typename T, int MODE>
-__device__ __forceinline__ void sweep_direction(const SweepArgs<T>& a, int d) {
+__device__ __forceinline__ void sweep_direction(const SweepArgs<T>& a, int d, int cs) {
   constexpr int Q = P + 1, N = Q * Q;
   using L = Rec<P, T>;
   constexpr int SPC = SweepSmem<P, T>::SPC;
   extern __shared__ __align__(16) unsigned char sweep_smem[];
   const int lane = threadIdx.x & 31;
   SweepSmem<P, T>& sm = reinterpret_cast<SweepSmem<P, T>*>(sweep_smem)[threadIdx.x >> 5];
-  const int cs = a.cluster_size;
   const int nw = cs * (blockDim.x >> 5);
   const int gw = (blockIdx.x % cs) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int ng = sweep_group_warps(nw);
@@ -602,7 +601,7 @@ __device__ __forceinline__ void sweep_direction(const SweepArgs<T>& a, int d) {
 // one cluster per direction of one problem
 template <int P, typename T, int MODE>
 __global__ void __maxnreg__(128) sweep_kernel(SweepArgs<T> a) {
-  sweep_direction<P, T, MODE>(a, blockIdx.x / a.cluster_size);
+  sweep_direction<P, T, MODE>(a, blockIdx.x / a.cluster_size, a.cluster_size);
 }
 
 // batch of independent problems of one DG order: cluster c runs direction cmap[c].y of
@@ -611,7 +610,7 @@ template <int P, typename T, int MODE>
 __global__ void __maxnreg__(128)
 sweep_batch_kernel(const SweepArgs<T>* __restrict__ tab, const int2* __restrict__ cmap, int cluster_size) {
   const int2 pd = cmap[blockIdx.x / cluster_size];
-  sweep_direction<P, T, MODE>(tab[pd.x], pd.y);
+  sweep_direction<P, T, MODE>(tab[pd.x], pd.y, cluster_size);   // the launch's cluster size
 }
 
 // ------------------------------------------------------------- single-CTA sweep
@@ -1465,12 +1464,18 @@ struct vef_batch_s {
   std::vector<vef::Schedule*> scheds;
   vef::BatchClass cls[vef::kMaxP + 1];
   bool swept = false;
+  // the pinned argument tables are copied to the device asynchronously; the host rewrites
+  // them only once the copies of the previous call have been done (event recorded after
+  // them, outside stream capture)
+  cudaEvent_t tab_copied = nullptr;
+  bool tab_pending = false;
   ~vef_batch_s() {
     for (auto& c : cls) {
       cudaFree(c.cmap);
       cudaFree(c.tab_dev);
       cudaFreeHost(c.tab_host);
     }
+    if (tab_copied) cudaEventDestroy(tab_copied);
   }
 };
 
@@ -1479,9 +1484,6 @@ namespace vef {
 template <int P>
 static vef_status batch_launch_class(vef_batch_s& B, BatchClass& C, int tile, cudaStream_t s) {
   const int cs = std::min(16, std::max(1, tile / 100)), warps = std::min(16, std::max(1, tile % 100));
-  for (size_t j = 0; j < C.probs.size(); ++j) C.tab_host[j].cluster_size = cs;
-  VEF_CUDA_TRY(cudaMemcpyAsync(C.tab_dev, C.tab_host, C.probs.size() * sizeof(SweepArgs<double>),
-                               cudaMemcpyHostToDevice, s));
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
   vef_status st = cluster_config<P, double>(sweep_batch_kernel<P, double, 0>, C.clusters, cs, warps, s, cfg, attr);
@@ -1584,6 +1586,13 @@ extern "C" vef_status vef_batch_sweep(vef_batch batch, const double* const* sigm
       set_last_error("sigma_t, sigma_s and psi entries are required for every problem");
       return VEF_ERR_INVALID_ARG;
     }
+  cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+  VEF_CUDA_TRY(cudaStreamIsCapturing(s, &capturing));
+  if (B.tab_pending && capturing == cudaStreamCaptureStatusNone) {
+    // the previous call's table copies must have read the tables before they change
+    VEF_CUDA_TRY(cudaEventSynchronize(B.tab_copied));
+    B.tab_pending = false;
+  }
   for (int p = 1; p <= kMaxP; ++p) {
     BatchClass& C = B.cls[p];
     for (size_t j = 0; j < C.probs.size(); ++j) {
@@ -1609,6 +1618,17 @@ extern "C" vef_status vef_batch_sweep(vef_batch batch, const double* const* sigm
       }
       if (st != VEF_OK) return st;
     }
+  }
+  for (int p = 1; p <= kMaxP; ++p) {
+    BatchClass& C = B.cls[p];
+    if (C.probs.empty()) continue;
+    VEF_CUDA_TRY(cudaMemcpyAsync(C.tab_dev, C.tab_host, C.probs.size() * sizeof(SweepArgs<double>),
+                                 cudaMemcpyHostToDevice, s));
+  }
+  if (capturing == cudaStreamCaptureStatusNone) {
+    if (!B.tab_copied) VEF_CUDA_TRY(cudaEventCreateWithFlags(&B.tab_copied, cudaEventDisableTiming));
+    VEF_CUDA_TRY(cudaEventRecord(B.tab_copied, s));
+    B.tab_pending = true;
   }
   for (int p = 1; p <= kMaxP; ++p) {
     BatchClass& C = B.cls[p];
@@ -1658,7 +1678,12 @@ extern "C" vef_status vef_batch_tune(vef_batch batch, void* stream, int* tiles_o
     int best_tile = kDefaultTile64;
     for (int tile : candidates) {
       vef_status st = batch_launch(*batch, p, tile, s);   // warm-up (also checks the shape launches)
-      if (st != VEF_OK) continue;
+      if (st != VEF_OK) {
+        // a shape that cannot launch is skipped; an error left by the device is not
+        const cudaError_t q = cudaStreamQuery(s);
+        if (q != cudaSuccess && q != cudaErrorNotReady) return cuda_fail(q, "batch tuning launch");
+        continue;
+      }
       VEF_CUDA_TRY(cudaEventRecord(e0, s));
       for (int r = 0; r < 3; ++r)
         if ((st = batch_launch(*batch, p, tile, s)) != VEF_OK) break;

@@ -45,6 +45,31 @@ def test_batch_matches_single_sweeps_and_tuning_keeps_results(lib):
         assert rel(host(a), b) < 1e-15
 
 
+def test_tuning_right_after_an_unsynchronised_sweep(lib):
+    """The first batched sweep returns without synchronising and the tuner starts at once:
+    the argument tables still being copied for that sweep must not change under it, and
+    every later sweep must reproduce the single-problem sweeps."""
+    from paper_2301_04758_gb300.api import Mesh, Batch
+    specs = [(48, 3, 12), (40, 4, 8), (64, 2, 16), (56, 1, 6)]
+    probs = []
+    for k, (N, p, sn) in enumerate(specs):
+        mesh = Mesh(N, N, 3, p, 0.05)
+        om, w = level_symmetric(sn)
+        st, ss = seeded_media(N * N, 500 + k)
+        probs.append(dict(mesh=mesh, om=om, w=w, st=dev(st), ss=dev(ss),
+                          q=dev(np.ones((N * N, (p + 1) ** 2)))))
+    single = [host(P["mesh"].sweep(P["st"], P["ss"], P["om"], P["w"], source=P["q"])) for P in probs]
+    batch = Batch([P["mesh"] for P in probs], [P["om"] for P in probs], [P["w"] for P in probs])
+    args = ([P["st"] for P in probs], [P["ss"] for P in probs])
+    psi = batch.sweep(*args, source=[P["q"] for P in probs])        # no info: returns at once
+    batch.tune()
+    for _ in range(2):
+        batch.sweep(*args, source=[P["q"] for P in probs], psi=psi)
+    torch.cuda.synchronize()
+    for a, b in zip(psi, single):
+        assert rel(host(a), b) < 1e-15
+
+
 def test_batch_sweep_replays_from_a_cuda_graph(lib):
     from paper_2301_04758_gb300.api import Batch
     probs = _problems()
