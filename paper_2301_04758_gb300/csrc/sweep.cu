@@ -837,10 +837,22 @@ __global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
         staged = -1;
       }
       if (k + 1 < k1) {
-        const int g1 = lev_g(k + 1) + gidx;
-        if (g1 < lev_b(k + 2) && direct(g1)) {
+        const int g1 = lev_g(k + 1) + gidx, ge = lev_b(k + 2);
+        if (g1 < ge && direct(g1)) {
           group_stage<P, T>(a, g1, gs);
           staged = g1;
+        }
+        // the next level's group records (never staged by the producer) into L2: the
+        // solves read their W slots twice
+        for (int g = g1; g < ge; g += Sh::kGroupWarps) {
+          const long long first = a.slot_first[g];
+          const int cnt = a.slot_count[g];
+          constexpr int kSL = (L::kStaged + 127) / 128, kXL = (L::kExtra + 127) / 128;
+          for (int t = lane; t < cnt * (kSL + kXL); t += 32) {
+            const int mi = t / (kSL + kXL), li = t % (kSL + kXL);
+            prefetch_l2(li < kSL ? L::s_at(a.rec, first + mi) + li * 128
+                                 : L::x_at(a.recx, first + mi) + (li - kSL) * 128);
+          }
         }
       }
     }
