@@ -861,8 +861,10 @@ __global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
 }
 
 // -------------------------------------------------------------- FP64 residual (mixed)
-// r = b - L psi for every (element, direction) in schedule order, one lane per dof row,
-// from the stored FP64 element matrix and inflow couplings; accumulates ||r||^2, ||b||^2.
+// r = b - L psi for every (element, direction) in schedule order, one thread per dof row
+// (the rows of consecutive tasks packed across the lanes: the kernel is bound by FP64
+// issue, and n = 9 rows would leave 5 of 32 lanes idle), from the stored FP64 element
+// matrix and inflow couplings; accumulates ||r||^2, ||b||^2.
 template <int P>
 __global__ void __launch_bounds__(128)
 residual_kernel(long long nmem, long long E, int nx, int ny, long long nbf,
@@ -874,15 +876,13 @@ residual_kernel(long long nmem, long long E, int nx, int ny, long long nbf,
                 const double* __restrict__ psi, FaceTab<double> ft, double* __restrict__ r,
                 double* __restrict__ norms) {
   constexpr int Q = P + 1, N = Q * Q, NQ = P + 2, B = N * N + 4 * Q * Q;
-  constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
   const int lane = threadIdx.x & 31;
-  const int i = lane % N;
   double rr = 0.0, bb = 0.0;
-  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-       warp * SPC < nmem; warp += nwarps) {
-  const long long m = warp * SPC + lane / N;
-  if (lane < SPC * N && m < nmem) {
+  const long long nthreads = (long long)gridDim.x * blockDim.x;
+  for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < nmem * N; row += nthreads) {
+  const long long m = row / N;
+  const int i = (int)(row - m * N);
+  {
     const uint32_t cd = code[m];
     const int d = (int)(cd >> 22), e = (int)(cd & 0x3fffffu);
     const uint16_t bits = finfo[(size_t)d * E + e];
@@ -1186,12 +1186,10 @@ static vef_status launch_residual(const SweepCall& c, const double* psi, double*
   Mesh& M = *c.mesh;
   Schedule& S = *c.S;
   constexpr int N = (P + 1) * (P + 1);
-  constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
-  const long long warps = (S.members + SPC - 1) / SPC;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const unsigned grid = (unsigned)std::min<long long>(nblk(warps * 32, 128), (long long)sms * 16);
+  const unsigned grid = (unsigned)std::min<long long>(nblk(S.members * N, 128), (long long)sms * 16);
   VEF_CUDA_TRY(cudaMemsetAsync(norms, 0, 2 * sizeof(double), c.stream));
   KTimer kt(&M, VEF_K_RESIDUAL, c.stream);
   residual_kernel<P><<<grid, 128, 0, c.stream>>>(
