@@ -171,8 +171,10 @@ class Mesh:
         return g
 
     def adjoint(self, sigma_t, sigma_s, omega, weights, psi, g, phi_in=None, want_lambda=False,
-                info=False, stream=None):
-        """Gradients of R = sum g * phi: returns (dR/dsigma_t [E], dR/dsigma_s [E] or None, lambda)."""
+                info=False, stream=None, kernel="cta"):
+        """Gradients of R = sum g * phi: returns (dR/dsigma_t [E], dR/dsigma_s [E] or None, lambda).
+
+        kernel: "cta" (one CTA per direction, the default) or "cluster"."""
         om, omp = _host(omega)
         w, wp = _host(weights)
         D = len(w)
@@ -180,9 +182,10 @@ class Mesh:
         dst = self._empty(self.E)
         dss = self._empty(self.E) if phi_in is not None else None
         inf = _lib.VefInfo() if info else None
+        o = _opts(kernel=kernel)
         st = self.lib.vef_adjoint_sweep(self.handle, _ptr(sigma_t), _ptr(sigma_s), _ptr(phi_in), omp,
                                         wp, D, _ptr(psi), _ptr(g), _ptr(lam), _ptr(dst), _ptr(dss),
-                                        None, ctypes.byref(inf) if info else None, _stream(stream))
+                                        ctypes.byref(o), ctypes.byref(inf) if info else None, _stream(stream))
         _lib.check(st, "vef_adjoint_sweep")
         res = (dst, dss, lam)
         return res + (inf.as_dict(),) if info else res

@@ -6,8 +6,9 @@
 // With r_e := A_e^T lambda_e and the stored W_{e',f'} = A_{e'}^{-1} Cin_{e',f'} of the
 // forward factorisation, C[e'][e]^T lambda_{e'} = W_{e',f'}^T r_{e'} placed on e's face
 // nodes, so each element needs its downstream neighbours' r, and lambda_e = A_e^{-T} r_e.
-// The sweep therefore runs the forward schedule backwards (downwind order), one
-// thread-block cluster per direction as in the forward sweep.
+// The sweep therefore runs the forward schedule backwards (downwind order): one CTA per
+// direction with the forward sweep's shared-memory slots (the default), or one
+// thread-block cluster per direction.
 //   dR/dsigma_t,e = - sum_d lambda_{d,e}^T M_e psi_{d,e}
 //   dR/dsigma_s,e =   sum_d lambda_{d,e}^T M_e phi_in,e / (4 pi)
 #include <algorithm>
@@ -17,10 +18,17 @@
 
 namespace vef {
 
+constexpr uint32_t kAdjWaitIters = 1u << 26;   // bounded waits of the single-CTA sweep
+
 struct AdjArgs {
   const int* dir_lev0;
   const int* lev_begin;
   const int* lev_gbegin;
+  const int* lev_mbegin;
+  const uint4* tslot;     // single-CTA sweep: the forward schedule's slot ids (roles swapped)
+  const double* yadj;     // single-CTA sweep: w_d g_e rows per member (16-byte padded)
+  int ring;               // single-CTA sweep: chunk buffers in the ring
+  int tr_bytes;           // single-CTA sweep: bytes of the trace slots
   int cluster_size;
   const int* slot_first;
   const int* slot_count;
@@ -49,7 +57,9 @@ struct AdjArgs {
 };
 
 // r_i of element e (lane = dof row i): w_d g_i minus the downstream couplings on e's faces
-template <int P>
+// (CG: the receivers' r are read at L2, as a cluster's other CTAs wrote them; in the
+// single-CTA sweep this SM wrote them, and they are read with ordinary loads)
+template <int P, bool CG = true>
 __device__ __forceinline__ double adj_rhs(const AdjArgs& a, int d, int e, long long m, int i, uint16_t bits,
                                           int first, int pos_self, int cnt, int it, bool in_group) {
   constexpr int Q = P + 1, N = Q * Q;
@@ -77,7 +87,7 @@ __device__ __forceinline__ double adj_rhs(const AdjArgs& a, int d, int e, long l
     const double* rn = a.radj + ((size_t)d * a.E + nb) * N;
     double s = 0.0;
 #pragma unroll
-    for (int j = 0; j < N; ++j) s += W[j] * __ldcg(rn + j);
+    for (int j = 0; j < N; ++j) s += W[j] * (CG ? __ldcg(rn + j) : rn[j]);
     r -= s;
   }
   (void)cnt;
@@ -128,7 +138,7 @@ __device__ __forceinline__ void adj_finish(const AdjArgs& a, long long m, int d,
 // One thread-block cluster per direction walks the direction's levels backwards; the
 // receivers of a task sit at later levels, so they are complete after the previous
 // cluster barrier.
-template <int P>
+template <int P, bool CG = true>
 __device__ __forceinline__ void adj_group(const AdjArgs& a, int d, int s0) {
   constexpr int Q = P + 1, N = Q * Q;
   constexpr unsigned FULL = 0xffffffffu;
@@ -145,9 +155,9 @@ __device__ __forceinline__ void adj_group(const AdjArgs& a, int d, int s0) {
       const int e = (int)(a.code[first + mi] & 0x3fffffu);
       const uint16_t bits = a.finfo[(size_t)d * a.E + e];
       if (act) {
-        const double r = adj_rhs<P>(a, d, e, first + mi, i, bits, first, mi, cnt, it, true);
+        const double r = adj_rhs<P, CG>(a, d, e, first + mi, i, bits, first, mi, cnt, it, true);
         double* o = a.radj + ((size_t)d * a.E + e) * N + i;
-        if (it > 0) dmax = fmax(dmax, fabs(r - __ldcg(o)));
+        if (it > 0) dmax = fmax(dmax, fabs(r - (CG ? __ldcg(o) : *o)));
         amax = fmax(amax, fabs(r));
         *o = r;
       }
@@ -196,6 +206,235 @@ __global__ void __maxnreg__(128) adjoint_kernel(AdjArgs a) {
     }
     for (int gs = sg + gw; gs < se; gs += nw) adj_group<P>(a, d, gs);
     cluster_barrier();
+  }
+}
+
+// ------------------------------------------------------------ single-CTA backward sweep
+// One CTA of 16 warps per direction walks the forward schedule's levels backwards.  The
+// couplings are the forward ones with the roles swapped: a receiver e' (done first)
+// projects its r onto the face of each donor that feeds one of its staged W slots,
+// s_t = sum_i W[t][i] r_i (the C^T lambda term of the donor's face nodes), and writes the
+// p+1 values into the slot through which the forward sweep passed the donor's face values;
+// the donor subtracts them from w_d g on its outflow face rows.  Warp 15 streams the
+// singles' records (info + W slots 0, 1), their w_d g rows and slot ids through a ring of
+// chunk buffers (bulk copies); warps 0..11 compute rounds of 12 SPC tasks, the
+// projections summed over a task's rows through a per-warp scratch; warps 12..14 run the
+// coupled groups (inner iteration on the transposed blocks); a named barrier separates
+// levels.  Couplings whose slot is missing (receivers in groups, third and fourth W
+// slots, capacity) are read from global memory (slot-id flag bit 1).
+template <int P>
+struct AdjShape {
+  static constexpr int Q = P + 1, N = Q * Q;
+  using L = Rec<P, double>;
+  static constexpr int kCompute = 12, kGroupWarps = 3, kProducer = 15, kThreads = 512;
+  static constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
+  static constexpr int CH = kCompute * SPC;
+  static constexpr int kTaskBytes = L::kStaged + L::kYBytes + 16;
+  static constexpr int RC = (48 * 1024) / (CH * kTaskBytes) > 8 ? 8
+                          : ((48 * 1024) / (CH * kTaskBytes) < 1 ? 1 : (48 * 1024) / (CH * kTaskBytes));
+  static constexpr int CK = RC * CH;
+  static constexpr int kYOff = CK * L::kStaged;
+  static constexpr int kTsOff = kYOff + CK * L::kYBytes;
+  static constexpr int kRound = kTsOff + CK * 16;
+  static constexpr int kMaxRing = 16;
+  static constexpr int kBars = 2 * kMaxRing * 8;
+  static constexpr int kScratch = kCompute * SPC * 2 * Q * N * 8;   // per warp [task][slot][t][row]
+  static constexpr int kSmemMax = 227 * 1024;
+  static constexpr int avail() { return kSmemMax - kBars - kScratch; }
+};
+
+__global__ void adj_yadj_kernel(long long nmem, int n, int ystride, long long E, const uint32_t* __restrict__ code,
+                                const double* __restrict__ weights, const double* __restrict__ g,
+                                double* __restrict__ y) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= nmem * n) return;
+  const long long m = t / n;
+  const int i = (int)(t - m * n);
+  const uint32_t c = code[m];
+  const int d = (int)(c >> 22), e = (int)(c & 0x3fffffu);
+  y[m * ystride + i] = weights[d] * g[(size_t)e * n + i];
+}
+
+template <int P>
+__global__ void __maxnreg__(128) adjoint_cta_kernel(AdjArgs a) {
+  using Sh = AdjShape<P>;
+  using L = Rec<P, double>;
+  constexpr int Q = P + 1, N = Q * Q, SPC = Sh::SPC, CH = Sh::CH, CK = Sh::CK;
+  constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char adj_smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(adj_smem);
+  uint64_t* empty = full + Sh::kMaxRing;
+  double* scratch_all = reinterpret_cast<double*>(adj_smem + Sh::kBars);
+  double* tr = reinterpret_cast<double*>(adj_smem + Sh::kBars + Sh::kScratch);
+  unsigned char* ring = adj_smem + Sh::kBars + Sh::kScratch + a.tr_bytes;
+  const unsigned NB = (unsigned)a.ring;
+  const int d = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (unsigned b = 0; b < NB; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&empty[b], Sh::kCompute);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const int k0 = a.dir_lev0[d], k1 = a.dir_lev0[d + 1];
+  // level tables of levels kt - j (lane j) and kt - 32 - j, read with shuffles, walking down
+  int kt = k1 - 1;
+  int lb0, le0, lg0, lm0, lb1, le1, lg1, lm1;
+  auto load_win = [&](int top, int& lb, int& le, int& lg, int& lm) {
+    const int kk = top - lane;
+    const bool ok = kk >= k0;
+    lb = ok ? a.lev_begin[kk] : 0;
+    le = ok ? a.lev_begin[kk + 1] : 0;
+    lg = ok ? a.lev_gbegin[kk] : 0;
+    lm = ok ? a.lev_mbegin[kk] : 0;
+  };
+  load_win(kt, lb0, le0, lg0, lm0);
+  load_win(kt - 32, lb1, le1, lg1, lm1);
+  auto lev = [&](int kk, int x0, int x1) { const int j = kt - kk; return __shfl_sync(FULL, j < 32 ? x0 : x1, j & 31); };
+  auto advance = [&](int k) {
+    if (kt - k >= 32) {
+      kt -= 32;
+      lb0 = lb1; le0 = le1; lg0 = lg1; lm0 = lm1;
+      load_win(kt - 32, lb1, le1, lg1, lm1);
+    }
+  };
+  auto bounded_wait = [&](uint64_t* bar, unsigned parity) {
+    uint32_t n = 0;
+    while (!mbar_try_wait(bar, parity) && ++n < kAdjWaitIters) {
+    }
+    if (n >= kAdjWaitIters) atomicOr(a.status, kDevTimeout);
+  };
+  auto next = [&](unsigned& b, unsigned& par) {
+    if (++b == NB) { b = 0; par ^= 1u; }
+  };
+
+  if (warp == Sh::kProducer) {
+    unsigned rc = 0, b = 0, par = 0;
+    for (int k = k1 - 1; k >= k0; --k) {
+      advance(k);
+      const int nsingle = lev(k, lg0, lg1) - lev(k, lb0, lb1), mb = lev(k, lm0, lm1);
+      for (int r0 = 0; r0 < nsingle; r0 += CK, ++rc, next(b, par)) {
+        if (lane != 0) continue;
+        if (rc >= NB) bounded_wait(&empty[b], par ^ 1u);
+        const int cnt = min(CK, nsingle - r0);
+        const long long m0 = (long long)mb + r0;
+        unsigned char* rb = ring + (size_t)b * Sh::kRound;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&full[b], (unsigned)(cnt * (L::kStaged + L::kYBytes + 16)));
+        bulk_g2s(rb, L::s_at(a.rec, m0), (unsigned)(cnt * L::kStaged), &full[b]);
+        bulk_g2s(rb + Sh::kYOff, a.yadj + m0 * L::kYStride, (unsigned)(cnt * L::kYBytes), &full[b]);
+        bulk_g2s(rb + Sh::kTsOff, a.tslot + m0, (unsigned)(cnt * 16), &full[b]);
+      }
+    }
+    if (lane == 0)
+      for (unsigned j = rc > NB ? rc - NB : 0u; j < rc; ++j) bounded_wait(&full[j % NB], (j / NB) & 1u);
+    return;
+  }
+
+  const bool compute = warp < Sh::kCompute;
+  const int i = lane % N, s_lane = lane / N;
+  const int task = warp * SPC + s_lane;
+  const bool lane_ok = compute && lane < SPC * N;
+  // the faces dof row i lies on (two at a corner) and its node position on each
+  const int ia = i % Q, ib = i / Q;
+  int fA = -1, pA = 0, fB = -1, pB = 0;
+  auto on_face = [&](int f, int pos) {
+    if (fA < 0) { fA = f; pA = pos; } else { fB = f; pB = pos; }
+  };
+  if (ib == 0) on_face(0, ia);
+  if (ia == P) on_face(1, ib);
+  if (ib == P) on_face(2, ia);
+  if (ia == 0) on_face(3, ib);
+  double* scratch = scratch_all + (compute ? warp : 0) * (SPC * 2 * Q * N);
+  double* radj = a.radj + (size_t)d * a.E * N;
+  if (threadIdx.x < Q) tr[kTraceZero * Q + threadIdx.x] = 0.0;
+  const int gidx = warp - Sh::kCompute;
+  unsigned rb_i = 0, rpar = 0;
+  named_barrier(1, (Sh::kCompute + Sh::kGroupWarps) * 32);   // the zero trace is in place
+  for (int k = k1 - 1; k >= k0; --k) {
+    advance(k);
+    const int sb = lev(k, lb0, lb1), sg = lev(k, lg0, lg1), se = lev(k, le0, le1), mb = lev(k, lm0, lm1);
+    if (compute) {
+      const int nsingle = sg - sb;
+      for (int c0 = 0; c0 < nsingle; c0 += CK) {
+        const unsigned char* rb = ring + (size_t)rb_i * Sh::kRound;
+        bounded_wait(&full[rb_i], rpar);
+        const int cend = min(CK, nsingle - c0);
+        for (int tk0 = 0; tk0 < cend; tk0 += CH) {   // the chunk's rounds
+          const int tk = tk0 + task;
+          const bool act = lane_ok && tk < cend;
+          double r = 0.0;
+          uint4 ts = make_uint4(0u, 0u, 0u, 0u);
+          const char* rs = (const char*)rb;
+          if (act) {
+            rs = (const char*)rb + tk * L::kStaged;
+            const uint4 info = *reinterpret_cast<const uint4*>(rs);
+            ts = *reinterpret_cast<const uint4*>(rb + Sh::kTsOff + tk * 16);
+            r = reinterpret_cast<const double*>(rb + Sh::kYOff + tk * L::kYBytes)[i];
+            // the receivers' projections on this row's faces (no slot: kTraceSink -> zero)
+            auto rd = [&](int f) {
+              if (f < 0) return kTraceZero;
+              const unsigned id = ((f >= 2 ? ts.z : ts.y) >> (16 * (f & 1))) & 0xffffu;
+              return id == kTraceSink ? kTraceZero : id;
+            };
+            r -= tr[rd(fA) * Q + pA];
+            r -= tr[rd(fB) * Q + pB];
+            const int e = (int)info.x;
+            if (ts.w & 2u) {   // rare: a receiver's projection read from global memory
+              const long long m = (long long)mb + c0 + tk;
+#pragma unroll 1
+              for (int f = 0; f < 4; ++f) {
+                if (!((info.y >> (8 + f)) & 1u)) continue;
+                if ((((f >= 2 ? ts.z : ts.y) >> (16 * (f & 1))) & 0xffffu) != kTraceSink) continue;
+                const int t = f == fA ? pA : (f == fB ? pB : -1);
+                if (t < 0) continue;
+                const uint32_t lk = a.link[m * 4 + f];
+                if (lk == ~0u) continue;
+                const long long mn = (long long)(lk >> 2);
+                const double* W = L::slot(L::s_at(a.rec, mn), L::x_at(a.recx, mn), (int)(lk & 3u)) + t * N;
+                const double* rn = radj + (size_t)nb_elem(a.nx, a.ny, e, f) * N;
+                double acc = 0.0;
+#pragma unroll
+                for (int j = 0; j < N; ++j) acc += W[j] * rn[j];
+                r -= acc;
+              }
+            }
+            radj[(size_t)e * N + i] = r;
+            // this task's projections onto its donors' faces, W slots 0 and 1 (zero slots
+            // of absent faces give zero products)
+            const double* W = L::slot(rs, nullptr, 0);
+#pragma unroll
+            for (int sl = 0; sl < 2; ++sl)
+#pragma unroll
+              for (int t = 0; t < Q; ++t)
+                scratch[((s_lane * 2 + sl) * Q + t) * N + i] = W[sl * L::kSlot + t * N + i] * r;
+          }
+          __syncwarp();
+          for (int q = lane; q < SPC * 2 * Q; q += 32) {
+            const int s = q / (2 * Q), sl = (q / Q) % 2, t = q % Q;
+            const int tks = tk0 + warp * SPC + s;
+            if (tks >= cend) continue;
+            const uint4 tss = *reinterpret_cast<const uint4*>(rb + Sh::kTsOff + tks * 16);
+            const unsigned wid = (tss.x >> (16 * sl)) & 0xffffu;
+            if (wid == kTraceZero) continue;
+            const double* pr = scratch + ((s * 2 + sl) * Q + t) * N;
+            double sum = 0.0;
+#pragma unroll
+            for (int j = 0; j < N; ++j) sum += pr[j];
+            tr[wid * Q + t] = sum;
+          }
+          __syncwarp();
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[rb_i]);
+        next(rb_i, rpar);
+      }
+    } else {
+      for (int g = sg + gidx; g < se; g += Sh::kGroupWarps) adj_group<P, false>(a, d, g);
+    }
+    named_barrier(1, (Sh::kCompute + Sh::kGroupWarps) * 32);
   }
 }
 
@@ -260,6 +499,40 @@ static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1
 // forward factorisation (FP64) from sweep.cu
 vef_status factor_fp64(Mesh* mesh, Schedule* S, const double* sigma_t, cudaStream_t stream);
 vef_status collect_status(Mesh& M, cudaStream_t stream, vef_info* info);
+
+template <int P>
+static vef_status launch_adjoint_cta(Mesh& M, Schedule& S, AdjArgs a, cudaStream_t s) {
+  using Sh = AdjShape<P>;
+  using L = Rec<P, double>;
+  constexpr int N = (P + 1) * (P + 1);
+  constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
+  vef_status st = ensure_buffer(&M.ybuf, &M.ybuf_cap, (size_t)S.members * L::kYBytes);
+  if (st != VEF_OK) return st;
+  a.recx = (const double*)((const char*)a.rec + a.nmem * (long long)L::kStaged);
+  a.yadj = (const double*)M.ybuf;
+  a.tslot = S.tslot;
+  a.tr_bytes = (S.trace_slots * (P + 1) * 8 + 15) / 16 * 16;
+  a.ring = std::min(Sh::kMaxRing, (Sh::avail() - a.tr_bytes) / Sh::kRound);
+  if (a.ring < 2) {
+    set_last_error("internal error: single-CTA adjoint ring does not fit in shared memory");
+    return VEF_ERR_INVALID_ARG;
+  }
+  const size_t smem = (size_t)Sh::kBars + Sh::kScratch + a.tr_bytes + (size_t)a.ring * Sh::kRound;
+  {
+    KTimer kt(&M, VEF_K_SOURCE, s);
+    adj_yadj_kernel<<<nblk(a.nmem * N, 256), 256, 0, s>>>(a.nmem, N, L::kYStride, a.E, a.code, a.weights, a.g,
+                                                          (double*)M.ybuf);
+    VEF_CUDA_TRY(cudaGetLastError());
+  }
+  VEF_CUDA_TRY(cudaFuncSetAttribute(adjoint_cta_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  KTimer kt(&M, VEF_K_ADJOINT, s);   // the backward sweep and the gradient post-pass
+  adjoint_cta_kernel<P><<<(unsigned)S.D, Sh::kThreads, smem, s>>>(a);
+  VEF_CUDA_TRY(cudaGetLastError());
+  const long long nwarp = (a.nmem + SPC - 1) / SPC;
+  adj_finish_kernel<P><<<nblk(nwarp * 32, 128), 128, 0, s>>>(a);
+  VEF_CUDA_TRY(cudaGetLastError());
+  return VEF_OK;
+}
 
 template <int P>
 static vef_status launch_adjoint(Mesh& M, AdjArgs a, int D, int cs, int warps, cudaStream_t s) {
@@ -335,6 +608,7 @@ extern "C" vef_status vef_adjoint_sweep(vef_mesh mesh, const double* sigma_t, co
   a.dir_lev0 = S->dir_lev0;
   a.lev_begin = S->lev_begin;
   a.lev_gbegin = S->lev_gbegin;
+  a.lev_mbegin = S->lev_mbegin;
   a.slot_first = S->slot_first;
   a.slot_count = S->slot_count;
   a.code = S->member_code;
@@ -369,11 +643,13 @@ extern "C" vef_status vef_adjoint_sweep(vef_mesh mesh, const double* sigma_t, co
   if (dR_dsigma_s) VEF_CUDA_TRY(cudaMemsetAsync(dR_dsigma_s, 0, M.E * sizeof(double), s));
   const int tile = (opts && opts->tile_override > 0) ? opts->tile_override : 804;
   const int cs = std::min(16, std::max(1, tile / 100)), warps = std::min(8, std::max(1, tile % 100));
+  // one CTA per direction unless the caller asks for the cluster sweep
+  const bool cta = !(opts && (opts->tile_override > 0 || (opts->flags & VEF_SWEEP_CLUSTER)));
   switch (M.p) {
-    case 1: st = launch_adjoint<1>(M, a, D, cs, warps, s); break;
-    case 2: st = launch_adjoint<2>(M, a, D, cs, warps, s); break;
-    case 3: st = launch_adjoint<3>(M, a, D, cs, warps, s); break;
-    default: st = launch_adjoint<4>(M, a, D, cs, warps, s); break;
+    case 1: st = cta ? launch_adjoint_cta<1>(M, *S, a, s) : launch_adjoint<1>(M, a, D, cs, warps, s); break;
+    case 2: st = cta ? launch_adjoint_cta<2>(M, *S, a, s) : launch_adjoint<2>(M, a, D, cs, warps, s); break;
+    case 3: st = cta ? launch_adjoint_cta<3>(M, *S, a, s) : launch_adjoint<3>(M, a, D, cs, warps, s); break;
+    default: st = cta ? launch_adjoint_cta<4>(M, *S, a, s) : launch_adjoint<4>(M, a, D, cs, warps, s); break;
   }
   if (st != VEF_OK) return st;
   if (info) {

@@ -114,8 +114,10 @@ struct Schedule {
   // x = the slots to read for the record's W slots 0 and 1 (the donors' face-node values;
   // kTraceZero when the slot is absent or its donor is read from global memory), y / z =
   // the slots the member's own face-node values go to, for faces 0, 1 / 2, 3 (kTraceSink
-  // when no later single-element task reads them); w = 1 when some upwind coupling of the
-  // member is read from global memory instead (see cta_trace_capacity).
+  // when no later single-element task reads them); w bit 0 when some upwind coupling of
+  // the member is read from global memory instead (see cta_trace_capacity), bit 1 when
+  // some coupling of the adjoint sweep is (it uses the same slots with the roles of
+  // reader and writer swapped).
   uint4* tslot = nullptr;
   int trace_slots = 0;          // slots in use at once (max over directions)
   long long trace_global = 0;   // single-to-single face couplings left to global memory

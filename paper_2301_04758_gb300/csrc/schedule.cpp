@@ -462,8 +462,10 @@ Schedule* get_schedule(Mesh* mesh, const double* omega, const double* weights, i
         live -= (int)release[L].size();
         std::vector<unsigned>().swap(release[L]);
       }
-      // members whose upwind couplings are not all in shared memory: an interior inflow
-      // face beyond the two staged W slots, or a staged one left without a slot
+      // members whose couplings are not all in shared memory.  Bit 0 (forward sweep): an
+      // interior inflow face beyond the two staged W slots, or a staged one left without a
+      // slot.  Bit 1 (adjoint sweep, where the receivers write and the donors read the same
+      // slots): a face toward a receiver whose slot is missing (kTraceSink).
       for (int L = 0; L < g.levels; ++L) {
         const int k = dir_lev0[d] + L;
         const int m0 = lev_mbegin[k];
@@ -473,8 +475,13 @@ Schedule* get_schedule(Mesh* mesh, const double* omega, const double* weights, i
           int rank = 0;
           for (int f = 0; f < 4; ++f) {
             if (!(g.info[e] & (1u << f)) || nb_of(M.nx, M.ny, e, f) < 0) continue;
-            if (rank >= 2 || ((tslot[m].x >> (16 * rank)) & 0xffffu) == kTraceZero) tslot[m].w = 1u;
+            if (rank >= 2 || ((tslot[m].x >> (16 * rank)) & 0xffffu) == kTraceZero) tslot[m].w |= 1u;
             ++rank;
+          }
+          for (int f = 0; f < 4; ++f) {
+            if (!(g.info[e] & (1u << (8 + f)))) continue;
+            const unsigned wid = ((f < 2 ? tslot[m].y : tslot[m].z) >> (16 * (f & 1))) & 0xffffu;
+            if (wid == kTraceSink) tslot[m].w |= 2u;
           }
         }
       }

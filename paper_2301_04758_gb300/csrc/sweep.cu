@@ -803,7 +803,7 @@ __global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
               y += yb;
             }
             const int e = (int)info.x;
-            if (ts.w) {   // rare: couplings read from global memory
+            if (ts.w & 1u) {   // rare: couplings read from global memory
 #pragma unroll 1
               for (int sl = 0; sl < 4; ++sl) {
                 const unsigned f = (info.z >> (8 * sl)) & 0xffu;

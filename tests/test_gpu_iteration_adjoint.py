@@ -51,7 +51,8 @@ def test_adjoint_gradients_match_oracle(lib):
     assert rel(host(gdss), dss) < 1e-12
 
 
-def test_adjoint_with_coupled_groups(lib):
+@pytest.mark.parametrize("kernel", ["cta", "cluster"])
+def test_adjoint_with_coupled_groups(lib, kernel):
     from paper_2301_04758_gb300.api import Mesh
     prob = random_problem(20, 20, 3, 0.1, 2, 8, seed=3, sigma_range=(-1.0, 0.5), with_inflow=False)
     disc = Discretization(20, 20, 3, 0.1, 2)
@@ -63,8 +64,9 @@ def test_adjoint_with_coupled_groups(lib):
     mesh = Mesh(20, 20, 3, 2, 0.1)
     gdst, gdss, glam, info = mesh.adjoint(dev(prob["sigma_t"]), dev(prob["sigma_s"]), prob["omega"],
                                           prob["weights"], dev(psi), dev(g),
-                                          phi_in=dev(prob["phi_in"]), want_lambda=True, info=True)
-    assert info["coupled_groups"] > 0
+                                          phi_in=dev(prob["phi_in"]), want_lambda=True, info=True,
+                                          kernel=kernel)
+    assert info["coupled_groups"] > 0 and info["timed_out"] == 0
     assert rel(host(glam), lam) < 1e-12, info
     assert rel(host(gdst), dst) < 1e-12
 
@@ -82,6 +84,31 @@ def test_adjoint_other_orders(lib, p):
     lam, dst, dss = o_adjoint(disc, prob["omega"], prob["weights"], prob["sigma_t"], prob["sigma_s"],
                               psi, g, phi_in=prob["phi_in"])
     mesh = Mesh(7, 6, 3, p, 0.06)
+    for kernel in ("cta", "cluster"):
+        gdst, gdss, glam, info = mesh.adjoint(dev(prob["sigma_t"]), dev(prob["sigma_s"]), prob["omega"],
+                                              prob["weights"], dev(psi), dev(g),
+                                              phi_in=dev(prob["phi_in"]), want_lambda=True, info=True,
+                                              kernel=kernel)
+        assert info["timed_out"] == 0
+        assert rel(host(glam), lam) < 1e-12, (kernel, info)
+        assert rel(host(gdst), dst) < 1e-12, kernel
+        assert rel(host(gdss), dss) < 1e-12, kernel
+
+
+@pytest.mark.parametrize("slots", ["0", "3"])
+def test_adjoint_trace_slot_capacity_fallback(lib, monkeypatch, slots):
+    """With the shared-memory slots capped the backward sweep reads the receivers'
+    couplings from global memory (the same slots serve the forward and the adjoint)."""
+    from paper_2301_04758_gb300.api import Mesh
+    monkeypatch.setenv("VEF_TRACE_SLOTS", slots)
+    prob = random_problem(12, 10, 3, 0.1, 2, 8, seed=90, with_inflow=False, sigma_range=(-1.0, 0.5))
+    disc = Discretization(12, 10, 3, 0.1, 2)
+    g = region_weights(disc, (0.1, 0.2), (0.7, 0.8))
+    psi = o_sweep(disc, prob["omega"], prob["weights"], prob["sigma_t"], prob["sigma_s"],
+                  phi_in=prob["phi_in"], source=prob["source"])
+    lam, dst, dss = o_adjoint(disc, prob["omega"], prob["weights"], prob["sigma_t"], prob["sigma_s"],
+                              psi, g, phi_in=prob["phi_in"])
+    mesh = Mesh(12, 10, 3, 2, 0.1)
     gdst, gdss, glam, info = mesh.adjoint(dev(prob["sigma_t"]), dev(prob["sigma_s"]), prob["omega"],
                                           prob["weights"], dev(psi), dev(g),
                                           phi_in=dev(prob["phi_in"]), want_lambda=True, info=True)
