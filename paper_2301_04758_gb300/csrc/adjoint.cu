@@ -29,6 +29,10 @@ struct AdjArgs {
   const double* yadj;     // single-CTA sweep: w_d g_e rows per member (16-byte padded)
   int ring;               // single-CTA sweep: chunk buffers in the ring
   int tr_bytes;           // single-CTA sweep: bytes of the trace slots
+  const uint32_t* member_nbpos;  // coupled groups solved directly: in-group neighbour positions
+  const int* slot_gid;           //   per slot its group index or -1 (null: none solved directly)
+  const long long* grp_toff;     //   offset of each group's trace-system inverse in grec
+  const double* grec;            //   T = (I + R)^{-1} per group, column-major (forward factorisation)
   int cluster_size;
   const int* slot_first;
   const int* slot_count;
@@ -209,6 +213,149 @@ __global__ void __maxnreg__(128) adjoint_kernel(AdjArgs a) {
   }
 }
 
+// Coupled group solved directly in the backward sweep.  The forward group operator is
+// L_G = A (I + W P) (W = A^{-1} Cin of the internal faces, P takes the neighbours'
+// face-node values), with L_G^{-1} = (I - W T P) A^{-1} and T = (I + P W)^{-1} formed by
+// the forward factorisation.  For the adjoint, r = A^T lambda solves
+//     r = (I - P^T T^T W^T) g~,   g~ = w_d g - (couplings from receivers outside the group),
+// i.e. v = W^T g~ (one value per trace unknown), w = T^T v, r = g~ - P^T w.
+template <int P>
+struct AdjGroupSmem {
+  static constexpr int Q = P + 1, N = Q * Q, GM = group_direct_members(P);
+  static constexpr int NC = kGroupMaxTrace / Q + 1;
+  double z[GM * N];                                 // g~, then r
+  double v[kGroupMaxTrace];
+  double w[kGroupMaxTrace];
+  double tinv[kGroupSmemTrace * kGroupSmemTrace];   // T (column-major) when nt <= kGroupSmemTrace
+  uint4 info[GM];
+  uint32_t cpl[NC];                                 // coupling: a | f << 8 | b << 16 | W slot << 24
+  int cbase[GM + 1];
+  int m, nt, gid;
+};
+
+template <int P>
+__device__ __forceinline__ void adj_group_stage(const AdjArgs& a, int s0, AdjGroupSmem<P>& g) {
+  constexpr int Q = P + 1;
+  using L = Rec<P, double>;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int first = a.slot_first[s0];
+  const int cnt = a.slot_count[s0];
+  const int gid = a.slot_gid[s0];
+  uint4 info = make_uint4(0u, 0u, 0xffffffffu, 0u);
+  uint32_t nbp = 0xffffffffu;
+  if (lane < cnt) {
+    info = *reinterpret_cast<const uint4*>(L::s_at(a.rec, first + lane));
+    nbp = a.member_nbpos[first + lane];
+    g.info[lane] = info;
+  }
+  const unsigned mine = lane < cnt ? (unsigned)__popc(info.y & (info.y >> 4) & 0xfu) : 0u;
+  unsigned incl = mine;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned v = __shfl_up_sync(FULL, incl, off);
+    if (lane >= off) incl += v;
+  }
+  unsigned c = incl - mine;
+  if (lane < cnt) {
+    g.cbase[lane] = (int)c;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      if (!((info.y >> f) & 1u) || !((info.y >> (4 + f)) & 1u)) continue;
+      g.cpl[c++] = (uint32_t)lane | ((uint32_t)f << 8) | (((nbp >> (8 * f)) & 0xffu) << 16) |
+                   ((uint32_t)rec_slot_of(info.z, f) << 24);
+    }
+  }
+  const int total = (int)__shfl_sync(FULL, incl, 31);
+  if (lane == 0) {
+    g.cbase[cnt] = total;
+    g.m = cnt;
+    g.nt = total * Q;
+    g.gid = gid;
+  }
+  const int nt = total * Q;
+  const double* Tg = a.grec + a.grp_toff[gid];
+  if (nt <= kGroupSmemTrace)
+    for (int t = lane; t < nt * nt; t += 32) g.tinv[t] = Tg[t];
+  __syncwarp();
+}
+
+template <int P>
+__device__ __forceinline__ void adj_group_direct(const AdjArgs& a, int d, int s0, AdjGroupSmem<P>& g) {
+  constexpr int Q = P + 1, N = Q * Q;
+  using L = Rec<P, double>;
+  const int lane = threadIdx.x & 31;
+  const int first = a.slot_first[s0];
+  const int m = g.m, nt = g.nt;
+  // g~: w_d g minus the couplings from receivers outside the group
+  for (int idx = lane; idx < m * N; idx += 32) {
+    const int mi = idx / N, i = idx % N;
+    const uint4 info = g.info[mi];
+    const int e = (int)info.x;
+    const unsigned bits = info.y;
+    double r = a.weights[d] * a.g[(size_t)e * N + i];
+    const int ia = i % Q, ib = i / Q;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      if (!((bits >> (8 + f)) & 1u) || ((bits >> (4 + f)) & 1u)) continue;   // no external receiver
+      const int t = f == 0 ? (ib == 0 ? ia : -1) : f == 1 ? (ia == P ? ib : -1)
+                  : f == 2 ? (ib == P ? ia : -1) : (ia == 0 ? ib : -1);
+      if (t < 0) continue;
+      const uint32_t lk = a.link[(long long)(first + mi) * 4 + f];
+      if (lk == ~0u) continue;
+      const long long mn = (long long)(lk >> 2);
+      const double* W = L::slot(L::s_at(a.rec, mn), L::x_at(a.recx, mn), (int)(lk & 3u)) + t * N;
+      const double* rn = a.radj + ((size_t)d * a.E + nb_elem(a.nx, a.ny, e, f)) * N;
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) s += W[j] * rn[j];
+      r -= s;
+    }
+    g.z[idx] = r;
+  }
+  __syncwarp();
+  // v = W^T g~ over the internal couplings: v_(c,t) = sum_i W_(a,f)[t][i] g~_a[i]
+  for (int j = lane; j < nt; j += 32) {
+    const uint32_t cp = g.cpl[j / Q];
+    const int am = (int)(cp & 0xffu), t = j % Q;
+    const double* W = L::slot(L::s_at(a.rec, first + am), L::x_at(a.recx, first + am), (int)(cp >> 24)) + t * N;
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) s += W[i] * g.z[am * N + i];
+    g.v[j] = s;
+  }
+  __syncwarp();
+  // w = T^T v (column r of T is contiguous)
+  const double* Tm = nt <= kGroupSmemTrace ? g.tinv : a.grec + a.grp_toff[g.gid];
+  for (int rr = lane; rr < nt; rr += 32) {
+    double acc0 = 0.0, acc1 = 0.0;
+    int j = 0;
+    for (; j + 1 < nt; j += 2) {
+      acc0 += Tm[rr * nt + j] * g.v[j];
+      acc1 += Tm[rr * nt + j + 1] * g.v[j + 1];
+    }
+    if (j < nt) acc0 += Tm[rr * nt + j] * g.v[j];
+    g.w[rr] = acc0 + acc1;
+  }
+  __syncwarp();
+  // r = g~ - P^T w: the trace unknown (c, t) is node t of face opp(f) of neighbour b
+  for (int idx = lane; idx < m * N; idx += 32) {
+    const int mi = idx / N, i = idx % N;
+    double r = g.z[idx];
+    const int ntc = nt / Q;
+    for (int c = 0; c < ntc; ++c) {
+      const uint32_t cp = g.cpl[c];
+      if ((int)((cp >> 16) & 0xffu) != mi) continue;
+      const int fo = ((int)((cp >> 8) & 0xffu) + 2) & 3;
+#pragma unroll
+      for (int t = 0; t < Q; ++t)
+        if (face_dof<P>(fo, t) == i) r -= g.w[c * Q + t];
+    }
+    a.radj[((size_t)d * a.E + g.info[mi].x) * N + i] = r;
+  }
+  __syncwarp();
+}
+
 // ------------------------------------------------------------ single-CTA backward sweep
 // One CTA of 16 warps per direction walks the forward schedule's levels backwards.  The
 // couplings are the forward ones with the roles swapped: a receiver e' (done first)
@@ -239,8 +386,10 @@ struct AdjShape {
   static constexpr int kMaxRing = 16;
   static constexpr int kBars = 2 * kMaxRing * 8;
   static constexpr int kScratch = kCompute * SPC * 2 * Q * N * 8;   // per warp [task][slot][t][row]
+  static constexpr int kGs = ((int)sizeof(AdjGroupSmem<P>) + 15) / 16 * 16;
+  static constexpr int kGroup = kGroupWarps * kGs;
   static constexpr int kSmemMax = 227 * 1024;
-  static constexpr int avail() { return kSmemMax - kBars - kScratch; }
+  static constexpr int avail() { return kSmemMax - kBars - kScratch - kGroup; }
 };
 
 __global__ void adj_yadj_kernel(long long nmem, int n, int ystride, long long E, const uint32_t* __restrict__ code,
@@ -265,8 +414,9 @@ __global__ void __maxnreg__(128) adjoint_cta_kernel(AdjArgs a) {
   uint64_t* full = reinterpret_cast<uint64_t*>(adj_smem);
   uint64_t* empty = full + Sh::kMaxRing;
   double* scratch_all = reinterpret_cast<double*>(adj_smem + Sh::kBars);
-  double* tr = reinterpret_cast<double*>(adj_smem + Sh::kBars + Sh::kScratch);
-  unsigned char* ring = adj_smem + Sh::kBars + Sh::kScratch + a.tr_bytes;
+  unsigned char* gsm_all = adj_smem + Sh::kBars + Sh::kScratch;
+  double* tr = reinterpret_cast<double*>(adj_smem + Sh::kBars + Sh::kScratch + Sh::kGroup);
+  unsigned char* ring = adj_smem + Sh::kBars + Sh::kScratch + Sh::kGroup + a.tr_bytes;
   const unsigned NB = (unsigned)a.ring;
   const int d = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -351,6 +501,8 @@ __global__ void __maxnreg__(128) adjoint_cta_kernel(AdjArgs a) {
   double* radj = a.radj + (size_t)d * a.E * N;
   if (threadIdx.x < Q) tr[kTraceZero * Q + threadIdx.x] = 0.0;
   const int gidx = warp - Sh::kCompute;
+  AdjGroupSmem<P>& gs = *reinterpret_cast<AdjGroupSmem<P>*>(gsm_all + (compute ? 0 : gidx) * Sh::kGs);
+  auto direct = [&](int slot) { return a.slot_gid != nullptr && a.slot_gid[slot] >= 0; };
   unsigned rb_i = 0, rpar = 0;
   named_barrier(1, (Sh::kCompute + Sh::kGroupWarps) * 32);   // the zero trace is in place
   for (int k = k1 - 1; k >= k0; --k) {
@@ -432,7 +584,14 @@ __global__ void __maxnreg__(128) adjoint_cta_kernel(AdjArgs a) {
         next(rb_i, rpar);
       }
     } else {
-      for (int g = sg + gidx; g < se; g += Sh::kGroupWarps) adj_group<P, false>(a, d, g);
+      for (int g = sg + gidx; g < se; g += Sh::kGroupWarps) {
+        if (direct(g)) {
+          adj_group_stage<P>(a, g, gs);
+          adj_group_direct<P>(a, d, g, gs);
+        } else {
+          adj_group<P, false>(a, d, g);
+        }
+      }
     }
     named_barrier(1, (Sh::kCompute + Sh::kGroupWarps) * 32);
   }
@@ -501,6 +660,9 @@ vef_status factor_fp64(Mesh* mesh, Schedule* S, const double* sigma_t, cudaStrea
 vef_status collect_status(Mesh& M, cudaStream_t stream, vef_info* info);
 
 template <int P>
+static vef_status launch_adjoint(Mesh& M, AdjArgs a, int D, int cs, int warps, cudaStream_t s);
+
+template <int P>
 static vef_status launch_adjoint_cta(Mesh& M, Schedule& S, AdjArgs a, cudaStream_t s) {
   using Sh = AdjShape<P>;
   using L = Rec<P, double>;
@@ -513,11 +675,12 @@ static vef_status launch_adjoint_cta(Mesh& M, Schedule& S, AdjArgs a, cudaStream
   a.tslot = S.tslot;
   a.tr_bytes = (S.trace_slots * (P + 1) * 8 + 15) / 16 * 16;
   a.ring = std::min(Sh::kMaxRing, (Sh::avail() - a.tr_bytes) / Sh::kRound);
-  if (a.ring < 2) {
-    set_last_error("internal error: single-CTA adjoint ring does not fit in shared memory");
-    return VEF_ERR_INVALID_ARG;
-  }
-  const size_t smem = (size_t)Sh::kBars + Sh::kScratch + a.tr_bytes + (size_t)a.ring * Sh::kRound;
+  if (a.ring < 2) return launch_adjoint<P>(M, a, S.D, 8, 4, s);   // slots too many: cluster sweep
+  const size_t smem = (size_t)Sh::kBars + Sh::kScratch + Sh::kGroup + a.tr_bytes + (size_t)a.ring * Sh::kRound;
+  if (!S.ngroups || !S.grec64) a.slot_gid = nullptr;   // every group by the inner iteration
+  a.member_nbpos = S.member_nbpos;
+  a.grp_toff = S.grp_toff;
+  a.grec = (const double*)S.grec64;
   {
     KTimer kt(&M, VEF_K_SOURCE, s);
     adj_yadj_kernel<<<nblk(a.nmem * N, 256), 256, 0, s>>>(a.nmem, N, L::kYStride, a.E, a.code, a.weights, a.g,
@@ -609,6 +772,7 @@ extern "C" vef_status vef_adjoint_sweep(vef_mesh mesh, const double* sigma_t, co
   a.lev_begin = S->lev_begin;
   a.lev_gbegin = S->lev_gbegin;
   a.lev_mbegin = S->lev_mbegin;
+  a.slot_gid = S->slot_gid;
   a.slot_first = S->slot_first;
   a.slot_count = S->slot_count;
   a.code = S->member_code;
