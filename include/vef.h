@@ -81,8 +81,9 @@ enum { VEF_FP64 = 0, VEF_MIXED = 1 };
 /* vef_opts.flags */
 enum {
   VEF_GROUPS_ITERATIVE = 1, /* solve every coupled group by the inner iteration */
-  VEF_SWEEP_CLUSTER = 2     /* sweep each direction with a thread-block cluster (as the
-                               batched and adjoint sweeps do) instead of one CTA */
+  VEF_SWEEP_CLUSTER = 2     /* sweep each direction (forward or adjoint) with a
+                               thread-block cluster, as the batched sweep does, instead of
+                               one CTA */
 };
 
 typedef struct vef_mesh_s* vef_mesh;
