@@ -195,7 +195,10 @@ vef_status vef_region_weights(vef_mesh mesh, double x0, double y0, double x1, do
  *   dR_dsigma_s[e] =   sum_d lambda_{d,e}^T M_e phi_in,e / (4 pi)
  * with M_e the element mass matrix.  psi_ckpt [device] [D][E][n] is the forward sweep's
  * psi (checkpoint); g [device] [E][n]; lambda [device] [D][E][n] output or NULL (then a
- * library buffer is used); dR_dsigma_t, dR_dsigma_s [device] [E] outputs. */
+ * library buffer is used); dR_dsigma_t, dR_dsigma_s [device] [E] outputs.  opts: tol and
+ * max_passes bound the inner iteration of coupled groups beyond the direct limits;
+ * VEF_SWEEP_CLUSTER or a tile_override selects the cluster form of the backward sweep
+ * (default: one CTA per direction with the forward sweep's shared-memory slots). */
 vef_status vef_adjoint_sweep(vef_mesh mesh, const double* sigma_t, const double* sigma_s,
                              const double* phi_in, const double* omega, const double* weights,
                              int D, const double* psi_ckpt, const double* g, double* lambda,
