@@ -88,6 +88,11 @@ enum {
 
 typedef struct vef_mesh_s* vef_mesh;
 
+/* Environment: VEF_TRACE_SLOTS=<k>, read when a schedule is built (the first sweep of a
+ * mesh with a given direction set), caps the shared-memory trace slots of the single-CTA
+ * sweeps at k; the couplings left over are read from global memory.  Meant for testing
+ * that path; results do not depend on it. */
+
 /* Sweep options.  NULL means the defaults listed. */
 typedef struct {
   int precision;     /* VEF_FP64 (default): FP64 assembly and solves.
