@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--sweep-only", type=int, default=0, metavar="NX",
                     help="profiling driver: build an NX x NX mesh with the workload's recipe and run "
                          "--steps sweeps (factorisation included; no timing line)")
+    ap.add_argument("--adjoint-only", type=int, default=0, metavar="NX",
+                    help="profiling driver: the adjoint workload's recipe on an NX x NX mesh, one forward "
+                         "sweep, then --steps adjoint sweeps (no timing line)")
     ap.add_argument("--order", type=int, default=2, help="--sweep-only: DG order p")
     ap.add_argument("--sn", type=int, default=8, help="--sweep-only: level-symmetric order N")
     ap.add_argument("--precision", default="fp64", choices=("fp64", "mixed"), help="--sweep-only: precision")
@@ -593,10 +596,41 @@ def sweep_only(args):
     mesh.sync()
 
 
+def adjoint_only(args):
+    """Small driver for ncu captures of the backward sweep: NX x NX sine mesh (alpha 0.05,
+    Q3 map), Q2, S8, seed-5 media, phi_in seeded, q = 1, R = int over [0.6,0.8]^2 of phi;
+    one forward sweep, then --steps adjoint sweeps through the public API."""
+    import numpy as np
+    import torch
+
+    from paper_2301_04758_gb300 import build as vbuild
+    vbuild.build()
+    from paper_2301_04758_gb300.api import Mesh
+    from vef_inputs import level_symmetric, seeded_media
+    N, p = args.adjoint_only, 2
+    n = (p + 1) ** 2
+    om, w = level_symmetric(8)
+    st, ss = seeded_media(N * N, 5)
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda").contiguous()
+    rng = np.random.Generator(np.random.PCG64(5))
+    phi_in = T(rng.uniform(0.5, 1.5, (N * N, n)))
+    mesh = Mesh(N, N, 3, p, 0.05)
+    q = torch.ones(N * N, n, dtype=torch.float64, device="cuda")
+    g = mesh.region_weights((0.6, 0.6), (0.8, 0.8))
+    psi = mesh.sweep(T(st), T(ss), om, w, phi_in=phi_in, source=q)
+    for _ in range(args.steps):
+        mesh.adjoint(T(st), T(ss), om, w, psi, g, phi_in=phi_in)
+    torch.cuda.synchronize()
+    mesh.sync()
+
+
 def main():
     args = parse()
     if args.sweep_only:
         sweep_only(args)
+        return
+    if args.adjoint_only:
+        adjoint_only(args)
         return
     if args.suite:
         from paper_2301_04758_gb300 import build as vbuild
