@@ -81,9 +81,12 @@ enum { VEF_FP64 = 0, VEF_MIXED = 1 };
 /* vef_opts.flags */
 enum {
   VEF_GROUPS_ITERATIVE = 1, /* solve every coupled group by the inner iteration */
-  VEF_SWEEP_CLUSTER = 2     /* sweep each direction (forward or adjoint) with a
+  VEF_SWEEP_CLUSTER = 2,    /* sweep each direction (forward or adjoint) with a
                                thread-block cluster, as the batched sweep does, instead of
                                one CTA */
+  VEF_APPLY_SEPARATE = 4    /* compute y = A^{-1} b by a launch of its own before the
+                               single-CTA sweep; by default the SMs the directions leave
+                               free do it inside the sweep launch */
 };
 
 typedef struct vef_mesh_s* vef_mesh;

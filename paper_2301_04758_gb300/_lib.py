@@ -23,6 +23,7 @@ VEF_FP64 = 0
 VEF_MIXED = 1
 VEF_GROUPS_ITERATIVE = 1
 VEF_SWEEP_CLUSTER = 2
+VEF_APPLY_SEPARATE = 4
 
 # every symbol include/vef.h declares
 EXPORTS = ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sync", "vef_sweep",

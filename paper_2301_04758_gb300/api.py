@@ -32,7 +32,7 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _opts(precision="fp64", tol=0.0, max_passes=0, tile=0, groups="direct", kernel="cta"):
+def _opts(precision="fp64", tol=0.0, max_passes=0, tile=0, groups="direct", kernel="cta", apply="fused"):
     o = _lib.VefOpts()
     o.precision = {"fp64": _lib.VEF_FP64, "mixed": _lib.VEF_MIXED}[precision]
     o.tol = float(tol)
@@ -40,6 +40,7 @@ def _opts(precision="fp64", tol=0.0, max_passes=0, tile=0, groups="direct", kern
     o.tile_override = int(tile)
     o.flags = {"direct": 0, "iterative": _lib.VEF_GROUPS_ITERATIVE}[groups]
     o.flags |= {"cta": 0, "cluster": _lib.VEF_SWEEP_CLUSTER}[kernel]
+    o.flags |= {"fused": 0, "separate": _lib.VEF_APPLY_SEPARATE}[apply]
     return o
 
 
@@ -102,7 +103,7 @@ class Mesh:
     # ---------------------------------------------------------------- transport
     def sweep(self, sigma_t, sigma_s, omega, weights, phi_in=None, source=None, inflow=None,
               precision="fp64", tol=0.0, max_passes=0, tile=0, groups="direct", psi=None, info=False,
-              stream=None, kernel="cta"):
+              stream=None, kernel="cta", apply="fused"):
         """psi [D][E][n] = L^{-1} b for every direction (see vef_sweep in include/vef.h).
 
         groups: "direct" (coupled element groups through their trace system) or
@@ -116,7 +117,7 @@ class Mesh:
         if psi is None:
             psi = self._empty(D, self.E, self.n)
         inf = _lib.VefInfo() if info else None
-        o = _opts(precision, tol, max_passes, tile, groups, kernel)
+        o = _opts(precision, tol, max_passes, tile, groups, kernel, apply)
         st = self.lib.vef_sweep(self.handle, _ptr(sigma_t), _ptr(sigma_s), _ptr(phi_in), _ptr(source),
                                 aniso, _ptr(inflow), omp, wp, D, ctypes.byref(o), _ptr(psi),
                                 ctypes.byref(inf) if info else None, _stream(stream))

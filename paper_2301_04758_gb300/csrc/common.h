@@ -161,6 +161,8 @@ struct Mesh {
   size_t work2_cap = 0;
   void* ybuf = nullptr;          // [D][E][n] A^{-1} b of the current sweep (FP64 or FP32)
   size_t ybuf_cap = 0;
+  int* ready_flags = nullptr;    // [D][bands] band flags of the sweep's fused apply
+  size_t ready_cap = 0;
   ~Mesh();
 };
 

@@ -232,6 +232,7 @@ Mesh::~Mesh() {
   cudaFree(work);
   cudaFree(work2);
   cudaFree(ybuf);
+  cudaFree(ready_flags);
 }
 
 Schedule::~Schedule() {

@@ -81,6 +81,10 @@ struct SweepArgs {
   T* y;                    // [D][E][n] A^{-1} b (apply_kernel)
   unsigned int* status;    // [0] status bits, [2] max inner iterations
   const uint4* tslot;      // single-CTA sweep: trace slot ids per member (Schedule::tslot)
+  int* ready;              // single-CTA sweep with fused apply: [nd][bands] band done flags
+  int nd;                  //   direction CTAs (the others apply A^{-1})
+  int bands;               //   bands per direction (kApplyBand levels each)
+  long long nmem;          //   members of the schedule
   int ring;                // single-CTA sweep: round buffers in the ring
   int tr_bytes;            // single-CTA sweep: bytes of the trace slots
   int nx, ny;
@@ -133,18 +137,18 @@ __device__ __forceinline__ T rhs_entry(const SweepArgs<T>& a, int d, int e, int 
 // y = A^{-1} b for every (element, direction): no dependencies, one lane per dof row,
 // records read in schedule order (consecutive members are adjacent in memory); y rows are
 // written in schedule order with a 16-byte-aligned stride.
+// one warp: tasks [m0, m0 + SPC) of those below mend (all lanes of the warp take part)
 template <int P, typename T, int MODE>
-__global__ void __launch_bounds__(128) apply_kernel(SweepArgs<T> a, long long nmem) {
+__device__ __forceinline__ void apply_warp(const SweepArgs<T>& a, long long m0, long long mend) {
   constexpr int Q = P + 1, N = Q * Q;
   using L = Rec<P, T>;
   constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
   constexpr unsigned FULL = 0xffffffffu;
   (void)Q;
   const int lane = threadIdx.x & 31;
-  const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const long long m = gw * SPC + lane / N;
+  const long long m = m0 + lane / N;
   const int i = lane % N;
-  const bool valid = (lane < SPC * N) && (m < nmem);
+  const bool valid = (lane < SPC * N) && (m < mend);
   T bi = 0;
   if (valid) {
     const uint32_t cd = a.code[m];
@@ -162,6 +166,14 @@ __global__ void __launch_bounds__(128) apply_kernel(SweepArgs<T> a, long long nm
     if (valid) y += ai[j * N + i] * bj;
   }
   if (valid) a.y[(size_t)m * L::kYStride + i] = y;
+}
+
+template <int P, typename T, int MODE>
+__global__ void __launch_bounds__(128) apply_kernel(SweepArgs<T> a, long long nmem) {
+  constexpr int N = (P + 1) * (P + 1);
+  constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
+  const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  apply_warp<P, T, MODE>(a, gw * SPC, nmem);
 }
 
 // upwind correction of row i for face f of member record r: sum_t W_f[t][i] u_t
@@ -203,7 +215,7 @@ __device__ __forceinline__ void group_solve(const SweepArgs<T>& a, int d, int s0
       const int e = (int)info.x;
       const unsigned bits = info.y;
       if (act) {
-        T y = a.y[(size_t)(first + mi) * L::kYStride + i];
+        T y = ldcg(a.y + (size_t)(first + mi) * L::kYStride + i);
         for (int f = 0; f < 4; ++f) {
           const int sl = rec_slot_of(info.z, f);
           if (sl < 0) continue;
@@ -298,7 +310,7 @@ __device__ __forceinline__ void group_stage(const SweepArgs<T>& a, int s0, Group
     g.nt = total * Q;
     g.gid = gid;
   }
-  for (int t = lane; t < cnt * N; t += 32) g.z[t] = a.y[(size_t)(first + t / N) * L::kYStride + t % N];
+  for (int t = lane; t < cnt * N; t += 32) g.z[t] = ldcg(a.y + (size_t)(first + t / N) * L::kYStride + t % N);
   const int nt = total * Q;
   const T* Tg = a.grec + a.grp_toff[gid];
   if (nt <= kGroupSmemTrace)
@@ -651,8 +663,47 @@ struct CtaShape {
   static constexpr int trace_budget(int rounds) { return kSmemMax - kGroup - kBars - rounds * kRound; }
 };
 
+// Fused apply: when the directions leave SMs free, the sweep launch is cooperative (every
+// CTA resident) and its CTAs past the direction CTAs compute y = A^{-1} b band by band
+// (kApplyBand levels of one direction, bands in order across the directions), publishing
+// a release flag per band; a direction's producer and group warps acquire a band's flag
+// before reading its y rows.  The workers wait for nothing, so the waits always end.
+constexpr int kApplyBand = 8;
+constexpr int kMinApplyCtas = 8;   // fewer free SMs: apply by a launch of its own
+constexpr uint32_t kReadyWaitIters = 1u << 22;
+
+template <int P, typename T, int MODE>
+__device__ __forceinline__ void apply_worker(const SweepArgs<T>& a) {
+  constexpr int N = (P + 1) * (P + 1);
+  constexpr int SPC = (32 / N) > 0 ? (32 / N) : 1;
+  const int w = (int)blockIdx.x - a.nd, nworkers = (int)gridDim.x - a.nd;
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int total_levels = a.dir_lev0[a.nd];
+  const long long units = (long long)a.bands * a.nd;
+  for (long long u = w; u < units; u += nworkers) {
+    const int band = (int)(u / a.nd), dd = (int)(u % a.nd);
+    const int k0d = a.dir_lev0[dd], k1d = a.dir_lev0[dd + 1];
+    const int ka = k0d + band * kApplyBand;
+    if (ka >= k1d) continue;
+    const int kz = min(k1d, ka + kApplyBand);
+    const long long mb = a.lev_mbegin[ka];
+    const long long me = kz < total_levels ? (long long)a.lev_mbegin[kz] : a.nmem;
+    for (long long m0 = mb + (long long)warp * SPC; m0 < me; m0 += (long long)nw * SPC)
+      apply_warp<P, T, MODE>(a, m0, me);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release_gpu(a.ready + (size_t)dd * a.bands + band, 1);
+    }
+  }
+}
+
 template <int P, typename T, int MODE>
 __global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
+  if (a.ready != nullptr && (int)blockIdx.x >= a.nd) {
+    apply_worker<P, T, MODE>(a);
+    return;
+  }
   using Sh = CtaShape<P, T>;
   using L = Rec<P, T>;
   constexpr int Q = P + 1, N = Q * Q, SPC = Sh::SPC, CH = Sh::CH, CK = Sh::CK;
@@ -706,12 +757,34 @@ __global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
   auto next = [&](unsigned& b, unsigned& par) {
     if (++b == NB) { b = 0; par ^= 1u; }
   };
+  // fused apply: wait (whole warp) until the y rows of level kk's band are written
+  int ready_band = -1;
+  auto wait_ready = [&](int kk) {
+    if (a.ready == nullptr) return;
+    const int band = (kk - k0) / kApplyBand;
+    if (band <= ready_band) return;
+    if (lane == 0) {
+      const int* flag = a.ready + (size_t)d * a.bands + band;
+      uint32_t n = 0;
+      while (ld_acquire_gpu(flag) == 0 && ++n < kReadyWaitIters) {
+        if (*(volatile unsigned int*)a.status & kDevTimeout) break;
+        __nanosleep(64);
+      }
+      if (n >= kReadyWaitIters) atomicOr(a.status, kDevTimeout);
+    }
+    __syncwarp();
+    ready_band = band;
+  };
 
   if (warp == Sh::kProducer) {
     unsigned rc = 0, b = 0, par = 0;
     for (int k = k0; k < k1; ++k) {
       advance(k);
       const int nsingle = lev_g(k) - lev_b(k), mb = lev_m(k);
+      if (nsingle > 0 && a.ready != nullptr) {
+        wait_ready(k);
+        if (lane == 0) fence_proxy_async_global();   // the y rows are read by bulk copies
+      }
       for (int r0 = 0; r0 < nsingle; r0 += CK, ++rc, next(b, par)) {
         if (lane != 0) continue;
         if (rc >= NB) bounded_wait(&empty[b], par ^ 1u);   // the buffer's previous use was released
@@ -762,6 +835,7 @@ __global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
   if (!compute) {
     const int g0 = lev_g(k0) + gidx;
     if (g0 < lev_b(k0 + 1) && direct(g0)) {
+      wait_ready(k0);
       group_stage<P, T>(a, g0, gs);
       staged = g0;
     }
@@ -827,6 +901,7 @@ __global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
         next(rb_i, rpar);
       }
     } else {
+      if (sg + gidx < se) wait_ready(k);
       for (int g = sg + gidx; g < se; g += Sh::kGroupWarps) {
         if (direct(g)) {
           if (staged != g) group_stage<P, T>(a, g, gs);
@@ -839,6 +914,7 @@ __global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
       if (k + 1 < k1) {
         const int g1 = lev_g(k + 1) + gidx, ge = lev_b(k + 2);
         if (g1 < ge && direct(g1)) {
+          wait_ready(k + 1);
           group_stage<P, T>(a, g1, gs);
           staged = g1;
         }
@@ -1001,6 +1077,7 @@ struct SweepCall {
   int cta_warps;     // warps per CTA
   bool group_iterative;  // solve every coupled group by the inner iteration
   bool cluster;      // cluster sweep kernel instead of the single-CTA one
+  bool apply_separate;   // y = A^{-1} b by its own launch even when SMs are free
 };
 
 // Host-side arguments of one problem's sweep (also the batch table entries).
@@ -1130,11 +1207,46 @@ static vef_status launch_sweep_cta(const SweepCall& c, SweepArgs<T>& a) {
   a.ring = rounds;
   a.tr_bytes = tr;
   const size_t smem = (size_t)Sh::kGroup + Sh::kBars + tr + (size_t)rounds * Sh::kRound;
-  VEF_CUDA_TRY(cudaFuncSetAttribute(sweep_cta_kernel<P, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-  KTimer kt(c.mesh, VEF_K_SWEEP, c.stream);
-  sweep_cta_kernel<P, T, MODE><<<(unsigned)S.D, Sh::kThreads, smem, c.stream>>>(a);
-  VEF_CUDA_TRY(cudaGetLastError());
+  auto kern = sweep_cta_kernel<P, T, MODE>;
+  VEF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // the SMs the directions leave free apply A^{-1} inside the same (cooperative) launch
+  int dev = 0, sms = 0, per_sm = 0;
+  VEF_CUDA_TRY(cudaGetDevice(&dev));
+  VEF_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  VEF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Sh::kThreads, smem));
+  const int workers = per_sm * sms - S.D;
+  cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+  VEF_CUDA_TRY(cudaStreamIsCapturing(c.stream, &capturing));
+  // graph capture keeps the plain launch pair (no cooperative node in the graph)
+  if (c.apply_separate || workers < kMinApplyCtas || capturing != cudaStreamCaptureStatusNone) {
+    vef_status st = launch_apply<P, T, MODE>(c, a);
+    if (st != VEF_OK) return st;
+    KTimer kt(c.mesh, VEF_K_SWEEP, c.stream);
+    kern<<<(unsigned)S.D, Sh::kThreads, smem, c.stream>>>(a);
+    VEF_CUDA_TRY(cudaGetLastError());
+    return VEF_OK;
+  }
+  Mesh& M = *c.mesh;
+  a.bands = (S.levels + kApplyBand - 1) / kApplyBand;
+  a.nd = S.D;
+  a.nmem = S.members;
+  const size_t flag_bytes = (size_t)S.D * a.bands * sizeof(int);
+  vef_status st = ensure_buffer((void**)&M.ready_flags, &M.ready_cap, flag_bytes);
+  if (st != VEF_OK) return st;
+  a.ready = M.ready_flags;
+  VEF_CUDA_TRY(cudaMemsetAsync(M.ready_flags, 0, flag_bytes, c.stream));
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute attr[1];
+  cfg.gridDim = dim3((unsigned)(S.D + workers));
+  cfg.blockDim = dim3(Sh::kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c.stream;
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  KTimer kt(c.mesh, VEF_K_SWEEP, c.stream);   // the sweep with its apply
+  VEF_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
   return VEF_OK;
 }
 
@@ -1160,7 +1272,6 @@ static vef_status launch_sweep(const SweepCall& c0, const double* rhs, T* out) {
     SweepArgs<T> a;
     vef_status st = make_sweep_args<P, T>(c, rhs, out, a);
     if (st != VEF_OK) return st;
-    if ((st = launch_apply<P, T, MODE>(c, a)) != VEF_OK) return st;
     return launch_sweep_cta<P, T, MODE>(c, a);
   }
   if (c.cluster_size == 0) {
@@ -1326,6 +1437,7 @@ static void fill_opts(const vef_opts* o, SweepCall& c) {
   c.cta_warps = t ? std::min(16, std::max(1, t % 100)) : 0;
   c.group_iterative = o && (o->flags & VEF_GROUPS_ITERATIVE);
   c.cluster = t != 0 || (o && (o->flags & VEF_SWEEP_CLUSTER));
+  c.apply_separate = o && (o->flags & VEF_APPLY_SEPARATE);
 }
 
 static void schedule_info(const Schedule& S, vef_info* info) {

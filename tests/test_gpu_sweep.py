@@ -97,6 +97,21 @@ def test_cta_and_cluster_kernels_agree(lib, p):
     assert rel(host(psi_cl), ref) < 1e-12, info_cl
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fused_and_separate_apply_agree(lib, precision):
+    """By default the SMs the directions leave free compute y = A^{-1} b inside the sweep
+    launch (band flags between the two roles); VEF_APPLY_SEPARATE keeps a launch of its
+    own.  Both reproduce the oracle."""
+    prob = random_problem(14, 12, 3, 0.1, 2, 8, seed=95, aniso=True, sigma_range=(-1.0, 0.5))
+    _, (psi_f, info_f) = _run(prob, precision=precision)
+    _, (psi_s, info_s) = _run(prob, precision=precision, apply="separate")
+    _, ref = _oracle(prob)
+    tol = 1e-12 if precision == "fp64" else 1e-10
+    assert info_f["timed_out"] == 0 and info_s["timed_out"] == 0
+    assert rel(host(psi_f), ref) < tol, info_f
+    assert rel(host(psi_s), ref) < tol, info_s
+
+
 @pytest.mark.parametrize("slots", ["0", "3"])
 def test_trace_slot_capacity_fallback(lib, monkeypatch, slots):
     """With the shared-memory trace slots capped (none, or three live at a time) the
