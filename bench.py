@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--order", type=int, default=2, help="--sweep-only: DG order p")
     ap.add_argument("--sn", type=int, default=8, help="--sweep-only: level-symmetric order N")
     ap.add_argument("--precision", default="fp64", choices=("fp64", "mixed"), help="--sweep-only: precision")
+    ap.add_argument("--apply", default="fused", choices=("fused", "separate"),
+                    help="--sweep-only: y = A^-1 b inside the sweep launch or as its own launch")
     ap.add_argument("--suite", default="", choices=("", "precision", "batch", "adjoint"),
                     help="other workloads (one JSON line each, not the headline): precision = 512x512 "
                          "Q3 S12 FP64 vs mixed; batch = the 64-problem batch; adjoint = 128x128 Q2 S8 "
@@ -577,7 +579,8 @@ def suite_adjoint(args):
 def sweep_only(args):
     """Small driver for ncu captures: NX x NX sine mesh (alpha 0.05, Q3 map), DG order
     --order (default 2), S_N --sn (default 8), seed-2 media, q = 1; runs --steps sweeps
-    (each with its factorisation) in --precision through the public API."""
+    (each with its factorisation) in --precision, with the apply --apply, through the public
+    API."""
     import torch
 
     from paper_2301_04758_gb300 import build as vbuild
@@ -593,7 +596,8 @@ def sweep_only(args):
     q = torch.ones(N * N, n, dtype=torch.float64, device="cuda")
     psi = torch.empty(len(w), N * N, n, dtype=torch.float64, device="cuda")
     for _ in range(args.steps):
-        mesh.sweep(T(st), T(ss), om, w, source=q, psi=psi, precision=args.precision)
+        mesh.sweep(T(st), T(ss), om, w, source=q, psi=psi, precision=args.precision,
+                   apply=args.apply)
     torch.cuda.synchronize()
     mesh.sync()
 
