@@ -33,7 +33,7 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -57,7 +57,7 @@ def parse():
                          "adjoint gradients with a central-difference check")
     ap.add_argument("--mixed-tol", type=float, default=1e-12,
                     help="relative residual target of the mixed-precision defect correction")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 # ------------------------------------------------------------------ accounting
@@ -185,6 +185,24 @@ class Clocks:
 
 
 # -------------------------------------------------------------------- our arm
+def max_over_ranks(values, world, device="cpu"):
+    """Each timing's maximum over the ranks (one all-reduce of the list); the identity on
+    one rank.  Every rank runs its own replica of the workload, so the job takes as long
+    as its slowest rank."""
+    if world == 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.cpu().tolist()]
+
+
+def job_rate(units_per_step, steps, ms, world):
+    """Whole-job throughput: `world` replicas each process `units_per_step` per step, and
+    `ms` (the maximum over the ranks) covers `steps` steps."""
+    return world * units_per_step * steps / (ms * 1e-3)
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -291,19 +309,11 @@ def run_ours(args, rank, world, local_rank):
     h2d = 8 * (2 * E + E * n)
     d2h = sum(8 * v.numel() for v in out.values())
 
-    # max over ranks
-    def rmax(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
-    ms64, ms32, ms_e2e = rmax(ms64), rmax(ms32), rmax(ms_e2e)
-
+    ms64, ms32, ms_e2e = max_over_ranks([ms64, ms32, ms_e2e], world, dev)
     steps = args.steps
-    value = world * updates * steps / (ms64 * 1e-3)
-    mixed_value = world * updates * steps / (ms32 * 1e-3)
-    e2e_value = world * updates * steps / (ms_e2e * 1e-3)
+    value = job_rate(updates, steps, ms64, world)
+    mixed_value = job_rate(updates, steps, ms32, world)
+    e2e_value = job_rate(updates, steps, ms_e2e, world)
 
     # roofline of the dominant kernel (FP64 run), from the live per-kernel CUDA events
     fp64_meas = fma_peak("fp64") / 1e9
