@@ -150,6 +150,26 @@ def test_edge_cases_single_element_and_ragged(lib):
         assert rel(host(psi), ref) < 1e-12, (nx, ny)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_void_and_optically_thick_elements(lib, precision):
+    """Cross sections from void (sigma_t = 0: the element solve has only the streaming
+    and outflow terms, and at p >= 2 the interior node's diagonal entry vanishes) to
+    1e4 (thick diffusive elements, sigma_s / sigma_t = 1 - 1e-8) in one curved mesh,
+    p = 1..4.  The unpivoted Gauss-Jordan on the element matrix must match the oracle's
+    pivoted sparse solve."""
+    for p in (1, 2, 3, 4):
+        prob = random_problem(6, 5, 3, 0.05, p, 8, seed=60 + p)
+        E = 30
+        kind = np.arange(E) % 3
+        st = np.where(kind == 0, 0.0, np.where(kind == 1, 1e4, prob["sigma_t"]))
+        ss = np.where(kind == 0, 0.0, np.where(kind == 1, st * (1 - 1e-8), prob["sigma_s"]))
+        prob = dict(prob, sigma_t=st, sigma_s=ss)
+        _, (psi, info) = _run(prob, precision=precision)
+        _, ref = _oracle(prob)
+        assert info["timed_out"] == 0
+        assert rel(host(psi), ref) < (1e-12 if precision == "fp64" else 1e-10), (p, precision)
+
+
 def test_axis_aligned_and_single_direction(lib):
     """Directions parallel to straight faces (Omega . n = 0 on two faces: outflow by
     convention, zero weight) and a one-direction set."""
