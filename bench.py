@@ -99,7 +99,57 @@ def bytes_sweep(p, word=8, inflow_faces=2.0):
     inflow_faces is kept for the flop count's signature)."""
     n = (p + 1) ** 2
     pad = lambda b: (b + 15) // 16 * 16
-    return pad(16 + 2 * word * n * (p + 1)) + pad(word * n) + 16 + 8 * n
+    return pad(16 + 2 * word * n * (p + 1)) + pad(word * n) + 16 + word * n
+
+
+def flops_residual(p):
+    """Per (element, direction) flops of the FP64 residual r = b - L psi (mixed path): the
+    element matrix times psi (2 n^2), the upwind couplings of two interior inflow faces
+    (2 x 2 (p+1)^2) and the two squared norms (4 n)."""
+    n, q = (p + 1) ** 2, p + 1
+    return 2 * n * n + 2 * 2 * q * q + 4 * n
+
+
+def bytes_residual(p, D):
+    """Per (element, direction) bytes of the FP64 residual: the stored FP64 element matrix
+    and four face couplings (n^2 + 4 (p+1)^2 words), psi read, the upwind face values of
+    two faces, the direction-independent rhs (/ D) and r written."""
+    n, q = (p + 1) ** 2, p + 1
+    return 8 * (n * n + 4 * q * q) + 8 * n + 2 * 8 * q + 8 * n / D + 8 * n
+
+
+HBM_MEASURED = "MEASURED_PEAKS.json hbm_gbs (measured)"
+HBM_FALLBACK = "fallback: 6.8 TB/s, an earlier GB300 copy measurement (MEASURED_PEAKS.json absent)"
+FP64_SRC = "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2070 MHz"
+FP32_SRC = "derived: 152 SM x 128 FP32 FMA/clk x 2 flop x 2070 MHz"
+
+
+def roofline_entries(prof, work, units, hbm_gbs, hbm_src=HBM_MEASURED):
+    """Roofline of each kernel class from its live CUDA-event times.
+
+    prof: {class: (launches, ms)}; work: {class: (flops per unit, bytes per unit, ALU peak
+    in GFLOP/s, how that peak was obtained)}; units: (element, direction) units one launch
+    processes.  The bound is whichever of the flops at the ALU peak and the bytes at the
+    measured HBM bandwidth takes longer; achieved = that quantity / the average launch time."""
+    roof = {}
+    for k, (fl_u, by_u, alu_gflops, alu_src) in work.items():
+        cnt, tms = prof.get(k, (0, 0.0))
+        if not cnt or tms <= 0.0:
+            continue
+        avg = tms / cnt
+        fl, by = fl_u * units, by_u * units
+        if fl / (alu_gflops * 1e9) >= by / (hbm_gbs * 1e9):
+            r = {"bound": "alu", "achieved": fl / (avg * 1e-3) / 1e12, "peak": alu_gflops / 1e3,
+                 "unit": "TFLOP/s", "peak_source": alu_src}
+        else:
+            r = {"bound": "hbm", "achieved": by / (avg * 1e-3) / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                 "peak_source": hbm_src}
+        r.update(frac=r["achieved"] / r["peak"], avg_ms=avg, flops_per_launch=fl, bytes_per_launch=by,
+                 tflops=fl / (avg * 1e-3) / 1e12, gbps=by / (avg * 1e-3) / 1e9)
+        roof[k] = r
+    return roof
+
+
 
 
 SWEEP_REGION = ("// upwind correction of row i for face f of member record r",
@@ -201,6 +251,51 @@ def job_rate(units_per_step, steps, ms, world):
     """Whole-job throughput: `world` replicas each process `units_per_step` per step, and
     `ms` (the maximum over the ranks) covers `steps` steps."""
     return world * units_per_step * steps / (ms * 1e-3)
+
+
+def dominant_roofline(prof, roof, traffic_of):
+    """The bench line's roofline object: the kernel class with the most event time among
+    those with a work model, its DRAM traffic per launch from traffic_of (or None)."""
+    timed = [k for k in roof if prof.get(k, (0, 0.0))[0]]
+    if not timed:
+        return None
+    k = max(timed, key=lambda c: prof[c][1])
+    r = roof[k]
+    return {"bound": r["bound"], "achieved": round(r["achieved"], 4), "peak": round(r["peak"], 4),
+            "unit": r["unit"], "frac": round(r["frac"], 4), "traffic": traffic_of(k), "kernel": k,
+            "peak_source": r["peak_source"]}
+
+
+def roofline_report(prof64, prof32, p, D, E, steps, hbm_gbs, fp64_meas_gflops, traffic_of=None,
+                    hbm_src=HBM_MEASURED):
+    """Rooflines of the FP64 and the mixed step from their per-class (launches, ms) event
+    times over `steps` timed steps of K_ITER source iterations each: returns (FP64 per-class
+    entries, FP64 dominant, mixed per-class entries, mixed dominant)."""
+    n = (p + 1) ** 2
+    traffic_of = traffic_of or ncu_traffic
+    # the sweep launch also applies A^{-1} (y = A^{-1} b) on the SMs its directions leave
+    # free (the 40 directions of this workload leave 112 of 152): its work counts with it
+    work = {"factor": (flops_factor(p), 8.0 * (3 * n * n) / D + 8.0 * (n * n + 4 * n * (p + 1)),
+                       FP64_PEAK_GFLOPS, FP64_SRC),
+            "sweep": (flops_sweep(p) + flops_apply(p), bytes_sweep(p) + bytes_apply(p, D),
+                      FP64_PEAK_GFLOPS, FP64_SRC)}
+    roof = roofline_entries(prof64, work, E * D, hbm_gbs, hbm_src)
+    roofline = dominant_roofline(prof64, roof, traffic_of)
+    if roofline:
+        roofline["peak_measured_fma_tflops"] = round(fp64_meas_gflops / 1e3, 4)
+
+    # mixed path: FP32 sweeps (one plain sweep per source iteration, the rest defect
+    # corrections, whose fused apply reads the FP64 residual row of each unit instead of
+    # the per-element rhs) and the FP64 residual
+    s32 = prof32.get("sweep", (0, 0.0))[0]
+    corr = max(s32 - K_ITER * steps, 0) / s32 if s32 else 0.0
+    work32 = {"sweep": (flops_sweep(p) + flops_apply(p),
+                        bytes_sweep(p, word=4) + bytes_apply(p, D, word=4) + corr * 8.0 * n * (1 - 1 / D),
+                        FP32_PEAK_GFLOPS, FP32_SRC),
+              "residual": (flops_residual(p), bytes_residual(p, D), FP64_PEAK_GFLOPS, FP64_SRC)}
+    roof32 = roofline_entries(prof32, work32, E * D, hbm_gbs, hbm_src)
+    roofline32 = dominant_roofline(prof32, roof32, lambda k: None)
+    return roof, roofline, roof32, roofline32
 
 
 def run_ours(args, rank, world, local_rank):
@@ -317,43 +412,13 @@ def run_ours(args, rank, world, local_rank):
 
     # roofline of the dominant kernel (FP64 run), from the live per-kernel CUDA events
     fp64_meas = fma_peak("fp64") / 1e9
-    hbm_peak = 6694.8
+    hbm_peak, hbm_src = 6800.0, HBM_FALLBACK
     try:
-        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
-    except Exception:
+        hbm_peak, hbm_src = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), HBM_MEASURED
+    except (OSError, KeyError, ValueError):
         pass
-    kern = {k: v for k, v in prof64.items() if v[0] > 0}
-    dom = max(kern, key=lambda k: kern[k][1])
-    # the sweep launch also applies A^{-1} (y = A^{-1} b) on the SMs its directions leave
-    # free (the 40 directions of this workload leave 112 of 152): its work counts with it
-    work = {"factor": (flops_factor(p), 8.0 * (3 * n * n) / D + 8.0 * (n * n + 4 * n * (p + 1))),
-            "sweep": (flops_sweep(p) + flops_apply(p), bytes_sweep(p) + bytes_apply(p, D))}
-    roof = {}
-    for k, (fl_u, by_u) in work.items():
-        cnt, tms = prof64.get(k, (0, 0.0))
-        if not cnt:
-            continue
-        avg = tms / cnt
-        fl, by = fl_u * E * D, by_u * E * D
-        t_alu, t_hbm = fl / (FP64_PEAK_GFLOPS * 1e9), by / (hbm_peak * 1e9)
-        if t_alu >= t_hbm:
-            r = {"bound": "alu", "achieved": fl / (avg * 1e-3) / 1e12, "peak": FP64_PEAK_GFLOPS / 1e3,
-                 "unit": "TFLOP/s"}
-        else:
-            r = {"bound": "hbm", "achieved": by / (avg * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s"}
-        r.update(frac=r["achieved"] / r["peak"], avg_ms=avg, flops_per_launch=fl, bytes_per_launch=by,
-                 tflops=fl / (avg * 1e-3) / 1e12, gbps=by / (avg * 1e-3) / 1e9)
-        roof[k] = r
-    main = roof.get(dom) or roof.get("sweep")
-    roofline = None
-    if main:
-        kname = dom if dom in roof else "sweep"
-        roofline = {"bound": main["bound"], "achieved": round(main["achieved"], 4),
-                    "peak": round(main["peak"], 4), "unit": main["unit"], "frac": round(main["frac"], 4),
-                    "traffic": ncu_traffic(kname), "kernel": kname,
-                    "peak_source": ("MEASURED_PEAKS.json hbm_gbs (measured)" if main["bound"] == "hbm" else
-                                    "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2070 MHz"),
-                    "peak_measured_fma_tflops": round(fp64_meas / 1e3, 4)}
+    roof, roofline, roof32, roofline32 = roofline_report(prof64, prof32, p, D, E, args.steps,
+                                                         hbm_peak, fp64_meas, hbm_src=hbm_src)
     launches = sum(v[0] for v in prof64.values())
 
     line = {
@@ -370,6 +435,7 @@ def run_ours(args, rank, world, local_rank):
         "mixed": {"value": mixed_value, "ms_per_step": ms32 / steps, "dtype": "f32 solve + f64 defect correction",
                   "defect_correction_rel_residual_target": args.mixed_tol,
                   "rel_err_vs_fp64": mixed_err, "clocks": clk2,
+                  "roofline": roofline32, "roofline_kernels": roof32,
                   "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof32.items() if v[0]}},
         "e2e": {"value": e2e_value, "unit": "angular-DOF updates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e / steps},
