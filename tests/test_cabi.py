@@ -48,3 +48,21 @@ def test_status_strings_and_no_device_failure(libpath):
     st = lib.vef_mesh_create(4, 4, 1, 1, 0.0, None, ctypes.byref(h))
     assert st == _lib.VEF_ERR_CUDA          # fails loudly, no CPU fallback
     assert not h.value
+
+
+def test_mesh_create_checks_its_ranges_before_the_device(libpath):
+    """Out-of-range sizes are refused by the host before any CUDA call, so the status is
+    VEF_ERR_INVALID_ARG with or without a GPU: at most 2^22 elements (the packed task code
+    holds 22 bits of element index), orders 1..4, a finite distortion, an output pointer."""
+    import ctypes
+    import math
+    from paper_2301_04758_gb300 import _lib
+    lib = _lib.load()
+    h = ctypes.c_void_p()
+    for args in [(2049, 2048, 3, 2, 0.05), (1 << 22, 2, 1, 1, 0.0), (0, 8, 1, 1, 0.0), (8, -1, 1, 1, 0.0),
+                 (8, 8, 0, 2, 0.0), (8, 8, 5, 2, 0.0), (8, 8, 3, 0, 0.0), (8, 8, 3, 5, 0.0),
+                 (8, 8, 3, 2, math.nan), (8, 8, 3, 2, math.inf)]:
+        assert lib.vef_mesh_create(*args, None, ctypes.byref(h)) == _lib.VEF_ERR_INVALID_ARG, args
+        assert not h.value
+        assert lib.vef_last_error() != b""
+    assert lib.vef_mesh_create(8, 8, 3, 2, 0.05, None, None) == _lib.VEF_ERR_INVALID_ARG

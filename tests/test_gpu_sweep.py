@@ -170,6 +170,37 @@ def test_void_and_optically_thick_elements(lib, precision):
         assert rel(host(psi), ref) < (1e-12 if precision == "fp64" else 1e-10), (p, precision)
 
 
+def test_maximum_direction_count(lib):
+    """D = 1023, the largest direction set a call takes (10 bits of direction index in a
+    packed task code), on a small curved mesh: 1023 direction CTAs leave no SMs for the
+    fused apply, so the separate apply launch runs.  psi and the closures match the oracle,
+    and D = 1024 is refused."""
+    import ctypes
+    from oracle.moments import closures
+    from paper_2301_04758_gb300 import _lib
+    rng = np.random.default_rng(1023)
+    D = 1023
+    z, ph = rng.uniform(0.02, 0.98, D), rng.uniform(0.0, 2 * np.pi, D)
+    om = np.stack([np.sqrt(1 - z * z) * np.cos(ph), np.sqrt(1 - z * z) * np.sin(ph)], axis=1)
+    w = np.full(D, 4 * np.pi / D)
+    prob = random_problem(3, 2, 3, 0.05, 2, 4, seed=5, with_inflow=False)
+    prob = dict(prob, omega=om, weights=w)
+    mesh, (psi, info) = _run(prob)
+    disc, ref = _oracle(prob)
+    assert info["timed_out"] == 0
+    assert rel(host(psi), ref) < 1e-12
+    out = mesh.moments(psi, om, w)
+    rc = closures(disc, ref, om, w)
+    for k in ("phi", "J", "E", "Eb"):
+        assert rel(host(out[k]), rc[k]) < 1e-12, k
+    om2 = np.ascontiguousarray(np.concatenate([om, om[:1]]), dtype=np.float64)
+    w2 = np.full(D + 1, 4 * np.pi / (D + 1))
+    st = lib.vef_sweep(mesh.handle, None, None, None, None, 0, None,
+                       om2.ctypes.data_as(ctypes.c_void_p), w2.ctypes.data_as(ctypes.c_void_p), D + 1,
+                       None, None, None, None)
+    assert st == _lib.VEF_ERR_INVALID_ARG and b"1..1023" in lib.vef_last_error()
+
+
 def test_axis_aligned_and_single_direction(lib):
     """Directions parallel to straight faces (Omega . n = 0 on two faces: outflow by
     convention, zero weight) and a one-direction set."""
