@@ -267,6 +267,19 @@ vef_status vef_profile_read(vef_mesh mesh, vef_kernel_stat* out);
  * the rate.  Diagnostic for roofline denominators; synchronises the device. */
 vef_status vef_measure_fma_peak(int precision, double* flops_per_s);
 
+/* Failure-detection self-test (the paper has no counterpart: its CPU sweeps do not wait on
+ * other processors' flags).  Every wait in the library's kernels is a bounded poll that, when
+ * it runs out, sets a timeout bit in a device status word and lets the kernel finish, so the
+ * call returns VEF_ERR_TIMEOUT and the CUDA context stays usable.  This call runs one such
+ * wait in a one-thread kernel on `stream` and synchronises it:
+ *   kind 0  acquire loads of a global flag (the form of the fused apply's band waits),
+ *   kind 1  try-waits on a shared-memory mbarrier phase (the form of the staging waits);
+ *   satisfied != 0: the flag is set / the phase completed before the wait -> VEF_OK;
+ *   satisfied == 0: nothing completes it -> VEF_ERR_TIMEOUT after `polls` polls.
+ * polls in 1..2^24, else VEF_ERR_INVALID_ARG (checked before any CUDA call).  Allocates and
+ * frees 8 bytes of device memory. */
+vef_status vef_wait_selftest(int kind, int satisfied, long long polls, void* stream);
+
 /* Eddington tensor without device allocation (the paper has no counterpart: this is a
  * library interface).  Same result as vef_moments with only Eten requested:
  *   Eten [device] [3][E][(p+2)^2] = P / phi at the volume Gauss points, from

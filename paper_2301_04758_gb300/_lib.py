@@ -28,7 +28,7 @@ VEF_APPLY_SEPARATE = 4
 # every symbol include/vef.h declares
 EXPORTS = ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sync", "vef_sweep",
            "vef_moments", "vef_source_iterate", "vef_adjoint_sweep", "vef_profile",
-           "vef_profile_read", "vef_measure_fma_peak", "vef_eddington_noalloc",
+           "vef_profile_read", "vef_measure_fma_peak", "vef_wait_selftest", "vef_eddington_noalloc",
            "vef_batch_create", "vef_batch_destroy", "vef_batch_sweep", "vef_batch_tune",
            "vef_region_weights",
            "vef_status_string", "vef_last_error")
@@ -89,6 +89,7 @@ def _declare(lib):
     lib.vef_profile.argtypes = [P, I]
     lib.vef_profile_read.argtypes = [P, ctypes.POINTER(VefKernelStat)]
     lib.vef_measure_fma_peak.argtypes = [I, ctypes.POINTER(ctypes.c_double)]
+    lib.vef_wait_selftest.argtypes = [I, I, ctypes.c_longlong, P]
     lib.vef_eddington_noalloc.argtypes = [P, P, P, I, ctypes.c_longlong, I, P, P]
     PP = ctypes.POINTER(ctypes.c_void_p)
     lib.vef_batch_create.argtypes = [PP, I, PP, PP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(P)]
@@ -99,7 +100,7 @@ def _declare(lib):
     lib.vef_region_weights.argtypes = [P, D, D, D, D, P, P]
     for name in ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sync",
                  "vef_sweep", "vef_moments", "vef_source_iterate", "vef_adjoint_sweep",
-                 "vef_profile", "vef_profile_read", "vef_measure_fma_peak",
+                 "vef_profile", "vef_profile_read", "vef_measure_fma_peak", "vef_wait_selftest",
                  "vef_eddington_noalloc", "vef_batch_create", "vef_batch_destroy",
                  "vef_batch_sweep", "vef_batch_tune", "vef_region_weights"):
         getattr(lib, name).restype = I

@@ -18,7 +18,7 @@
 
 namespace vef {
 
-constexpr uint32_t kAdjWaitIters = 1u << 26;   // bounded waits of the single-CTA sweep
+constexpr uint32_t kAdjWaitIters = 1u << 18;   // bounded staging waits (~1 s, as the forward sweep's)
 
 struct AdjArgs {
   const int* dir_lev0;

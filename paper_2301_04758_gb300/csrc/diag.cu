@@ -3,6 +3,7 @@
 #include <algorithm>
 
 #include "common.h"
+#include "device.cuh"
 
 namespace vef {
 
@@ -48,7 +49,53 @@ static vef_status measure(int iters, double* rate) {
   return VEF_OK;
 }
 
+// Failure-detection self-test.  One thread polls, in the bounded form the sweep's waits
+// take, for something that is already complete (satisfied != 0) or that nothing completes:
+// kind 0 an acquire load of a global flag (with a short sleep between polls, like the wait
+// for a band of the fused apply), kind 1 the parity of a shared-memory mbarrier phase (like
+// the wait for a staged chunk).  After `polls` failed polls it sets the timeout bit of the
+// status word and returns; the loop count is the only bound, so the kernel always ends.
+__global__ void wait_selftest_kernel(int kind, int satisfied, uint32_t polls, const int* flag,
+                                     unsigned int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  uint32_t n = 0;
+  if (kind == 0) {
+    while (ld_acquire_gpu(flag) == 0 && ++n < polls) __nanosleep(64);
+  } else {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+    if (satisfied) mbar_arrive(&bar);
+    while (!mbar_try_wait(&bar, 0) && ++n < polls) {
+    }
+  }
+  if (n >= polls) atomicOr(status, kDevTimeout);
+}
+
 }  // namespace vef
+
+extern "C" vef_status vef_wait_selftest(int kind, int satisfied, long long polls, void* stream) {
+  using namespace vef;
+  if (kind != 0 && kind != 1) { set_last_error("kind must be 0 (global flag) or 1 (mbarrier)"); return VEF_ERR_INVALID_ARG; }
+  if (polls < 1 || polls > (1LL << 24)) { set_last_error("polls must be in 1..2^24"); return VEF_ERR_INVALID_ARG; }
+  cudaStream_t s = (cudaStream_t)stream;
+  int* buf = nullptr;   // [0] the flag, [1] the status word
+  VEF_CUDA_TRY(cudaMalloc(&buf, 2 * sizeof(int)));
+  cudaError_t err = cudaMemsetAsync(buf, 0, 2 * sizeof(int), s);
+  if (err == cudaSuccess && satisfied && kind == 0) err = cudaMemsetAsync(buf, 1, 1, s);
+  if (err == cudaSuccess) {
+    wait_selftest_kernel<<<1, 32, 0, s>>>(kind, satisfied ? 1 : 0, (uint32_t)polls, buf,
+                                          reinterpret_cast<unsigned int*>(buf + 1));
+    err = cudaGetLastError();
+  }
+  unsigned int bits = 0;
+  if (err == cudaSuccess) err = cudaMemcpyAsync(&bits, buf + 1, sizeof(bits), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  cudaFree(buf);
+  if (err != cudaSuccess) return cuda_fail(err, "wait self-test");
+  if (bits & kDevTimeout) { set_last_error("the bounded wait ran out and reported a timeout"); return VEF_ERR_TIMEOUT; }
+  return VEF_OK;
+}
 
 extern "C" vef_status vef_measure_fma_peak(int precision, double* flops_per_s) {
   if (!flops_per_s) { vef::set_last_error("flops_per_s is NULL"); return VEF_ERR_INVALID_ARG; }

@@ -399,7 +399,12 @@ __host__ __device__ constexpr size_t sweep_smem_bytes(int cta_warps, int cluster
          sizeof(GroupSmem<P, T>) * (size_t)sweep_group_warps(cluster_warps);
 }
 
-constexpr uint32_t kStageWaitIters = 1u << 26;
+// Poll limits of the bounded waits.  A try-wait on an mbarrier phase that is not complete
+// suspends the thread for ~3.9 us per poll on GB300 (vef_wait_selftest measures it), so a
+// staging wait gives up after ~1 s; a flag poll with its 64 ns sleep takes ~0.26 us, so a
+// band wait of the fused apply gives up after ~1.1 s.  The longest legitimate wait (a
+// direction waiting for the fused apply to reach its band) lasts milliseconds.
+constexpr uint32_t kStageWaitIters = 1u << 18;
 
 // Warps [0, nws) of a cluster take the single-element tasks; the last ng warps take the
 // coupled groups, so a group's inner iteration never delays a warp's singles and its

@@ -66,3 +66,13 @@ def test_mesh_create_checks_its_ranges_before_the_device(libpath):
         assert not h.value
         assert lib.vef_last_error() != b""
     assert lib.vef_mesh_create(8, 8, 3, 2, 0.05, None, None) == _lib.VEF_ERR_INVALID_ARG
+
+
+def test_wait_selftest_checks_arguments_before_the_device(libpath):
+    from paper_2301_04758_gb300 import _lib
+    lib = _lib.load()
+    for kind, polls in [(2, 10), (-1, 10), (0, 0), (1, (1 << 24) + 1)]:
+        assert lib.vef_wait_selftest(kind, 0, polls, None) == _lib.VEF_ERR_INVALID_ARG, (kind, polls)
+    import torch
+    if not torch.cuda.is_available():
+        assert lib.vef_wait_selftest(0, 0, 16, None) == _lib.VEF_ERR_CUDA
