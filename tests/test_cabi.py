@@ -76,3 +76,18 @@ def test_wait_selftest_checks_arguments_before_the_device(libpath):
     import torch
     if not torch.cuda.is_available():
         assert lib.vef_wait_selftest(0, 0, 16, None) == _lib.VEF_ERR_CUDA
+
+
+def test_python_api_fails_loudly_without_library_or_gpu(libpath, tmp_path):
+    """No CPU fallback anywhere on the product path: a missing library is an error that
+    says how to build it, and without a GPU the wrappers raise the library's status."""
+    from paper_2301_04758_gb300 import _lib
+    with pytest.raises(RuntimeError, match="build"):
+        _lib.load(str(tmp_path / "libvef.so"))
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2301_04758_gb300.api import Mesh
+    with pytest.raises(_lib.VefError) as e:
+        Mesh(4, 4, 1, 1, 0.0)
+    assert e.value.status == _lib.VEF_ERR_CUDA
