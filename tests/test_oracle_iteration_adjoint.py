@@ -129,3 +129,18 @@ def test_adjoint_pure_absorber_closed_form():
         s = np.minimum(dx / abs(mu), dy / abs(eta))
         expect -= w[d] * np.sum(s * ex(X, Y, om[d])) * h * h
     np.testing.assert_allclose(dst.sum(), expect, rtol=2e-3)
+
+
+def test_region_weights_integrate_exactly_on_an_aligned_region():
+    """On a straight 10 x 10 mesh the region [0.6, 0.8]^2 is a union of whole elements, so
+    sum g * phi is the exact integral of any phi in Q_p over it: phi = x^2 y (p = 2)
+    gives (0.8^3 - 0.6^3)/3 * (0.8^2 - 0.6^2)/2, and phi = 1 the area 0.04."""
+    from _problems import nodal_xy
+    disc = Discretization(10, 10, 1, 0.0, 2)
+    g = region_weights(disc, (0.6, 0.6), (0.8, 0.8))
+    xn, yn = nodal_xy(disc)
+    exact = (0.8 ** 3 - 0.6 ** 3) / 3 * (0.8 ** 2 - 0.6 ** 2) / 2
+    np.testing.assert_allclose(np.sum(g * xn ** 2 * yn), exact, rtol=1e-13)
+    np.testing.assert_allclose(np.sum(g), 0.04, rtol=1e-13)
+    # only the four elements inside carry weight
+    assert np.count_nonzero(np.abs(g).sum(axis=1) > 0) == 4
