@@ -1,5 +1,6 @@
-// Transport sweep: dependency-free right-hand-side apply, cluster wavefront solve, FP64
-// residual and mixed-precision defect correction, and source iteration.
+// Transport sweep: dependency-free right-hand-side apply, wavefront solve (one CTA per
+// direction by default, one cluster per direction for batches), FP64 residual and
+// mixed-precision defect correction, and source iteration.
 //
 // The element equations (upwind DG, pointwise upwinding at face Gauss points) give, for
 // direction d and element e,
@@ -10,8 +11,10 @@
 // is spanned by its p+1 face nodes).  Only the u_f terms depend on other elements.
 //
 // factor_kernel (factor_impl.cuh) stores per (element, direction) A^{-1} and
-// W_f = A^{-1} Cin_f.  apply_kernel forms y = A^{-1} b for every (element, direction) with
-// no dependencies; sweep_kernel then only computes psi = y - sum_f W_f u_f along the
+// W_f = A^{-1} Cin_f.  y = A^{-1} b is formed for every (element, direction) with no
+// dependencies: by apply workers inside the sweep launch when the directions leave SMs
+// free (apply_worker), else by apply_kernel before it.  The wavefront kernels
+// (sweep_cta_kernel, sweep_kernel) then only compute psi = y - sum_f W_f u_f along the
 // dependency levels, one lane per dof row, so the chain of dependent work per level is a
 // few FMAs (on this GPU a warp-wide FP64 FMA occupies its SM sub-partition for ~64
 // cycles, so per-element latency, not total flops, bounds a wavefront).
@@ -78,7 +81,7 @@ struct SweepArgs {
   const T* nds;            // [E][4][nq][2]
   const double* rhs;       // [D][E][n] (mode 1)
   T* out;                  // [D][E][n]
-  T* y;                    // [D][E][n] A^{-1} b (apply_kernel)
+  T* y;                    // [D][E][n] A^{-1} b (apply_kernel or the apply workers)
   unsigned int* status;    // [0] status bits, [2] max inner iterations
   const uint4* tslot;      // single-CTA sweep: trace slot ids per member (Schedule::tslot)
   int* ready;              // single-CTA sweep with fused apply: [nd][bands] band done flags
