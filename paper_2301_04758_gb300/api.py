@@ -109,7 +109,10 @@ class Mesh:
         groups: "direct" (coupled element groups through their trace system) or
         "iterative" (inner block Gauss-Seidel for every group).
         kernel: "cta" (one CTA per direction, the default) or "cluster" (a thread-block
-        cluster per direction; a nonzero tile also selects it)."""
+        cluster per direction; a nonzero tile also selects it).
+        apply: "fused" (y = A^{-1} b computed inside the sweep launch on the SMs the
+        directions leave free, when enough are free and the stream is not being captured)
+        or "separate" (its own launch before the sweep); both give the same psi."""
         om, omp = _host(omega)
         w, wp = _host(weights)
         D = len(w)
