@@ -175,7 +175,7 @@ def src_hash(kernel):
 def ncu_traffic(kernel):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source is
     unchanged since the capture (else None)."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    path = os.path.join(ROOT, "profiles", "sweep_cta_kernel_dram_traffic_sine128_q2_s8.txt")
     if not os.path.exists(path):
         return None
     want = src_hash(kernel)

@@ -54,3 +54,15 @@ def test_classes_without_launches_are_left_out():
     roof, main, roof32, main32 = bench.roofline_report({"sweep": (0, 0.0)}, {}, P, D, E, 1, 6792.4, 1e3,
                                                        traffic_of=lambda k: None)
     assert roof == {} and main is None and roof32 == {} and main32 is None
+
+
+def test_committed_traffic_summary_parses():
+    """The DRAM-traffic summary behind roofline.traffic lists the sweep launch of the bench
+    workload with a source hash in the form src_hash() produces."""
+    import os
+    path = os.path.join(os.path.dirname(bench.__file__), "profiles",
+                        "sweep_cta_kernel_dram_traffic_sine128_q2_s8.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    sweep = [r for r in rows if r[0] == "sweep" and r[1] == bench.WORKLOAD]
+    assert len(sweep) == 1
+    assert float(sweep[0][2]) > 0 and len(sweep[0][3]) == len(bench.src_hash("sweep"))
