@@ -91,3 +91,20 @@ def test_python_api_fails_loudly_without_library_or_gpu(libpath, tmp_path):
     with pytest.raises(_lib.VefError) as e:
         Mesh(4, 4, 1, 1, 0.0)
     assert e.value.status == _lib.VEF_ERR_CUDA
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/vef.h is a C interface: it compiles as strict C99 (no CUDA or C++ types in
+    the signatures) and as C++."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(ROOT, "include")
+    src = tmp_path / "use_vef.c"
+    src.write_text('#include "vef.h"\nint main(void) { vef_opts o = {0}; (void)o; return (int)VEF_OK; }\n')
+    for lang in (["-x", "c", "-std=c99", "-pedantic"], ["-x", "c++", "-std=c++17"]):
+        r = subprocess.run([gcc, *lang, "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-I", inc, str(src)],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
