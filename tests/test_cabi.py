@@ -103,7 +103,8 @@ def test_header_is_plain_c(tmp_path):
         pytest.skip("no C compiler")
     inc = os.path.join(ROOT, "include")
     src = tmp_path / "use_vef.c"
-    src.write_text('#include "vef.h"\nint main(void) { vef_opts o = {0}; (void)o; return (int)VEF_OK; }\n')
+    src.write_text('#include <string.h>\n#include "vef.h"\n'
+                   'int main(void) { vef_opts o; memset(&o, 0, sizeof o); return (int)VEF_OK + o.flags; }\n')
     for lang in (["-x", "c", "-std=c99", "-pedantic"], ["-x", "c++", "-std=c++17"]):
         r = subprocess.run([gcc, *lang, "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-I", inc, str(src)],
                            capture_output=True, text=True)
