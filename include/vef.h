@@ -267,6 +267,25 @@ vef_status vef_profile_read(vef_mesh mesh, vef_kernel_stat* out);
  * the rate.  Diagnostic for roofline denominators; synchronises the device. */
 vef_status vef_measure_fma_peak(int precision, double* flops_per_s);
 
+/* Dependency schedule of the sweep, computed on the host from the face normals alone (the
+ * scheduler behind vef_sweep; no CUDA call, for tests and tooling).  The paper sweeps in a
+ * topological order of the elements and lags the couplings that re-entrant faces make
+ * cyclic (Sec. "Thick Diffusion Limit", citing its graph-sweep reference); here the
+ * upwind graph, decided pointwise at the face Gauss points, is condensed by its strongly
+ * connected components, which the sweep solves as coupled groups, and the components are
+ * levelled (Kahn) so that every donor lies at an earlier level.
+ *   nds    [E][4][p+2][2] outward n ds at the face Gauss points, E = nx*ny, element
+ *          e = j*nx + i, faces 0..3 towards (i, j-1), (i+1, j), (i, j+1), (i-1, j);
+ *          a face point with Omega . n ds < 0 is inflow, = 0 neither (host array)
+ *   omega  [D][2] directions (host); D in 1..1023
+ *   levels [D] out: dependency levels of each direction
+ *   groups [D] out: coupled groups of two or more elements
+ *   level, comp_size  [D][E] out, each may be NULL: the level of each element's component
+ *          and that component's size (1 for an element swept on its own).
+ * Errors: VEF_ERR_INVALID_ARG (sizes, NULL required pointers), VEF_ERR_OOM (host memory). */
+vef_status vef_schedule_host(int nx, int ny, int p, const double* nds, const double* omega, int D,
+                             int* levels, long long* groups, int* level, int* comp_size);
+
 /* Failure-detection self-test (the paper has no counterpart: its CPU sweeps do not wait on
  * other processors' flags).  Every wait in the library's kernels is a bounded poll that, when
  * it runs out, sets a timeout bit in a device status word and lets the kernel finish, so the

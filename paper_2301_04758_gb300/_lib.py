@@ -30,7 +30,7 @@ EXPORTS = ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sy
            "vef_moments", "vef_source_iterate", "vef_adjoint_sweep", "vef_profile",
            "vef_profile_read", "vef_measure_fma_peak", "vef_wait_selftest", "vef_eddington_noalloc",
            "vef_batch_create", "vef_batch_destroy", "vef_batch_sweep", "vef_batch_tune",
-           "vef_region_weights",
+           "vef_region_weights", "vef_schedule_host",
            "vef_status_string", "vef_last_error")
 
 KERNEL_CLASSES = ("geometry", "factor", "sweep", "residual", "source", "moments", "adjoint")
@@ -90,6 +90,7 @@ def _declare(lib):
     lib.vef_profile_read.argtypes = [P, ctypes.POINTER(VefKernelStat)]
     lib.vef_measure_fma_peak.argtypes = [I, ctypes.POINTER(ctypes.c_double)]
     lib.vef_wait_selftest.argtypes = [I, I, ctypes.c_longlong, P]
+    lib.vef_schedule_host.argtypes = [I, I, I, P, P, I, P, P, P, P]
     lib.vef_eddington_noalloc.argtypes = [P, P, P, I, ctypes.c_longlong, I, P, P]
     PP = ctypes.POINTER(ctypes.c_void_p)
     lib.vef_batch_create.argtypes = [PP, I, PP, PP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(P)]
@@ -102,7 +103,7 @@ def _declare(lib):
                  "vef_sweep", "vef_moments", "vef_source_iterate", "vef_adjoint_sweep",
                  "vef_profile", "vef_profile_read", "vef_measure_fma_peak", "vef_wait_selftest",
                  "vef_eddington_noalloc", "vef_batch_create", "vef_batch_destroy",
-                 "vef_batch_sweep", "vef_batch_tune", "vef_region_weights"):
+                 "vef_batch_sweep", "vef_batch_tune", "vef_region_weights", "vef_schedule_host"):
         getattr(lib, name).restype = I
     lib.vef_status_string.argtypes = [I]
     lib.vef_status_string.restype = ctypes.c_char_p

@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <new>
 #include <numeric>
 #include <thread>
 
@@ -50,10 +51,18 @@ inline int nb_of(int nx, int ny, int e, int f) {
 }
 constexpr int kOpp[4] = {2, 3, 0, 1};
 
-void build_direction(const Mesh& M, double mu, double eta, DirGraph& G) {
+// What the schedule of one direction depends on: the structured mesh's sizes, the outward
+// n ds at the face Gauss points ([E][4][nq][2], host copy) and the Gauss weights.
+struct HostGeom {
+  int nx, ny, nq;
+  const double* nds;
+  const double* glw;
+};
+
+void build_direction(const HostGeom& M, double mu, double eta, DirGraph& G) {
   const int nx = M.nx, ny = M.ny, nq = M.nq;
-  const int E = (int)M.E;
-  const double* nds = M.nds_host.data();
+  const int E = nx * ny;
+  const double* nds = M.nds;
   G.info.assign(E, 0);
   // face signs
   for (int e = 0; e < E; ++e) {
@@ -155,7 +164,7 @@ void build_direction(const Mesh& M, double mu, double eta, DirGraph& G) {
         for (int k = 0; k < nq; ++k) {
           const double* v = nds + (((size_t)u * 4 + f) * nq + k) * 2;
           double s = mu * v[0] + eta * v[1];
-          net += M.tab.glw[k] * s;
+          net += M.glw[k] * s;
           if (s < 0.0) G.lagged++;
         }
         if (net > 0.0) {  // u feeds w on balance
@@ -233,6 +242,7 @@ Schedule* get_schedule(Mesh* mesh, const double* omega, const double* weights, i
   }
   const Mesh& M = *mesh;
   const int E = (int)M.E;
+  const HostGeom H{M.nx, M.ny, M.nq, M.nds_host.data(), M.tab.glw};
   std::vector<DirGraph> graphs(D);
   {
     unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 32));
@@ -241,7 +251,7 @@ Schedule* get_schedule(Mesh* mesh, const double* omega, const double* weights, i
     for (unsigned t = 0; t < nt; ++t)
       pool.emplace_back([&, t]() {
         for (int d = (int)t; d < D; d += (int)nt)
-          build_direction(M, omega[2 * d], omega[2 * d + 1], graphs[d]);
+          build_direction(H, omega[2 * d], omega[2 * d + 1], graphs[d]);
       });
     for (auto& th : pool) th.join();
   }
@@ -513,3 +523,39 @@ Schedule* get_schedule(Mesh* mesh, const double* omega, const double* weights, i
 }
 
 }  // namespace vef
+
+extern "C" vef_status vef_schedule_host(int nx, int ny, int p, const double* nds, const double* omega,
+                                        int D, int* levels, long long* groups, int* level,
+                                        int* comp_size) {
+  using namespace vef;
+  if (nx < 1 || ny < 1 || (long long)nx * ny > kMaxE) {
+    set_last_error("nx, ny must be >= 1 with nx*ny <= 2^22");
+    return VEF_ERR_INVALID_ARG;
+  }
+  if (p < 1 || p > kMaxP) { set_last_error("p must be in 1..4"); return VEF_ERR_INVALID_ARG; }
+  if (D < 1 || D > kMaxD) { set_last_error("D must be in 1..1023"); return VEF_ERR_INVALID_ARG; }
+  if (!nds || !omega || !levels || !groups) {
+    set_last_error("nds, omega, levels and groups are required");
+    return VEF_ERR_INVALID_ARG;
+  }
+  try {
+    const Tab1D tab = make_tab1d(p);
+    const HostGeom H{nx, ny, p + 2, nds, tab.glw};
+    const size_t E = (size_t)nx * ny;
+    for (int d = 0; d < D; ++d) {
+      DirGraph G;
+      build_direction(H, omega[2 * d], omega[2 * d + 1], G);
+      levels[d] = G.levels;
+      groups[d] = G.groups;
+      for (size_t e = 0; e < E; ++e) {
+        const int c = G.comp[e];
+        if (level) level[d * E + e] = G.comp_level[c];
+        if (comp_size) comp_size[d * E + e] = G.comp_first[c + 1] - G.comp_first[c];
+      }
+    }
+  } catch (const std::bad_alloc&) {
+    set_last_error("out of host memory");
+    return VEF_ERR_OOM;
+  }
+  return VEF_OK;
+}
