@@ -86,7 +86,11 @@ enum {
                                one CTA */
   VEF_APPLY_SEPARATE = 4    /* compute y = A^{-1} b by a launch of its own before the
                                single-CTA sweep; by default the SMs the directions leave
-                               free do it inside the sweep launch */
+                               free do it inside the sweep launch, which is then a
+                               cooperative launch sized from the device's SM count (a
+                               context limited to fewer SMs, e.g. under MPS, should set
+                               this flag: the driver refuses a cooperative grid that
+                               does not fit, and the call returns VEF_ERR_CUDA) */
 };
 
 typedef struct vef_mesh_s* vef_mesh;
