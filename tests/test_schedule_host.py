@@ -124,3 +124,21 @@ def test_arguments_are_checked():
     assert lib.vef_schedule_host(2, 2, 1, ptr(nds), ptr(om), 0, ptr(out), ptr(out), None, None) == _l.VEF_ERR_INVALID_ARG
     assert lib.vef_schedule_host(2, 2, 1, None, ptr(om), 1, ptr(out), ptr(out), None, None) == _l.VEF_ERR_INVALID_ARG
     assert lib.vef_schedule_host(0, 2, 1, ptr(nds), ptr(om), 1, ptr(out), ptr(out), None, None) == _l.VEF_ERR_INVALID_ARG
+
+
+def test_degenerate_meshes_and_the_largest_direction_set():
+    """One element: one level for every direction.  A 1 x 9 strip: the sweep runs along
+    the strip, so a direction going up or down has 9 levels.  1023 directions (the most a
+    call takes) on a 4 x 3 straight mesh: every one a quadrant wavefront or, on an axis,
+    a chain."""
+    rng = np.random.default_rng(5)
+    ph = rng.uniform(0.0, 2 * np.pi, 1023)
+    r = np.sqrt(rng.uniform(0.0, 1.0, 1023))
+    om = np.stack([r * np.cos(ph), r * np.sin(ph)], axis=1)
+    levels, groups, _, _ = _schedule(1, 1, 3, _straight_nds(1, 1, 3), om[:5])
+    assert levels.tolist() == [1] * 5 and groups.tolist() == [0] * 5
+    levels, groups, level, _ = _schedule(1, 9, 1, _straight_nds(1, 9, 1), [[0.3, 0.7], [0.3, -0.7]])
+    assert levels.tolist() == [9, 9] and level[0].tolist() == list(range(9))
+    assert level[1].tolist() == list(range(8, -1, -1))
+    levels, groups, _, _ = _schedule(4, 3, 4, _straight_nds(4, 3, 4), om)
+    assert np.all(levels == 6) and np.all(groups == 0)
