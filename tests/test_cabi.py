@@ -109,3 +109,30 @@ def test_header_is_plain_c(tmp_path):
         r = subprocess.run([gcc, *lang, "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-I", inc, str(src)],
                            capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def test_option_marshalling():
+    """The Python keywords map onto vef_opts as include/vef.h defines it."""
+    from paper_2301_04758_gb300 import _lib
+    from paper_2301_04758_gb300.api import _opts
+    o = _opts()
+    assert (o.precision, o.tol, o.max_passes, o.tile_override, o.flags) == (_lib.VEF_FP64, 0.0, 0, 0, 0)
+    o = _opts("mixed", 1e-12, 5, 408, "iterative", "cluster", "separate")
+    assert (o.precision, o.tol, o.max_passes, o.tile_override) == (_lib.VEF_MIXED, 1e-12, 5, 408)
+    assert o.flags == _lib.VEF_GROUPS_ITERATIVE | _lib.VEF_SWEEP_CLUSTER | _lib.VEF_APPLY_SEPARATE == 7
+    for bad in (dict(precision="fp16"), dict(groups="lagged"), dict(kernel="warp"), dict(apply="later")):
+        with pytest.raises(KeyError):
+            _opts(**bad)
+    hdr = open(os.path.join(ROOT, "include", "vef.h")).read()
+    for name in ("VEF_GROUPS_ITERATIVE", "VEF_SWEEP_CLUSTER", "VEF_APPLY_SEPARATE", "VEF_FP64", "VEF_MIXED"):
+        m = re.search(name + r"\s*=\s*(\d+)", hdr)
+        assert m and int(m.group(1)) == getattr(_lib, name), name
+
+
+def test_status_codes_agree_with_the_library(libpath):
+    from paper_2301_04758_gb300 import _lib
+    lib = _lib.load()
+    names = ["VEF_OK", "VEF_ERR_INVALID_ARG", "VEF_ERR_CUDA", "VEF_ERR_OOM", "VEF_ERR_TIMEOUT",
+             "VEF_ERR_NOT_CONVERGED", "VEF_ERR_NONPOSITIVE_DENOM", "VEF_ERR_NOT_IMPLEMENTED"]
+    for name in names:
+        assert lib.vef_status_string(getattr(_lib, name)).decode() == name
