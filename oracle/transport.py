@@ -132,7 +132,8 @@ def sweep(disc, omega, weights, sigma_t, sigma_s, phi_in=None, source=None, infl
 
 
 def residual(disc, omega, sigma_t, sigma_s, psi, phi_in=None, source=None, inflow=None):
-    """r_d = b_d - L_d psi_d [D][E][n] (used to check a candidate solution)."""
+    """r_d = b_d - L_d psi_d [D][E][n] with the globally assembled L_d (used to check a
+    candidate solution)."""
     D = psi.shape[0]
     r = np.zeros_like(psi)
     for d in range(D):
@@ -140,3 +141,41 @@ def residual(disc, omega, sigma_t, sigma_s, psi, phi_in=None, source=None, inflo
         b = disc.rhs(c, d, sigma_s, phi_in, source, inflow)
         r[d] = b - (L @ psi[d].ravel()).reshape(b.shape)
     return r
+
+
+def residual_terms(disc, omega, sigma_t, sigma_s, psi, phi_in=None, source=None, inflow=None,
+                   directions=None):
+    """Element-by-element r_d = b_d - L_d psi_d and the size of the terms it sums.
+
+    The same upwind system as `operator` / `rhs`, evaluated without assembling L_d: each
+    element's block A_e acts on its own psi, and each interior inflow face adds the
+    coupling to the neighbour's trace at the face Gauss points.  `size` is the sum of the
+    absolute values of every term entering r (|A_e||psi_e| + |couplings| + |b|), the scale
+    of its rounding.  directions: indices into omega / psi / source / inflow (default all).
+    Returns (r, size), each [len(directions)][E][n]."""
+    g = disc.mesh
+    sigma_t = np.asarray(sigma_t, np.float64)
+    sigma_s = np.asarray(sigma_s, np.float64)
+    dirs = range(psi.shape[0]) if directions is None else list(directions)
+    r_all = np.zeros((len(dirs), g.E, disc.n))
+    s_all = np.zeros_like(r_all)
+    for out, d in enumerate(dirs):
+        P = psi[d]
+        A, c = disc.element_matrices(omega[d], sigma_t)
+        b = disc.rhs(c, d, sigma_s, phi_in, source, inflow)
+        r = b - np.einsum("eij,ej->ei", A, P)
+        size = np.einsum("eij,ej->ei", np.abs(A), np.abs(P)) + np.abs(b)
+        for f in range(4):
+            nb = g.nb[:, f]
+            ok = nb >= 0
+            src = np.where(ok, nb, 0)
+            cin = np.where(c[:, f] < 0.0, c[:, f], 0.0)
+            Bo = disc.Bf[OPPOSITE[f]]
+            tr = np.einsum("kj,ej->ek", Bo, P[src])
+            atr = np.einsum("kj,ej->ek", np.abs(Bo), np.abs(P[src]))
+            r -= np.where(ok[:, None], np.einsum("ek,ki,ek->ei", cin, disc.Bf[f], tr), 0.0)
+            size += np.where(ok[:, None],
+                             np.einsum("ek,ki,ek->ei", np.abs(cin), np.abs(disc.Bf[f]), atr), 0.0)
+        r_all[out] = r
+        s_all[out] = size
+    return r_all, s_all
