@@ -1,21 +1,26 @@
 #!/usr/bin/env python
 """Benchmark: DG S_N sweep + VEF closure pass on one GB300 (or N replicas).
 
-Workload (one "step"): the 256 x 256 sine-curved (alpha = 0.05, third-order map) mesh of
-[0,1]^2, DG Q2, level-symmetric S8 (40 directions), per-element sigma_t log-uniform in
-[0.1, 100] and sigma_s/sigma_t uniform in [0.9, 0.9999] (seed 2), isotropic source 1,
-vacuum inflow: 10 source iterations (local factorisation once, 10 sweeps, 10 scalar-flux
-updates) followed by the closure pass (phi, J, E, E_b, J_in).  Metric: angular-DOF
-updates per second = E (p+1)^2 D * 10 / step time, FP64 (`value`) and mixed precision
-(`mixed`).  Inputs live in HBM for `value`; `e2e` adds the host->device copy of the
-step's inputs and the device->host copy of its outputs through the same C-ABI calls.
+Default workload (one "step"): the 512 x 512 sine-curved (alpha = 0.05, third-order map)
+mesh of [0,1]^2, DG Q3, level-symmetric S12 (84 directions), per-element sigma_t
+log-uniform in [0.1, 100] and sigma_s/sigma_t uniform in [0.9, 0.9999] (seed 3),
+isotropic source 1, vacuum inflow: one transport inversion (local factorisation of every
+(element, direction) system, then the wavefront sweep) followed by the closure pass (phi,
+J, E, E_b, J_in).  Metric: angular-DOF updates per second = E (p+1)^2 D / step time, in
+FP64 (`value`) and in mixed precision beside it (`mixed`: FP32 factorisation and sweeps
+inside FP64 defect correction, two passes), with the mixed path's psi / phi / J / E / E_b
+errors against FP64.  Inputs live in HBM for `value`; `e2e` adds the host->device copy
+of the step's inputs and the device->host copy of its outputs through the same C-ABI
+calls.  `--workload sine256_q2_s8` runs the 256 x 256 Q2 S8 source-iteration workload
+(10 inversions per step) instead.
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
 """
 import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -26,13 +31,21 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = "sine256_q2_s8"
-K_ITER = 10
-# the headline: FP64 throughput of the whole step; the mixed-precision step is reported
-# beside it with its phi / J / E / E_b errors against FP64, and each path's roofline
-METRIC = ("sweep angular-DOF updates/s, FP64 (10 source iterations + closures); mixed "
-          "precision beside it at phi,E rel.err <= 1e-10; % roofline")
+# workloads this script times: (transport inversions per step, description)
+BENCH_WORKLOADS = {
+    "sine512_q3_s12": (1, "512x512 sine-curved Q3 mesh (alpha 0.05), DG Q3, S12 (84 dirs), seeded "
+                          "sigma_t/sigma_s (seed 3), q=1, vacuum; one transport inversion (local "
+                          "factorisation + sweep) + closures per step"),
+    "sine256_q2_s8": (10, "256x256 sine-curved Q3 mesh (alpha 0.05), DG Q2, S8 (40 dirs), seeded "
+                          "sigma_t/sigma_s (seed 2), q=1, vacuum; 10 source iterations (one "
+                          "factorisation, 10 sweeps) + closures per step"),
+}
+WORKLOAD = "sine512_q3_s12"
+# the headline: FP64 throughput of the whole step, the mixed-precision step beside it with
+# its errors against FP64, and each path's roofline
+METRIC = "sweep angular-DOF updates/s, mixed vs FP64 at phi,E rel.err<=1e-10; % roofline"
 MIXED_ERR_BOUND = 1e-10
+MIXED_PASSES = 2
 # FP64 peak from unit counts: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2070 MHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070
@@ -44,6 +57,7 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--workload", default=WORKLOAD, choices=tuple(BENCH_WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep-only", type=int, default=0, metavar="NX",
                     help="profiling driver: build an NX x NX mesh with the workload's recipe and run "
@@ -53,15 +67,19 @@ def parse(argv=None):
                          "sweep, then --steps adjoint sweeps (no timing line)")
     ap.add_argument("--order", type=int, default=2, help="--sweep-only: DG order p")
     ap.add_argument("--sn", type=int, default=8, help="--sweep-only: level-symmetric order N")
+    ap.add_argument("--seed", type=int, default=2, help="--sweep-only: media seed")
     ap.add_argument("--precision", default="fp64", choices=("fp64", "mixed"), help="--sweep-only: precision")
     ap.add_argument("--apply", default="fused", choices=("fused", "separate"),
                     help="--sweep-only: y = A^-1 b inside the sweep launch or as its own launch")
-    ap.add_argument("--suite", default="", choices=("", "precision", "batch", "adjoint"),
-                    help="other workloads (one JSON line each, not the headline): precision = 512x512 "
-                         "Q3 S12 FP64 vs mixed; batch = the 64-problem batch; adjoint = 128x128 Q2 S8 "
-                         "adjoint gradients with a central-difference check")
-    ap.add_argument("--mixed-tol", type=float, default=1e-12,
-                    help="relative residual target of the mixed-precision defect correction")
+    ap.add_argument("--suite", default="", choices=("", "batch", "adjoint"),
+                    help="other workloads (one JSON line each, not the headline): batch = the "
+                         "64-problem batch; adjoint = 128x128 Q2 S8 adjoint gradients with a "
+                         "central-difference check")
+    ap.add_argument("--mixed-tol", type=float, default=-1.0,
+                    help="mixed precision: relative residual target of the defect correction, or < 0 "
+                         "for a fixed %d passes" % MIXED_PASSES)
+    ap.add_argument("--cpu-sample", type=int, default=64, metavar="NX",
+                    help="mesh size of the oracle's bounded CPU sample (the workload's recipe)")
     return ap.parse_args(argv)
 
 
@@ -123,6 +141,47 @@ def bytes_residual(p, D):
     return 8 * (n * n + 4 * q * q) + 8 * n + 2 * 8 * q + 8 * n / D + 8 * n
 
 
+def flops_residual_mf(p):
+    """Per (element, direction) flops of the matrix-free FP64 residual (a single inversion's
+    defect correction): the volume operator from M, Gx, Gy (3 n^2 FMAs and their 3 n
+    combinations), the 4 (p+2) face points (Omega . n ds: 3, one trace: 2 (p+1), the product:
+    1), the face-node rows (4 faces x (p+1) rows x 2 (p+2)) and the two squared norms (4 n)."""
+    n, q, nq = (p + 1) ** 2, p + 1, p + 2
+    return 6 * n * n + 3 * n + 4 * nq * (4 + 2 * q) + 4 * q * 2 * nq + 4 * n
+
+
+def bytes_residual_mf(p, D):
+    """Per (element, direction) bytes of the matrix-free residual: psi read, two upwind
+    faces' node values, r written, and the per-element M, Gx, Gy, normals and right-hand side
+    read once per element (/ D)."""
+    n, q, nq = (p + 1) ** 2, p + 1, p + 2
+    return 8 * n + 2 * 8 * q + 8 * n + (3 * 8 * n * n + 8 * 4 * nq * 2 + 8 * n) / D
+
+
+def bytes_factor(p, D, word=8):
+    """Per (element, direction) bytes of the factorisation: the per-element M, Gx, Gy read
+    once per element (/ D), the record written (16 bytes of element info, A^{-1} and two W
+    slots)."""
+    n, q = (p + 1) ** 2, p + 1
+    return 8.0 * 3 * n * n / D + 16 + word * (n * n + 2 * n * q)
+
+
+def flops_moments(p, D):
+    """Per (element, direction) flops of the moment and closure pass: six FP64 FMAs per psi
+    value for the nodal phi, J, P (12 n), and, once per element (/ D), the Eddington tensor
+    at the (p+2)^2 Gauss points (four interpolations of n terms and three quotients)."""
+    n, nq2 = (p + 1) ** 2, (p + 2) ** 2
+    return 12 * n + nq2 * (8 * n + 3) / D
+
+
+def bytes_moments(p, D, nq2=None):
+    """Per (element, direction) bytes of the moment and closure pass: psi read once; the
+    nodal phi, J, P (six fields) and the Eddington tensor written once per element (/ D)."""
+    n = (p + 1) ** 2
+    nq2 = nq2 or (p + 2) ** 2
+    return 8 * n + (8 * 6 * n + 8 * 3 * nq2) / D
+
+
 HBM_MEASURED = "MEASURED_PEAKS.json hbm_gbs (measured)"
 HBM_FALLBACK = "fallback: 6.8 TB/s, an earlier GB300 copy measurement (MEASURED_PEAKS.json absent)"
 FP64_SRC = "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2070 MHz"
@@ -159,6 +218,10 @@ def roofline_entries(prof, work, units, hbm_gbs, hbm_src=HBM_MEASURED):
 
 SWEEP_REGION = ("// upwind correction of row i for face f of member record r",
                 "// -------------------------------------------------------------- FP64 residual (mixed)")
+# committed ncu summaries of DRAM traffic per kernel class: lines
+#   <class> <workload> <bytes per launch at the workload's full size> <source hash>
+TRAFFIC_FILES = {"sweep": "sweep_cta_kernel_dram_traffic_sine128_q2_s8.txt",
+                 "factor": "factor_elem_kernel_dram_traffic_sine96_q3_s12.txt"}
 
 
 def src_hash(kernel):
@@ -177,16 +240,18 @@ def src_hash(kernel):
     return h.hexdigest()[:12]
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel source is
-    unchanged since the capture (else None)."""
-    path = os.path.join(ROOT, "profiles", "sweep_cta_kernel_dram_traffic_sine128_q2_s8.txt")
-    if not os.path.exists(path):
+def ncu_traffic(kernel, workload=None):
+    """DRAM bytes per launch from the committed ncu summary of that kernel class on the
+    workload, if the kernel source is unchanged since the capture (else None)."""
+    workload = workload or WORKLOAD
+    name = TRAFFIC_FILES.get(kernel)
+    path = os.path.join(ROOT, "profiles", name) if name else None
+    if not path or not os.path.exists(path):
         return None
     want = src_hash(kernel)
     for line in open(path):
         parts = line.split()
-        if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == WORKLOAD:
+        if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == workload:
             return float(parts[2]) if parts[3] == want else None
     return None
 
@@ -271,40 +336,46 @@ def dominant_roofline(prof, roof, traffic_of):
             "peak_source": r["peak_source"]}
 
 
-def roofline_report(prof64, prof32, p, D, E, steps, hbm_gbs, fp64_meas_gflops, traffic_of=None,
-                    hbm_src=HBM_MEASURED):
+def roofline_report(prof64, prof32, p, D, E, steps, K, hbm_gbs, fp64_meas_gflops, traffic_of=None,
+                    hbm_src=HBM_MEASURED, residual_stored=None):
     """Rooflines of the FP64 and the mixed step from their per-class (launches, ms) event
-    times over `steps` timed steps of K_ITER source iterations each: returns (FP64 per-class
-    entries, FP64 dominant, mixed per-class entries, mixed dominant)."""
+    times over `steps` timed steps of K transport inversions each: returns (FP64 per-class
+    entries, FP64 dominant, mixed per-class entries, mixed dominant).  The mixed residual is
+    the stored-system form under source iteration (K > 1), else the matrix-free form."""
     n = (p + 1) ** 2
     traffic_of = traffic_of or ncu_traffic
+    if residual_stored is None:
+        residual_stored = K > 1
     # the sweep launch also applies A^{-1} (y = A^{-1} b) on the SMs its directions leave
-    # free (the 40 directions of this workload leave 112 of 152): its work counts with it
-    work = {"factor": (flops_factor(p), 8.0 * (3 * n * n) / D + 8.0 * (n * n + 4 * n * (p + 1)),
-                       FP64_PEAK_GFLOPS, FP64_SRC),
+    # free: its work counts with it
+    work = {"factor": (flops_factor(p), bytes_factor(p, D), FP64_PEAK_GFLOPS, FP64_SRC),
             "sweep": (flops_sweep(p) + flops_apply(p), bytes_sweep(p) + bytes_apply(p, D),
-                      FP64_PEAK_GFLOPS, FP64_SRC)}
+                      FP64_PEAK_GFLOPS, FP64_SRC),
+            "moments": (flops_moments(p, D), bytes_moments(p, D), FP64_PEAK_GFLOPS, FP64_SRC)}
     roof = roofline_entries(prof64, work, E * D, hbm_gbs, hbm_src)
     roofline = dominant_roofline(prof64, roof, traffic_of)
     if roofline:
         roofline["peak_measured_fma_tflops"] = round(fp64_meas_gflops / 1e3, 4)
 
-    # mixed path: FP32 sweeps (one plain sweep per source iteration, the rest defect
-    # corrections, whose fused apply reads the FP64 residual row of each unit instead of
-    # the per-element rhs) and the FP64 residual
+    # mixed path: FP32 factorisation and sweeps (one plain sweep per inversion, the rest
+    # defect corrections, whose fused apply reads the FP64 residual row of each unit instead
+    # of the per-element rhs) and the FP64 residual
     s32 = prof32.get("sweep", (0, 0.0))[0]
-    corr = max(s32 - K_ITER * steps, 0) / s32 if s32 else 0.0
-    work32 = {"sweep": (flops_sweep(p) + flops_apply(p),
+    corr = max(s32 - K * steps, 0) / s32 if s32 else 0.0
+    res = ((flops_residual(p), bytes_residual(p, D)) if residual_stored
+           else (flops_residual_mf(p), bytes_residual_mf(p, D)))
+    work32 = {"factor": (flops_factor(p), bytes_factor(p, D, word=4), FP32_PEAK_GFLOPS, FP32_SRC),
+              "sweep": (flops_sweep(p) + flops_apply(p),
                         bytes_sweep(p, word=4) + bytes_apply(p, D, word=4) + corr * 8.0 * n * (1 - 1 / D),
                         FP32_PEAK_GFLOPS, FP32_SRC),
-              "residual": (flops_residual(p), bytes_residual(p, D), FP64_PEAK_GFLOPS, FP64_SRC)}
+              "residual": res + (FP64_PEAK_GFLOPS, FP64_SRC),
+              "moments": (flops_moments(p, D), bytes_moments(p, D), FP64_PEAK_GFLOPS, FP64_SRC)}
     roof32 = roofline_entries(prof32, work32, E * D, hbm_gbs, hbm_src)
     roofline32 = dominant_roofline(prof32, roof32, lambda k: None)
     return roof, roofline, roof32, roofline32
 
 
 def run_ours(args, rank, world, local_rank):
-    import numpy as np
     import torch
 
     from paper_2301_04758_gb300 import build as vbuild
@@ -314,35 +385,41 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    wl = config_workload(WORKLOAD)
+    K, desc = BENCH_WORKLOADS[args.workload]
+    wl = config_workload(args.workload)
     om, w = wl["omega"], wl["weights"]
     E, n, D, p = wl["E"], wl["n"], wl["D"], wl["p"]
-    updates = E * n * D * K_ITER
+    updates = E * n * D * K
     mesh = Mesh(wl["nx"], wl["ny"], wl["mesh_order"], p, wl["alpha"])
     T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev).contiguous()
     st, ss, q = T(wl["sigma_t"]), T(wl["sigma_s"]), T(wl["source"])
     psi = torch.empty(D, E, n, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
+    outputs = ("phi", "J", "E", "Eb", "Jin")
+    mixed_kw = (dict(tol=-1.0, max_passes=MIXED_PASSES) if args.mixed_tol < 0
+                else dict(tol=args.mixed_tol))
 
     def step(precision, st_=None, ss_=None, q_=None):
-        phi, ps, dphi = mesh.source_iterate(st_ if st_ is not None else st, ss_ if ss_ is not None else ss,
-                                            om, w, K_ITER, source=q_ if q_ is not None else q,
-                                            precision=precision, psi=psi,
-                                            tol=args.mixed_tol if precision == "mixed" else 0.0)
-        out = mesh.moments(ps, om, w, outputs=("phi", "J", "E", "Eb", "Jin"))
-        return phi, out, dphi
+        st_ = st if st_ is None else st_
+        ss_ = ss if ss_ is None else ss_
+        q_ = q if q_ is None else q_
+        kw = mixed_kw if precision == "mixed" else {}
+        if K == 1:
+            ps = mesh.sweep(st_, ss_, om, w, source=q_, psi=psi, precision=precision, **kw)
+        else:
+            _, ps, _ = mesh.source_iterate(st_, ss_, om, w, K, source=q_, precision=precision, psi=psi, **kw)
+        return mesh.moments(ps, om, w, outputs=outputs)
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
-    def timed(precision, steps, profile=False):
+    def timed(precision, steps):
         for _ in range(args.warmup):
             step(precision)
         torch.cuda.synchronize()
         mesh.sync()
-        if profile:
-            mesh.profile(True)
+        mesh.profile(True)
         barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -353,26 +430,29 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         barrier()
         ms = e0.elapsed_time(e1)
-        prof = mesh.profile_read() if profile else None
-        if profile:
-            mesh.profile(False)
+        prof = mesh.profile_read()
+        mesh.profile(False)
         mesh.sync()
         return ms, prof, res
 
     clocks = Clocks(local_rank)
     clocks.start()
-    ms64, prof64, res64 = timed("fp64", args.steps, profile=True)
+    ms64, prof64, res64 = timed("fp64", args.steps)
     clk = clocks.stop()
+    res64 = {k: v.clone() for k, v in res64.items()}
+    psi64 = psi.clone() if K == 1 else None
     clocks2 = Clocks(local_rank)
     clocks2.start()
-    ms32, prof32, res32 = timed("mixed", args.steps, profile=True)
+    ms32, prof32, res32 = timed("mixed", args.steps)
     clk2 = clocks2.stop()
 
-    # errors of the mixed path against the FP64 path (same inputs)
+    # errors of the mixed path against the FP64 path (same inputs), each output separately
     def relerr(a, b):
         return float(torch.linalg.norm((a - b).flatten()) / torch.linalg.norm(b.flatten()))
-    mixed_err = {"phi": relerr(res32[1]["phi"], res64[1]["phi"]), "J": relerr(res32[1]["J"], res64[1]["J"]),
-                 "E": relerr(res32[1]["E"], res64[1]["E"]), "Eb": relerr(res32[1]["Eb"], res64[1]["Eb"])}
+    mixed_err = {k: relerr(res32[k], res64[k]) for k in ("phi", "J", "E", "Eb")}
+    if psi64 is not None:
+        mixed_err["psi"] = relerr(psi, psi64)
+    del psi64
 
     # end to end through the public API: pinned host inputs -> device, outputs -> host
     h_st = torch.tensor(wl["sigma_t"], dtype=torch.float64).pin_memory()
@@ -386,7 +466,7 @@ def run_ours(args, rank, world, local_rank):
         d_st.copy_(h_st, non_blocking=True)
         d_ss.copy_(h_ss, non_blocking=True)
         d_q.copy_(h_q, non_blocking=True)
-        phi, out, _ = step("fp64", d_st, d_ss, d_q)
+        out = step("fp64", d_st, d_ss, d_q)
         if outs_host is None:
             outs_host = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
         for k, v in out.items():
@@ -422,8 +502,9 @@ def run_ours(args, rank, world, local_rank):
         hbm_peak, hbm_src = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), HBM_MEASURED
     except (OSError, KeyError, ValueError):
         pass
-    roof, roofline, roof32, roofline32 = roofline_report(prof64, prof32, p, D, E, args.steps,
-                                                         hbm_peak, fp64_meas, hbm_src=hbm_src)
+    roof, roofline, roof32, roofline32 = roofline_report(
+        prof64, prof32, p, D, E, args.steps, K, hbm_peak, fp64_meas,
+        traffic_of=lambda k: ncu_traffic(k, args.workload), hbm_src=hbm_src)
     launches = sum(v[0] for v in prof64.values())
 
     line = {
@@ -431,14 +512,18 @@ def run_ours(args, rank, world, local_rank):
         "value": value, "unit": "angular-DOF updates/s", "n_gpus": world, "steps": steps,
         "warmup": args.warmup, "ms_per_step": ms64 / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "256x256 sine-curved Q3 mesh (alpha 0.05), DG Q2, S8 (40 dirs), "
-                               "seeded sigma_t/sigma_s (seed 2), q=1, vacuum, 10 source iterations + closures",
-                   "nx": 256, "ny": 256, "p": p, "mesh_order": 3, "directions": D,
-                   "source_iterations": K_ITER, "angular_dof_updates_per_step": updates,
-                   "l2": "inputs larger than L2 (factor records ~4 GB)",
+        "config": {"workload": desc, "name": args.workload,
+                   "nx": wl["nx"], "ny": wl["ny"], "p": p, "mesh_order": wl["mesh_order"], "directions": D,
+                   "transport_inversions_per_step": K, "angular_dof_updates_per_step": updates,
+                   "l2": "inputs larger than L2 (factor records %.0f GB)" % (
+                       E * D * bytes_factor(p, D) / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
-        "mixed": {"value": mixed_value, "ms_per_step": ms32 / steps, "dtype": "f32 solve + f64 defect correction",
-                  "defect_correction_rel_residual_target": args.mixed_tol,
+        "mixed": {"value": mixed_value, "ms_per_step": ms32 / steps,
+                  "speedup_vs_fp64": ms64 / ms32,
+                  "dtype": "f32 factorisation and sweeps + f64 defect correction",
+                  "defect_correction": (f"{MIXED_PASSES} passes (FP32 sweep, FP64 residual, FP32 "
+                                        "correction sweep)" if args.mixed_tol < 0 else
+                                        f"to ||r||/||b|| <= {args.mixed_tol}"),
                   "rel_err_vs_fp64": mixed_err, "rel_err_bound": MIXED_ERR_BOUND,
                   "within_bound": all(mixed_err[k] <= MIXED_ERR_BOUND for k in ("phi", "E")),
                   "clocks": clk2,
@@ -451,7 +536,6 @@ def run_ours(args, rank, world, local_rank):
         "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof64.items() if v[0]},
         "gpu_launches": launches,
         "clocks": clk,
-        "info": {"coupled_groups_and_levels": None},
     }
     _, info = mesh.sweep(st, ss, om, w, source=q, info=True, psi=psi)
     line["info"] = {"levels": info["levels"], "coupled_groups": info["coupled_groups"],
@@ -461,49 +545,149 @@ def run_ours(args, rank, world, local_rank):
 
 
 # ------------------------------------------------------------ oracle (CPU) arm
-def oracle_sample():
-    """Time the oracle on a bounded sample: one transport inversion for the first S8
-    direction on a 128 x 128 mesh built with the same recipe as the 256 x 256 workload.
-    Returns (updates/s, seconds, threads)."""
+# The oracle is timed on a bounded sample: an NX x NX mesh built with the workload's recipe
+# (same map, order, direction set and media recipe), one transport inversion for some of
+# its directions.  Worker processes are started with `spawn` and one BLAS / OpenMP thread
+# each, so `cores` is the number of processes that ran.
+_ORACLE = {}
+
+
+def _directions(workload):
+    from vef_inputs import WORKLOADS, level_symmetric
+    return level_symmetric(WORKLOADS[workload]["sn"])
+
+
+def _oracle_setup(workload, nx):
     import numpy as np
-    from oracle.transport import Discretization, sweep
-    from vef_inputs import level_symmetric, seeded_media
-    N, p = 128, 2
-    om, w = level_symmetric(8)
-    st, ss = seeded_media(N * N, 2)
-    disc = Discretization(N, N, 3, 0.05, p)
-    q = np.ones((N * N, (p + 1) ** 2))
+    from oracle.transport import Discretization
+    from vef_inputs import WORKLOADS, seeded_media
+    spec = WORKLOADS[workload]
+    om, w = _directions(workload)
+    E, n = nx * nx, (spec["p"] + 1) ** 2
+    st, ss = seeded_media(E, spec["media"][1])
+    disc = Discretization(nx, nx, spec["mesh_order"], spec["alpha"], spec["p"])
+    q = np.full((E, n), float(spec["source"]))
+    _ORACLE.update(disc=disc, om=om, w=w, st=st, ss=ss, q=q, n=n, E=E)
+    return True
+
+
+def _oracle_solve(dirs):
+    """One transport inversion of the sample for the directions `dirs`: (updates, seconds)."""
+    from oracle.transport import sweep
+    o = _ORACLE
     t = time.perf_counter()
-    sweep(disc, om[:1], w[:1], st, ss, source=q)
-    dt = time.perf_counter() - t
-    return N * N * (p + 1) ** 2 / dt, dt, 1
+    sweep(o["disc"], o["om"][dirs], o["w"][dirs], o["st"], o["ss"], source=o["q"])
+    return o["E"] * o["n"] * len(dirs), time.perf_counter() - t
 
 
-SAMPLE_DESC = ("oracle (FP64 NumPy/SciPy, global sparse direct solve) for 1 of the 40 S8 "
-               "directions on a 128x128 mesh with the 256x256 workload's recipe (sine alpha 0.05, "
-               "Q3 map, Q2, seed-2 media)")
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+class OraclePool:
+    """`cores` spawned worker processes, each holding the sample's discretisation."""
+
+    def __init__(self, workload, nx, cores):
+        import multiprocessing as mp
+        keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in keep:
+            os.environ[k] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(cores, initializer=_oracle_setup, initargs=(workload, nx))
+        finally:
+            for k, v in keep.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.cores = cores
+
+    def run(self, per_worker, D):
+        """Every worker solves `per_worker` directions (round robin over the set); returns
+        (updates, wall seconds)."""
+        jobs = [[(k * per_worker + j) % D for j in range(per_worker)] for k in range(self.cores)]
+        t = time.perf_counter()
+        res = self.pool.map(_oracle_solve, jobs, chunksize=1)
+        return sum(r[0] for r in res), time.perf_counter() - t
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def sample_desc(workload, nx, cores, per_worker):
+    K, _ = BENCH_WORKLOADS[workload]
+    from vef_inputs import WORKLOADS as W
+    spec = W[workload]
+    return (f"oracle (FP64 NumPy/SciPy, global sparse direct solve per direction) on a {nx}x{nx} mesh "
+            f"built with the {spec['nx']}x{spec['ny']} workload's recipe (sine alpha {spec['alpha']}, "
+            f"Q{spec['mesh_order']} map, DG Q{spec['p']}, S{spec['sn']}, seed-{spec['media'][1]} media, "
+            f"q=1, vacuum): {per_worker} direction(s) per process on {cores} process(es)")
+
+
+def cpu_baseline(workload, nx, per_worker=2):
+    """The oracle's rate on one core and on all host cores (bounded samples)."""
+    D = len(_directions(workload)[1])
+    all_cores = host_cores()
+    out = {"unit": "angular-DOF updates/s", "kind": "oracle", "host_cpu": _cpu_model(),
+           "nproc": os.cpu_count()}
+    for cores in (1, all_cores):
+        pool = OraclePool(workload, nx, cores)
+        try:
+            pool.run(1, D)                       # warm: imports and first solve
+            upd, sec = pool.run(per_worker, D)
+        finally:
+            pool.close()
+        out["1_core" if cores == 1 else "all_cores"] = {
+            "value": upd / sec, "cores": cores, "seconds": sec,
+            "sample": sample_desc(workload, nx, cores, per_worker)}
+    out.update(value=out["all_cores"]["value"], cores=all_cores, sample=out["all_cores"]["sample"])
+    return out
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm: rank 0 only; each step is one inversion of one
+    direction per process of the bounded sample, on every host core."""
     if rank != 0:
         return None
-    for _ in range(args.warmup):
-        pass   # the CPU oracle has no warm-up state; the sample below is timed per step
-    rates, secs = [], []
-    for _ in range(args.steps):
-        r, dt, cores = oracle_sample()
-        rates.append(r)
-        secs.append(dt)
+    D = len(_directions(args.workload)[1])
+    cores = host_cores()
+    pool = OraclePool(args.workload, args.cpu_sample, cores)
+    try:
+        for _ in range(max(1, args.warmup)):
+            pool.run(1, D)
+        rates, secs = [], []
+        for _ in range(args.steps):
+            upd, sec = pool.run(1, D)
+            rates.append(upd / sec)
+            secs.append(sec)
+    finally:
+        pool.close()
     value = statistics.median(rates)
+    desc = sample_desc(args.workload, args.cpu_sample, cores, 1)
     return {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "angular-DOF updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "256x256 sine-curved Q3 mesh (alpha 0.05), DG Q2, S8 (40 dirs), "
-                                   "seeded sigma_t/sigma_s (seed 2), q=1, vacuum, 10 source iterations + closures"},
-            "cpu_baseline": {"value": value, "unit": "angular-DOF updates/s", "cores": 1,
-                             "kind": "oracle", "sample": SAMPLE_DESC},
+            "config": {"workload": desc, "name": args.workload, "sample_nx": args.cpu_sample,
+                       "directions_per_step": cores},
+            "cpu_baseline": {"value": value, "unit": "angular-DOF updates/s", "cores": cores,
+                             "kind": "oracle", "sample": desc, "host_cpu": _cpu_model()},
             "e2e": {"value": value, "unit": "angular-DOF updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -520,47 +704,6 @@ def _cuda_time(fn, reps=1):
     e1.record(s)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps, out
-
-
-def suite_precision(args):
-    """512 x 512 sine mesh (alpha 0.05, Q3 map), DG Q3, S12 (84 directions), seed-3 media,
-    q = 1, vacuum: one transport inversion + closures, FP64 against mixed precision
-    (FP32 factorisation and sweeps inside FP64 defect correction)."""
-    import torch
-    from paper_2301_04758_gb300.api import Mesh
-    from vef_inputs import config_workload
-    wl = config_workload("sine512_q3_s12")
-    om, w = wl["omega"], wl["weights"]
-    E, n, D = wl["E"], wl["n"], wl["D"]
-    T = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda").contiguous()
-    st, ss, q = T(wl["sigma_t"]), T(wl["sigma_s"]), T(wl["source"])
-    mesh = Mesh(512, 512, 3, 3, 0.05)
-    psi = torch.empty(D, E, n, dtype=torch.float64, device="cuda")
-    res = {}
-    outs = {}
-    for prec in ("fp64", "mixed"):
-        def step():
-            ps = mesh.sweep(st, ss, om, w, source=q, psi=psi, precision=prec,
-                            tol=args.mixed_tol if prec == "mixed" else 0.0)
-            return mesh.moments(ps, om, w, outputs=("phi", "J", "E", "Eb"))
-        step()
-        mesh.profile(True)
-        ms, out = _cuda_time(step, reps=max(1, args.steps))
-        prof = mesh.profile_read()
-        mesh.profile(False)
-        mesh.sync()
-        outs[prec] = {k: v.clone() for k, v in out.items()}
-        outs[prec]["psi"] = psi.clone() if prec == "fp64" else psi
-        res[prec] = {"ms_per_step": ms, "angular_dof_updates_per_s": E * n * D / (ms * 1e-3),
-                     "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items() if v[0]}}
-    err = {k: float(torch.linalg.norm((outs["mixed"][k] - outs["fp64"][k]).flatten())
-                    / torch.linalg.norm(outs["fp64"][k].flatten())) for k in ("psi", "phi", "J", "E", "Eb")}
-    _, info = mesh.sweep(st, ss, om, w, source=q, psi=psi, info=True)
-    return {"suite": "precision", "workload": "512x512 sine-curved Q3 mesh, DG Q3, S12 (84 dirs), seed-3 media, "
-            "q=1, vacuum; one sweep + closures", "fp64": res["fp64"], "mixed": res["mixed"],
-            "mixed_rel_err_vs_fp64": err, "mixed_speedup": res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"],
-            "defect_correction_rel_residual_target": args.mixed_tol,
-            "levels": info["levels"], "coupled_groups": info["coupled_groups"]}
 
 
 def suite_batch(args):
@@ -661,9 +804,9 @@ def suite_adjoint(args):
 
 def sweep_only(args):
     """Small driver for ncu captures: NX x NX sine mesh (alpha 0.05, Q3 map), DG order
-    --order (default 2), S_N --sn (default 8), seed-2 media, q = 1; runs --steps sweeps
-    (each with its factorisation) in --precision, with the apply --apply, through the public
-    API."""
+    --order (default 2), S_N --sn (default 8), media of seed --seed (default 2), q = 1; runs
+    --steps sweeps (each with its factorisation) in --precision (mixed: the benchmark's fixed
+    passes), with the apply --apply, through the public API."""
     import torch
 
     from paper_2301_04758_gb300 import build as vbuild
@@ -673,14 +816,15 @@ def sweep_only(args):
     N, p = args.sweep_only, args.order
     n = (p + 1) ** 2
     om, w = level_symmetric(args.sn)
-    st, ss = seeded_media(N * N, 2)
+    st, ss = seeded_media(N * N, args.seed)
     T = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda").contiguous()
     mesh = Mesh(N, N, 3, p, 0.05)
     q = torch.ones(N * N, n, dtype=torch.float64, device="cuda")
     psi = torch.empty(len(w), N * N, n, dtype=torch.float64, device="cuda")
+    kw = dict(tol=-1.0, max_passes=MIXED_PASSES) if args.precision == "mixed" else {}
     for _ in range(args.steps):
         mesh.sweep(T(st), T(ss), om, w, source=q, psi=psi, precision=args.precision,
-                   apply=args.apply)
+                   apply=args.apply, **kw)
     torch.cuda.synchronize()
     mesh.sync()
 
@@ -724,7 +868,7 @@ def main():
     if args.suite:
         from paper_2301_04758_gb300 import build as vbuild
         vbuild.build()
-        fn = {"precision": suite_precision, "batch": suite_batch, "adjoint": suite_adjoint}[args.suite]
+        fn = {"batch": suite_batch, "adjoint": suite_adjoint}[args.suite]
         print(json.dumps(fn(args)))
         return
     rank = int(os.environ.get("RANK", "0"))
@@ -742,9 +886,7 @@ def main():
     line = run_ours(args, rank, world, local_rank)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
-            r, dt, cores = oracle_sample()
-            line["cpu_baseline"] = {"value": r, "unit": "angular-DOF updates/s", "cores": cores,
-                                    "kind": "oracle", "sample": SAMPLE_DESC, "seconds": dt}
+            line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample)
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

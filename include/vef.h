@@ -84,16 +84,30 @@ enum {
   VEF_SWEEP_CLUSTER = 2,    /* sweep each direction (forward or adjoint) with a
                                thread-block cluster, as the batched sweep does, instead of
                                one CTA */
-  VEF_APPLY_SEPARATE = 4    /* compute y = A^{-1} b by a launch of its own before the
+  VEF_APPLY_SEPARATE = 4,   /* compute y = A^{-1} b by a launch of its own before the
                                single-CTA sweep; by default the SMs the directions leave
                                free do it inside the sweep launch, which is then a
                                cooperative launch sized from the device's SM count (a
                                context limited to fewer SMs, e.g. under MPS, should set
                                this flag: the driver refuses a cooperative grid that
                                does not fit, and the call returns VEF_ERR_CUDA) */
+  VEF_PIVOT_ALWAYS = 8      /* refactorise every (element, direction) system with partial
+                               pivoting, as the library does by itself only for the systems
+                               whose unpivoted elimination meets a small pivot (see
+                               VEF_PIVOT_FLOOR_LOG2_FP64); slow, meant for testing */
 };
 
 typedef struct vef_mesh_s* vef_mesh;
+
+/* Pivot guard of the element solves.  Each (element, direction) system is inverted by
+ * Gauss-Jordan elimination without pivoting; a system whose pivot at some step is zero, not
+ * finite, or below 2^VEF_PIVOT_FLOOR_LOG2_FP64 (FP64 solves) / 2^VEF_PIVOT_FLOOR_LOG2_FP32
+ * (FP32 solves) times the largest entry of that row of the assembled matrix is inverted
+ * again with partial pivoting.  vef_info.pivoted_tasks reports how many were.  (Over the
+ * level-symmetric sets S4..S16, p = 1..4, void to optically thick elements and sine-curved
+ * meshes up to alpha = 0.1 the smallest such ratio is about 0.1.) */
+#define VEF_PIVOT_FLOOR_LOG2_FP64 (-33)
+#define VEF_PIVOT_FLOOR_LOG2_FP32 (-13)
 
 /* Environment: VEF_TRACE_SLOTS=<k>, read when a schedule is built (the first sweep of a
  * mesh with a given direction set), caps the shared-memory trace slots of the single-CTA
@@ -104,16 +118,27 @@ typedef struct vef_mesh_s* vef_mesh;
 typedef struct {
   int precision;     /* VEF_FP64 (default): FP64 assembly and solves.
                         VEF_MIXED: FP32 assembly and solves inside an FP64
-                        defect-correction loop r = b - L psi (FP64), psi += L32^{-1} r. */
+                        defect-correction loop r = b - L psi (FP64), psi += L32^{-1} r.
+                        vef_sweep forms r matrix-free from the element's M, Gx, Gy and
+                        its face terms; vef_source_iterate stores the FP64 element
+                        systems once and reuses them for the residuals of its K
+                        inversions. */
   double tol;        /* relative tolerance: inner coupled-group iteration (FP64: 1e-15) and
-                        defect correction ||r||_2 / ||b||_2 (mixed: 1e-13) */
+                        defect correction ||r||_2 / ||b||_2 (mixed: 1e-13).
+                        tol < 0 with VEF_MIXED: a fixed number of passes instead, exactly
+                        max_passes sweeps (default 2) with an FP64 residual between
+                        consecutive ones and none after the last, and no host
+                        synchronisation inside the call; vef_info.rel_residual then
+                        reports the residual the last correction started from */
   int max_passes;    /* cap on defect-correction passes (default 8) and, x4, on inner
                         coupled-group iterations */
   int tile_override; /* 0 = library choice; else 100 * (CTAs per direction cluster, 1..16)
                         + (warps per CTA, 1..16) of the cluster sweep kernel (implies
                         VEF_SWEEP_CLUSTER) */
-  int flags;         /* bit set of VEF_GROUPS_ITERATIVE, VEF_SWEEP_CLUSTER (default 0:
-                        direct group solves, one CTA per direction) */
+  int flags;         /* bit set of VEF_GROUPS_ITERATIVE, VEF_SWEEP_CLUSTER,
+                        VEF_APPLY_SEPARATE, VEF_PIVOT_ALWAYS (default 0: direct group
+                        solves, one CTA per direction, fused apply, pivoting only where
+                        the guard asks for it) */
 } vef_opts;
 
 /* Filled by calls given a non-NULL pointer (those calls synchronise `stream`). */
@@ -126,6 +151,8 @@ typedef struct {
                                  (0 when every group was solved directly) */
   int timed_out;              /* 1 if a bounded device-side wait gave up */
   int levels;                 /* dependency levels of the schedule (critical path length) */
+  long long pivoted_tasks;    /* element systems of the last factorisation inverted with
+                                 partial pivoting (see VEF_PIVOT_FLOOR_LOG2_FP64) */
 } vef_info;
 
 /* Mesh description returned by vef_mesh_query. */
@@ -253,7 +280,8 @@ enum {
   VEF_K_SOURCE = 4,   /* direction-independent right-hand side and scalar-flux updates */
   VEF_K_MOMENTS = 5,  /* moments, Eddington tensor, boundary factor */
   VEF_K_ADJOINT = 6,  /* adjoint sweep */
-  VEF_K_COUNT = 7
+  VEF_K_GROUP = 7,    /* trace systems of the coupled element groups (after VEF_K_FACTOR) */
+  VEF_K_COUNT = 8
 };
 typedef struct {
   long long launches;  /* kernel launches since the counters were last reset */
@@ -302,6 +330,27 @@ vef_status vef_schedule_host(int nx, int ny, int p, const double* nds, const dou
  * polls in 1..2^24, else VEF_ERR_INVALID_ARG (checked before any CUDA call).  Allocates and
  * frees 8 bytes of device memory. */
 vef_status vef_wait_selftest(int kind, int satisfied, long long polls, void* stream);
+
+/* Device status bits: what a kernel records when a bounded wait runs out, an iteration
+ * hits its cap, a closure denominator is not positive or an element system is singular;
+ * the next synchronising call maps them to VEF_ERR_TIMEOUT, VEF_ERR_NOT_CONVERGED,
+ * VEF_ERR_NONPOSITIVE_DENOM and VEF_ERR_NOT_CONVERGED. */
+enum {
+  VEF_STATUS_TIMEOUT = 1,
+  VEF_STATUS_NOT_CONVERGED = 2,
+  VEF_STATUS_NONPOSITIVE = 4,
+  VEF_STATUS_SINGULAR = 8
+};
+
+/* Failure-detection test hook (the paper has no counterpart): ORs `bits` (VEF_STATUS_*)
+ * into the handle's device status word on `stream`, as a device-side failure would.  Kernels
+ * launched after it see the bits: a staging wait of the sweeps finding VEF_STATUS_TIMEOUT
+ * set stops polling at once, and its warp stops reading staged data (the call's results are
+ * then undefined), so a call made while a timeout is recorded and not yet collected returns
+ * quickly; the next synchronising call returns the error and clears the word.
+ * Errors: VEF_ERR_INVALID_ARG (NULL mesh, bits empty or outside the four values, another
+ * device). */
+vef_status vef_mesh_inject_status(vef_mesh mesh, unsigned int bits, void* stream);
 
 /* Eddington tensor without device allocation (the paper has no counterpart: this is a
  * library interface).  Same result as vef_moments with only Eten requested:

@@ -24,16 +24,21 @@ VEF_MIXED = 1
 VEF_GROUPS_ITERATIVE = 1
 VEF_SWEEP_CLUSTER = 2
 VEF_APPLY_SEPARATE = 4
+VEF_PIVOT_ALWAYS = 8
+VEF_STATUS_TIMEOUT = 1
+VEF_STATUS_NOT_CONVERGED = 2
+VEF_STATUS_NONPOSITIVE = 4
+VEF_STATUS_SINGULAR = 8
 
 # every symbol include/vef.h declares
 EXPORTS = ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sync", "vef_sweep",
            "vef_moments", "vef_source_iterate", "vef_adjoint_sweep", "vef_profile",
            "vef_profile_read", "vef_measure_fma_peak", "vef_wait_selftest", "vef_eddington_noalloc",
            "vef_batch_create", "vef_batch_destroy", "vef_batch_sweep", "vef_batch_tune",
-           "vef_region_weights", "vef_schedule_host",
+           "vef_region_weights", "vef_schedule_host", "vef_mesh_inject_status",
            "vef_status_string", "vef_last_error")
 
-KERNEL_CLASSES = ("geometry", "factor", "sweep", "residual", "source", "moments", "adjoint")
+KERNEL_CLASSES = ("geometry", "factor", "sweep", "residual", "source", "moments", "adjoint", "group")
 
 
 class VefOpts(ctypes.Structure):
@@ -46,7 +51,7 @@ class VefInfo(ctypes.Structure):
     _fields_ = [("passes", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("coupled_groups", ctypes.c_longlong), ("lagged_face_points", ctypes.c_longlong),
                 ("max_inner_iterations", ctypes.c_int), ("timed_out", ctypes.c_int),
-                ("levels", ctypes.c_int)]
+                ("levels", ctypes.c_int), ("pivoted_tasks", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -99,6 +104,7 @@ def _declare(lib):
                                     ctypes.POINTER(VefInfo), P]
     lib.vef_batch_tune.argtypes = [P, P, ctypes.POINTER(ctypes.c_int)]
     lib.vef_region_weights.argtypes = [P, D, D, D, D, P, P]
+    lib.vef_mesh_inject_status.argtypes = [P, ctypes.c_uint, P]
     for name in ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sync",
                  "vef_sweep", "vef_moments", "vef_source_iterate", "vef_adjoint_sweep",
                  "vef_profile", "vef_profile_read", "vef_measure_fma_peak", "vef_wait_selftest",

@@ -32,7 +32,8 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _opts(precision="fp64", tol=0.0, max_passes=0, tile=0, groups="direct", kernel="cta", apply="fused"):
+def _opts(precision="fp64", tol=0.0, max_passes=0, tile=0, groups="direct", kernel="cta", apply="fused",
+          pivot="guard"):
     o = _lib.VefOpts()
     o.precision = {"fp64": _lib.VEF_FP64, "mixed": _lib.VEF_MIXED}[precision]
     o.tol = float(tol)
@@ -41,6 +42,7 @@ def _opts(precision="fp64", tol=0.0, max_passes=0, tile=0, groups="direct", kern
     o.flags = {"direct": 0, "iterative": _lib.VEF_GROUPS_ITERATIVE}[groups]
     o.flags |= {"cta": 0, "cluster": _lib.VEF_SWEEP_CLUSTER}[kernel]
     o.flags |= {"fused": 0, "separate": _lib.VEF_APPLY_SEPARATE}[apply]
+    o.flags |= {"guard": 0, "always": _lib.VEF_PIVOT_ALWAYS}[pivot]
     return o
 
 
@@ -103,7 +105,7 @@ class Mesh:
     # ---------------------------------------------------------------- transport
     def sweep(self, sigma_t, sigma_s, omega, weights, phi_in=None, source=None, inflow=None,
               precision="fp64", tol=0.0, max_passes=0, tile=0, groups="direct", psi=None, info=False,
-              stream=None, kernel="cta", apply="fused"):
+              stream=None, kernel="cta", apply="fused", pivot="guard"):
         """psi [D][E][n] = L^{-1} b for every direction (see vef_sweep in include/vef.h).
 
         groups: "direct" (coupled element groups through their trace system) or
@@ -112,7 +114,10 @@ class Mesh:
         cluster per direction; a nonzero tile also selects it).
         apply: "fused" (y = A^{-1} b computed inside the sweep launch on the SMs the
         directions leave free, when enough are free and the stream is not being captured)
-        or "separate" (its own launch before the sweep); both give the same psi."""
+        or "separate" (its own launch before the sweep); both give the same psi.
+        pivot: "guard" (element systems eliminated without pivoting, those meeting a small
+        pivot redone with partial pivoting) or "always" (every system with partial
+        pivoting; slow, for tests)."""
         om, omp = _host(omega)
         w, wp = _host(weights)
         D = len(w)
@@ -120,7 +125,7 @@ class Mesh:
         if psi is None:
             psi = self._empty(D, self.E, self.n)
         inf = _lib.VefInfo() if info else None
-        o = _opts(precision, tol, max_passes, tile, groups, kernel, apply)
+        o = _opts(precision, tol, max_passes, tile, groups, kernel, apply, pivot)
         st = self.lib.vef_sweep(self.handle, _ptr(sigma_t), _ptr(sigma_s), _ptr(phi_in), _ptr(source),
                                 aniso, _ptr(inflow), omp, wp, D, ctypes.byref(o), _ptr(psi),
                                 ctypes.byref(inf) if info else None, _stream(stream))

@@ -450,11 +450,21 @@ __global__ void __maxnreg__(128) adjoint_cta_kernel(AdjArgs a) {
       load_win(kt - 32, lb1, le1, lg1, lm1);
     }
   };
+  // producer waits (a buffer released, copies drained) do not stop on the status bit
   auto bounded_wait = [&](uint64_t* bar, unsigned parity) {
     uint32_t n = 0;
     while (!mbar_try_wait(bar, parity) && ++n < kAdjWaitIters) {
     }
     if (n >= kAdjWaitIters) atomicOr(a.status, kDevTimeout);
+  };
+  // consumer waits for a staged chunk give up early on the status bit; a warp whose wait
+  // gave up never reads a staged chunk again but still releases every buffer and reaches
+  // every level barrier
+  bool failed = false;
+  auto data_wait = [&](uint64_t* bar, unsigned parity) {
+    const bool ok = mbar_wait_data(bar, parity, kAdjWaitIters, a.status);
+    if (!ok) atomicOr(a.status, kDevTimeout);
+    failed = failed || __any_sync(0xffffffffu, !ok);
   };
   auto next = [&](unsigned& b, unsigned& par) {
     if (++b == NB) { b = 0; par ^= 1u; }
@@ -512,11 +522,11 @@ __global__ void __maxnreg__(128) adjoint_cta_kernel(AdjArgs a) {
       const int nsingle = sg - sb;
       for (int c0 = 0; c0 < nsingle; c0 += CK) {
         const unsigned char* rb = ring + (size_t)rb_i * Sh::kRound;
-        bounded_wait(&full[rb_i], rpar);
+        data_wait(&full[rb_i], rpar);
         const int cend = min(CK, nsingle - c0);
         for (int tk0 = 0; tk0 < cend; tk0 += CH) {   // the chunk's rounds
           const int tk = tk0 + task;
-          const bool act = lane_ok && tk < cend;
+          const bool act = !failed && lane_ok && tk < cend;
           double r = 0.0;
           uint4 ts = make_uint4(0u, 0u, 0u, 0u);
           const char* rs = (const char*)rb;
@@ -564,7 +574,7 @@ __global__ void __maxnreg__(128) adjoint_cta_kernel(AdjArgs a) {
                 scratch[((s_lane * 2 + sl) * Q + t) * N + i] = W[sl * L::kSlot + t * N + i] * r;
           }
           __syncwarp();
-          for (int q = lane; q < SPC * 2 * Q; q += 32) {
+          for (int q = lane; !failed && q < SPC * 2 * Q; q += 32) {
             const int s = q / (2 * Q), sl = (q / Q) % 2, t = q % Q;
             const int tks = tk0 + warp * SPC + s;
             if (tks >= cend) continue;

@@ -53,6 +53,9 @@ enum : unsigned int {
   kDevNonpositive = 4u,
   kDevSingular = 8u,
 };
+// word of the device status array holding the number of tasks the last factorisation
+// refactorised with partial pivoting
+constexpr int kStatusPivoted = 6;
 
 // Coupled element groups are solved directly through a trace system precomputed by the
 // factorisation (schedule.cpp, factor_impl.cuh) when they have at most this many members
@@ -108,6 +111,7 @@ struct Schedule {
   void* rec64 = nullptr;
   void* rec32 = nullptr;
   void* a64 = nullptr;         // FP64 element matrices + inflow couplings (mixed residual)
+  unsigned int* pivot_list = nullptr;  // [members] tasks the pivot guard sent to the fallback
   uint32_t* adj_link = nullptr;  // [members][4] downstream receiver across each face:
                                  // (receiver member << 2) | its W slot, or ~0 (adjoint)
   // Shared-memory trace slots of the single-CTA sweep, per member four 16-bit slot ids:
@@ -181,8 +185,14 @@ class KTimer {
 
 vef_status ensure_buffer(void** ptr, size_t* cap, size_t bytes);
 vef_status mesh_float_copies(Mesh* mesh, cudaStream_t stream);
+// Local factorisation of every (element, direction) system in `precision`.  With
+// VEF_MIXED and store_systems, also the FP64 element systems the stored-form residual of
+// the defect correction reads (S->a64); without, the residual is formed matrix-free.
+// Tasks whose unpivoted elimination meets a small pivot are refactorised with partial
+// pivoting (all tasks when force_pivot != 0); their count lands in
+// dev_status[kStatusPivoted].
 vef_status factor_records(Mesh* mesh, Schedule* S, const double* sigma_t, int precision,
-                          cudaStream_t stream);
+                          bool store_systems, int force_pivot, cudaStream_t stream);
 Schedule* get_schedule(Mesh* mesh, const double* omega, const double* weights, int D,
                        cudaStream_t stream, vef_status* st);
 

@@ -116,6 +116,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
+// Bounded wait for staged data: polls the mbarrier phase up to `iters` times and gives up
+// early, every 16 polls, once `status` carries the timeout bit (another wait ran out, or
+// the call started with an uncollected timeout).  Returns whether the phase completed; a
+// consumer that gets false must not use the staged buffer (it may never have been filled).
+__device__ __forceinline__ bool mbar_wait_data(uint64_t* bar, unsigned parity, uint32_t iters,
+                                               const unsigned int* status) {
+  uint32_t n = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if (++n >= iters) return false;
+    if ((n & 15u) == 0 && (*(const volatile unsigned int*)status & kDevTimeout)) return false;
+  }
+  return true;
+}
 // 1D bulk copy global -> this CTA's shared memory, completion counted on bar (bytes and
 // both addresses must be multiples of 16)
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {

@@ -104,3 +104,24 @@ extern "C" vef_status vef_measure_fma_peak(int precision, double* flops_per_s) {
   vef::set_last_error("precision must be VEF_FP64 or VEF_MIXED");
   return VEF_ERR_INVALID_ARG;
 }
+
+// Failure-detection test hook: OR status bits into a mesh handle's device status word from a
+// one-thread kernel on `stream`, as a device-side wait that ran out would.
+namespace vef {
+__global__ void inject_status_kernel(unsigned int* status, unsigned int bits) { atomicOr(status, bits); }
+}  // namespace vef
+
+static_assert(VEF_STATUS_TIMEOUT == vef::kDevTimeout && VEF_STATUS_NOT_CONVERGED == vef::kDevNotConverged &&
+                  VEF_STATUS_NONPOSITIVE == vef::kDevNonpositive && VEF_STATUS_SINGULAR == vef::kDevSingular,
+              "public status bits match the device status word");
+
+extern "C" vef_status vef_mesh_inject_status(vef_mesh mesh, unsigned int bits, void* stream) {
+  if (!mesh) { vef::set_last_error("mesh is NULL"); return VEF_ERR_INVALID_ARG; }
+  if (bits == 0 || (bits & ~0xfu)) { vef::set_last_error("bits must be a non-empty set of VEF_STATUS_* values"); return VEF_ERR_INVALID_ARG; }
+  int dev = 0;
+  VEF_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != mesh->impl.device) { vef::set_last_error("mesh belongs to another device"); return VEF_ERR_INVALID_ARG; }
+  vef::inject_status_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(mesh->impl.dev_status, bits);
+  VEF_CUDA_TRY(cudaGetLastError());
+  return VEF_OK;
+}

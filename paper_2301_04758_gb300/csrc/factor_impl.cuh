@@ -40,18 +40,46 @@ inline FaceLL<T> make_facell(const Tab1D& t) {
   return f;
 }
 
+// ------------------------------------------------------------------- pivot guard
+// The element solves eliminate without pivoting.  A task whose pivot at some step falls
+// below 2^VEF_PIVOT_FLOOR_LOG2_* times the largest entry of that row of the assembled
+// matrix (or is zero or not finite) is appended to a list and refactorised with partial
+// pivoting by factor_pivot_kernel, which overwrites its record.  Magnitudes are compared
+// through the high word of their bit pattern with the sign cleared (exponent and leading
+// mantissa bits), so the guard costs integer operations only.
+template <typename T> struct PivotFloor;
+template <> struct PivotFloor<double> {
+  static __device__ __forceinline__ int mag(double x) { return __double2hiint(x) & 0x7fffffff; }
+  static constexpr int kShift = (-VEF_PIVOT_FLOOR_LOG2_FP64) << 20;
+};
+template <> struct PivotFloor<float> {
+  static __device__ __forceinline__ int mag(float x) { return __float_as_int(x) & 0x7fffffff; }
+  static constexpr int kShift = (-VEF_PIVOT_FLOOR_LOG2_FP32) << 23;
+};
+// pivot too small against the row scale (given as mag() of the row's largest entry)
+template <typename T>
+__device__ __forceinline__ bool small_pivot(T piv, int scale_mag) {
+  return !(fabs(piv) > tiny_pivot<T>()) || PivotFloor<T>::mag(piv) < scale_mag - PivotFloor<T>::kShift;
+}
+__device__ __forceinline__ void pivot_list_append(unsigned int* count, unsigned int* list, long long m) {
+  const unsigned idx = atomicAdd(count, 1u);
+  list[idx] = (unsigned)m;   // at most one entry per task: the list holds every task
+}
+
 // ------------------------------------------------------------------- factorisation
-template <int P, typename T>
-__global__ void __launch_bounds__(128)
-factor_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t* __restrict__ finfo,
-              const double* __restrict__ omega, const double* __restrict__ sigma_t,
-              const T* __restrict__ Mm, const T* __restrict__ Gxm, const T* __restrict__ Gym,
-              const T* __restrict__ nds, FaceTab<T> ft, FaceLL<T> fll, int nx, int ny, long long E,
-              T* __restrict__ rec, unsigned int* status) {
+// One (element, direction) task in one thread: assemble A and the inflow couplings,
+// invert A in place by Gauss-Jordan (without pivoting and with the guard above, or with
+// partial pivoting for the fallback), write the record.  Returns whether the guard fired.
+template <int P, typename T, bool PIVOTED>
+__device__ __forceinline__ bool factor_task(long long m, long long nmem, const uint32_t* __restrict__ code,
+                                            const uint16_t* __restrict__ finfo, const double* __restrict__ omega,
+                                            const double* __restrict__ sigma_t, const T* __restrict__ Mm,
+                                            const T* __restrict__ Gxm, const T* __restrict__ Gym,
+                                            const T* __restrict__ nds, const FaceTab<T>& ft, const FaceLL<T>& fll,
+                                            int nx, int ny, long long E, T* __restrict__ rec,
+                                            unsigned int* status) {
   constexpr int Q = P + 1, N = Q * Q, NQ = P + 2;
   using L = Rec<P, T>;
-  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (m >= nmem) return;
   const uint32_t c = code[m];
   const int d = (int)(c >> 22), e = (int)(c & 0x3fffffu);
   const T mu = (T)omega[2 * d], eta = (T)omega[2 * d + 1];
@@ -102,26 +130,86 @@ factor_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t*
         Cin[f][a][b] = vi;
       }
   }
-  // in-place Gauss-Jordan inversion (no pivoting: the upwind element matrix has a
-  // positive definite symmetric part, sigma_t M + (1/2) sum |Omega.n| face mass)
-  constexpr int KU = P <= 2 ? N : 1;
-#pragma unroll KU
-  for (int k = 0; k < N; ++k) {
-    const T piv = A[k * N + k];
-    if (!(fabs(piv) > tiny_pivot<T>())) atomicOr(status, kDevSingular);
-    const T inv = (T)1 / piv;
-#pragma unroll
-    for (int j = 0; j < N; ++j)
-      if (j != k) A[k * N + j] *= inv;
-    A[k * N + k] = inv;
+  bool bad = false;
+  if constexpr (!PIVOTED) {
+    // in-place Gauss-Jordan inversion without pivoting: the upwind element matrices keep
+    // their pivots well away from zero (a scan over the level-symmetric sets, p = 1..4,
+    // void to optically thick and strongly curved elements finds the smallest pivot at
+    // 0.1 of its row's largest entry); the guard hands any other task to the fallback
+    int scl[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      if (i == k) continue;
-      const T fct = A[i * N + k];
+      int mx = 0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) mx = max(mx, PivotFloor<T>::mag(A[i * N + j]));
+      scl[i] = mx;
+    }
+    constexpr int KU = P <= 2 ? N : 1;
+#pragma unroll KU
+    for (int k = 0; k < N; ++k) {
+      const T piv = A[k * N + k];
+      bad = bad || small_pivot<T>(piv, scl[k]);
+      const T inv = (T)1 / piv;
 #pragma unroll
       for (int j = 0; j < N; ++j)
-        if (j != k) A[i * N + j] -= fct * A[k * N + j];
-      A[i * N + k] = -fct * inv;
+        if (j != k) A[k * N + j] *= inv;
+      A[k * N + k] = inv;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        if (i == k) continue;
+        const T fct = A[i * N + k];
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+          if (j != k) A[i * N + j] -= fct * A[k * N + j];
+        A[i * N + k] = -fct * inv;
+      }
+    }
+  } else {
+    // Gauss-Jordan with partial pivoting: rows interchanged at each step, the
+    // interchanges undone as column interchanges (last first) at the end
+    int perm[N];
+#pragma unroll 1
+    for (int k = 0; k < N; ++k) {
+      int r = k;
+      T best = fabs(A[k * N + k]);
+#pragma unroll 1
+      for (int i = k + 1; i < N; ++i)
+        if (fabs(A[i * N + k]) > best) { best = fabs(A[i * N + k]); r = i; }
+      perm[k] = r;
+      if (!(best > tiny_pivot<T>())) atomicOr(status, kDevSingular);
+      if (r != k) {
+#pragma unroll 1
+        for (int j = 0; j < N; ++j) {
+          const T t = A[k * N + j];
+          A[k * N + j] = A[r * N + j];
+          A[r * N + j] = t;
+        }
+      }
+      const T inv = (T)1 / A[k * N + k];
+#pragma unroll 1
+      for (int j = 0; j < N; ++j)
+        if (j != k) A[k * N + j] *= inv;
+      A[k * N + k] = inv;
+#pragma unroll 1
+      for (int i = 0; i < N; ++i) {
+        if (i == k) continue;
+        const T fct = A[i * N + k];
+#pragma unroll 1
+        for (int j = 0; j < N; ++j)
+          if (j != k) A[i * N + j] -= fct * A[k * N + j];
+        A[i * N + k] = -fct * inv;
+      }
+    }
+#pragma unroll 1
+    for (int k = N - 1; k >= 0; --k) {
+      const int r = perm[k];
+      if (r == k) continue;
+#pragma unroll 1
+      for (int i = 0; i < N; ++i) {
+        const T t = A[i * N + k];
+        A[i * N + k] = A[i * N + r];
+        A[i * N + r] = t;
+      }
     }
   }
   char* out = L::s_at(rec, m);
@@ -150,6 +238,41 @@ factor_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t*
       }
   }
   *reinterpret_cast<uint4*>(out) = make_uint4((unsigned)e, (unsigned)bits, faces, 0u);
+  return bad;
+}
+
+template <int P, typename T>
+__global__ void __launch_bounds__(128)
+factor_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t* __restrict__ finfo,
+              const double* __restrict__ omega, const double* __restrict__ sigma_t,
+              const T* __restrict__ Mm, const T* __restrict__ Gxm, const T* __restrict__ Gym,
+              const T* __restrict__ nds, FaceTab<T> ft, FaceLL<T> fll, int nx, int ny, long long E,
+              T* __restrict__ rec, unsigned int* status, unsigned int* piv_count, unsigned int* piv_list,
+              int force_pivot) {
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (m >= nmem) return;
+  const bool bad = factor_task<P, T, false>(m, nmem, code, finfo, omega, sigma_t, Mm, Gxm, Gym, nds, ft, fll,
+                                            nx, ny, E, rec, status);
+  if (bad || force_pivot) pivot_list_append(piv_count, piv_list, m);
+}
+
+// Fallback for the tasks the guard listed: the same assembly, Gauss-Jordan with partial
+// pivoting, the record rewritten.  Grid-stride over the list (its length is read on the
+// device, so the launch needs no host synchronisation); whole matrices per thread live in
+// local memory, which is acceptable for the few tasks that come here.
+template <int P, typename T>
+__global__ void __launch_bounds__(128)
+factor_pivot_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t* __restrict__ finfo,
+                    const double* __restrict__ omega, const double* __restrict__ sigma_t,
+                    const T* __restrict__ Mm, const T* __restrict__ Gxm, const T* __restrict__ Gym,
+                    const T* __restrict__ nds, FaceTab<T> ft, FaceLL<T> fll, int nx, int ny, long long E,
+                    T* __restrict__ rec, unsigned int* status, const unsigned int* piv_count,
+                    const unsigned int* __restrict__ piv_list) {
+  const long long cnt = (long long)*piv_count;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < cnt && t < nmem;
+       t += (long long)gridDim.x * blockDim.x)
+    factor_task<P, T, true>((long long)piv_list[t], nmem, code, finfo, omega, sigma_t, Mm, Gxm, Gym, nds, ft,
+                            fll, nx, ny, E, rec, status);
 }
 
 // Element-major factorisation (used for p >= 3, where a whole element matrix per thread
@@ -172,7 +295,8 @@ factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const 
                    const double* __restrict__ omega, const double* __restrict__ sigma_t,
                    const T* __restrict__ Mm, const T* __restrict__ Gxm, const T* __restrict__ Gym,
                    const T* __restrict__ nds, FaceTab<T> ft, int nx, int ny, long long nmem,
-                   T* __restrict__ rec, unsigned int* status) {
+                   T* __restrict__ rec, unsigned int* status, unsigned int* piv_count,
+                   unsigned int* piv_list, int force_pivot) {
   constexpr int Q = P + 1, N = Q * Q, NQ = P + 2;
   constexpr int RPL = ElemShape<P>::RPL, LPU = ElemShape<P>::LPU, UPW = 32 / LPU;
   constexpr int LD = N + 1;                  // padded shared-memory row stride
@@ -245,14 +369,25 @@ factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const 
         }
       }
     }
-    // in-place Gauss-Jordan over the task's LPU lanes
+    // row scales of the owned rows for the pivot guard (integer operations only)
+    int scl[RPL];
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+      int mx = 0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) mx = max(mx, PivotFloor<T>::mag(row[r][j]));
+      scl[r] = mx;
+    }
+    bool bad = false;
+    // in-place Gauss-Jordan over the task's LPU lanes (no pivoting; the owner of row k
+    // checks its pivot against the row's scale)
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       const int owner = k % LPU, slot = k / LPU;
       T pr[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) pr[j] = __shfl_sync(FULL, row[slot][j], (base + owner) & 31);
-      if (valid && li == 0 && !(fabs(pr[k]) > tiny_pivot<T>())) atomicOr(status, kDevSingular);
+      if (li == owner) bad = bad || small_pivot<T>(pr[k], scl[slot]);
       const T inv = (T)1 / pr[k];
 #pragma unroll
       for (int r = 0; r < RPL; ++r) {
@@ -331,6 +466,9 @@ factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const 
       }
     }
     if (valid && li == 0) *reinterpret_cast<uint4*>(out) = make_uint4((unsigned)e, (unsigned)bits, faces, 0u);
+    // a task any of whose lanes saw a small pivot goes to the pivoted fallback
+    const unsigned bal = __ballot_sync(FULL, bad || force_pivot);
+    if (valid && li == 0 && ((bal >> base) & ((1u << LPU) - 1u))) pivot_list_append(piv_count, piv_list, m);
   }
 }
 
@@ -780,7 +918,8 @@ static vef_status launch_group_factor(Schedule& S, const void* rec, cudaStream_t
 }
 
 template <int P, typename T>
-static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, cudaStream_t stream) {
+static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, bool store_systems,
+                                int force_pivot, cudaStream_t stream) {
   void** recp = std::is_same<T, double>::value ? &S.rec64 : &S.rec32;
   if (!*recp) {
     // zero-filled once: the W slots of faces without interior inflow are never written
@@ -802,7 +941,7 @@ static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, cud
     if (st != VEF_OK) return st;
     Mm = (const T*)M.Mmat32; Gx = (const T*)M.Gx32; Gy = (const T*)M.Gy32; nds = (const T*)M.nds32;
   }
-  if (!std::is_same<T, double>::value) {
+  if (!std::is_same<T, double>::value && store_systems) {
     constexpr int Q = P + 1, N = Q * Q;
     if (!S.a64) {
       size_t cap = 0;
@@ -822,19 +961,40 @@ static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, cud
           make_facetab<double>(M.tab), M.nx, M.ny, M.E, (double*)S.a64);
     }
   }
+  if (!S.pivot_list) {
+    size_t cap = 0;
+    vef_status st = ensure_buffer((void**)&S.pivot_list, &cap, (size_t)S.members * sizeof(unsigned int));
+    if (st != VEF_OK) return st;
+  }
+  unsigned int* piv_count = M.dev_status + kStatusPivoted;
+  VEF_CUDA_TRY(cudaMemsetAsync(piv_count, 0, sizeof(unsigned int), stream));
+  {
   KTimer kt(&M, VEF_K_FACTOR, stream);
   if constexpr (P >= 3) {
     constexpr int UPW = 32 / ElemShape<P>::LPU;
     const int warps = std::max(1, std::min(4, (S.D + UPW - 1) / UPW));
     factor_elem_kernel<P, T><<<(unsigned)M.E, 32 * warps, 0, stream>>>(
         S.D, M.E, S.member_of, S.faceinfo, S.omega_dev, sigma_t, Mm, Gx, Gy, nds, make_facetab<T>(M.tab),
-        M.nx, M.ny, S.members, (T*)*recp, M.dev_status);
+        M.nx, M.ny, S.members, (T*)*recp, M.dev_status, piv_count, S.pivot_list, force_pivot);
   } else {
     factor_kernel<P, T><<<nblk(S.members, 128), 128, 0, stream>>>(
         S.members, S.member_code, S.faceinfo, S.omega_dev, sigma_t, Mm, Gx, Gy, nds,
-        make_facetab<T>(M.tab), make_facell<T>(M.tab), M.nx, M.ny, M.E, (T*)*recp, M.dev_status);
+        make_facetab<T>(M.tab), make_facell<T>(M.tab), M.nx, M.ny, M.E, (T*)*recp, M.dev_status,
+        piv_count, S.pivot_list, force_pivot);
   }
   VEF_CUDA_TRY(cudaGetLastError());
+  // the listed tasks again, with partial pivoting (the list's length is read on the device)
+  int dev = 0, sms = 0;
+  VEF_CUDA_TRY(cudaGetDevice(&dev));
+  VEF_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  factor_pivot_kernel<P, T><<<(unsigned)std::max(1LL, std::min<long long>(nblk(S.members, 128), sms * 2LL)), 128, 0,
+                              stream>>>(
+      S.members, S.member_code, S.faceinfo, S.omega_dev, sigma_t, Mm, Gx, Gy, nds, make_facetab<T>(M.tab),
+      make_facell<T>(M.tab), M.nx, M.ny, M.E, (T*)*recp, M.dev_status, piv_count, S.pivot_list);
+  VEF_CUDA_TRY(cudaGetLastError());
+  }
+  if (S.ngroups == 0) return VEF_OK;
+  KTimer kt(&M, VEF_K_GROUP, stream);
   return launch_group_factor<P, T>(S, *recp, stream, M.dev_status);
 }
 
@@ -843,9 +1003,10 @@ static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, cud
 
 // instantiation for one DG order (one translation unit per order keeps builds parallel)
 vef_status VEF_FACTOR_FN(Mesh* mesh, Schedule* S, const double* sigma_t, int precision,
-                         cudaStream_t stream) {
-  if (precision == VEF_FP64) return launch_factor<VEF_FACTOR_P, double>(*mesh, *S, sigma_t, stream);
-  return launch_factor<VEF_FACTOR_P, float>(*mesh, *S, sigma_t, stream);
+                         bool store_systems, int force_pivot, cudaStream_t stream) {
+  if (precision == VEF_FP64)
+    return launch_factor<VEF_FACTOR_P, double>(*mesh, *S, sigma_t, false, force_pivot, stream);
+  return launch_factor<VEF_FACTOR_P, float>(*mesh, *S, sigma_t, store_systems, force_pivot, stream);
 }
 
 }  // namespace vef

@@ -252,6 +252,7 @@ Schedule::~Schedule() {
   cudaFree(rec64);
   cudaFree(rec32);
   cudaFree(a64);
+  cudaFree(pivot_list);
   cudaFree(adj_link);
   cudaFree(tslot);
   cudaFree(slot_gid);

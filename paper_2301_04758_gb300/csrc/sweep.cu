@@ -491,12 +491,14 @@ __device__ __forceinline__ void sweep_direction(const SweepArgs<T>& a, int d, in
       }
     }
   };
+  // once a staging wait gave up, this warp's staged buffers are never read again (they may
+  // not have been filled); it keeps walking the levels so every barrier is still reached
+  bool failed = false;
   auto wait_level = [&](int b) {
     if (!pending[b]) return;
-    uint32_t n = 0;
-    while (!mbar_try_wait(&sm.bar[b], phase[b]) && ++n < kStageWaitIters) {
-    }
-    if (n >= kStageWaitIters && lane == 0) atomicOr(a.status, kDevTimeout);
+    const bool ok = mbar_wait_data(&sm.bar[b], phase[b], kStageWaitIters, a.status);
+    if (!ok && lane == 0) atomicOr(a.status, kDevTimeout);
+    failed = failed || __any_sync(0xffffffffu, !ok);
     phase[b] ^= 1u;
     pending[b] = false;
   };
@@ -528,7 +530,7 @@ __device__ __forceinline__ void sweep_direction(const SweepArgs<T>& a, int d, in
       bool has[kSweepRounds];
 #pragma unroll
       for (int r = 0; r < kSweepRounds; ++r) {
-        has[r] = lane_ok && wb + r * stride + s_lane < nsingle;
+        has[r] = !failed && lane_ok && wb + r * stride + s_lane < nsingle;
         if (!has[r]) continue;
         const uint4 info = *reinterpret_cast<const uint4*>(sm.rec[b][r][s_lane]);
 #pragma unroll
@@ -574,7 +576,7 @@ __device__ __forceinline__ void sweep_direction(const SweepArgs<T>& a, int d, in
       // rounds beyond the staged ones (levels wider than kSweepRounds * stride)
       for (int r = kSweepRounds; wb + r * stride < nsingle; ++r) {
         const int tl = wb + r * stride + s_lane;
-        if (lane_ok && tl < nsingle) {
+        if (!failed && lane_ok && tl < nsingle) {
           const char* rg = L::s_at(a.rec, mb + tl);
           const char* rgx = L::x_at(a.recx, mb + tl);
           const uint4 info = *reinterpret_cast<const uint4*>(rg);
@@ -755,11 +757,22 @@ __global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
       load_win(kb + 32, lb1, lg1, lm1);
     }
   };
+  // producer waits (a buffer released, copies drained): they do not stop on the status bit,
+  // the consumers always release and copies in flight must land before the CTA exits
   auto bounded_wait = [&](uint64_t* bar, unsigned parity) {
     uint32_t n = 0;
     while (!mbar_try_wait(bar, parity) && ++n < kStageWaitIters) {
     }
     if (n >= kStageWaitIters) atomicOr(a.status, kDevTimeout);
+  };
+  // consumer waits for a staged chunk: give up early on the status bit; a warp whose wait
+  // gave up never reads a staged chunk again, but still releases every buffer and reaches
+  // every level barrier
+  bool failed = false;
+  auto data_wait = [&](uint64_t* bar, unsigned parity) {
+    const bool ok = mbar_wait_data(bar, parity, kStageWaitIters, a.status);
+    if (!ok) atomicOr(a.status, kDevTimeout);
+    failed = failed || __any_sync(0xffffffffu, !ok);
   };
   // ring position and phase parity of the next round
   auto next = [&](unsigned& b, unsigned& par) {
@@ -856,11 +869,11 @@ __global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
       const int nsingle = sg - sb, mb = lev_m(k);
       for (int c0 = 0; c0 < nsingle; c0 += CK) {
         const unsigned char* rb = ring + (size_t)rb_i * Sh::kRound;
-        bounded_wait(&full[rb_i], rpar);
+        data_wait(&full[rb_i], rpar);
         const int cend = min(CK, nsingle - c0);
         for (int tk = task; tk - task < cend; tk += CH) {   // the chunk's rounds
           const int r0 = c0 + tk - task;
-          if (lane_ok && tk < cend) {
+          if (!failed && lane_ok && tk < cend) {
             const char* rs = (const char*)rb + tk * L::kStaged;
             const uint4 info = *reinterpret_cast<const uint4*>(rs);
             const uint4 ts = *reinterpret_cast<const uint4*>(rb + Sh::kTsOff + tk * 16);
@@ -1038,6 +1051,170 @@ residual_kernel(long long nmem, long long E, int nx, int ny, long long nbf,
   }
 }
 
+// Matrix-free form of the same residual, for a single transport inversion: nothing per
+// (element, direction) is stored, the element operator is applied from the
+// direction-independent M, Gx, Gy (A psi = sigma_t M psi - mu Gx psi - eta Gy psi) and the
+// face terms at the face Gauss points,
+//     sum_k c_k psi_hat(s_k) l_a(s_k),  c_k = w_k Omega.(n ds)_k,
+// psi_hat = own trace where c_k >= 0, else the upwind neighbour's trace or psi_bar (the
+// boundary data move to the right-hand side with the same sign, so they enter r alike).
+// Per task this costs 3 n^2 FP64 FMAs for the volume part where the stored form costs
+// n^2, but it skips the FP64 assembly (3 n^2 per task) and its n^2 + 4 (p+1)^2 stored
+// words, so it is cheaper whenever the systems serve a single residual.
+// Element-major: a CTA holds one element's M, Gx, Gy and normals in shared memory and walks
+// its directions; a task spans N lanes (row i on lane i), 32 / N tasks per warp.  The face
+// points (4 (p+2) per task) are spread over the task's lanes, their c_k psi_hat go through
+// shared memory to the lanes of the face-node rows.  Grid-stride over the elements.
+template <int P>
+__global__ void __launch_bounds__(128)
+residual_mf_kernel(int D, long long E, int nx, int ny, long long nbf, const double* __restrict__ omega,
+                   const double* __restrict__ sigma_t, const double* __restrict__ Mm,
+                   const double* __restrict__ Gxm, const double* __restrict__ Gym,
+                   const double* __restrict__ nds, const double* __restrict__ bvol,
+                   const double* __restrict__ src_aniso, const double* __restrict__ inflow,
+                   const double* __restrict__ psi, FaceTab<double> ft, double* __restrict__ r,
+                   double* __restrict__ norms) {
+  constexpr int Q = P + 1, N = Q * Q, NQ = P + 2, LD = N + 1;
+  constexpr int UPW = 32 / N, NPT = 4 * NQ, ROUNDS = (NPT + N - 1) / N;
+  constexpr int GZ = NPT;                   // a zero block after the face points
+  __shared__ double sM[N * LD], sX[N * LD], sY[N * LD];
+  __shared__ double sN[4 * NQ * 2];
+  __shared__ double sP[4][UPW][N];          // psi of each warp's tasks
+  __shared__ double sG[4][UPW][NPT + NQ];   // c_k psi_hat at the face points, then zeros
+  __shared__ double sB[4][UPW][NPT + NQ];   // c_k psi_bar at boundary inflow points (for ||b||)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int u = lane / N, li = lane % N;
+  const int uc = u < UPW ? u : UPW - 1;
+  // the faces row li lies on (two at a corner, none inside): offsets of their points in
+  // sG (the zero block for a missing face) and the node position on each
+  const int ia = li % Q, ib = li / Q;
+  int oA = GZ, pA = 0, oB = GZ, pB = 0;
+  {
+    int nf = 0;
+    auto on = [&](int f, int pos) {
+      if (nf++ == 0) { oA = f * NQ; pA = pos; } else { oB = f * NQ; pB = pos; }
+    };
+    if (ib == 0) on(0, ia);
+    if (ia == P) on(1, ib);
+    if (ib == P) on(2, ia);
+    if (ia == 0) on(3, ib);
+  }
+  double lA[NQ], lB[NQ];
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    lA[k] = ft.l[pA][k];
+    lB[k] = ft.l[pB][k];
+  }
+  if (u < UPW)
+    for (int k = li; k < NQ; k += N) sG[warp][u][GZ + k] = sB[warp][u][GZ + k] = 0.0;
+  double rr = 0.0, bb = 0.0;
+  for (long long e = blockIdx.x; e < E; e += gridDim.x) {
+    __syncthreads();   // the previous element's tables are no longer read
+    for (int idx = tid; idx < N * N; idx += blockDim.x) {
+      const int ra = idx / N, j = idx % N;
+      const size_t g = (size_t)e * N * N + idx;
+      sM[ra * LD + j] = Mm[g];
+      sX[ra * LD + j] = Gxm[g];
+      sY[ra * LD + j] = Gym[g];
+    }
+    for (int idx = tid; idx < 4 * NQ * 2; idx += blockDim.x) sN[idx] = nds[(size_t)e * 4 * NQ * 2 + idx];
+    __syncthreads();
+    const double st = sigma_t[e];
+    const int ie = (int)(e % nx), je = (int)(e / nx);
+    const bool on_boundary = ie == 0 || je == 0 || ie == nx - 1 || je == ny - 1;
+    const double bv = bvol[(size_t)e * N + li];
+    for (int d0 = warp * UPW; d0 < D; d0 += nwarps * UPW) {
+      const int d = d0 + u;
+      const bool valid = u < UPW && d < D;
+      const int dd = valid ? d : 0;
+      const double mu = omega[2 * dd], eta = omega[2 * dd + 1];
+      const size_t rowbase = ((size_t)dd * E + e) * N;
+      const double pi = valid ? psi[rowbase + li] : 0.0;
+      __syncwarp();
+      if (u < UPW) sP[warp][u][li] = pi;
+      __syncwarp();
+      // face points: c_k psi_hat, the trace taken from this element (c_k >= 0) or from the
+      // upwind neighbour, one FMA chain either way; psi_bar where the face is the boundary
+#pragma unroll
+      for (int rd = 0; rd < ROUNDS; ++rd) {
+        const int q = li + N * rd;
+        if (u < UPW && q < NPT) {
+          const int f = q / NQ, k = q % NQ;
+          const double c = ft.w[k] * (mu * sN[(f * NQ + k) * 2] + eta * sN[(f * NQ + k) * 2 + 1]);
+          const int nb = nb_elem(nx, ny, (int)e, f);
+          const bool own = c >= 0.0;
+          double tr = 0.0, tb = 0.0;
+          if (own || nb >= 0) {
+            const double* src = own ? &sP[warp][u][0] : psi + ((size_t)dd * E + nb) * N;
+            const int fs = own ? f : ((f + 2) & 3);
+#pragma unroll
+            for (int t = 0; t < Q; ++t) tr = fma(ft.l[t][k], src[face_dof<P>(fs, t)], tr);
+          } else if (inflow) {
+            tr = tb = inflow[((size_t)dd * nbf + bface(nx, ny, (int)e, f)) * NQ + k];
+          }
+          sG[warp][u][q] = c * tr;
+          sB[warp][u][q] = c * tb;
+        }
+      }
+      // volume part, row li
+      double am = 0.0, ax = 0.0, ay = 0.0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const double pj = sP[warp][uc][j];
+        am = fma(sM[li * LD + j], pj, am);
+        ax = fma(sX[li * LD + j], pj, ax);
+        ay = fma(sY[li * LD + j], pj, ay);
+      }
+      double b = bv;
+      if (src_aniso) {
+        const double* qd = src_aniso + rowbase;
+#pragma unroll
+        for (int j = 0; j < N; ++j) b = fma(sM[li * LD + j], qd[j], b);
+      }
+      __syncwarp();
+      double fs = 0.0, bs = 0.0;
+#pragma unroll
+      for (int k = 0; k < NQ; ++k) {
+        fs = fma(sG[warp][uc][oA + k], lA[k], fs);
+        fs = fma(sG[warp][uc][oB + k], lB[k], fs);
+      }
+      if (on_boundary && inflow) {
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+          bs = fma(sB[warp][uc][oA + k], lA[k], bs);
+          bs = fma(sB[warp][uc][oB + k], lB[k], bs);
+        }
+      }
+      const double ri = b - (st * am - mu * ax - eta * ay) - fs;
+      if (valid) {
+        r[rowbase + li] = ri;
+        rr = fma(ri, ri, rr);
+        bb = fma(b - bs, b - bs, bb);
+      }
+    }
+  }
+  __shared__ double red[2][32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    rr += __shfl_xor_sync(0xffffffffu, rr, off);
+    bb += __shfl_xor_sync(0xffffffffu, bb, off);
+  }
+  if (lane == 0) {
+    red[0][warp] = rr;
+    red[1][warp] = bb;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double sr = 0.0, sb = 0.0;
+    for (int w = 0; w < nwarps; ++w) {
+      sr += red[0][w];
+      sb += red[1][w];
+    }
+    atomicAdd(norms, sr);
+    atomicAdd(norms + 1, sb);
+  }
+}
+
 __global__ void cast_add_kernel(long long n, const float* __restrict__ delta, double* __restrict__ psi,
                                 int accumulate) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1086,6 +1263,9 @@ struct SweepCall {
   bool group_iterative;  // solve every coupled group by the inner iteration
   bool cluster;      // cluster sweep kernel instead of the single-CTA one
   bool apply_separate;   // y = A^{-1} b by its own launch even when SMs are free
+  bool fixed_passes;     // mixed: exactly max_passes sweeps, no residual of the last one
+  bool residual_stored;  // mixed: residual from stored FP64 element systems (else matrix-free)
+  int force_pivot;       // refactorise every task with partial pivoting (tests of the fallback)
 };
 
 // Host-side arguments of one problem's sweep (also the batch table entries).
@@ -1308,8 +1488,17 @@ static vef_status launch_residual(const SweepCall& c, const double* psi, double*
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const unsigned grid = (unsigned)std::min<long long>(nblk(S.members * N, 128), (long long)sms * 16);
   VEF_CUDA_TRY(cudaMemsetAsync(norms, 0, 2 * sizeof(double), c.stream));
+  if (!c.residual_stored) {
+    const unsigned egrid = (unsigned)std::min<long long>(M.E, (long long)sms * 16);
+    KTimer kt(&M, VEF_K_RESIDUAL, c.stream);
+    residual_mf_kernel<P><<<egrid, 128, 0, c.stream>>>(
+        S.D, M.E, M.nx, M.ny, M.nbf, S.omega_dev, c.sigma_t, M.Mmat, M.Gx, M.Gy, M.nds, M.bvol,
+        c.src_aniso, c.inflow, psi, make_facetab<double>(M.tab), r, norms);
+    VEF_CUDA_TRY(cudaGetLastError());
+    return VEF_OK;
+  }
+  const unsigned grid = (unsigned)std::min<long long>(nblk(S.members * N, 128), (long long)sms * 16);
   KTimer kt(&M, VEF_K_RESIDUAL, c.stream);
   residual_kernel<P><<<grid, 128, 0, c.stream>>>(
       S.members, M.E, M.nx, M.ny, M.nbf, S.member_code, S.faceinfo, S.omega_dev, M.Mmat, M.nds,
@@ -1345,13 +1534,17 @@ static vef_status solve_p(const SweepCall& c, double* psi, vef_info* info) {
   int passes = 1;
   double rel = -1.0;
   for (int pass = 0; pass < c.max_passes; ++pass) {
+    // fixed passes: the last sweep's residual is not formed, and nothing is read back
+    if (c.fixed_passes && pass == c.max_passes - 1) break;
     if ((st = launch_residual<P>(c, psi, r, norms)) != VEF_OK) return st;
-    double h[2];
-    VEF_CUDA_TRY(cudaMemcpyAsync(h, norms, sizeof(h), cudaMemcpyDeviceToHost, c.stream));
-    VEF_CUDA_TRY(cudaStreamSynchronize(c.stream));
-    rel = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
-    if (rel <= c.tol) break;
-    if (pass == c.max_passes - 1) {
+    if (!c.fixed_passes) {
+      double h[2];
+      VEF_CUDA_TRY(cudaMemcpyAsync(h, norms, sizeof(h), cudaMemcpyDeviceToHost, c.stream));
+      VEF_CUDA_TRY(cudaStreamSynchronize(c.stream));
+      rel = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
+      if (rel <= c.tol) break;
+    }
+    if (!c.fixed_passes && pass == c.max_passes - 1) {
       unsigned int bit = kDevNotConverged;
       VEF_CUDA_TRY(cudaMemcpyAsync(M.dev_status + 4, &bit, sizeof(bit), cudaMemcpyHostToDevice, c.stream));
       break;
@@ -1362,6 +1555,13 @@ static vef_status solve_p(const SweepCall& c, double* psi, vef_info* info) {
       cast_add_kernel<<<nblk(tot, 256), 256, 0, c.stream>>>(tot, delta, psi, 1);
     }
     ++passes;
+  }
+  if (info && c.fixed_passes && passes > 1) {
+    // the residual of the iterate the last correction started from
+    double h[2];
+    VEF_CUDA_TRY(cudaMemcpyAsync(h, norms, sizeof(h), cudaMemcpyDeviceToHost, c.stream));
+    VEF_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    rel = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
   }
   if (info) { info->passes = passes; info->rel_residual = rel; }
   return VEF_OK;
@@ -1377,7 +1577,7 @@ static vef_status solve(const SweepCall& c, double* psi, vef_info* info) {
 }
 
 static vef_status factor(const SweepCall& c) {
-  return factor_records(c.mesh, c.S, c.sigma_t, c.precision, c.stream);
+  return factor_records(c.mesh, c.S, c.sigma_t, c.precision, c.residual_stored, c.force_pivot, c.stream);
 }
 
 static vef_status launch_bvol(Mesh& M, const double* sigma_s, const double* phi_in,
@@ -1405,6 +1605,7 @@ vef_status collect_status(Mesh& M, cudaStream_t stream, vef_info* info) {
   if (info) {
     info->timed_out = (bits & kDevTimeout) ? 1 : 0;
     info->max_inner_iterations = (int)h[2];
+    info->pivoted_tasks = (long long)h[kStatusPivoted];
   }
   if (bits & kDevTimeout) { set_last_error("a sweep dependency wait ran out"); return VEF_ERR_TIMEOUT; }
   if (bits & kDevSingular) { set_last_error("singular local element system"); return VEF_ERR_NOT_CONVERGED; }
@@ -1438,7 +1639,8 @@ static void fill_opts(const vef_opts* o, SweepCall& c) {
   c.precision = o ? o->precision : VEF_FP64;
   const double deftol = c.precision == VEF_FP64 ? 1e-15 : 1e-13;
   c.tol = (o && o->tol > 0.0) ? o->tol : deftol;
-  c.max_passes = (o && o->max_passes > 0) ? o->max_passes : 8;
+  c.fixed_passes = o && o->tol < 0.0 && c.precision == VEF_MIXED;
+  c.max_passes = (o && o->max_passes > 0) ? o->max_passes : (c.fixed_passes ? 2 : 8);
   // tile_override = 100 * (CTAs per direction cluster) + (warps per CTA); 0 = automatic
   const int t = (o && o->tile_override > 0) ? o->tile_override : 0;
   c.cluster_size = t ? std::min(16, std::max(1, t / 100)) : 0;
@@ -1446,6 +1648,7 @@ static void fill_opts(const vef_opts* o, SweepCall& c) {
   c.group_iterative = o && (o->flags & VEF_GROUPS_ITERATIVE);
   c.cluster = t != 0 || (o && (o->flags & VEF_SWEEP_CLUSTER));
   c.apply_separate = o && (o->flags & VEF_APPLY_SEPARATE);
+  c.force_pivot = (o && (o->flags & VEF_PIVOT_ALWAYS)) ? 1 : 0;
 }
 
 static void schedule_info(const Schedule& S, vef_info* info) {
@@ -1515,6 +1718,7 @@ extern "C" vef_status vef_source_iterate(vef_mesh mesh, const double* sigma_t, c
   c.inflow = inflow;
   c.stream = s;
   fill_opts(opts, c);
+  c.residual_stored = true;   // the FP64 systems serve the residuals of all K inversions
   const long long En = M.E * M.n;
   if ((st = ensure_buffer((void**)&M.work, &M.work_cap, (size_t)2 * En * sizeof(double))) != VEF_OK)
     return st;

@@ -33,3 +33,31 @@ def random_problem(nx, ny, m, alpha, p, sn, seed, aniso=False, with_inflow=True,
     inflow = rng.uniform(0.0, 1.0, (D, 2 * nx + 2 * ny, nq)) if with_inflow else None
     return dict(nx=nx, ny=ny, m=m, alpha=alpha, p=p, omega=om, weights=w, sigma_t=st,
                 sigma_s=ss, phi_in=phi_in, source=q, inflow=inflow)
+
+
+def _oracle_part(args):
+    """Worker: the oracle's direct solve for a subset of the directions."""
+    (nx, ny, m, alpha, p), om, w, st, ss, phi_in, source, inflow = args
+    from oracle.transport import Discretization, sweep
+    disc = Discretization(nx, ny, m, alpha, p)
+    return sweep(disc, om, w, st, ss, phi_in=phi_in, source=source, inflow=inflow)
+
+
+def oracle_sweep_parallel(mesh_args, omega, weights, sigma_t, sigma_s, phi_in=None, source=None,
+                          inflow=None, directions=None, procs=None):
+    """psi [len(directions)][E][n] from oracle.transport.sweep, the directions split over
+    spawned worker processes (each solve is independent of the others; spawn, so that no
+    worker inherits a CUDA context).  mesh_args = (nx, ny, m, alpha, p)."""
+    import multiprocessing as mp
+    import os
+    dirs = np.arange(len(weights)) if directions is None else np.asarray(directions)
+    procs = procs or max(1, min(len(dirs), os.cpu_count() or 1, 16))
+    chunks = [c for c in np.array_split(dirs, procs) if len(c)]
+
+    def sub(a, c):
+        return None if a is None else (a[c] if np.ndim(a) == 3 else a)
+    jobs = [(tuple(mesh_args), omega[c], weights[c], sigma_t, sigma_s, phi_in, sub(source, c), sub(inflow, c))
+            for c in chunks]
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        parts = pool.map(_oracle_part, jobs, chunksize=1)
+    return np.concatenate(parts, axis=0)
