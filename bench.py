@@ -709,8 +709,10 @@ def _cuda_time(fn, reps=1):
 def suite_batch(args):
     """The 64-problem batch: problem k (seed 400 + k) has N in {16,32,64,128,256} (k mod 5),
     p = 1 + (k mod 4), S_N in {4,6,8,12,16} (k mod 5 shifted by k // 5), sine mesh alpha 0.05,
-    Q3 map, q = 1, vacuum.  One batched FP64 sweep (cluster shapes from the autotuner),
-    timed directly and as a CUDA-graph replay."""
+    Q3 map, q = 1, vacuum.  One batched FP64 inversion of all 64 (the sweep forms as tuned),
+    timed with its factorisations, with the factorisations kept (sigma_t unchanged, as in the
+    outer iterations of the VEF method) and as a CUDA-graph replay; beside it the same 64
+    problems inverted one call after another."""
     import torch
     from paper_2301_04758_gb300.api import Mesh, Batch
     from vef_inputs.media import batch_problem
@@ -730,22 +732,37 @@ def suite_batch(args):
         sss.append(T(ss))
         qs.append(torch.ones(N * N, (p + 1) ** 2, dtype=torch.float64, device="cuda"))
         updates += N * N * (p + 1) ** 2 * len(w)
+    reps = max(1, args.steps)
+    # one problem after another, each its own call (schedules built and warm first)
+    psis = [m.sweep(st, ss, om, w, source=q) for m, st, ss, om, w, q in zip(meshes, sts, sss, oms, ws, qs)]
+    one_by_one = lambda reuse: [m.sweep(st, ss, om, w, source=q, psi=ps, reuse=reuse)
+                                for m, st, ss, om, w, q, ps in zip(meshes, sts, sss, oms, ws, qs, psis)]
+    ms_single, _ = _cuda_time(lambda: one_by_one(False), reps=reps)
+    ms_single_reuse, _ = _cuda_time(lambda: one_by_one(True), reps=reps)
     t0 = time.perf_counter()
     batch = Batch(meshes, oms, ws)
     build_s = time.perf_counter() - t0
     psi = batch.sweep(sts, sss, source=qs)
+    ms_default, _ = _cuda_time(lambda: batch.sweep(sts, sss, source=qs, psi=psi), reps=reps)
     tiles = batch.tune()
-    ms, _ = _cuda_time(lambda: batch.sweep(sts, sss, source=qs, psi=psi), reps=max(1, args.steps))
+    ms, _ = _cuda_time(lambda: batch.sweep(sts, sss, source=qs, psi=psi), reps=reps)
+    ms_reuse, _ = _cuda_time(lambda: batch.sweep(sts, sss, source=qs, psi=psi, reuse=True), reps=reps)
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
         batch.sweep(sts, sss, source=qs, psi=psi, stream=s)
-    ms_g, _ = _cuda_time(g.replay, reps=max(1, args.steps))
+    ms_g, _ = _cuda_time(g.replay, reps=reps)
+    rate = lambda t: updates / (t * 1e-3)
     return {"suite": "batch", "workload": "64 problems, N 16..256, Q1..Q4, S4..S16, sine alpha 0.05, seeds 400+k",
-            "problems": 64, "angular_dof_updates_per_sweep": updates, "ms_per_sweep": ms,
-            "angular_dof_updates_per_s": updates / (ms * 1e-3), "graph_replay_ms": ms_g,
-            "graph_angular_dof_updates_per_s": updates / (ms_g * 1e-3), "tuned_tiles": tiles,
+            "problems": 64, "angular_dof_updates_per_inversion": updates,
+            "batched": {"ms": ms, "angular_dof_updates_per_s": rate(ms), "tuned_tiles": tiles,
+                        "ms_before_tuning": ms_default},
+            "batched_factors_kept": {"ms": ms_reuse, "angular_dof_updates_per_s": rate(ms_reuse)},
+            "graph_replay": {"ms": ms_g, "angular_dof_updates_per_s": rate(ms_g)},
+            "one_call_per_problem": {"ms": ms_single, "angular_dof_updates_per_s": rate(ms_single),
+                                     "ms_factors_kept": ms_single_reuse,
+                                     "angular_dof_updates_per_s_factors_kept": rate(ms_single_reuse)},
             "schedule_build_s": build_s}
 
 

@@ -91,10 +91,17 @@ enum {
                                context limited to fewer SMs, e.g. under MPS, should set
                                this flag: the driver refuses a cooperative grid that
                                does not fit, and the call returns VEF_ERR_CUDA) */
-  VEF_PIVOT_ALWAYS = 8      /* refactorise every (element, direction) system with partial
+  VEF_PIVOT_ALWAYS = 8,     /* refactorise every (element, direction) system with partial
                                pivoting, as the library does by itself only for the systems
                                whose unpivoted elimination meets a small pivot (see
                                VEF_PIVOT_FLOOR_LOG2_FP64); slow, meant for testing */
+  VEF_REUSE_FACTORS = 16    /* keep the local factorisation of the previous call with this
+                               mesh and direction set in this precision instead of forming it
+                               again (vef_sweep, vef_source_iterate, vef_batch_sweep): the
+                               caller guarantees sigma_t is unchanged, as in the outer
+                               iterations of the VEF method, where only the scattering
+                               source changes.  Without a previous factorisation the call
+                               factorises as usual. */
 };
 
 typedef struct vef_mesh_s* vef_mesh;
@@ -248,9 +255,12 @@ vef_status vef_adjoint_sweep(vef_mesh mesh, const double* sigma_t, const double*
  * Each problem has its own mesh handle (distinct handles); the batch fixes each problem's direction set
  * (omega[k] [host] [D[k]][2], weights[k] [host] [D[k]]) and builds its schedule.  One
  * vef_batch_sweep call runs, per problem, the dependency-free kernels (right-hand side,
- * local factorisation, apply), then one cluster launch per DG order sweeps every
- * (problem, direction) of that order.  FP64 only.  No device synchronisation unless info
- * is given, so a call can be captured in a CUDA graph after a first (allocating) call. */
+ * local factorisation unless VEF_REUSE_FACTORS, apply), then one launch per DG order sweeps
+ * every (problem, direction) of that order: one CTA per (problem, direction) with the
+ * single-CTA sweep, largest problems first, or one cluster per (problem, direction) when
+ * the tuner or opts->tile_override chose a cluster shape.  FP64 only.  No device
+ * synchronisation unless info is given, so a call can be captured in a CUDA graph after a
+ * first (allocating) call. */
 typedef struct vef_batch_s* vef_batch;
 vef_status vef_batch_create(const vef_mesh* meshes, int nprob, const double* const* omega,
                             const double* const* weights, const int* D, vef_batch* out);
@@ -265,10 +275,16 @@ vef_status vef_batch_sweep(vef_batch batch, const double* const* sigma_t, const 
                            const double* const* phi_in, const double* const* source,
                            const double* const* inflow, double* const* psi, const vef_opts* opts,
                            vef_info* info, void* stream);
-/* Autotuner: times the batched sweep of each DG order for a set of cluster shapes
- * (CTAs per direction x warps per CTA) on the data of the last vef_batch_sweep call and
- * keeps the fastest for later calls; tiles_out (optional, [4]) receives the choice per
- * order p = 1..4 (0 = no problem of that order).  Synchronises `stream`. */
+/* Autotuner: times the batched sweep of each DG order in its single-CTA form (one CTA per
+ * (problem, direction), the default) and in a set of cluster shapes (CTAs per direction x
+ * warps per CTA) on the data of the last vef_batch_sweep call and keeps the fastest for later
+ * calls; tiles_out (optional, [4]) receives the choice per order p = 1..4 as 100 x CTAs +
+ * warps for a cluster shape, 1 for the single-CTA form, 0 when no problem has that order.
+ * When the environment variable VEF_TUNE_CACHE names a file, the choices are appended to it
+ * keyed by the device and the problems of each order, and vef_batch_create reads them back
+ * for a batch with the same key (a missing or unreadable file is ignored; the last line
+ * for a key wins); an order whose choice came from the file is not timed again.
+ * Synchronises `stream`. */
 vef_status vef_batch_tune(vef_batch batch, void* stream, int* tiles_out);
 
 /* Kernel classes for the per-kernel timing counters. */
@@ -364,7 +380,9 @@ vef_status vef_mesh_inject_status(vef_mesh mesh, unsigned int bits, void* stream
  * the library holds until the process exits.  Limits: D <= 256 and
  * E * (p+1)^2 <= 524288; larger inputs return VEF_ERR_INVALID_ARG.
  * The first call on a device looks up that array's device address (with the device
- * current); make that first call before any stream capture.  All calls share the
+ * current) and keeps it; make that first call before any stream capture.  A
+ * cudaDeviceReset of that device invalidates the kept address: do not call this entry
+ * point on a device after resetting it in the same process.  All calls share the
  * array: calls that overlap on the GPU (different streams or devices' work racing on
  * one device) corrupt each other's result, so serialise them.  Each call writes every
  * scratch entry it reads, so nothing carries over between calls.  A non-positive

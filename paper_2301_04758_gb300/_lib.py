@@ -25,6 +25,7 @@ VEF_GROUPS_ITERATIVE = 1
 VEF_SWEEP_CLUSTER = 2
 VEF_APPLY_SEPARATE = 4
 VEF_PIVOT_ALWAYS = 8
+VEF_REUSE_FACTORS = 16
 VEF_STATUS_TIMEOUT = 1
 VEF_STATUS_NOT_CONVERGED = 2
 VEF_STATUS_NONPOSITIVE = 4
@@ -109,7 +110,8 @@ def _declare(lib):
                  "vef_sweep", "vef_moments", "vef_source_iterate", "vef_adjoint_sweep",
                  "vef_profile", "vef_profile_read", "vef_measure_fma_peak", "vef_wait_selftest",
                  "vef_eddington_noalloc", "vef_batch_create", "vef_batch_destroy",
-                 "vef_batch_sweep", "vef_batch_tune", "vef_region_weights", "vef_schedule_host"):
+                 "vef_batch_sweep", "vef_batch_tune", "vef_region_weights", "vef_schedule_host",
+                 "vef_mesh_inject_status"):
         getattr(lib, name).restype = I
     lib.vef_status_string.argtypes = [I]
     lib.vef_status_string.restype = ctypes.c_char_p

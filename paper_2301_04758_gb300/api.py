@@ -33,7 +33,7 @@ def _stream(stream):
 
 
 def _opts(precision="fp64", tol=0.0, max_passes=0, tile=0, groups="direct", kernel="cta", apply="fused",
-          pivot="guard"):
+          pivot="guard", reuse=False):
     o = _lib.VefOpts()
     o.precision = {"fp64": _lib.VEF_FP64, "mixed": _lib.VEF_MIXED}[precision]
     o.tol = float(tol)
@@ -43,6 +43,7 @@ def _opts(precision="fp64", tol=0.0, max_passes=0, tile=0, groups="direct", kern
     o.flags |= {"cta": 0, "cluster": _lib.VEF_SWEEP_CLUSTER}[kernel]
     o.flags |= {"fused": 0, "separate": _lib.VEF_APPLY_SEPARATE}[apply]
     o.flags |= {"guard": 0, "always": _lib.VEF_PIVOT_ALWAYS}[pivot]
+    o.flags |= _lib.VEF_REUSE_FACTORS if reuse else 0
     return o
 
 
@@ -105,7 +106,7 @@ class Mesh:
     # ---------------------------------------------------------------- transport
     def sweep(self, sigma_t, sigma_s, omega, weights, phi_in=None, source=None, inflow=None,
               precision="fp64", tol=0.0, max_passes=0, tile=0, groups="direct", psi=None, info=False,
-              stream=None, kernel="cta", apply="fused", pivot="guard"):
+              stream=None, kernel="cta", apply="fused", pivot="guard", reuse=False):
         """psi [D][E][n] = L^{-1} b for every direction (see vef_sweep in include/vef.h).
 
         groups: "direct" (coupled element groups through their trace system) or
@@ -117,7 +118,9 @@ class Mesh:
         or "separate" (its own launch before the sweep); both give the same psi.
         pivot: "guard" (element systems eliminated without pivoting, those meeting a small
         pivot redone with partial pivoting) or "always" (every system with partial
-        pivoting; slow, for tests)."""
+        pivoting; slow, for tests).
+        reuse: keep the local factorisation of the previous call with this direction set and
+        precision (the caller guarantees sigma_t is unchanged)."""
         om, omp = _host(omega)
         w, wp = _host(weights)
         D = len(w)
@@ -125,7 +128,7 @@ class Mesh:
         if psi is None:
             psi = self._empty(D, self.E, self.n)
         inf = _lib.VefInfo() if info else None
-        o = _opts(precision, tol, max_passes, tile, groups, kernel, apply, pivot)
+        o = _opts(precision, tol, max_passes, tile, groups, kernel, apply, pivot, reuse)
         st = self.lib.vef_sweep(self.handle, _ptr(sigma_t), _ptr(sigma_s), _ptr(phi_in), _ptr(source),
                                 aniso, _ptr(inflow), omp, wp, D, ctypes.byref(o), _ptr(psi),
                                 ctypes.byref(inf) if info else None, _stream(stream))
@@ -236,13 +239,15 @@ class Batch:
             pass
 
     def sweep(self, sigma_t, sigma_s, phi_in=None, source=None, inflow=None, psi=None, tile=0,
-              info=False, stream=None):
-        """Lists of per-problem tensors; returns the list of psi [D_k][E_k][n_k]."""
+              info=False, stream=None, reuse=False):
+        """Lists of per-problem tensors; returns the list of psi [D_k][E_k][n_k].
+        tile: 0 = the tuned (or default single-CTA) form, else a cluster shape 100 x CTAs +
+        warps; reuse: keep the previous call's factorisations (sigma_t unchanged)."""
         n = len(self.meshes)
         if psi is None:
             psi = [m._empty(len(w), m.E, m.n) for m, w in zip(self.meshes, self._w)]
         none = lambda lst: None if lst is None else _ptr_array(lst)
-        o = _opts("fp64", 0.0, 0, tile)
+        o = _opts("fp64", 0.0, 0, tile, reuse=reuse)
         inf = _lib.VefInfo() if info else None
         st = self.lib.vef_batch_sweep(self.handle, _ptr_array(sigma_t), _ptr_array(sigma_s), none(phi_in),
                                       none(source), none(inflow), _ptr_array(psi), ctypes.byref(o),
@@ -251,7 +256,8 @@ class Batch:
         return (psi, inf.as_dict()) if info else psi
 
     def tune(self, stream=None):
-        """Autotune the cluster shape per DG order; returns {p: tile}."""
+        """Autotune the sweep form per DG order; returns {p: tile} (1 = one CTA per
+        (problem, direction), else 100 x CTAs per cluster + warps per CTA)."""
         tiles = (ctypes.c_int * 4)()
         _lib.check(self.lib.vef_batch_tune(self.handle, _stream(stream), tiles), "vef_batch_tune")
         return {p + 1: tiles[p] for p in range(4) if tiles[p]}

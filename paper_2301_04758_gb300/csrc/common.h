@@ -112,6 +112,9 @@ struct Schedule {
   void* rec32 = nullptr;
   void* a64 = nullptr;         // FP64 element matrices + inflow couplings (mixed residual)
   unsigned int* pivot_list = nullptr;  // [members] tasks the pivot guard sent to the fallback
+  // which factorisations the records hold (for VEF_REUSE_FACTORS): bit 0 FP64 records,
+  // bit 1 FP32 records, bit 2 the stored FP64 element systems
+  unsigned factored = 0;
   uint32_t* adj_link = nullptr;  // [members][4] downstream receiver across each face:
                                  // (receiver member << 2) | its W slot, or ~0 (adjoint)
   // Shared-memory trace slots of the single-CTA sweep, per member four 16-bit slot ids:

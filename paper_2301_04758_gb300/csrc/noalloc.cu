@@ -10,6 +10,7 @@
 // file-scope device array of fixed size and the direction set passed by value, so the
 // call allocates nothing.
 #include <cmath>
+#include <mutex>
 
 #include "common.h"
 
@@ -78,9 +79,11 @@ __global__ void noalloc_eddington_kernel(long long E, Tab1D tab, const double* _
 
 // Device address of the scratch array, looked up once per device (with that device
 // current) by cudaGetSymbolAddress; the host-side name of the array is not a device
-// address and is never passed to a kernel.
+// address and is never passed to a kernel.  The table is filled under a mutex, so host
+// threads making their first calls at the same time do not race on it.
 constexpr int kMaxDevices = 64;
 static double* g_scratch_addr[kMaxDevices] = {};
+static std::mutex g_scratch_mutex;
 
 static vef_status scratch_address(double** out) {
   int dev = 0;
@@ -89,6 +92,7 @@ static vef_status scratch_address(double** out) {
     set_last_error("device ordinal out of range for the no-allocation scratch table");
     return VEF_ERR_INVALID_ARG;
   }
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;
     cudaError_t err = cudaGetSymbolAddress(&p, g_noalloc_scratch);

@@ -1,6 +1,6 @@
 // Transport sweep: dependency-free right-hand-side apply, wavefront solve (one CTA per
-// direction by default, one cluster per direction for batches), FP64 residual and
-// mixed-precision defect correction, and source iteration.
+// direction, also for batches; one cluster per direction on request or when the batch tuner
+// picks it), FP64 residual and mixed-precision defect correction, and source iteration.
 //
 // The element equations (upwind DG, pointwise upwinding at face Gauss points) give, for
 // direction d and element e,
@@ -23,14 +23,13 @@
 #include <cstdlib>
 #include <map>
 #include <mutex>
+#include <string>
+#include <cstdio>
 
 #include "device.cuh"
 
 namespace vef {
 
-// sweep launch defaults, 100 * (CTAs per direction cluster) + (warps per CTA), measured
-// on the 256 x 256 Q2 S8 sine-mesh sweep (FP64: 4 x 8 warps, FP32: 8 x 8 warps)
-constexpr int kDefaultTile64 = 408;   // batches before tuning (their clusters outnumber the SMs)
 
 
 // ----------------------------------------------------------------- right-hand sides
@@ -708,12 +707,9 @@ __device__ __forceinline__ void apply_worker(const SweepArgs<T>& a) {
   }
 }
 
+// One direction d of one problem in this CTA (the single-CTA sweep proper).
 template <int P, typename T, int MODE>
-__global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
-  if (a.ready != nullptr && (int)blockIdx.x >= a.nd) {
-    apply_worker<P, T, MODE>(a);
-    return;
-  }
+__device__ __forceinline__ void sweep_cta_direction(const SweepArgs<T>& a, const int d) {
   using Sh = CtaShape<P, T>;
   using L = Rec<P, T>;
   constexpr int Q = P + 1, N = Q * Q, SPC = Sh::SPC, CH = Sh::CH, CK = Sh::CK;
@@ -725,7 +721,6 @@ __global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
   T* tr = reinterpret_cast<T*>(cta_smem + Sh::kGroup + Sh::kBars);
   unsigned char* ring = cta_smem + Sh::kGroup + Sh::kBars + a.tr_bytes;
   const unsigned NB = (unsigned)a.ring;
-  const int d = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (unsigned b = 0; b < NB; ++b) {
@@ -955,6 +950,25 @@ __global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
     }
     named_barrier(1, (Sh::kCompute + Sh::kGroupWarps) * 32);
   }
+}
+
+template <int P, typename T, int MODE>
+__global__ void __maxnreg__(128) sweep_cta_kernel(SweepArgs<T> a) {
+  if (a.ready != nullptr && (int)blockIdx.x >= a.nd) {
+    apply_worker<P, T, MODE>(a);
+    return;
+  }
+  sweep_cta_direction<P, T, MODE>(a, blockIdx.x);
+}
+
+// Batch of independent problems of one DG order: CTA c runs direction cmap[c].y of problem
+// cmap[c].x, whose arguments (ring and trace-slot sizes included) sit in tab; the launch's
+// dynamic shared memory covers the largest of them.
+template <int P, typename T, int MODE>
+__global__ void __maxnreg__(128)
+sweep_cta_batch_kernel(const SweepArgs<T>* __restrict__ tab, const int2* __restrict__ cmap) {
+  const int2 pd = cmap[blockIdx.x];
+  sweep_cta_direction<P, T, MODE>(tab[pd.x], pd.y);
 }
 
 // -------------------------------------------------------------- FP64 residual (mixed)
@@ -1266,6 +1280,7 @@ struct SweepCall {
   bool fixed_passes;     // mixed: exactly max_passes sweeps, no residual of the last one
   bool residual_stored;  // mixed: residual from stored FP64 element systems (else matrix-free)
   int force_pivot;       // refactorise every task with partial pivoting (tests of the fallback)
+  bool reuse_factors;    // keep the schedule's factorisation from the previous call
 };
 
 // Host-side arguments of one problem's sweep (also the batch table entries).
@@ -1576,8 +1591,15 @@ static vef_status solve(const SweepCall& c, double* psi, vef_info* info) {
   }
 }
 
+// The local factorisation, unless the caller asked to keep the one the schedule holds for
+// this precision (VEF_REUSE_FACTORS: sigma_t unchanged).  Any fresh factorisation may
+// follow a change of sigma_t, so it leaves only what it has just formed marked as current.
 static vef_status factor(const SweepCall& c) {
-  return factor_records(c.mesh, c.S, c.sigma_t, c.precision, c.residual_stored, c.force_pivot, c.stream);
+  const unsigned need = c.precision == VEF_FP64 ? 1u : (2u | (c.residual_stored ? 4u : 0u));
+  if (c.reuse_factors && (c.S->factored & need) == need) return VEF_OK;
+  vef_status st = factor_records(c.mesh, c.S, c.sigma_t, c.precision, c.residual_stored, c.force_pivot, c.stream);
+  if (st == VEF_OK) c.S->factored = need;
+  return st;
 }
 
 static vef_status launch_bvol(Mesh& M, const double* sigma_s, const double* phi_in,
@@ -1649,6 +1671,7 @@ static void fill_opts(const vef_opts* o, SweepCall& c) {
   c.cluster = t != 0 || (o && (o->flags & VEF_SWEEP_CLUSTER));
   c.apply_separate = o && (o->flags & VEF_APPLY_SEPARATE);
   c.force_pivot = (o && (o->flags & VEF_PIVOT_ALWAYS)) ? 1 : 0;
+  c.reuse_factors = o && (o->flags & VEF_REUSE_FACTORS);
 }
 
 static void schedule_info(const Schedule& S, vef_info* info) {
@@ -1777,17 +1800,24 @@ vef_status factor_fp64(Mesh* mesh, Schedule* S, const double* sigma_t, cudaStrea
 
 // ------------------------------------------------------------------------- batches
 // Many independent problems: per problem the dependency-free kernels (right-hand side,
-// factorisation, apply) run as usual; the sweep of all problems of one DG order is one
-// cluster launch with a cluster per (problem, direction).
+// factorisation unless reused, apply) run as usual; the sweep of all problems of one DG
+// order is one launch with a CTA (or, as tuned, a cluster) per (problem, direction).
 namespace vef {
 
+// sweep form of a batch class: kBatchCta = one CTA per (problem, direction); otherwise
+// 100 x (CTAs per direction cluster) + (warps per CTA) of the cluster form
+constexpr int kBatchCta = 1;
+
 struct BatchClass {
-  std::vector<int> probs;          // problem indices of this DG order
+  std::vector<int> probs;          // problem indices of this DG order, largest first
   int2* cmap = nullptr;            // [clusters] (position in probs, direction)
   long long clusters = 0;
   SweepArgs<double>* tab_dev = nullptr;
   SweepArgs<double>* tab_host = nullptr;   // pinned
-  int tile = 0;                    // tuned cluster shape (0 = library default)
+  int tile = 0;                    // tuned form (0 = library default, the single-CTA form)
+  bool tile_cached = false;        // tile came from the tuner cache (not timed again)
+  size_t cta_smem = 0;             // dynamic shared memory of the single-CTA form (largest problem)
+  std::string key;                 // tuner cache key: device and problems of this class
 };
 
 }  // namespace vef
@@ -1817,6 +1847,16 @@ namespace vef {
 
 template <int P>
 static vef_status batch_launch_class(vef_batch_s& B, BatchClass& C, int tile, cudaStream_t s) {
+  if (tile == kBatchCta) {
+    using Sh = CtaShape<P, double>;
+    auto kern = sweep_cta_batch_kernel<P, double, 0>;
+    VEF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C.cta_smem));
+    KTimer kt(B.meshes[C.probs[0]], VEF_K_SWEEP, s);
+    kern<<<(unsigned)C.clusters, Sh::kThreads, C.cta_smem, s>>>((const SweepArgs<double>*)C.tab_dev,
+                                                               (const int2*)C.cmap);
+    VEF_CUDA_TRY(cudaGetLastError());
+    return VEF_OK;
+  }
   const int cs = std::min(16, std::max(1, tile / 100)), warps = std::min(16, std::max(1, tile % 100));
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
@@ -1838,11 +1878,89 @@ static vef_status batch_launch(vef_batch_s& B, int p, int tile, cudaStream_t s) 
   }
 }
 
+// shared memory layout of one problem's single-CTA sweep: trace slots, then as many ring
+// buffers as fit (at most CtaShape::kMaxRing)
+template <int P>
+static vef_status cta_layout(const Schedule& S, int& tr, int& rounds, size_t& smem) {
+  using Sh = CtaShape<P, double>;
+  tr = (S.trace_slots * (P + 1) * (int)sizeof(double) + 15) / 16 * 16;
+  rounds = std::min(Sh::kMaxRing, (Sh::trace_budget(0) - tr) / Sh::kRound);
+  if (rounds < 2) {
+    set_last_error("internal error: single-CTA sweep ring does not fit in shared memory");
+    return VEF_ERR_INVALID_ARG;
+  }
+  smem = (size_t)Sh::kGroup + Sh::kBars + tr + (size_t)rounds * Sh::kRound;
+  return VEF_OK;
+}
+
 template <int P>
 static vef_status batch_prepare(const SweepCall& c, double* psi, SweepArgs<double>& a) {
   vef_status st = make_sweep_args<P, double>(c, nullptr, psi, a);
   if (st != VEF_OK) return st;
+  int tr = 0, rounds = 0;
+  size_t smem = 0;
+  if ((st = cta_layout<P>(*c.S, tr, rounds, smem)) != VEF_OK) return st;
+  a.tslot = c.S->tslot;
+  a.ring = rounds;
+  a.tr_bytes = tr;
+  a.ready = nullptr;   // no fused apply in batches: the apply runs just below
   return launch_apply<P, double, 0>(c, a);
+}
+
+template <int P>
+static size_t batch_cta_smem(const vef_batch_s& B, const BatchClass& C, vef_status* st) {
+  size_t most = 0;
+  for (int k : C.probs) {
+    int tr = 0, rounds = 0;
+    size_t smem = 0;
+    if ((*st = cta_layout<P>(*B.scheds[k], tr, rounds, smem)) != VEF_OK) return 0;
+    most = std::max(most, smem);
+  }
+  return most;
+}
+
+// ---- tuner cache: lines "<key> <tile>" in the file VEF_TUNE_CACHE names
+static std::string batch_class_key(const vef_batch_s& B, const BatchClass& C, int p) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, dev);
+  uint64_t h = 1469598103934665603ull;   // FNV-1a over the class's problems
+  auto mix = [&](long long v) {
+    for (int b = 0; b < 8; ++b) { h ^= (uint64_t)((v >> (8 * b)) & 0xff); h *= 1099511628211ull; }
+  };
+  mix(p);
+  for (int k : C.probs) {
+    const Mesh& M = *B.meshes[k];
+    mix(M.nx); mix(M.ny); mix(M.m); mix(B.scheds[k]->D); mix(B.scheds[k]->levels);
+  }
+  std::string name(prop.name);
+  for (char& ch : name) if (ch == ' ') ch = '_';
+  char buf[64];
+  snprintf(buf, sizeof(buf), "-sm%d-p%d-%016llx", prop.multiProcessorCount, p, (unsigned long long)h);
+  return name + buf;
+}
+
+static int tune_cache_lookup(const std::string& key) {
+  const char* path = std::getenv("VEF_TUNE_CACHE");
+  if (!path || !*path) return 0;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return 0;
+  char k[256];
+  int tile = 0, found = 0;
+  while (std::fscanf(f, "%255s %d", k, &tile) == 2)
+    if (key == k && (tile == kBatchCta || (tile >= 101 && tile <= 1616))) found = tile;
+  std::fclose(f);
+  return found;
+}
+
+static void tune_cache_store(const std::string& key, int tile) {
+  const char* path = std::getenv("VEF_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d\n", key.c_str(), tile);
+  std::fclose(f);
 }
 
 }  // namespace vef
@@ -1876,6 +1994,23 @@ extern "C" vef_status vef_batch_create(const vef_mesh* meshes, int nprob, const 
   for (int p = 1; p <= kMaxP; ++p) {
     BatchClass& C = B->cls[p];
     if (C.probs.empty()) continue;
+    // longest dependency chains first, so the short problems fill in behind them
+    std::stable_sort(C.probs.begin(), C.probs.end(), [&](int x, int y) {
+      const Schedule& a = *B->scheds[x];
+      const Schedule& b = *B->scheds[y];
+      return a.levels != b.levels ? a.levels > b.levels : a.members > b.members;
+    });
+    vef_status st = VEF_OK;
+    switch (p) {
+      case 1: C.cta_smem = batch_cta_smem<1>(*B, C, &st); break;
+      case 2: C.cta_smem = batch_cta_smem<2>(*B, C, &st); break;
+      case 3: C.cta_smem = batch_cta_smem<3>(*B, C, &st); break;
+      default: C.cta_smem = batch_cta_smem<4>(*B, C, &st); break;
+    }
+    if (st != VEF_OK) return st;
+    C.key = batch_class_key(*B, C, p);
+    C.tile = tune_cache_lookup(C.key);
+    C.tile_cached = C.tile != 0;
     std::vector<int2> cmap;
     for (size_t j = 0; j < C.probs.size(); ++j)
       for (int d = 0; d < B->scheds[C.probs[j]]->D; ++d) cmap.push_back(make_int2((int)j, d));
@@ -1967,7 +2102,7 @@ extern "C" vef_status vef_batch_sweep(vef_batch batch, const double* const* sigm
   for (int p = 1; p <= kMaxP; ++p) {
     BatchClass& C = B.cls[p];
     if (C.probs.empty()) continue;
-    const int tile = (opts && opts->tile_override > 0) ? opts->tile_override : (C.tile ? C.tile : kDefaultTile64);
+    const int tile = (opts && opts->tile_override > 0) ? opts->tile_override : (C.tile ? C.tile : kBatchCta);
     vef_status st = batch_launch(B, p, tile, s);
     if (st != VEF_OK) return st;
   }
@@ -2000,7 +2135,7 @@ extern "C" vef_status vef_batch_tune(vef_batch batch, void* stream, int* tiles_o
   if (!batch) { set_last_error("batch is NULL"); return VEF_ERR_INVALID_ARG; }
   if (!batch->swept) { set_last_error("call vef_batch_sweep once before tuning"); return VEF_ERR_INVALID_ARG; }
   cudaStream_t s = (cudaStream_t)stream;
-  static const int candidates[] = {204, 208, 404, 408, 804, 808, 1604};
+  static const int candidates[] = {kBatchCta, 204, 208, 404, 408, 804, 808, 1604};
   cudaEvent_t e0, e1;
   VEF_CUDA_TRY(cudaEventCreate(&e0));
   VEF_CUDA_TRY(cudaEventCreate(&e1));
@@ -2008,8 +2143,12 @@ extern "C" vef_status vef_batch_tune(vef_batch batch, void* stream, int* tiles_o
     BatchClass& C = batch->cls[p];
     if (tiles_out) tiles_out[p - 1] = 0;
     if (C.probs.empty()) continue;
+    if (C.tile_cached) {   // chosen by an earlier tuning of the same problems on this device
+      if (tiles_out) tiles_out[p - 1] = C.tile;
+      continue;
+    }
     float best = 1e30f;
-    int best_tile = kDefaultTile64;
+    int best_tile = kBatchCta;
     for (int tile : candidates) {
       vef_status st = batch_launch(*batch, p, tile, s);   // warm-up (also checks the shape launches)
       if (st != VEF_OK) {
@@ -2031,6 +2170,7 @@ extern "C" vef_status vef_batch_tune(vef_batch batch, void* stream, int* tiles_o
       }
     }
     C.tile = best_tile;
+    tune_cache_store(C.key, best_tile);
     if (tiles_out) tiles_out[p - 1] = best_tile;
   }
   cudaEventDestroy(e0);

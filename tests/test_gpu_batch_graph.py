@@ -87,6 +87,41 @@ def test_mixed_order_batch_and_graph_replay_match_the_oracle(lib):
         assert rel(host(a), ref) < 1e-12
 
 
+def test_tuner_cache_and_factor_reuse(lib, tmp_path, monkeypatch):
+    """With VEF_TUNE_CACHE set, the tuner's choices go to the file, a new batch of the same
+    problems reads them back (an order found there is not timed again, so edited choices
+    come back as written), every form reproduces the single sweeps, and a sweep keeping the
+    previous factorisation (sigma_t unchanged) gives the same psi."""
+    from paper_2301_04758_gb300.api import Batch
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("VEF_TUNE_CACHE", str(cache))
+    probs = _problems()
+    single = [host(P["mesh"].sweep(P["st"], P["ss"], P["om"], P["w"], phi_in=P["phi"], source=P["q"]))
+              for P in probs]
+    args = ([P["st"] for P in probs], [P["ss"] for P in probs])
+    kw = dict(phi_in=[P["phi"] for P in probs], source=[P["q"] for P in probs])
+    batch = Batch([P["mesh"] for P in probs], [P["om"] for P in probs], [P["w"] for P in probs])
+    batch.sweep(*args, **kw)
+    tiles = batch.tune()
+    lines = [l.split() for l in cache.read_text().splitlines()]
+    assert len(lines) == 4 and sorted(int(t) for _, t in lines) == sorted(tiles.values())
+    # rewrite every choice: the single-CTA form for p = 1, 2, a cluster shape for p = 3, 4
+    want = {}
+    with open(cache, "w") as f:
+        for key, _ in lines:
+            p = int(key.split("-p")[-1].split("-")[0])
+            want[p] = 1 if p <= 2 else 204
+            f.write(f"{key} {want[p]}\n")
+    batch2 = Batch([P["mesh"] for P in probs], [P["om"] for P in probs], [P["w"] for P in probs])
+    out = batch2.sweep(*args, **kw)
+    assert batch2.tune() == want
+    out_reuse = batch2.sweep(*args, reuse=True, **kw)
+    torch.cuda.synchronize()
+    for a, r, b in zip(out, out_reuse, single):
+        assert rel(host(a), b) < 1e-15 and rel(host(r), b) < 1e-15
+    assert len(cache.read_text().splitlines()) == 4   # nothing re-timed, nothing appended
+
+
 def test_tuning_right_after_an_unsynchronised_sweep(lib):
     """The first batched sweep returns without synchronising and the tuner starts at once:
     the argument tables still being copied for that sweep must not change under it, and
