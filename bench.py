@@ -346,11 +346,15 @@ def roofline_report(prof64, prof32, p, D, E, steps, K, hbm_gbs, fp64_meas_gflops
     traffic_of = traffic_of or ncu_traffic
     if residual_stored is None:
         residual_stored = K > 1
-    # the sweep launch also applies A^{-1} (y = A^{-1} b) on the SMs its directions leave
-    # free: its work counts with it
-    work = {"factor": (flops_factor(p), bytes_factor(p, D), FP64_PEAK_GFLOPS, FP64_SRC),
-            "sweep": (flops_sweep(p) + flops_apply(p), bytes_sweep(p) + bytes_apply(p, D),
-                      FP64_PEAK_GFLOPS, FP64_SRC),
+    # y = A^{-1} b: for a single inversion (K == 1) the factorisation forms it (2 n^2 flop and
+    # the y row written); under source iteration the sweep launch applies A^{-1} on the SMs
+    # its directions leave free, and the work counts with the sweep
+    fused = K == 1
+    ypad = (8 * n + 15) // 16 * 16
+    work = {"factor": (flops_factor(p) + (flops_apply(p) if fused else 0),
+                       bytes_factor(p, D) + (ypad if fused else 0), FP64_PEAK_GFLOPS, FP64_SRC),
+            "sweep": (flops_sweep(p) + (0 if fused else flops_apply(p)),
+                      bytes_sweep(p) + (0 if fused else bytes_apply(p, D)), FP64_PEAK_GFLOPS, FP64_SRC),
             "moments": (flops_moments(p, D), bytes_moments(p, D), FP64_PEAK_GFLOPS, FP64_SRC)}
     roof = roofline_entries(prof64, work, E * D, hbm_gbs, hbm_src)
     roofline = dominant_roofline(prof64, roof, traffic_of)
@@ -364,9 +368,14 @@ def roofline_report(prof64, prof32, p, D, E, steps, K, hbm_gbs, fp64_meas_gflops
     corr = max(s32 - K * steps, 0) / s32 if s32 else 0.0
     res = ((flops_residual(p), bytes_residual(p, D)) if residual_stored
            else (flops_residual_mf(p), bytes_residual_mf(p, D)))
-    work32 = {"factor": (flops_factor(p), bytes_factor(p, D, word=4), FP32_PEAK_GFLOPS, FP32_SRC),
-              "sweep": (flops_sweep(p) + flops_apply(p),
-                        bytes_sweep(p, word=4) + bytes_apply(p, D, word=4) + corr * 8.0 * n * (1 - 1 / D),
+    # mixed: a single inversion's first FP32 sweep has its y from the factorisation; the
+    # correction sweeps apply A^{-1} to the residual themselves
+    ypad32 = (4 * n + 15) // 16 * 16
+    work32 = {"factor": (flops_factor(p) + (flops_apply(p) if fused else 0),
+                         bytes_factor(p, D, word=4) + (ypad32 if fused else 0), FP32_PEAK_GFLOPS, FP32_SRC),
+              "sweep": (flops_sweep(p) + flops_apply(p) * (corr if fused else 1.0),
+                        bytes_sweep(p, word=4) + bytes_apply(p, D, word=4) * (corr if fused else 1.0)
+                        + corr * 8.0 * n * (1 - 1 / D),
                         FP32_PEAK_GFLOPS, FP32_SRC),
               "residual": res + (FP64_PEAK_GFLOPS, FP64_SRC),
               "moments": (flops_moments(p, D), bytes_moments(p, D), FP64_PEAK_GFLOPS, FP64_SRC)}

@@ -188,14 +188,25 @@ class KTimer {
 
 vef_status ensure_buffer(void** ptr, size_t* cap, size_t bytes);
 vef_status mesh_float_copies(Mesh* mesh, cudaStream_t stream);
+// Right-hand side of a single transport inversion, applied by the factorisation itself:
+// y = A^{-1} b for every task, written in schedule order into the mesh's y buffer, so the
+// sweep that follows needs no apply pass.  b = bvol (+ M q_d) minus the boundary inflow.
+struct FactorRhs {
+  const double* bvol = nullptr;       // [E][n] direction-independent part
+  const double* src_aniso = nullptr;  // [D][E][n] anisotropic source or null
+  const double* inflow = nullptr;     // [D][nbf][nq] or null (vacuum)
+};
+
 // Local factorisation of every (element, direction) system in `precision`.  With
 // VEF_MIXED and store_systems, also the FP64 element systems the stored-form residual of
 // the defect correction reads (S->a64); without, the residual is formed matrix-free.
 // Tasks whose unpivoted elimination meets a small pivot are refactorised with partial
 // pivoting (all tasks when force_pivot != 0); their count lands in
 // dev_status[kStatusPivoted].
+// With rhs non-null, also y = A^{-1} b (see FactorRhs).
 vef_status factor_records(Mesh* mesh, Schedule* S, const double* sigma_t, int precision,
-                          bool store_systems, int force_pivot, cudaStream_t stream);
+                          bool store_systems, int force_pivot, const FactorRhs* rhs,
+                          cudaStream_t stream);
 Schedule* get_schedule(Mesh* mesh, const double* omega, const double* weights, int D,
                        cudaStream_t stream, vef_status* st);
 

@@ -40,6 +40,58 @@ inline FaceLL<T> make_facell(const Tab1D& t) {
   return f;
 }
 
+// ------------------------------------------------------------------- fused right-hand side
+// For a single transport inversion the factorisation also forms y = A^{-1} b, with b the
+// task's right-hand side entry as the sweep's own apply forms it (bvol, the anisotropic
+// source's M q_d, minus the boundary inflow where the face point is inflow), so the sweep
+// launch that follows needs no apply pass.  bvol == null: no y.
+template <typename T>
+struct RhsArgs {
+  const double* bvol;       // [E][n]
+  const double* src_aniso;  // [D][E][n] or null
+  const double* inflow;     // [D][nbf][nq] or null
+  const double* Mm64;       // FP64 mass matrices (anisotropic source)
+  T* y;                     // y rows in schedule order, Rec<P, T>::kYStride apart
+  long long nbf;
+};
+
+template <int P, typename T>
+__device__ __forceinline__ T rhs_b(const RhsArgs<T>& r, const FaceTab<T>& ft, const T* __restrict__ nds,
+                                   int nx, int ny, long long E, int d, int e, int j, uint16_t bits, T mu,
+                                   T eta) {
+  constexpr int Q = P + 1, N = Q * Q, NQ = P + 2;
+  double b = r.bvol[(size_t)e * N + j];
+  if (r.src_aniso) {
+    const double* Mr = r.Mm64 + ((size_t)e * N + j) * N;
+    const double* qd = r.src_aniso + ((size_t)d * E + e) * N;
+#pragma unroll
+    for (int jj = 0; jj < N; ++jj) b += Mr[jj] * qd[jj];
+  }
+  T bt = (T)b;
+  if (r.inflow) {
+    const int ia = j % Q, ib = j / Q;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      if (!(bits & (1u << f))) continue;
+      if (nb_elem(nx, ny, e, f) >= 0) continue;
+      int pos = -1;
+      if (f == 0 && ib == 0) pos = ia;
+      if (f == 1 && ia == P) pos = ib;
+      if (f == 2 && ib == P) pos = ia;
+      if (f == 3 && ia == 0) pos = ib;
+      if (pos < 0) continue;
+      const double* pb = r.inflow + ((size_t)d * r.nbf + bface(nx, ny, e, f)) * NQ;
+#pragma unroll
+      for (int k = 0; k < NQ; ++k) {
+        const T* v = nds + (((size_t)e * 4 + f) * NQ + k) * 2;
+        const T sv = ft.w[k] * (mu * v[0] + eta * v[1]);
+        if (sv < (T)0) bt -= sv * (T)pb[k] * ft.l[pos][k];
+      }
+    }
+  }
+  return bt;
+}
+
 // ------------------------------------------------------------------- pivot guard
 // The element solves eliminate without pivoting.  A task whose pivot at some step falls
 // below 2^VEF_PIVOT_FLOOR_LOG2_* times the largest entry of that row of the assembled
@@ -70,14 +122,14 @@ __device__ __forceinline__ void pivot_list_append(unsigned int* count, unsigned 
 // One (element, direction) task in one thread: assemble A and the inflow couplings,
 // invert A in place by Gauss-Jordan (without pivoting and with the guard above, or with
 // partial pivoting for the fallback), write the record.  Returns whether the guard fired.
-template <int P, typename T, bool PIVOTED>
+template <int P, typename T, bool PIVOTED, bool Y>
 __device__ __forceinline__ bool factor_task(long long m, long long nmem, const uint32_t* __restrict__ code,
                                             const uint16_t* __restrict__ finfo, const double* __restrict__ omega,
                                             const double* __restrict__ sigma_t, const T* __restrict__ Mm,
                                             const T* __restrict__ Gxm, const T* __restrict__ Gym,
                                             const T* __restrict__ nds, const FaceTab<T>& ft, const FaceLL<T>& fll,
                                             int nx, int ny, long long E, T* __restrict__ rec,
-                                            unsigned int* status) {
+                                            unsigned int* status, const RhsArgs<T>& rhs) {
   constexpr int Q = P + 1, N = Q * Q, NQ = P + 2;
   using L = Rec<P, T>;
   const uint32_t c = code[m];
@@ -219,6 +271,19 @@ __device__ __forceinline__ bool factor_task(long long m, long long nmem, const u
   for (int j = 0; j < N; ++j)
 #pragma unroll
     for (int i = 0; i < N; ++i) ai[j * N + i] = A[i * N + j];
+  if (Y && rhs.bvol) {   // y = A^{-1} b (the sweep's apply, done here)
+    T b[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) b[j] = rhs_b<P, T>(rhs, ft, nds, nx, ny, E, d, e, j, bits, mu, eta);
+    T* yo = rhs.y + (size_t)m * L::kYStride;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      T yi = 0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) yi += A[i * N + j] * b[j];
+      yo[i] = yi;
+    }
+  }
   unsigned faces = 0xffffffffu;
   int slot = 0;
 #pragma unroll
@@ -241,18 +306,18 @@ __device__ __forceinline__ bool factor_task(long long m, long long nmem, const u
   return bad;
 }
 
-template <int P, typename T>
+template <int P, typename T, bool Y>
 __global__ void __launch_bounds__(128)
 factor_kernel(long long nmem, const uint32_t* __restrict__ code, const uint16_t* __restrict__ finfo,
               const double* __restrict__ omega, const double* __restrict__ sigma_t,
               const T* __restrict__ Mm, const T* __restrict__ Gxm, const T* __restrict__ Gym,
               const T* __restrict__ nds, FaceTab<T> ft, FaceLL<T> fll, int nx, int ny, long long E,
               T* __restrict__ rec, unsigned int* status, unsigned int* piv_count, unsigned int* piv_list,
-              int force_pivot) {
+              int force_pivot, RhsArgs<T> rhs) {
   const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (m >= nmem) return;
-  const bool bad = factor_task<P, T, false>(m, nmem, code, finfo, omega, sigma_t, Mm, Gxm, Gym, nds, ft, fll,
-                                            nx, ny, E, rec, status);
+  const bool bad = factor_task<P, T, false, Y>(m, nmem, code, finfo, omega, sigma_t, Mm, Gxm, Gym, nds, ft,
+                                               fll, nx, ny, E, rec, status, rhs);
   if (bad || force_pivot) pivot_list_append(piv_count, piv_list, m);
 }
 
@@ -267,12 +332,12 @@ factor_pivot_kernel(long long nmem, const uint32_t* __restrict__ code, const uin
                     const T* __restrict__ Mm, const T* __restrict__ Gxm, const T* __restrict__ Gym,
                     const T* __restrict__ nds, FaceTab<T> ft, FaceLL<T> fll, int nx, int ny, long long E,
                     T* __restrict__ rec, unsigned int* status, const unsigned int* piv_count,
-                    const unsigned int* __restrict__ piv_list) {
+                    const unsigned int* __restrict__ piv_list, RhsArgs<T> rhs) {
   const long long cnt = (long long)*piv_count;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < cnt && t < nmem;
        t += (long long)gridDim.x * blockDim.x)
-    factor_task<P, T, true>((long long)piv_list[t], nmem, code, finfo, omega, sigma_t, Mm, Gxm, Gym, nds, ft,
-                            fll, nx, ny, E, rec, status);
+    factor_task<P, T, true, true>((long long)piv_list[t], nmem, code, finfo, omega, sigma_t, Mm, Gxm, Gym, nds,
+                                  ft, fll, nx, ny, E, rec, status, rhs);
 }
 
 // Element-major factorisation (used for p >= 3, where a whole element matrix per thread
@@ -289,14 +354,14 @@ template <int P> struct ElemShape;
 template <> struct ElemShape<3> { static constexpr int RPL = 4, LPU = 4; };
 template <> struct ElemShape<4> { static constexpr int RPL = 2, LPU = 13; };
 
-template <int P, typename T>
+template <int P, typename T, bool Y>
 __global__ void __launch_bounds__(128)
 factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const uint16_t* __restrict__ finfo,
                    const double* __restrict__ omega, const double* __restrict__ sigma_t,
                    const T* __restrict__ Mm, const T* __restrict__ Gxm, const T* __restrict__ Gym,
                    const T* __restrict__ nds, FaceTab<T> ft, int nx, int ny, long long nmem,
                    T* __restrict__ rec, unsigned int* status, unsigned int* piv_count,
-                   unsigned int* piv_list, int force_pivot) {
+                   unsigned int* piv_list, int force_pivot, RhsArgs<T> rhs) {
   constexpr int Q = P + 1, N = Q * Q, NQ = P + 2;
   constexpr int RPL = ElemShape<P>::RPL, LPU = ElemShape<P>::LPU, UPW = 32 / LPU;
   constexpr int LD = N + 1;                  // padded shared-memory row stride
@@ -412,6 +477,29 @@ factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const 
         if (i >= N) continue;
 #pragma unroll
         for (int j = 0; j < N; ++j) ai[j * N + i] = row[r][j];
+      }
+    }
+    if constexpr (Y) {   // y = A^{-1} b for the owned rows (the sweep's apply, done here)
+      T bown[RPL], yr[RPL];
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        const int i = li + LPU * r;
+        bown[r] = (valid && i < N) ? rhs_b<P, T>(rhs, ft, nds, nx, ny, E, dd, (int)e, i, bits, mu, eta) : (T)0;
+        yr[r] = 0;
+      }
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const T bj = __shfl_sync(FULL, bown[j / LPU], (base + j % LPU) & 31);
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) yr[r] = fma(row[r][j], bj, yr[r]);
+      }
+      if (valid) {
+        T* yo = rhs.y + (size_t)m * L::kYStride;
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+          const int i = li + LPU * r;
+          if (i < N) yo[i] = yr[r];
+        }
       }
     }
     unsigned faces = 0xffffffffu;
@@ -919,7 +1007,7 @@ static vef_status launch_group_factor(Schedule& S, const void* rec, cudaStream_t
 
 template <int P, typename T>
 static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, bool store_systems,
-                                int force_pivot, cudaStream_t stream) {
+                                int force_pivot, const FactorRhs* rhs, cudaStream_t stream) {
   void** recp = std::is_same<T, double>::value ? &S.rec64 : &S.rec32;
   if (!*recp) {
     // zero-filled once: the W slots of faces without interior inflow are never written
@@ -966,6 +1054,12 @@ static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, boo
     vef_status st = ensure_buffer((void**)&S.pivot_list, &cap, (size_t)S.members * sizeof(unsigned int));
     if (st != VEF_OK) return st;
   }
+  RhsArgs<T> ra{};
+  if (rhs) {
+    vef_status st = ensure_buffer(&M.ybuf, &M.ybuf_cap, (size_t)S.members * Rec<P, T>::kYBytes);
+    if (st != VEF_OK) return st;
+    ra = RhsArgs<T>{rhs->bvol, rhs->src_aniso, rhs->inflow, M.Mmat, (T*)M.ybuf, M.nbf};
+  }
   unsigned int* piv_count = M.dev_status + kStatusPivoted;
   VEF_CUDA_TRY(cudaMemsetAsync(piv_count, 0, sizeof(unsigned int), stream));
   {
@@ -973,14 +1067,16 @@ static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, boo
   if constexpr (P >= 3) {
     constexpr int UPW = 32 / ElemShape<P>::LPU;
     const int warps = std::max(1, std::min(4, (S.D + UPW - 1) / UPW));
-    factor_elem_kernel<P, T><<<(unsigned)M.E, 32 * warps, 0, stream>>>(
+    auto kern = rhs ? factor_elem_kernel<P, T, true> : factor_elem_kernel<P, T, false>;
+    kern<<<(unsigned)M.E, 32 * warps, 0, stream>>>(
         S.D, M.E, S.member_of, S.faceinfo, S.omega_dev, sigma_t, Mm, Gx, Gy, nds, make_facetab<T>(M.tab),
-        M.nx, M.ny, S.members, (T*)*recp, M.dev_status, piv_count, S.pivot_list, force_pivot);
+        M.nx, M.ny, S.members, (T*)*recp, M.dev_status, piv_count, S.pivot_list, force_pivot, ra);
   } else {
-    factor_kernel<P, T><<<nblk(S.members, 128), 128, 0, stream>>>(
+    auto kern = rhs ? factor_kernel<P, T, true> : factor_kernel<P, T, false>;
+    kern<<<nblk(S.members, 128), 128, 0, stream>>>(
         S.members, S.member_code, S.faceinfo, S.omega_dev, sigma_t, Mm, Gx, Gy, nds,
         make_facetab<T>(M.tab), make_facell<T>(M.tab), M.nx, M.ny, M.E, (T*)*recp, M.dev_status,
-        piv_count, S.pivot_list, force_pivot);
+        piv_count, S.pivot_list, force_pivot, ra);
   }
   VEF_CUDA_TRY(cudaGetLastError());
   // the listed tasks again, with partial pivoting (the list's length is read on the device)
@@ -990,7 +1086,7 @@ static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, boo
   factor_pivot_kernel<P, T><<<(unsigned)std::max(1LL, std::min<long long>(nblk(S.members, 128), sms * 2LL)), 128, 0,
                               stream>>>(
       S.members, S.member_code, S.faceinfo, S.omega_dev, sigma_t, Mm, Gx, Gy, nds, make_facetab<T>(M.tab),
-      make_facell<T>(M.tab), M.nx, M.ny, M.E, (T*)*recp, M.dev_status, piv_count, S.pivot_list);
+      make_facell<T>(M.tab), M.nx, M.ny, M.E, (T*)*recp, M.dev_status, piv_count, S.pivot_list, ra);
   VEF_CUDA_TRY(cudaGetLastError());
   }
   if (S.ngroups == 0) return VEF_OK;
@@ -1003,10 +1099,10 @@ static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, boo
 
 // instantiation for one DG order (one translation unit per order keeps builds parallel)
 vef_status VEF_FACTOR_FN(Mesh* mesh, Schedule* S, const double* sigma_t, int precision,
-                         bool store_systems, int force_pivot, cudaStream_t stream) {
+                         bool store_systems, int force_pivot, const FactorRhs* rhs, cudaStream_t stream) {
   if (precision == VEF_FP64)
-    return launch_factor<VEF_FACTOR_P, double>(*mesh, *S, sigma_t, false, force_pivot, stream);
-  return launch_factor<VEF_FACTOR_P, float>(*mesh, *S, sigma_t, store_systems, force_pivot, stream);
+    return launch_factor<VEF_FACTOR_P, double>(*mesh, *S, sigma_t, false, force_pivot, rhs, stream);
+  return launch_factor<VEF_FACTOR_P, float>(*mesh, *S, sigma_t, store_systems, force_pivot, rhs, stream);
 }
 
 }  // namespace vef

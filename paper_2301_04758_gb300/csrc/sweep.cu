@@ -1281,6 +1281,8 @@ struct SweepCall {
   bool residual_stored;  // mixed: residual from stored FP64 element systems (else matrix-free)
   int force_pivot;       // refactorise every task with partial pivoting (tests of the fallback)
   bool reuse_factors;    // keep the schedule's factorisation from the previous call
+  bool fuse_rhs;         // single inversion: the factorisation also forms y = A^{-1} b
+  bool y_ready;          // y of the current right-hand side is in place: no apply pass
 };
 
 // Host-side arguments of one problem's sweep (also the batch table entries).
@@ -1421,9 +1423,11 @@ static vef_status launch_sweep_cta(const SweepCall& c, SweepArgs<T>& a) {
   cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
   VEF_CUDA_TRY(cudaStreamIsCapturing(c.stream, &capturing));
   // graph capture keeps the plain launch pair (no cooperative node in the graph)
-  if (c.apply_separate || workers < kMinApplyCtas || capturing != cudaStreamCaptureStatusNone) {
-    vef_status st = launch_apply<P, T, MODE>(c, a);
-    if (st != VEF_OK) return st;
+  if (c.y_ready || c.apply_separate || workers < kMinApplyCtas || capturing != cudaStreamCaptureStatusNone) {
+    if (!c.y_ready) {   // y already formed by the factorisation otherwise
+      vef_status st = launch_apply<P, T, MODE>(c, a);
+      if (st != VEF_OK) return st;
+    }
     KTimer kt(c.mesh, VEF_K_SWEEP, c.stream);
     kern<<<(unsigned)S.D, Sh::kThreads, smem, c.stream>>>(a);
     VEF_CUDA_TRY(cudaGetLastError());
@@ -1484,7 +1488,7 @@ static vef_status launch_sweep(const SweepCall& c0, const double* rhs, T* out) {
   SweepArgs<T> a;
   vef_status st = make_sweep_args<P, T>(c, rhs, out, a);
   if (st != VEF_OK) return st;
-  if ((st = launch_apply<P, T, MODE>(c, a)) != VEF_OK) return st;
+  if (!c.y_ready && (st = launch_apply<P, T, MODE>(c, a)) != VEF_OK) return st;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
   if ((st = cluster_config<P, T>(sweep_kernel<P, T, MODE>, c.S->D, c.cluster_size, c.cta_warps, c.stream,
@@ -1546,6 +1550,8 @@ static vef_status solve_p(const SweepCall& c, double* psi, vef_info* info) {
     KTimer kt(&M, VEF_K_SOURCE, c.stream);
     cast_add_kernel<<<nblk(tot, 256), 256, 0, c.stream>>>(tot, delta, psi, 0);
   }
+  SweepCall cc = c;      // correction sweeps apply A^{-1} to the residual themselves
+  cc.y_ready = false;
   int passes = 1;
   double rel = -1.0;
   for (int pass = 0; pass < c.max_passes; ++pass) {
@@ -1564,7 +1570,7 @@ static vef_status solve_p(const SweepCall& c, double* psi, vef_info* info) {
       VEF_CUDA_TRY(cudaMemcpyAsync(M.dev_status + 4, &bit, sizeof(bit), cudaMemcpyHostToDevice, c.stream));
       break;
     }
-    if ((st = launch_sweep<P, float, 1>(c, r, delta)) != VEF_OK) return st;
+    if ((st = launch_sweep<P, float, 1>(cc, r, delta)) != VEF_OK) return st;
     {
       KTimer kt(&M, VEF_K_SOURCE, c.stream);
       cast_add_kernel<<<nblk(tot, 256), 256, 0, c.stream>>>(tot, delta, psi, 1);
@@ -1594,11 +1600,22 @@ static vef_status solve(const SweepCall& c, double* psi, vef_info* info) {
 // The local factorisation, unless the caller asked to keep the one the schedule holds for
 // this precision (VEF_REUSE_FACTORS: sigma_t unchanged).  Any fresh factorisation may
 // follow a change of sigma_t, so it leaves only what it has just formed marked as current.
-static vef_status factor(const SweepCall& c) {
+// With c.fuse_rhs the factorisation also forms y = A^{-1} b for the current right-hand side
+// (bvol computed before), and the first sweep that follows skips its apply (c.y_ready).
+static vef_status factor(SweepCall& c) {
+  c.y_ready = false;
   const unsigned need = c.precision == VEF_FP64 ? 1u : (2u | (c.residual_stored ? 4u : 0u));
   if (c.reuse_factors && (c.S->factored & need) == need) return VEF_OK;
-  vef_status st = factor_records(c.mesh, c.S, c.sigma_t, c.precision, c.residual_stored, c.force_pivot, c.stream);
-  if (st == VEF_OK) c.S->factored = need;
+  FactorRhs rhs;
+  rhs.bvol = c.mesh->bvol;
+  rhs.src_aniso = c.src_aniso;
+  rhs.inflow = c.inflow;
+  vef_status st = factor_records(c.mesh, c.S, c.sigma_t, c.precision, c.residual_stored, c.force_pivot,
+                                 c.fuse_rhs ? &rhs : nullptr, c.stream);
+  if (st == VEF_OK) {
+    c.S->factored = need;
+    c.y_ready = c.fuse_rhs;
+  }
   return st;
 }
 
@@ -1706,6 +1723,7 @@ extern "C" vef_status vef_sweep(vef_mesh mesh, const double* sigma_t, const doub
   c.inflow = inflow;
   c.stream = s;
   fill_opts(opts, c);
+  c.fuse_rhs = !c.apply_separate;   // a single inversion: y = A^{-1} b formed with the factors
   if ((st = launch_bvol(M, sigma_s, phi_in, source_aniso ? nullptr : source, s)) != VEF_OK) return st;
   if ((st = factor(c)) != VEF_OK) return st;
   if ((st = solve(c, psi, info)) != VEF_OK) return st;

@@ -75,7 +75,9 @@ def test_roofline_of_a_single_inversion_step():
                                                        traffic_of=lambda k: None)
     units = E3 * D3
     assert main["kernel"] == "factor" and main["bound"] == "alu"
-    assert main["achieved"] == pytest.approx(11728 * units / (888.3 / 3 * 1e-3) / 1e12, rel=1e-3)
+    # a single inversion's factorisation also forms y = A^{-1} b: + 2 n^2 = 512 flop
+    assert main["achieved"] == pytest.approx((11728 + 512) * units / (888.3 / 3 * 1e-3) / 1e12, rel=1e-3)
+    assert roof["sweep"]["flops_per_launch"] == bench.flops_sweep(P3) * units
     assert "group" not in roof                    # no work model: never the reported kernel
     # 6 FP64 FMAs per psi value: far above GB300's FP64 ridge (~0.19 flop/B), so ALU-bound
     assert bench.flops_moments(P3, D3) == pytest.approx(12 * 16 + 25 * (8 * 16 + 3) / D3)

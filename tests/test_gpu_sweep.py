@@ -277,6 +277,34 @@ def test_mixed_precision_q3_s12_against_the_oracle(lib):
             assert rel(host(out[k]), rc[k]) < 1e-10, (k, kw)
 
 
+@pytest.mark.parametrize("p,sn", [(2, 8), (3, 12)])
+def test_taylor_green_mesh_from_user_control_points(lib, p, sn):
+    """The paper's third-order Taylor-Green mesh (an orthogonal mesh advected by the vortex
+    to T = 0.3 pi, 300 forward Euler steps; its x = 1 and y = 1 sides move with it), given
+    to vef_mesh_create as control points: the faces tilt enough that many are partly inflow
+    and partly outflow, so the sweep solves coupled element groups; psi matches the oracle
+    on the same control points."""
+    from vef_inputs import taylor_green_control_points
+    from paper_2301_04758_gb300.api import Mesh
+    nx = ny = 10
+    ctrl = taylor_green_control_points(nx, ny, 3)
+    prob = random_problem(nx, ny, 3, 0.0, p, sn, seed=120 + p, aniso=True)
+    mesh = Mesh(nx, ny, 3, p, 0.0, ctrl=ctrl)
+    psi, info = mesh.sweep(dev(prob["sigma_t"]), dev(prob["sigma_s"]), prob["omega"], prob["weights"],
+                           phi_in=dev(prob["phi_in"]), source=dev(prob["source"]),
+                           inflow=dev(prob["inflow"]), info=True)
+    disc = Discretization(nx, ny, 3, 0.0, p, ctrl=ctrl)
+    ref = o_sweep(disc, prob["omega"], prob["weights"], prob["sigma_t"], prob["sigma_s"],
+                  phi_in=prob["phi_in"], source=prob["source"], inflow=prob["inflow"])
+    assert info["coupled_groups"] > 0 and info["timed_out"] == 0, info
+    assert rel(host(psi), ref) < 1e-12, info
+    from oracle.moments import closures
+    out = mesh.moments(psi, prob["omega"], prob["weights"], inflow=dev(prob["inflow"]))
+    rc = closures(disc, ref, prob["omega"], prob["weights"], inflow=prob["inflow"])
+    for k in ("phi", "J", "E", "Eb", "Jin"):
+        assert rel(host(out[k]), rc[k]) < 1e-12, k
+
+
 def test_invalid_arguments_are_rejected(lib):
     import ctypes
     from paper_2301_04758_gb300 import _lib
