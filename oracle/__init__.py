@@ -18,6 +18,10 @@ What it computes (plain, slow, FP64, NumPy + SciPy):
   * iteration.py  source iteration phi^{k+1} = sum_d w_d psi_d(phi^k)
   * adjoint.py    adjoint solves L_d^T lambda_d = w_d g and the sigma gradients
   * mms.py        the manufactured solution of the paper's MMS section
+  * hrt.py        the hybridized Raviart-Thomas VEF discretisation: element-local
+                  blocks, their elimination to the multiplier system H = C1 W C2,
+                  the back substitution, and the global saddle-point solve
+                  (paper Sec. "Hybridization")
 
 The sweep's discrete equations are not written out in the paper (it defers to the
 cited transport solvers).  The oracle follows the standard once-integrated upwind DG
@@ -29,4 +33,4 @@ Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
 against closed forms, invariants, convergence orders and brute force; nothing here
 is "parity unpinned".
 """
-from . import basis, mesh, transport, moments, iteration, adjoint, mms  # noqa: F401
+from . import basis, mesh, transport, moments, iteration, adjoint, mms, hrt  # noqa: F401

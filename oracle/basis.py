@@ -61,6 +61,27 @@ def lagrange_deriv(nodes, x):
     return D
 
 
+def lagrange_deriv2(nodes, x):
+    """Second derivatives S[k, a] = l_a''(x_k): sum over ordered pairs of dropped factors."""
+    nodes = np.asarray(nodes, dtype=np.float64)
+    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    q = len(nodes)
+    S = np.zeros((len(x), q))
+    for a in range(q):
+        for k in range(q):
+            if k == a:
+                continue
+            for l in range(q):
+                if l == a or l == k:
+                    continue
+                term = np.full(len(x), 1.0 / ((nodes[a] - nodes[k]) * (nodes[a] - nodes[l])))
+                for c in range(q):
+                    if c != a and c != k and c != l:
+                        term *= (x - nodes[c]) / (nodes[a] - nodes[c])
+                S[:, a] += term
+    return S
+
+
 def tensor_values(nodes, px, py):
     """2D tensor basis l_{a}(x) l_{b}(y) at points (px[k], py[k]); dof a + (p+1) b.
     Returns (V, dV/dxi, dV/deta), each [npts][(p+1)^2]."""

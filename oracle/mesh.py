@@ -25,7 +25,7 @@ i = 0..nx-1, left column j = 0..ny-1, in that order (N_bf = 2 nx + 2 ny).
 """
 import numpy as np
 
-from .basis import gll_points, gauss_legendre, lagrange, lagrange_deriv
+from .basis import gll_points, gauss_legendre, lagrange, lagrange_deriv, lagrange_deriv2
 
 FACE_NREF = np.array([[0.0, -1.0], [1.0, 0.0], [0.0, 1.0], [-1.0, 0.0]])
 OPPOSITE = (2, 3, 0, 1)
@@ -81,6 +81,23 @@ def map_jacobian(ctrl, m, px, py):
     F[..., :, 0] = np.einsum("kc,ecd->ekd", Dxi, ctrl)   # dx/dxi, dy/dxi
     F[..., :, 1] = np.einsum("kc,ecd->ekd", Deta, ctrl)  # dx/deta, dy/deta
     return x, F
+
+
+def map_hessian(ctrl, m, px, py):
+    """Second derivatives H [E][k][i][j][l] = d^2 x_i / (dxi_j dxi_l) of the Q_m map at
+    reference points (xi_0 = xi, xi_1 = eta); symmetric in j, l."""
+    g = gll_points(m)
+    vx, vy = lagrange(g, px), lagrange(g, py)
+    dx, dy = lagrange_deriv(g, px), lagrange_deriv(g, py)
+    sx, sy = lagrange_deriv2(g, px), lagrange_deriv2(g, py)
+    q = m + 1
+    tab = lambda A, B: np.einsum("ka,kb->kba", A, B).reshape(len(px), q * q)
+    Dxx, Dxy, Dyy = tab(sx, vy), tab(dx, dy), tab(vx, sy)
+    H = np.zeros((ctrl.shape[0], len(px), 2, 2, 2))
+    for (j, l), T in (((0, 0), Dxx), ((0, 1), Dxy), ((1, 1), Dyy)):
+        H[:, :, :, j, l] = np.einsum("kc,ecd->ekd", T, ctrl)
+    H[:, :, :, 1, 0] = H[:, :, :, 0, 1]
+    return H
 
 
 def adjugate(F):
