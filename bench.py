@@ -71,10 +71,11 @@ def parse(argv=None):
     ap.add_argument("--precision", default="fp64", choices=("fp64", "mixed"), help="--sweep-only: precision")
     ap.add_argument("--apply", default="fused", choices=("fused", "separate"),
                     help="--sweep-only: y = A^-1 b inside the sweep launch or as its own launch")
-    ap.add_argument("--suite", default="", choices=("", "batch", "adjoint"),
+    ap.add_argument("--suite", default="", choices=("", "batch", "adjoint", "hrt"),
                     help="other workloads (one JSON line each, not the headline): batch = the "
                          "64-problem batch; adjoint = 128x128 Q2 S8 adjoint gradients with a "
-                         "central-difference check")
+                         "central-difference check; hrt = the hybridized RT VEF solve after a "
+                         "128x128 Q2 S8 sweep")
     ap.add_argument("--mixed-tol", type=float, default=-1.0,
                     help="mixed precision: relative residual target of the defect correction, or < 0 "
                          "for a fixed %d passes" % MIXED_PASSES)
@@ -775,6 +776,61 @@ def suite_batch(args):
             "schedule_build_s": build_s}
 
 
+def flops_hrt_local(p):
+    """Algorithmic flops of one element's hybridized RT elimination: the local blocks (A:
+    2 (p+2)^2 NJ^2 with NJ = 2 (p+2)(p+1); G: (p+2)^2 NJ (n + 8); D: 2 (p+2)^2 n NJ), the
+    Gauss-Jordan inverse of the (NJ + n) system (2 m^3), and H_e = C1 (W C2), r_e (2 NJ^2 NL4
+    + 2 NL4^2 NJ + 2 NJ m + 2 NL4 NJ, NL4 = 4 (p+1))."""
+    n, nq2 = (p + 1) ** 2, (p + 2) ** 2
+    nJ = 2 * (p + 2) * (p + 1)
+    m, nl4 = nJ + n, 4 * (p + 1)
+    return (2 * nq2 * nJ * nJ + nq2 * nJ * (n + 8) + 2 * nq2 * n * nJ + 2 * m ** 3
+            + 2 * nJ * nJ * nl4 + 2 * nl4 * nl4 * nJ + 2 * nJ * m + 2 * nl4 * nJ)
+
+
+def suite_hrt(args):
+    """Hybridized RT VEF solve after one transport inversion: 128 x 128 sine-curved Q3 mesh,
+    DG Q2 (RT_2 current), S8, seed-2 media, q = 1, vacuum: the sweep's closures give E, E_b,
+    J_in; the solve eliminates every element's local system on the GPU, solves the
+    multiplier system (Jacobi-BiCGStab) and recovers phi and J."""
+    import torch
+    from paper_2301_04758_gb300.api import Mesh
+    from vef_inputs import level_symmetric, seeded_media
+    N, p = 128, 2
+    om, w = level_symmetric(8)
+    st, ss = seeded_media(N * N, 2)
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda").contiguous()
+    mesh = Mesh(N, N, 3, p, 0.05)
+    st_d, ss_d = T(st), T(ss)
+    q = torch.ones(N * N, (p + 1) ** 2, dtype=torch.float64, device="cuda")
+    psi = mesh.sweep(st_d, ss_d, om, w, source=q)
+    mom = mesh.moments(psi, om, w, outputs=("phi", "P", "Eb", "Jin"))
+    Q0 = q * (4.0 * 3.141592653589793)      # Q0 = int q dOmega for the isotropic q = 1
+    mesh.hrt_solve(st_d, ss_d, mom["phi"], mom["P"], mom["Eb"], mom["Jin"], Q0, tol=1e-10)   # warm
+    torch.cuda.synchronize()
+    reps = max(1, min(args.steps, 5))
+    mesh.profile(True)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        phi, J, lam, info = mesh.hrt_solve(st_d, ss_d, mom["phi"], mom["P"], mom["Eb"], mom["Jin"], Q0, tol=1e-10)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) / reps
+    prof = mesh.profile_read()
+    mesh.profile(False)
+    launches, ms = prof["hrt"]
+    # the class times the local elimination and the recovery; the elimination dominates
+    local_ms = ms / reps
+    fl = flops_hrt_local(p) * N * N
+    return {"suite": "hrt", "workload": "128x128 sine-curved Q3 mesh, DG Q2 / RT_2, S8 closures, seed-2 media",
+            "elements": N * N, "multipliers": info["multipliers"], "bicgstab_iterations": info["iterations"],
+            "rel_residual": info["rel_residual"], "wall_ms_per_solve": wall * 1e3,
+            "local_elimination_and_recovery_ms": local_ms,
+            "local_roofline": {"bound": "alu", "achieved": fl / (local_ms * 1e-3) / 1e12,
+                               "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                               "frac": fl / (local_ms * 1e-3) / 1e12 / (FP64_PEAK_GFLOPS / 1e3),
+                               "flops_per_element": flops_hrt_local(p), "peak_source": FP64_SRC}}
+
+
 def suite_adjoint(args):
     """128 x 128 sine mesh, Q2, S8, seed-5 media: forward sweep, adjoint sweep and the
     gradients of R = int_[0.6,0.8]^2 phi; central differences (relative step 1e-6) on 64
@@ -894,7 +950,7 @@ def main():
     if args.suite:
         from paper_2301_04758_gb300 import build as vbuild
         vbuild.build()
-        fn = {"batch": suite_batch, "adjoint": suite_adjoint}[args.suite]
+        fn = {"batch": suite_batch, "adjoint": suite_adjoint, "hrt": suite_hrt}[args.suite]
         print(json.dumps(fn(args)))
         return
     rank = int(os.environ.get("RANK", "0"))

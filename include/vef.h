@@ -287,6 +287,43 @@ vef_status vef_batch_sweep(vef_batch batch, const double* const* sigma_t, const 
  * Synchronises `stream`. */
 vef_status vef_batch_tune(vef_batch batch, void* stream, int* tiles_out);
 
+/* Hybridized Raviart-Thomas VEF solve (paper Sec. "Hybridization": "Extension to VEF" and
+ * "Implementation Details"), the VEF step of the outer iteration that follows a transport
+ * sweep and its closures.  On the mesh's elements it discretises
+ *     div J + sigma_a phi = Q0,   div(E phi) + sigma_t J = Q1,   J.n = E_b phi + 2 J_in on the boundary
+ * (paper Eqs. zeroth, first, mlbc) with a broken RT_p current (x component in Q_{p+1} x Q_p,
+ * y component in Q_p x Q_{p+1}, nodal at the p+2 Gauss-Lobatto points across and the p+1
+ * Gauss-Legendre points along, contravariant Piola transform), the transport's DG scalar
+ * flux and degree-p Lagrange multipliers on the interior faces (nodal at the p+1
+ * Gauss-Legendre points; {E n} averaged from the two sides).  Each element's local mixed
+ * system is assembled and inverted on the GPU (block inverse [[W, X], [Y, Z]]); its share
+ * of the reduced system H = C1 W C2 for the multiplier is solved by BiCGStab with a Jacobi
+ * preconditioner (standing in for the paper's algebraic multigrid), the matrix applied
+ * element by element; the current and scalar flux then follow element by element.
+ *   sigma_t, sigma_s [device] [E];  phi_tr [device] [E][n], P_tr [device] [3][E][n]: the
+ *   transport's nodal scalar flux and second moment (vef_moments' phi and P), giving
+ *   E = P / phi at the quadrature points and on each side of each face;  Eb, Jin [device]
+ *   [N_bf][nq] (vef_moments' Eb and Jin);  Q0 [device] [E][n] nodal zeroth source moment,
+ *   Q1 [device] [2][E][n] nodal first moment or NULL (zero);
+ *   tol: relative residual of the multiplier solve; max_iter: its iteration cap;
+ *   outputs phi [device] [E][n] (DG nodal), J [device] [E][2 (p+2)(p+1)] (RT dofs: x part
+ *   a + (p+2) b, then y part a + (p+1) b), lambda [device] [faces][p+1] or NULL (interior
+ *   faces: vertical ones first, j (nx-1) + i, then horizontal, (nx-1) ny + j nx + i).
+ * Synchronises `stream` (the Krylov iteration reads its scalars back).  Uses the handle's
+ * scratch.  Errors: VEF_ERR_INVALID_ARG, VEF_ERR_NOT_CONVERGED (tolerance not reached in
+ * max_iter iterations, or a singular local system). */
+typedef struct {
+  int iterations;          /* BiCGStab iterations of the multiplier system */
+  double rel_residual;     /* final ||r - H lambda||_2 / ||r||_2 */
+  long long multipliers;   /* unknowns of the reduced system: interior faces x (p+1) */
+} vef_hrt_info;
+
+vef_status vef_hrt_solve(vef_mesh mesh, const double* sigma_t, const double* sigma_s,
+                         const double* phi_tr, const double* P_tr, const double* Eb,
+                         const double* Jin, const double* Q0, const double* Q1, double tol,
+                         int max_iter, double* phi, double* J, double* lambda,
+                         vef_hrt_info* info, void* stream);
+
 /* Kernel classes for the per-kernel timing counters. */
 enum {
   VEF_K_GEOMETRY = 0, /* mesh geometric factors */
@@ -297,7 +334,8 @@ enum {
   VEF_K_MOMENTS = 5,  /* moments, Eddington tensor, boundary factor */
   VEF_K_ADJOINT = 6,  /* adjoint sweep */
   VEF_K_GROUP = 7,    /* trace systems of the coupled element groups (after VEF_K_FACTOR) */
-  VEF_K_COUNT = 8
+  VEF_K_HRT = 8,      /* hybridized RT VEF solve: element-local elimination and recovery */
+  VEF_K_COUNT = 9
 };
 typedef struct {
   long long launches;  /* kernel launches since the counters were last reset */

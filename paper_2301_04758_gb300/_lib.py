@@ -36,10 +36,10 @@ EXPORTS = ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sy
            "vef_moments", "vef_source_iterate", "vef_adjoint_sweep", "vef_profile",
            "vef_profile_read", "vef_measure_fma_peak", "vef_wait_selftest", "vef_eddington_noalloc",
            "vef_batch_create", "vef_batch_destroy", "vef_batch_sweep", "vef_batch_tune",
-           "vef_region_weights", "vef_schedule_host", "vef_mesh_inject_status",
+           "vef_region_weights", "vef_schedule_host", "vef_mesh_inject_status", "vef_hrt_solve",
            "vef_status_string", "vef_last_error")
 
-KERNEL_CLASSES = ("geometry", "factor", "sweep", "residual", "source", "moments", "adjoint", "group")
+KERNEL_CLASSES = ("geometry", "factor", "sweep", "residual", "source", "moments", "adjoint", "group", "hrt")
 
 
 class VefOpts(ctypes.Structure):
@@ -53,6 +53,14 @@ class VefInfo(ctypes.Structure):
                 ("coupled_groups", ctypes.c_longlong), ("lagged_face_points", ctypes.c_longlong),
                 ("max_inner_iterations", ctypes.c_int), ("timed_out", ctypes.c_int),
                 ("levels", ctypes.c_int), ("pivoted_tasks", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class VefHrtInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("multipliers", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -106,12 +114,13 @@ def _declare(lib):
     lib.vef_batch_tune.argtypes = [P, P, ctypes.POINTER(ctypes.c_int)]
     lib.vef_region_weights.argtypes = [P, D, D, D, D, P, P]
     lib.vef_mesh_inject_status.argtypes = [P, ctypes.c_uint, P]
+    lib.vef_hrt_solve.argtypes = [P, P, P, P, P, P, P, P, P, D, I, P, P, P, ctypes.POINTER(VefHrtInfo), P]
     for name in ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sync",
                  "vef_sweep", "vef_moments", "vef_source_iterate", "vef_adjoint_sweep",
                  "vef_profile", "vef_profile_read", "vef_measure_fma_peak", "vef_wait_selftest",
                  "vef_eddington_noalloc", "vef_batch_create", "vef_batch_destroy",
                  "vef_batch_sweep", "vef_batch_tune", "vef_region_weights", "vef_schedule_host",
-                 "vef_mesh_inject_status"):
+                 "vef_mesh_inject_status", "vef_hrt_solve"):
         getattr(lib, name).restype = I
     lib.vef_status_string.argtypes = [I]
     lib.vef_status_string.restype = ctypes.c_char_p

@@ -175,6 +175,22 @@ class Mesh:
         _lib.check(st, "vef_source_iterate")
         return (phi, psi, dphi, inf.as_dict()) if info else (phi, psi, dphi)
 
+    def hrt_solve(self, sigma_t, sigma_s, phi_tr, P_tr, Eb, Jin, Q0, Q1=None, tol=1e-13, max_iter=2000,
+                  stream=None):
+        """Hybridized RT VEF solve (see vef_hrt_solve in include/vef.h): returns
+        (phi [E][n], J [E][2 (p+2)(p+1)], lambda [faces][p+1], info dict)."""
+        nJ = 2 * (self.p + 2) * (self.p + 1)
+        nfaces = (self.nx - 1) * self.ny + self.nx * (self.ny - 1)
+        phi = self._empty(self.E, self.n)
+        J = self._empty(self.E, nJ)
+        lam = self._empty(max(nfaces, 1), self.p + 1)
+        inf = _lib.VefHrtInfo()
+        st = self.lib.vef_hrt_solve(self.handle, _ptr(sigma_t), _ptr(sigma_s), _ptr(phi_tr), _ptr(P_tr),
+                                    _ptr(Eb), _ptr(Jin), _ptr(Q0), _ptr(Q1), float(tol), int(max_iter),
+                                    _ptr(phi), _ptr(J), _ptr(lam), ctypes.byref(inf), _stream(stream))
+        _lib.check(st, "vef_hrt_solve")
+        return phi, J, lam[:nfaces], inf.as_dict()
+
     def region_weights(self, lo=(0.6, 0.6), hi=(0.8, 0.8), stream=None):
         """g [E][n] with sum g * phi = int over the box [lo, hi] of phi dx."""
         g = self._empty(self.E, self.n)

@@ -209,6 +209,8 @@ vef_status factor_records(Mesh* mesh, Schedule* S, const double* sigma_t, int pr
                           cudaStream_t stream);
 Schedule* get_schedule(Mesh* mesh, const double* omega, const double* weights, int D,
                        cudaStream_t stream, vef_status* st);
+// Waits for `stream`, reads and clears the handle's device status word, maps it to a status.
+vef_status collect_status(Mesh& M, cudaStream_t stream, vef_info* info);
 
 }  // namespace vef
 
