@@ -71,11 +71,12 @@ def parse(argv=None):
     ap.add_argument("--precision", default="fp64", choices=("fp64", "mixed"), help="--sweep-only: precision")
     ap.add_argument("--apply", default="fused", choices=("fused", "separate"),
                     help="--sweep-only: y = A^-1 b inside the sweep launch or as its own launch")
-    ap.add_argument("--suite", default="", choices=("", "batch", "adjoint", "hrt"),
+    ap.add_argument("--suite", default="", choices=("", "batch", "adjoint", "hrt", "vef"),
                     help="other workloads (one JSON line each, not the headline): batch = the "
                          "64-problem batch; adjoint = 128x128 Q2 S8 adjoint gradients with a "
                          "central-difference check; hrt = the hybridized RT VEF solve after a "
-                         "128x128 Q2 S8 sweep")
+                         "128x128 Q2 S8 sweep; vef = the VEF fixed-point iteration on a 64x64 "
+                         "thick-diffusion-limit problem")
     ap.add_argument("--mixed-tol", type=float, default=-1.0,
                     help="mixed precision: relative residual target of the defect correction, or < 0 "
                          "for a fixed %d passes" % MIXED_PASSES)
@@ -806,13 +807,15 @@ def suite_hrt(args):
     psi = mesh.sweep(st_d, ss_d, om, w, source=q)
     mom = mesh.moments(psi, om, w, outputs=("phi", "P", "Eb", "Jin"))
     Q0 = q * (4.0 * 3.141592653589793)      # Q0 = int q dOmega for the isotropic q = 1
-    mesh.hrt_solve(st_d, ss_d, mom["phi"], mom["P"], mom["Eb"], mom["Jin"], Q0, tol=1e-10)   # warm
+    solve = lambda: mesh.hrt_solve(st_d, ss_d, mom["phi"], mom["P"], mom["Eb"], mom["Jin"], Q0, tol=1e-8,
+                                   max_iter=20000, check=False)
+    solve()   # warm
     torch.cuda.synchronize()
     reps = max(1, min(args.steps, 5))
     mesh.profile(True)
     t0 = time.perf_counter()
     for _ in range(reps):
-        phi, J, lam, info = mesh.hrt_solve(st_d, ss_d, mom["phi"], mom["P"], mom["Eb"], mom["Jin"], Q0, tol=1e-10)
+        phi, J, lam, info = solve()
     torch.cuda.synchronize()
     wall = (time.perf_counter() - t0) / reps
     prof = mesh.profile_read()
@@ -823,12 +826,47 @@ def suite_hrt(args):
     fl = flops_hrt_local(p) * N * N
     return {"suite": "hrt", "workload": "128x128 sine-curved Q3 mesh, DG Q2 / RT_2, S8 closures, seed-2 media",
             "elements": N * N, "multipliers": info["multipliers"], "bicgstab_iterations": info["iterations"],
-            "rel_residual": info["rel_residual"], "wall_ms_per_solve": wall * 1e3,
+            "rel_residual": info["rel_residual"], "bicgstab_converged_to_1e-8": info["converged"],
+            "wall_ms_per_solve": wall * 1e3,
             "local_elimination_and_recovery_ms": local_ms,
             "local_roofline": {"bound": "alu", "achieved": fl / (local_ms * 1e-3) / 1e12,
                                "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
                                "frac": fl / (local_ms * 1e-3) / 1e12 / (FP64_PEAK_GFLOPS / 1e3),
                                "flops_per_element": flops_hrt_local(p), "peak_source": FP64_SRC}}
+
+
+def suite_vef(args):
+    """The VEF fixed-point iteration (sweep, closures, hybridized RT VEF solve per iteration)
+    on the thick-diffusion-limit recipe at a larger size: 64 x 64 orthogonal mesh, DG Q2,
+    S8, sigma_t = 1/eps, sigma_s = 1/eps - eps, q = eps, eps = 1e-2, vacuum, tolerance 1e-6
+    on the max norm of successive scalar fluxes."""
+    import torch
+    from paper_2301_04758_gb300.api import Mesh
+    from vef_inputs import level_symmetric
+    N, p, eps = 64, 2, 1e-2
+    om, w = level_symmetric(8)
+    mesh = Mesh(N, N, 1, p, 0.0)
+    E, n = mesh.E, mesh.n
+    st = torch.full((E,), 1.0 / eps, dtype=torch.float64, device="cuda")
+    ss = torch.full((E,), 1.0 / eps - eps, dtype=torch.float64, device="cuda")
+    q = torch.full((E, n), eps, dtype=torch.float64, device="cuda")
+    mesh.vef_iterate(st, ss, om, w, source=q, tol=1e-6, hrt_tol=1e-10)     # warm (schedules, buffers)
+    torch.cuda.synchronize()
+    mesh.profile(True)
+    t0 = time.perf_counter()
+    phi, J, psi, dphi, info = mesh.vef_iterate(st, ss, om, w, source=q, tol=1e-6, hrt_tol=1e-10)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    prof = mesh.profile_read()
+    mesh.profile(False)
+    its = info["iterations"]
+    return {"suite": "vef", "workload": "64x64 orthogonal mesh, DG Q2 / RT_2, S8, thick diffusion limit eps = 1e-2",
+            "iterations": its, "converged": info["converged"], "last_change": info["last_change"],
+            "hrt_bicgstab_iterations": info["hrt_iterations"], "wall_ms": wall * 1e3,
+            "wall_ms_per_iteration": wall * 1e3 / max(its, 1),
+            "angular_dof_updates_per_s": E * n * len(w) * its / wall,
+            "kernels_ms": {k: round(v[1], 3) for k, v in prof.items() if v[0]},
+            "dphi": [float(x) for x in dphi.cpu()]}
 
 
 def suite_adjoint(args):
@@ -950,7 +988,7 @@ def main():
     if args.suite:
         from paper_2301_04758_gb300 import build as vbuild
         vbuild.build()
-        fn = {"batch": suite_batch, "adjoint": suite_adjoint, "hrt": suite_hrt}[args.suite]
+        fn = {"batch": suite_batch, "adjoint": suite_adjoint, "hrt": suite_hrt, "vef": suite_vef}[args.suite]
         print(json.dumps(fn(args)))
         return
     rank = int(os.environ.get("RANK", "0"))

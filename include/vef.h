@@ -324,6 +324,39 @@ vef_status vef_hrt_solve(vef_mesh mesh, const double* sigma_t, const double* sig
                          int max_iter, double* phi, double* J, double* lambda,
                          vef_hrt_info* info, void* stream);
 
+/* VEF fixed-point iteration (paper Sec. "VEF Algorithm"): from phi^0 ([device] [E][n],
+ * NULL = 0), repeat
+ *   1) invert the transport equation with the scattering source sigma_s phi^k / (4 pi) + q
+ *      (vef_sweep; the factorisation is formed on the first iteration and kept after it,
+ *      sigma_t being fixed; opts selects the precision and sweep forms as for vef_sweep);
+ *   2) form the Eddington tensor, boundary factor and inflow partial current from its
+ *      angular flux (vef_moments);
+ *   3) solve the VEF equations by the hybridized RT method (vef_hrt_solve) with
+ *      Q0 = 4 pi q and Q1 = 0, and take their scalar flux as phi^{k+1};
+ * until max |phi^{k+1} - phi^k| <= tol (the max norm of the difference of successive
+ * iterates, the paper's stopping rule) or max_outer iterations.
+ *   source [device] [E][n] isotropic q per steradian (NULL = 0); inflow [device]
+ *   [D][N_bf][nq] or NULL (vacuum); omega, weights [host] as for vef_sweep;
+ *   hrt_tol, hrt_max_iter: the multiplier solve of each VEF step;
+ *   phi_out [device] [E][n] the last VEF scalar flux; J_out [device] [E][2 (p+2)(p+1)] its
+ *   current (RT dofs) or NULL; psi [device] [D][E][n] the last transport solution
+ *   (required); dphi [device] [max_outer] the max-norm changes, or NULL.
+ * Synchronises `stream`.  Returns VEF_ERR_NOT_CONVERGED if max_outer iterations did not
+ * reach tol (the outputs then hold the last iterate). */
+typedef struct {
+  int iterations;        /* fixed-point iterations performed */
+  int converged;         /* 1 if the last change was <= tol */
+  double last_change;    /* max |phi^{k+1} - phi^k| of the last iteration */
+  int hrt_iterations;    /* BiCGStab iterations summed over the VEF solves */
+} vef_vef_info;
+
+vef_status vef_vef_iterate(vef_mesh mesh, const double* sigma_t, const double* sigma_s,
+                           const double* source, const double* inflow, const double* omega,
+                           const double* weights, int D, const double* phi0, int max_outer,
+                           double tol, double hrt_tol, int hrt_max_iter, const vef_opts* opts,
+                           double* phi_out, double* J_out, double* psi, double* dphi,
+                           vef_vef_info* info, void* stream);
+
 /* Kernel classes for the per-kernel timing counters. */
 enum {
   VEF_K_GEOMETRY = 0, /* mesh geometric factors */

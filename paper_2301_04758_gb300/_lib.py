@@ -37,6 +37,7 @@ EXPORTS = ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sy
            "vef_profile_read", "vef_measure_fma_peak", "vef_wait_selftest", "vef_eddington_noalloc",
            "vef_batch_create", "vef_batch_destroy", "vef_batch_sweep", "vef_batch_tune",
            "vef_region_weights", "vef_schedule_host", "vef_mesh_inject_status", "vef_hrt_solve",
+           "vef_vef_iterate",
            "vef_status_string", "vef_last_error")
 
 KERNEL_CLASSES = ("geometry", "factor", "sweep", "residual", "source", "moments", "adjoint", "group", "hrt")
@@ -61,6 +62,14 @@ class VefInfo(ctypes.Structure):
 class VefHrtInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("multipliers", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class VefVefInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("last_change", ctypes.c_double),
+                ("hrt_iterations", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -115,12 +124,14 @@ def _declare(lib):
     lib.vef_region_weights.argtypes = [P, D, D, D, D, P, P]
     lib.vef_mesh_inject_status.argtypes = [P, ctypes.c_uint, P]
     lib.vef_hrt_solve.argtypes = [P, P, P, P, P, P, P, P, P, D, I, P, P, P, ctypes.POINTER(VefHrtInfo), P]
+    lib.vef_vef_iterate.argtypes = [P, P, P, P, P, P, P, I, P, I, D, D, I, ctypes.POINTER(VefOpts), P, P, P, P,
+                                    ctypes.POINTER(VefVefInfo), P]
     for name in ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sync",
                  "vef_sweep", "vef_moments", "vef_source_iterate", "vef_adjoint_sweep",
                  "vef_profile", "vef_profile_read", "vef_measure_fma_peak", "vef_wait_selftest",
                  "vef_eddington_noalloc", "vef_batch_create", "vef_batch_destroy",
                  "vef_batch_sweep", "vef_batch_tune", "vef_region_weights", "vef_schedule_host",
-                 "vef_mesh_inject_status", "vef_hrt_solve"):
+                 "vef_mesh_inject_status", "vef_hrt_solve", "vef_vef_iterate"):
         getattr(lib, name).restype = I
     lib.vef_status_string.argtypes = [I]
     lib.vef_status_string.restype = ctypes.c_char_p

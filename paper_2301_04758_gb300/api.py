@@ -176,9 +176,11 @@ class Mesh:
         return (phi, psi, dphi, inf.as_dict()) if info else (phi, psi, dphi)
 
     def hrt_solve(self, sigma_t, sigma_s, phi_tr, P_tr, Eb, Jin, Q0, Q1=None, tol=1e-13, max_iter=2000,
-                  stream=None):
+                  check=True, stream=None):
         """Hybridized RT VEF solve (see vef_hrt_solve in include/vef.h): returns
-        (phi [E][n], J [E][2 (p+2)(p+1)], lambda [faces][p+1], info dict)."""
+        (phi [E][n], J [E][2 (p+2)(p+1)], lambda [faces][p+1], info dict).  check=False
+        returns the last iterate with info["converged"] = False instead of raising when the
+        multiplier solve stops at max_iter."""
         nJ = 2 * (self.p + 2) * (self.p + 1)
         nfaces = (self.nx - 1) * self.ny + self.nx * (self.ny - 1)
         phi = self._empty(self.E, self.n)
@@ -188,8 +190,36 @@ class Mesh:
         st = self.lib.vef_hrt_solve(self.handle, _ptr(sigma_t), _ptr(sigma_s), _ptr(phi_tr), _ptr(P_tr),
                                     _ptr(Eb), _ptr(Jin), _ptr(Q0), _ptr(Q1), float(tol), int(max_iter),
                                     _ptr(phi), _ptr(J), _ptr(lam), ctypes.byref(inf), _stream(stream))
-        _lib.check(st, "vef_hrt_solve")
-        return phi, J, lam[:nfaces], inf.as_dict()
+        if check or st != _lib.VEF_ERR_NOT_CONVERGED:
+            _lib.check(st, "vef_hrt_solve")
+        d = inf.as_dict()
+        d["converged"] = st == _lib.VEF_OK
+        return phi, J, lam[:nfaces], d
+
+    def vef_iterate(self, sigma_t, sigma_s, omega, weights, source=None, inflow=None, phi0=None, max_outer=50,
+                    tol=1e-6, hrt_tol=1e-12, hrt_max_iter=5000, precision="fp64", psi=None, check=True,
+                    stream=None):
+        """VEF fixed-point iteration (see vef_vef_iterate in include/vef.h): returns
+        (phi [E][n], J [E][2 (p+2)(p+1)], psi [D][E][n], dphi [iterations], info dict)."""
+        om, omp = _host(omega)
+        w, wp = _host(weights)
+        D = len(w)
+        nJ = 2 * (self.p + 2) * (self.p + 1)
+        phi = self._empty(self.E, self.n)
+        J = self._empty(self.E, nJ)
+        if psi is None:
+            psi = self._empty(D, self.E, self.n)
+        dphi = self._empty(max_outer)
+        inf = _lib.VefVefInfo()
+        o = _opts(precision)
+        st = self.lib.vef_vef_iterate(self.handle, _ptr(sigma_t), _ptr(sigma_s), _ptr(source), _ptr(inflow), omp,
+                                      wp, D, _ptr(phi0), int(max_outer), float(tol), float(hrt_tol),
+                                      int(hrt_max_iter), ctypes.byref(o), _ptr(phi), _ptr(J), _ptr(psi),
+                                      _ptr(dphi), ctypes.byref(inf), _stream(stream))
+        if check or st != _lib.VEF_ERR_NOT_CONVERGED:
+            _lib.check(st, "vef_vef_iterate")
+        d = inf.as_dict()
+        return phi, J, psi, dphi[:d["iterations"]], d
 
     def region_weights(self, lo=(0.6, 0.6), hi=(0.8, 0.8), stream=None):
         """g [E][n] with sum g * phi = int over the box [lo, hi] of phi dx."""

@@ -170,6 +170,8 @@ struct Mesh {
   size_t ybuf_cap = 0;
   int* ready_flags = nullptr;    // [D][bands] band flags of the sweep's fused apply
   size_t ready_cap = 0;
+  void* vef_work = nullptr;      // VEF fixed-point iteration: iterates, moments, closures
+  size_t vef_work_cap = 0;
   ~Mesh();
 };
 

@@ -228,6 +228,7 @@ Mesh::~Mesh() {
   cudaFree(Gy32);
   cudaFree(nds32);
   cudaFree(dev_status);
+  cudaFree(vef_work);
   cudaFree(bvol);
   cudaFree(work);
   cudaFree(work2);
