@@ -85,8 +85,10 @@ enum {
                                thread-block cluster, as the batched sweep does, instead of
                                one CTA */
   VEF_APPLY_SEPARATE = 4,   /* compute y = A^{-1} b by a launch of its own before the
-                               single-CTA sweep; by default the SMs the directions leave
-                               free do it inside the sweep launch, which is then a
+                               single-CTA sweep (always so for p >= 3, whose A^{-1} reads
+                               the free SMs alone cannot stream fast enough); by default,
+                               for p <= 2, the SMs the directions leave free do it inside
+                               the sweep launch, which is then a
                                cooperative launch sized from the device's SM count (a
                                context limited to fewer SMs, e.g. under MPS, should set
                                this flag: the driver refuses a cooperative grid that
@@ -297,9 +299,10 @@ vef_status vef_batch_tune(vef_batch batch, void* stream, int* tiles_out);
  * flux and degree-p Lagrange multipliers on the interior faces (nodal at the p+1
  * Gauss-Legendre points; {E n} averaged from the two sides).  Each element's local mixed
  * system is assembled and inverted on the GPU (block inverse [[W, X], [Y, Z]]); its share
- * of the reduced system H = C1 W C2 for the multiplier is solved by BiCGStab with a Jacobi
- * preconditioner (standing in for the paper's algebraic multigrid), the matrix applied
- * element by element; the current and scalar flux then follow element by element.
+ * of the reduced system H = C1 W C2 for the multiplier is solved by BiCGStab with a
+ * face-block Jacobi preconditioner (the (p+1)-square diagonal block of H per interior face,
+ * standing in for the paper's algebraic multigrid), the matrix applied face by face from
+ * the elements' H_e; the current and scalar flux then follow element by element.
  *   sigma_t, sigma_s [device] [E];  phi_tr [device] [E][n], P_tr [device] [3][E][n]: the
  *   transport's nodal scalar flux and second moment (vef_moments' phi and P), giving
  *   E = P / phi at the quadrature points and on each side of each face;  Eb, Jin [device]
@@ -309,7 +312,8 @@ vef_status vef_batch_tune(vef_batch batch, void* stream, int* tiles_out);
  *   outputs phi [device] [E][n] (DG nodal), J [device] [E][2 (p+2)(p+1)] (RT dofs: x part
  *   a + (p+2) b, then y part a + (p+1) b), lambda [device] [faces][p+1] or NULL (interior
  *   faces: vertical ones first, j (nx-1) + i, then horizontal, (nx-1) ny + j nx + i).
- * Synchronises `stream` (the Krylov iteration reads its scalars back).  Uses the handle's
+ * Synchronises `stream` (the Krylov scalars stay on the device; the host reads the
+ * convergence state back every 16 iterations).  Uses the handle's
  * scratch.  Errors: VEF_ERR_INVALID_ARG, VEF_ERR_NOT_CONVERGED (tolerance not reached in
  * max_iter iterations, or a singular local system). */
 typedef struct {

@@ -11,14 +11,16 @@
 //                                             f  = int u Q0
 // with C2 lambda = int_G0 (v.{E} n) lambda (the face multipliers) and the constraint
 // C1 J = int_G0 mu [[J.n]] = 0.  hrt_local_kernel assembles these blocks for one element per
-// CTA in shared memory, inverts [[A, G], [D, Ma]] by Gauss-Jordan elimination with partial
-// pivoting (the block is indefinite in general), and forms the element's share of the
-// reduced system,
+// CTA in shared memory (the map's derivatives and the Eddington tensor evaluated once per
+// Gauss point; D and C1 are the same on every element and come from host tables), inverts
+// [[A, G], [D, Ma]] by Gauss-Jordan elimination with partial pivoting (the block is
+// indefinite in general), and forms the element's share of the reduced system,
 //     H_e = C1 W C2,   r_e = C1 (W g + X f),   [[W, X], [Y, Z]] = [[A, G], [D, Ma]]^{-1}.
 // The multiplier system H lambda = r (H = sum_e H_e over the interior faces, not symmetric
-// for a general Eddington tensor) is solved by BiCGStab with a Jacobi preconditioner,
-// the matrix applied element by element (z_e = H_e lambda_e, then a per-face gather of the
-// two sides, no atomics).  hrt_recover_kernel then forms J and phi element by element.
+// for a general Eddington tensor) is solved by BiCGStab with a face-block Jacobi
+// preconditioner, the matrix applied face by face from the two sides' rows of H_e (no
+// atomics) and the Krylov scalars kept on the device.  hrt_recover_kernel then forms J and
+// phi element by element.
 //
 // Spaces (identical to the CPU reference of this discretisation): RT_p on the reference
 // square with the x component in Q_{p+1} x Q_p and the y component in Q_p x Q_{p+1}, nodal
@@ -106,7 +108,7 @@ struct HrtShape {
 
 // reference RT basis function a at table points (kx, ky): value (2) and d/dxi, d/deta (2 each)
 template <int P>
-__device__ __forceinline__ void rt_ref(const HrtTab& t, int a, int kx, int ky, double v[2], double dxi[2],
+__host__ __device__ __forceinline__ void rt_ref(const HrtTab& t, int a, int kx, int ky, double v[2], double dxi[2],
                                        double deta[2]) {
   using S = HrtShape<P>;
   v[0] = v[1] = dxi[0] = dxi[1] = deta[0] = deta[1] = 0.0;
@@ -143,7 +145,7 @@ __device__ __forceinline__ void map_geom(const double* __restrict__ c, const Hrt
 }
 
 // face-point table indices of face f, point k
-__device__ __forceinline__ void face_pt(int f, int k, int nq, int& kx, int& ky) {
+__host__ __device__ __forceinline__ void face_pt(int f, int k, int nq, int& kx, int& ky) {
   kx = f == 0 ? k : (f == 1 ? nq + 1 : (f == 2 ? k : nq));
   ky = f == 0 ? nq : (f == 1 ? k : (f == 2 ? nq + 1 : k));
 }
@@ -195,9 +197,53 @@ struct HrtOut {
   double* re;   // [E][NL4]
 };
 
+// Geometry-independent blocks of the local system, formed once on the host from the same
+// 1D tables: D_ref [n][NJ] = int u div_hat v_hat (the Piola transform makes int u div J dx
+// the reference integral) and C1_ref [4 (p+1)][NJ] = int_f mu (v_hat . n_hat) (the reference
+// normal flux against the multiplier basis; rows of boundary faces are dropped per element).
+struct HrtRef {
+  const double* D;    // [n][NJ]
+  const double* C1;   // [4 (p+1)][NJ]
+};
+
+template <int P>
+static void make_hrt_ref(const HrtTab& t, std::vector<double>& out) {
+  using S = HrtShape<P>;
+  constexpr int Q = P + 1, N = S::N, NQ = S::NQ, NJ = S::NJ, NL = S::NL;
+  out.assign((size_t)N * NJ + (size_t)4 * NL * NJ, 0.0);
+  for (int r = 0; r < N; ++r)
+    for (int c = 0; c < NJ; ++c) {
+      double s = 0.0;
+      for (int k2 = 0; k2 < NQ; ++k2)
+        for (int k1 = 0; k1 < NQ; ++k1) {
+          double vh[2], dx[2], dy[2];
+          rt_ref<P>(t, c, k1, k2, vh, dx, dy);
+          s += t.w[k1] * t.w[k2] * t.dg[r % Q][k1] * t.dg[r / Q][k2] * (dx[0] + dy[1]);
+        }
+      out[(size_t)r * NJ + c] = s;
+    }
+  double* C1 = out.data() + (size_t)N * NJ;
+  for (int f = 0; f < 4; ++f) {
+    const double n0 = f == 1 ? 1.0 : (f == 3 ? -1.0 : 0.0), n1 = f == 2 ? 1.0 : (f == 0 ? -1.0 : 0.0);
+    for (int tt = 0; tt < NL; ++tt)
+      for (int a = 0; a < NJ; ++a) {
+        double s = 0.0;
+        for (int k = 0; k < NQ; ++k) {
+          int kx, ky;
+          face_pt(f, k, NQ, kx, ky);
+          double vh[2], dx[2], dy[2];
+          rt_ref<P>(t, a, kx, ky, vh, dx, dy);
+          s += t.w[k] * t.op[tt][k] * (vh[0] * n0 + vh[1] * n1);
+        }
+        C1[(size_t)(f * NL + tt) * NJ + a] = s;
+      }
+  }
+}
+
 template <int P>
 struct HrtSmem {
   using S = HrtShape<P>;
+  static constexpr int NF = 4 * S::NQ;   // face points
   double L[S::MM * S::LD];
   double vq[S::NQ2][S::NJ][2];       // physical v at the volume points
   double sg[S::NJ][S::NQ2];          // -w J (grad v : E) at the volume points
@@ -209,37 +255,102 @@ struct HrtSmem {
   double u[S::NJ];                   // W g + X f
   double colk[S::MM];
   double ctrl[(kMaxM + 1) * (kMaxM + 1) * 2];
+  // per volume point: F (4, row-major), J, dJ/dxi (2), second derivatives (8), E (3), Q1 (2)
+  double pv[S::NQ2][20];
+  // per face point: interior faces w (F^T {E} n ds) / J (2); boundary faces (F^T E n^) / J (2),
+  // (F^T n^) / J (2), w |n ds| / E_b and 2 w |n ds| J_in / E_b
+  double pf[NF][6];
+  double pa[S::NQ][S::NJ], pb[S::NQ][S::NJ];   // boundary face: v_hat . the two vectors above
   int perm[S::MM];
   int piv;
 };
 
 template <int P>
 __global__ void __launch_bounds__(256)
-hrt_local_kernel(long long E, int nx, int ny, HrtTab t, HrtIn in, HrtOut out, unsigned int* status) {
+hrt_local_kernel(long long E, int nx, int ny, HrtTab t, HrtRef ref, HrtIn in, HrtOut out, unsigned int* status) {
   using S = HrtShape<P>;
   constexpr int N = S::N, NQ = S::NQ, NQ2 = S::NQ2, NJ = S::NJ, MM = S::MM, LD = S::LD, NL = S::NL, NL4 = S::NL4;
+  constexpr int NF = HrtSmem<P>::NF;
   extern __shared__ __align__(16) unsigned char hrt_smem[];
   HrtSmem<P>& sm = *reinterpret_cast<HrtSmem<P>*>(hrt_smem);
   const int tid = threadIdx.x, nth = blockDim.x;
   const long long En = E * N;
-  const long long nbf = 2LL * nx + 2LL * ny;
   const int qc = (t.m + 1) * (t.m + 1);
   for (long long e = blockIdx.x; e < E; e += gridDim.x) {
     __syncthreads();
     for (int i = tid; i < 2 * qc; i += nth) sm.ctrl[i] = in.ctrl[(size_t)e * 2 * qc + i];
     const double st = in.sigma_t[e], sa = in.sigma_t[e] - in.sigma_s[e];
     __syncthreads();
-    // volume points: physical v and -w J (grad v : E) for every basis function
+    // (1) once per point: the map's derivatives and the Eddington tensor (both sides of an
+    // interior face, averaged), at the volume and face Gauss points
+    for (int pt = tid; pt < NQ2 + NF; pt += nth) {
+      const bool vol = pt < NQ2;
+      const int f = vol ? -1 : (pt - NQ2) / NQ, k = vol ? 0 : (pt - NQ2) % NQ;
+      int kx, ky;
+      if (vol) { kx = pt % NQ; ky = pt / NQ; }
+      else face_pt(f, k, NQ, kx, ky);
+      double F[4], H[8];
+      map_geom(sm.ctrl, t, kx, ky, F, H);
+      const double J = F[0] * F[3] - F[1] * F[2];
+      double B[N], Eo[3];
+      dg_at<P>(t, kx, ky, B);
+      eddington_at<N>(in.phi, in.P, En, e, B, Eo);
+      if (vol) {
+        double* g = sm.pv[pt];
+        const double adj[4] = {F[3], -F[1], -F[2], F[0]};
+        for (int i = 0; i < 4; ++i) g[i] = F[i];
+        g[4] = J;
+        for (int l = 0; l < 2; ++l)   // Jacobi's formula: dJ = tr(adj F dF)
+          g[5 + l] = adj[0] * H[0 * 4 + 0 * 2 + l] + adj[1] * H[1 * 4 + 0 * 2 + l] +
+                     adj[2] * H[0 * 4 + 1 * 2 + l] + adj[3] * H[1 * 4 + 1 * 2 + l];
+        for (int i = 0; i < 8; ++i) g[7 + i] = H[i];
+        for (int i = 0; i < 3; ++i) g[15 + i] = Eo[i];
+        double q1x = 0.0, q1y = 0.0;
+        if (in.Q1)
+          for (int j = 0; j < N; ++j) {
+            q1x += B[j] * in.Q1[(size_t)e * N + j];
+            q1y += B[j] * in.Q1[En + (size_t)e * N + j];
+          }
+        g[18] = q1x;
+        g[19] = q1y;
+      } else {
+        double* o = sm.pf[pt - NQ2];
+        const double* nd = in.nds + (((size_t)e * 4 + f) * NQ + k) * 2;
+        const int nb = nb_elem(nx, ny, (int)e, f);
+        if (nb >= 0) {
+          int nkx, nky;
+          face_pt((f + 2) & 3, k, NQ, nkx, nky);
+          double Bn[N], Enb[3];
+          dg_at<P>(t, nkx, nky, Bn);
+          eddington_at<N>(in.phi, in.P, En, nb, Bn, Enb);
+          const double a00 = 0.5 * (Eo[0] + Enb[0]), a01 = 0.5 * (Eo[1] + Enb[1]), a11 = 0.5 * (Eo[2] + Enb[2]);
+          const double En0 = a00 * nd[0] + a01 * nd[1], En1 = a01 * nd[0] + a11 * nd[1];
+          // v_a . {E} n ds = v_hat_a . F^T ({E} n ds) / J
+          o[0] = t.w[k] * (F[0] * En0 + F[2] * En1) / J;
+          o[1] = t.w[k] * (F[1] * En0 + F[3] * En1) / J;
+        } else {
+          const long long bf = bface(nx, ny, (int)e, f);
+          const double ln = sqrt(nd[0] * nd[0] + nd[1] * nd[1]);
+          const double un0 = nd[0] / ln, un1 = nd[1] / ln;
+          const double En0 = Eo[0] * un0 + Eo[1] * un1, En1 = Eo[1] * un0 + Eo[2] * un1;
+          const double eb = in.Eb[bf * NQ + k];
+          o[0] = (F[0] * En0 + F[2] * En1) / J;
+          o[1] = (F[1] * En0 + F[3] * En1) / J;
+          o[2] = (F[0] * un0 + F[2] * un1) / J;
+          o[3] = (F[1] * un0 + F[3] * un1) / J;
+          o[4] = t.w[k] * ln / eb;
+          o[5] = 2.0 * t.w[k] * ln * in.Jin[bf * NQ + k] / eb;
+        }
+      }
+    }
+    __syncthreads();
+    // (2) per (volume point, basis function): the physical v and -w J (grad v : E)
     for (int idx = tid; idx < NQ2 * NJ; idx += nth) {
       const int q = idx / NJ, a = idx % NJ, k1 = q % NQ, k2 = q / NQ;
-      double F[4], H[8];
-      map_geom(sm.ctrl, t, k1, k2, F, H);
-      const double J = F[0] * F[3] - F[1] * F[2];
+      const double* g = sm.pv[q];
+      const double F[4] = {g[0], g[1], g[2], g[3]};
+      const double J = g[4];
       const double adj[4] = {F[3], -F[1], -F[2], F[0]};
-      double dJ[2];
-      for (int l = 0; l < 2; ++l)   // Jacobi: dJ = tr(adj F dF)
-        dJ[l] = adj[0] * H[0 * 4 + 0 * 2 + l] + adj[1] * H[1 * 4 + 0 * 2 + l] + adj[2] * H[0 * 4 + 1 * 2 + l] +
-                adj[3] * H[1 * 4 + 1 * 2 + l];
       double vh[2], dx[2], dy[2];
       rt_ref<P>(t, a, k1, k2, vh, dx, dy);
       double v[2], dv[2][2];   // dv[i][l] = d v_i / d xi_l
@@ -247,20 +358,17 @@ hrt_local_kernel(long long E, int nx, int ny, HrtTab t, HrtIn in, HrtOut out, un
       for (int l = 0; l < 2; ++l) {
         const double* dvh = l == 0 ? dx : dy;
         for (int i = 0; i < 2; ++i) {
-          const double dFv = H[i * 4 + 0 * 2 + l] * vh[0] + H[i * 4 + 1 * 2 + l] * vh[1];
+          const double dFv = g[7 + i * 4 + 0 * 2 + l] * vh[0] + g[7 + i * 4 + 1 * 2 + l] * vh[1];
           const double Fdv = F[2 * i] * dvh[0] + F[2 * i + 1] * dvh[1];
-          dv[i][l] = (dFv + Fdv) / J - dJ[l] / J * v[i];
+          dv[i][l] = (dFv + Fdv) / J - g[5 + l] / J * v[i];
         }
       }
-      double B[N], Eq[3];
-      dg_at<P>(t, k1, k2, B);
-      eddington_at<N>(in.phi, in.P, En, e, B, Eq);
-      // grad v = dv F^{-1}, F^{-1} = adj / J ; grad v : E
+      // grad v = dv F^{-1}, F^{-1} = adj / J; grad v : E
       double gE = 0.0;
       for (int i = 0; i < 2; ++i)
         for (int mcol = 0; mcol < 2; ++mcol) {
           const double gim = (dv[i][0] * adj[0 * 2 + mcol] + dv[i][1] * adj[1 * 2 + mcol]) / J;
-          const double Eim = (i == mcol) ? (i == 0 ? Eq[0] : Eq[2]) : Eq[1];
+          const double Eim = (i == mcol) ? (i == 0 ? g[15] : g[17]) : g[16];
           gE += gim * Eim;
         }
       const double w = t.w[k1] * t.w[k2];
@@ -270,30 +378,32 @@ hrt_local_kernel(long long E, int nx, int ny, HrtTab t, HrtIn in, HrtOut out, un
       if (a == 0) sm.wJ[q] = w * J;
     }
     for (int idx = tid; idx < NL4 * NJ; idx += nth) {
-      (&sm.C1[0][0])[idx] = 0.0;
+      const int r = idx / NJ;
+      (&sm.C1[0][0])[idx] = nb_elem(nx, ny, (int)e, r / NL) >= 0 ? ref.C1[idx] : 0.0;
       (&sm.C2[0][0])[idx] = 0.0;
     }
     __syncthreads();
-    // A (volume), G, D, Ma, f, g (volume)
+    // (3) A (symmetric: one triangle computed), G, D (reference), sigma_a M, f, g
     for (int idx = tid; idx < MM * MM; idx += nth) {
       const int r = idx / MM, c = idx % MM;
-      double val = 0.0;
       if (r < NJ && c < NJ) {
+        if (c < r) continue;
+        double val = 0.0;
         for (int q = 0; q < NQ2; ++q)
           val += sm.wJ[q] * (sm.vq[q][r][0] * sm.vq[q][c][0] + sm.vq[q][r][1] * sm.vq[q][c][1]);
         val *= st;
-      } else if (r < NJ) {
+        sm.L[r * LD + c] = val;
+        sm.L[c * LD + r] = val;
+        continue;
+      }
+      double val;
+      if (r < NJ) {
         const int cc = c - NJ;
+        val = 0.0;
         for (int q = 0; q < NQ2; ++q)
           val += sm.sg[r][q] * t.dg[cc % (P + 1)][q % NQ] * t.dg[cc / (P + 1)][q / NQ];
       } else if (c < NJ) {
-        const int rr = r - NJ;
-        for (int q = 0; q < NQ2; ++q) {
-          const int k1 = q % NQ, k2 = q / NQ;
-          double vh[2], dx[2], dy[2];
-          rt_ref<P>(t, c, k1, k2, vh, dx, dy);
-          val += t.w[k1] * t.w[k2] * t.dg[rr % (P + 1)][k1] * t.dg[rr / (P + 1)][k2] * (dx[0] + dy[1]);
-        }
+        val = ref.D[(r - NJ) * NJ + c];
       } else {
         val = sa * in.Mm[((size_t)e * N + (r - NJ)) * N + (c - NJ)];
       }
@@ -306,97 +416,55 @@ hrt_local_kernel(long long E, int nx, int ny, HrtTab t, HrtIn in, HrtOut out, un
     }
     for (int a = tid; a < NJ; a += nth) {
       double s = 0.0;
-      if (in.Q1) {
-        for (int q = 0; q < NQ2; ++q) {
-          double B[N];
-          dg_at<P>(t, q % NQ, q / NQ, B);
-          double q1x = 0.0, q1y = 0.0;
-          for (int j = 0; j < N; ++j) {
-            q1x += B[j] * in.Q1[(size_t)e * N + j];
-            q1y += B[j] * in.Q1[En + (size_t)e * N + j];
-          }
-          s += sm.wJ[q] * (sm.vq[q][a][0] * q1x + sm.vq[q][a][1] * q1y);
-        }
-      }
+      if (in.Q1)
+        for (int q = 0; q < NQ2; ++q)
+          s += sm.wJ[q] * (sm.vq[q][a][0] * sm.pv[q][18] + sm.vq[q][a][1] * sm.pv[q][19]);
       sm.gv[a] = s;
     }
     __syncthreads();
-    // faces: multiplier couplings on interior faces, Miften-Larsen terms on boundary faces
-    const int ie = (int)(e % nx), je = (int)(e / nx);
+    // (4) faces: multiplier couplings on interior faces, Miften-Larsen terms on boundary faces
     for (int f = 0; f < 4; ++f) {
-      const int nb = nb_elem(nx, ny, (int)e, f);
-      if (nb >= 0) {
-        const int fo = (f + 2) & 3;
+      const double* o0 = sm.pf[f * NQ];
+      if (nb_elem(nx, ny, (int)e, f) >= 0) {
         for (int idx = tid; idx < NJ * NL; idx += nth) {
           const int a = idx / NL, tt = idx % NL;
-          double c2 = 0.0, c1 = 0.0;
+          double c2 = 0.0;
           for (int k = 0; k < NQ; ++k) {
             int kx, ky;
             face_pt(f, k, NQ, kx, ky);
-            double F[4], H[8];
-            map_geom(sm.ctrl, t, kx, ky, F, H);
-            const double J = F[0] * F[3] - F[1] * F[2];
             double vh[2], dx[2], dy[2];
             rt_ref<P>(t, a, kx, ky, vh, dx, dy);
-            const double v0 = (F[0] * vh[0] + F[1] * vh[1]) / J, v1 = (F[2] * vh[0] + F[3] * vh[1]) / J;
-            // the two sides' Eddington tensors at this face point (their own traces)
-            double Bo[N], Bn[N], Eo[3], Enb[3];
-            dg_at<P>(t, kx, ky, Bo);
-            int nkx, nky;
-            face_pt(fo, k, NQ, nkx, nky);
-            dg_at<P>(t, nkx, nky, Bn);
-            eddington_at<N>(in.phi, in.P, En, e, Bo, Eo);
-            eddington_at<N>(in.phi, in.P, En, nb, Bn, Enb);
-            const double a00 = 0.5 * (Eo[0] + Enb[0]), a01 = 0.5 * (Eo[1] + Enb[1]), a11 = 0.5 * (Eo[2] + Enb[2]);
-            const double* nd = in.nds + (((size_t)e * 4 + f) * NQ + k) * 2;
-            const double En0 = a00 * nd[0] + a01 * nd[1], En1 = a01 * nd[0] + a11 * nd[1];
-            const double lam = t.op[tt][k];
-            c2 += t.w[k] * lam * (v0 * En0 + v1 * En1);
-            const double nref0 = f == 1 ? 1.0 : (f == 3 ? -1.0 : 0.0), nref1 = f == 2 ? 1.0 : (f == 0 ? -1.0 : 0.0);
-            c1 += t.w[k] * lam * (vh[0] * nref0 + vh[1] * nref1);
+            c2 += t.op[tt][k] * (vh[0] * o0[6 * k] + vh[1] * o0[6 * k + 1]);
           }
           sm.C2[a][f * NL + tt] = c2;
-          sm.C1[f * NL + tt][a] = c1;
         }
       } else {
-        const long long bf = bface(nx, ny, (int)e, f);
+        for (int idx = tid; idx < NQ * NJ; idx += nth) {
+          const int k = idx / NJ, a = idx % NJ;
+          int kx, ky;
+          face_pt(f, k, NQ, kx, ky);
+          double vh[2], dx[2], dy[2];
+          rt_ref<P>(t, a, kx, ky, vh, dx, dy);
+          const double* o = o0 + 6 * k;
+          sm.pa[k][a] = vh[0] * o[0] + vh[1] * o[1];
+          sm.pb[k][a] = vh[0] * o[2] + vh[1] * o[3];
+        }
+        __syncthreads();
         for (int idx = tid; idx < NJ * NJ + NJ; idx += nth) {
           const int a = idx < NJ * NJ ? idx / NJ : idx - NJ * NJ;
           const int b = idx < NJ * NJ ? idx % NJ : -1;
           double s = 0.0;
-          for (int k = 0; k < NQ; ++k) {
-            int kx, ky;
-            face_pt(f, k, NQ, kx, ky);
-            double F[4], H[8];
-            map_geom(sm.ctrl, t, kx, ky, F, H);
-            const double J = F[0] * F[3] - F[1] * F[2];
-            const double* nd = in.nds + (((size_t)e * 4 + f) * NQ + k) * 2;
-            const double ln = sqrt(nd[0] * nd[0] + nd[1] * nd[1]);
-            const double un0 = nd[0] / ln, un1 = nd[1] / ln;
-            double Bo[N], Eo[3];
-            dg_at<P>(t, kx, ky, Bo);
-            eddington_at<N>(in.phi, in.P, En, e, Bo, Eo);
-            const double En0 = Eo[0] * un0 + Eo[1] * un1, En1 = Eo[1] * un0 + Eo[2] * un1;
-            double vh[2], dx[2], dy[2];
-            rt_ref<P>(t, a, kx, ky, vh, dx, dy);
-            const double va0 = (F[0] * vh[0] + F[1] * vh[1]) / J, va1 = (F[2] * vh[0] + F[3] * vh[1]) / J;
-            const double vEn = va0 * En0 + va1 * En1;
-            const double eb = in.Eb[bf * NQ + k];
-            if (b >= 0) {
-              rt_ref<P>(t, b, kx, ky, vh, dx, dy);
-              const double vb0 = (F[0] * vh[0] + F[1] * vh[1]) / J, vb1 = (F[2] * vh[0] + F[3] * vh[1]) / J;
-              s += t.w[k] * ln / eb * vEn * (vb0 * un0 + vb1 * un1);
-            } else {
-              s += 2.0 * t.w[k] * ln * in.Jin[bf * NQ + k] / eb * vEn;
-            }
+          if (b >= 0) {
+            for (int k = 0; k < NQ; ++k) s += o0[6 * k + 4] * sm.pa[k][a] * sm.pb[k][b];
+            sm.L[a * LD + b] += s;
+          } else {
+            for (int k = 0; k < NQ; ++k) s += o0[6 * k + 5] * sm.pa[k][a];
+            sm.gv[a] += s;
           }
-          if (b >= 0) sm.L[a * LD + b] += s;
-          else sm.gv[a] += s;
         }
       }
       __syncthreads();
     }
-    (void)ie; (void)je;
     // in-place Gauss-Jordan inversion of L with partial pivoting
     for (int k = 0; k < MM; ++k) {
       if (tid < 32) {
@@ -498,37 +566,10 @@ __device__ __forceinline__ long long face_index(int nx, int ny, int e, int f) {
   return j > 0 ? nv + (long long)(j - 1) * nx + i : -1;
 }
 
-// z_e = H_e x_e (x gathered from the element's interior faces; boundary faces give 0)
-template <int P>
-__global__ void hrt_local_apply_kernel(long long E, int nx, int ny, const double* __restrict__ He,
-                                       const double* __restrict__ x, double* __restrict__ z) {
-  constexpr int NL = P + 1, NL4 = 4 * NL;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= E * NL4) return;
-  const long long e = t / NL4;
-  const int r = (int)(t % NL4);
-  const double* h = He + (size_t)e * NL4 * NL4 + (size_t)r * NL4;
-  double s = 0.0;
-  for (int f = 0; f < 4; ++f) {
-    const long long fi = face_index(nx, ny, (int)e, f);
-    if (fi < 0) continue;
-    for (int tt = 0; tt < NL; ++tt) s += h[f * NL + tt] * x[fi * NL + tt];
-  }
-  z[t] = s;
-}
-
-// y[face dof] = sum of the two sides' z rows (or their H_e diagonals for the preconditioner)
-template <int P>
-__global__ void hrt_gather_kernel(int nx, int ny, long long nfaces, const double* __restrict__ z,
-                                  const double* __restrict__ He, double* __restrict__ y) {
-  constexpr int NL = P + 1, NL4 = 4 * NL;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= nfaces * NL) return;
-  const long long fid = t / NL;
-  const int tt = (int)(t % NL);
+// the two elements and local faces on either side of interior face fid
+__device__ __forceinline__ void face_sides(int nx, int ny, long long fid, long long& e1, int& f1, long long& e2,
+                                           int& f2) {
   const long long nv = (long long)(nx - 1) * ny;
-  long long e1, e2;
-  int f1, f2;
   if (fid < nv) {
     const long long j = fid / (nx - 1), i = fid % (nx - 1);
     e1 = j * nx + i; f1 = 1; e2 = e1 + 1; f2 = 3;
@@ -536,9 +577,94 @@ __global__ void hrt_gather_kernel(int nx, int ny, long long nfaces, const double
     const long long h = fid - nv, j = h / nx, i = h % nx;
     e1 = j * nx + i; f1 = 2; e2 = e1 + nx; f2 = 0;
   }
-  const int r1 = f1 * NL + tt, r2 = f2 * NL + tt;
-  if (z) y[t] = z[e1 * NL4 + r1] + z[e2 * NL4 + r2];
-  else y[t] = He[(size_t)e1 * NL4 * NL4 + (size_t)r1 * NL4 + r1] + He[(size_t)e2 * NL4 * NL4 + (size_t)r2 * NL4 + r2];
+}
+
+// r[face dof] = the two sides' rows of r_e (the reduced right-hand side)
+template <int P>
+__global__ void hrt_gather_kernel(int nx, int ny, long long nfaces, const double* __restrict__ z,
+                                  double* __restrict__ y) {
+  constexpr int NL = P + 1, NL4 = 4 * NL;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= nfaces * NL) return;
+  long long e1, e2;
+  int f1, f2;
+  face_sides(nx, ny, t / NL, e1, f1, e2, f2);
+  const int tt = (int)(t % NL);
+  y[t] = z[e1 * NL4 + f1 * NL + tt] + z[e2 * NL4 + f2 * NL + tt];
+}
+
+// row (f NL + tt) of H_e applied to the element's multipliers (boundary faces carry none)
+template <int P>
+__device__ __forceinline__ double he_row(int nx, int ny, const double* __restrict__ He,
+                                         const double* __restrict__ x, long long e, int f, int tt) {
+  constexpr int NL = P + 1, NL4 = 4 * NL;
+  const double* row = He + (size_t)e * NL4 * NL4 + (size_t)(f * NL + tt) * NL4;
+  double s = 0.0;
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const long long fi = face_index(nx, ny, (int)e, g);
+    if (fi < 0) continue;
+#pragma unroll
+    for (int u = 0; u < NL; ++u) s = fma(row[g * NL + u], x[fi * NL + u], s);
+  }
+  return s;
+}
+
+// Face-block Jacobi preconditioner: the (p+1)-square diagonal block of H for each interior
+// face (the sum of its two sides' blocks of H_e), inverted by Gauss-Jordan with partial
+// pivoting, one face per thread.
+template <int P>
+__global__ void hrt_face_block_kernel(int nx, int ny, long long nfaces, const double* __restrict__ He,
+                                      double* __restrict__ Minv, unsigned int* status) {
+  constexpr int NL = P + 1, NL4 = 4 * NL;
+  const long long fid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (fid >= nfaces) return;
+  long long e1, e2;
+  int f1, f2;
+  face_sides(nx, ny, fid, e1, f1, e2, f2);
+  double B[NL][NL], X[NL][NL];
+#pragma unroll
+  for (int a = 0; a < NL; ++a)
+#pragma unroll
+    for (int b = 0; b < NL; ++b) {
+      B[a][b] = He[(size_t)e1 * NL4 * NL4 + (size_t)(f1 * NL + a) * NL4 + f1 * NL + b] +
+                He[(size_t)e2 * NL4 * NL4 + (size_t)(f2 * NL + a) * NL4 + f2 * NL + b];
+      X[a][b] = a == b ? 1.0 : 0.0;
+    }
+  bool singular = false;
+#pragma unroll
+  for (int k = 0; k < NL; ++k) {
+    int pr = k;
+#pragma unroll
+    for (int i = k + 1; i < NL; ++i)
+      if (fabs(B[i][k]) > fabs(B[pr][k])) pr = i;
+#pragma unroll
+    for (int i = k + 1; i < NL; ++i)   // swap rows k and pr (register-resident: by select)
+      if (i == pr) {
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+          const double tb = B[k][j], tx = X[k][j];
+          B[k][j] = B[i][j]; B[i][j] = tb;
+          X[k][j] = X[i][j]; X[i][j] = tx;
+        }
+      }
+    singular = singular || !(fabs(B[k][k]) > 1e-300);
+    const double inv = 1.0 / B[k][k];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) { B[k][j] *= inv; X[k][j] *= inv; }
+#pragma unroll
+    for (int i = 0; i < NL; ++i) {
+      if (i == k) continue;
+      const double fct = B[i][k];
+#pragma unroll
+      for (int j = 0; j < NL; ++j) { B[i][j] -= fct * B[k][j]; X[i][j] -= fct * X[k][j]; }
+    }
+  }
+  if (singular) atomicOr(status, kDevSingular);
+#pragma unroll
+  for (int a = 0; a < NL; ++a)
+#pragma unroll
+    for (int b = 0; b < NL; ++b) Minv[(size_t)fid * NL * NL + a * NL + b] = X[a][b];
 }
 
 // [J; phi] = Li [g - C2 lambda_e; f]
@@ -578,78 +704,212 @@ __global__ void hrt_recover_kernel(long long E, int nx, int ny, const double* __
   }
 }
 
-// ---- vector kernels of the Krylov solve (deterministic two-stage dot products)
-constexpr int kDotBlocks = 256, kDotThreads = 256;
+// ---- the multiplier system's Krylov solve: BiCGStab (van der Vorst) with the face-block
+// Jacobi preconditioner above.  Its scalars stay on the device: every dot product is
+// reduced in two fixed stages (per-block partial sums, then each reader sums the kKB
+// partials in the same order), so the iteration is deterministic and no kernel waits on
+// the host; the host reads the convergence state once every kCheck iterations.  One
+// iteration is five launches: p and its preconditioned copy; v = H p_hat with r_hat.v;
+// s and s_hat; t = H s_hat with t.s and t.t; lambda and r with r_hat.r and r.r.
+constexpr int kKB = 256, kKT = 256, kCheck = 16;
+enum { kDotRV = 0, kDotTS = 1, kDotTT = 2, kDotRR_hat = 3, kDotRR = 4, kNumDots = 5 };
 
-__global__ void dot_partial_kernel(long long n, const double* __restrict__ a, const double* __restrict__ b,
-                                   const double* __restrict__ c, const double* __restrict__ d,
-                                   double* __restrict__ part) {
-  // part[blockIdx] = (a.b, c.d) over this block's grid-stride share
-  __shared__ double s0[kDotThreads], s1[kDotThreads];
-  double x = 0.0, y = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    x += a[i] * b[i];
-    if (c) y += c[i] * d[i];
-  }
-  s0[threadIdx.x] = x;
-  s1[threadIdx.x] = y;
+struct KScal { double rho, alpha, omega; };
+struct KState {
+  int done;      // 1: converged, 2: breakdown
+  int iters;     // iterations completed when done was set
+  double bb;     // ||r0||^2
+  double rr;     // ||r||^2 at the last check
+};
+
+struct Kry {
+  int nx, ny;
+  long long nfaces, nl;
+  const double* He;
+  const double* Minv;
+  double *x, *r, *rh, *p, *v, *s, *t, *ph, *sh;
+  double* part;   // [kNumDots][kKB]
+  KScal* sc;      // [iterations + 1]: sc[i] holds iteration i's rho, alpha, omega (sc[0] = 1)
+  KState* st;
+  double tol2;
+};
+
+// whether an earlier launch ended the iteration (read once per block, so the whole block
+// leaves together)
+__device__ __forceinline__ bool kry_stopped(const Kry& k) {
+  __shared__ int done;
+  if (threadIdx.x == 0) done = *(volatile const int*)&k.st->done;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) {
-      s0[threadIdx.x] += s0[threadIdx.x + o];
-      s1[threadIdx.x] += s1[threadIdx.x + o];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = s0[0];
-    part[2 * blockIdx.x + 1] = s1[0];
-  }
+  return done != 0;
 }
 
-__global__ void dot_final_kernel(int nparts, const double* __restrict__ part, double* __restrict__ out) {
-  __shared__ double s0[kDotThreads], s1[kDotThreads];
-  double x = 0.0, y = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-    x += part[2 * i];
-    y += part[2 * i + 1];
+// sum of the kKB partials of dot q, in a fixed order, broadcast to the block
+__device__ double kry_sum(const double* __restrict__ part, int q, double* red) {
+  if (threadIdx.x < 32) {
+    double a = 0.0;
+#pragma unroll
+    for (int i = 0; i < kKB / 32; ++i) a += part[q * kKB + threadIdx.x + 32 * i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (threadIdx.x == 0) *red = a;
   }
-  s0[threadIdx.x] = x;
-  s1[threadIdx.x] = y;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) {
-      s0[threadIdx.x] += s0[threadIdx.x + o];
-      s1[threadIdx.x] += s1[threadIdx.x + o];
-    }
-    __syncthreads();
+  const double v = *red;
+  __syncthreads();
+  return v;
+}
+
+// block sums of a and b into part[qa][blockIdx], part[qb][blockIdx] (qb < 0: a only)
+__device__ void kry_partial(double a, double b, double* part, int qa, int qb) {
+  __shared__ double ra[kKT / 32], rb[kKT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
   }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { ra[w] = a; rb[w] = b; }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    out[0] = s0[0];
-    out[1] = s1[0];
+    double sa = 0.0, sb = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { sa += ra[i]; sb += rb[i]; }
+    part[qa * kKB + blockIdx.x] = sa;
+    if (qb >= 0) part[qb * kKB + blockIdx.x] = sb;
   }
 }
 
-// y = a x + b y (+ c z) elementwise; mode 1: y = x / d (Jacobi)
-__global__ void axpby_kernel(long long n, double a, const double* __restrict__ x, double b, double* __restrict__ y,
-                             double c, const double* __restrict__ z) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  y[i] = a * x[i] + b * y[i] + (z ? c * z[i] : 0.0);
+// y = M^{-1} x on face fid's p+1 dofs
+template <int P>
+__device__ __forceinline__ void kry_precond(const Kry& k, long long fid, const double* xf, double* y) {
+  constexpr int NL = P + 1;
+  const double* Mi = k.Minv + (size_t)fid * NL * NL;
+#pragma unroll
+  for (int a = 0; a < NL; ++a) {
+    double s = 0.0;
+#pragma unroll
+    for (int b = 0; b < NL; ++b) s = fma(Mi[a * NL + b], xf[b], s);
+    y[fid * NL + a] = s;
+  }
 }
 
-__global__ void jacobi_kernel(long long n, const double* __restrict__ x, const double* __restrict__ d,
-                              double* __restrict__ y) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < n) y[i] = x[i] / d[i];
+// r_hat = r, x = p = v = 0, partials of r_hat.r and r.r, sc[0] = 1, state cleared
+__global__ void kry_init_kernel(Kry k) {
+  double a = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < k.nl; i += (long long)gridDim.x * blockDim.x) {
+    const double ri = k.r[i];
+    k.rh[i] = ri;
+    k.x[i] = 0.0; k.p[i] = 0.0; k.v[i] = 0.0;
+    a = fma(ri, ri, a);
+  }
+  kry_partial(a, a, k.part, kDotRR_hat, kDotRR);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    k.sc[0] = KScal{1.0, 1.0, 1.0};
+    *k.st = KState{0, 0, 0.0, 0.0};
+  }
+}
+
+// iteration it, step 1: convergence test on the previous residual, rho, p, p_hat.  With
+// update == false it only records the state (the final check after the last iteration).
+template <int P>
+__global__ void kry_p_kernel(Kry k, int it, bool update) {
+  constexpr int NL = P + 1;
+  __shared__ double red;
+  if (kry_stopped(k)) return;
+  const double rr = kry_sum(k.part, kDotRR, &red);
+  const double rho = kry_sum(k.part, kDotRR_hat, &red);
+  const double bb = it == 0 ? rr : k.st->bb;
+  const bool conv = rr <= k.tol2 * bb;
+  const KScal pv = k.sc[it];
+  const bool brk = !conv && update && (rho == 0.0 || !isfinite(rho) || pv.omega == 0.0);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (it == 0) k.st->bb = rr;
+    k.st->rr = rr;
+    if (conv || brk) { k.st->done = conv ? 1 : 2; k.st->iters = it; }
+    k.sc[it + 1].rho = rho;
+  }
+  if (conv || brk || !update) return;
+  const double beta = (rho / pv.rho) * (pv.alpha / pv.omega);
+  for (long long fid = blockIdx.x * (long long)blockDim.x + threadIdx.x; fid < k.nfaces;
+       fid += (long long)gridDim.x * blockDim.x) {
+    double pf[NL];
+#pragma unroll
+    for (int a = 0; a < NL; ++a) {
+      const long long i = fid * NL + a;
+      pf[a] = k.r[i] + beta * (k.p[i] - pv.omega * k.v[i]);
+      k.p[i] = pf[a];
+    }
+    kry_precond<P>(k, fid, pf, k.ph);
+  }
+}
+
+// y = H x with the partial dots w.y (into qa) and, when qb >= 0, y.y (into qb)
+template <int P>
+__global__ void kry_matvec_kernel(Kry k, const double* __restrict__ x, double* __restrict__ y,
+                                  const double* __restrict__ w, int qa, int qb) {
+  constexpr int NL = P + 1;
+  if (kry_stopped(k)) return;
+  double a = 0.0, b = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < k.nl; i += (long long)gridDim.x * blockDim.x) {
+    long long e1, e2;
+    int f1, f2;
+    face_sides(k.nx, k.ny, i / NL, e1, f1, e2, f2);
+    const int tt = (int)(i % NL);
+    const double yi = he_row<P>(k.nx, k.ny, k.He, x, e1, f1, tt) + he_row<P>(k.nx, k.ny, k.He, x, e2, f2, tt);
+    y[i] = yi;
+    a = fma(w[i], yi, a);
+    b = fma(yi, yi, b);
+  }
+  kry_partial(a, b, k.part, qa, qb);
+}
+
+// step 3: alpha, s = r - alpha v, s_hat
+template <int P>
+__global__ void kry_s_kernel(Kry k, int it) {
+  constexpr int NL = P + 1;
+  __shared__ double red;
+  if (kry_stopped(k)) return;
+  const double rv = kry_sum(k.part, kDotRV, &red);
+  const double alpha = k.sc[it + 1].rho / rv;
+  if (!isfinite(alpha)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) { k.st->done = 2; k.st->iters = it; }
+    return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) k.sc[it + 1].alpha = alpha;
+  for (long long fid = blockIdx.x * (long long)blockDim.x + threadIdx.x; fid < k.nfaces;
+       fid += (long long)gridDim.x * blockDim.x) {
+    double sf[NL];
+#pragma unroll
+    for (int a = 0; a < NL; ++a) {
+      const long long i = fid * NL + a;
+      sf[a] = k.r[i] - alpha * k.v[i];
+      k.s[i] = sf[a];
+    }
+    kry_precond<P>(k, fid, sf, k.sh);
+  }
+}
+
+// step 5: omega, lambda += alpha p_hat + omega s_hat, r = s - omega t, and the partials of
+// r_hat.r and r.r for the next iteration's test
+__global__ void kry_x_kernel(Kry k, int it) {
+  __shared__ double red;
+  if (kry_stopped(k)) return;
+  const double ts = kry_sum(k.part, kDotTS, &red);
+  const double tt = kry_sum(k.part, kDotTT, &red);
+  const double alpha = k.sc[it + 1].alpha;
+  const double omega = tt > 0.0 ? ts / tt : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) k.sc[it + 1].omega = omega;
+  double a = 0.0, b = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < k.nl; i += (long long)gridDim.x * blockDim.x) {
+    k.x[i] += alpha * k.ph[i] + omega * k.sh[i];
+    const double ri = k.s[i] - omega * k.t[i];
+    k.r[i] = ri;
+    a = fma(k.rh[i], ri, a);
+    b = fma(ri, ri, b);
+  }
+  kry_partial(a, b, k.part, kDotRR_hat, kDotRR);
 }
 
 static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
-
-struct HrtWork {
-  double *Li, *C2, *g, *f, *He, *re, *z;
-  double *r, *rh, *pv, *vv, *sv, *tv, *ph, *sh, *diag, *part, *dots;
-};
 
 template <int P>
 static vef_status hrt_run(Mesh& M, const HrtIn& in, double tol, int max_iter, double* phi, double* J,
@@ -659,36 +919,41 @@ static vef_status hrt_run(Mesh& M, const HrtIn& in, double tol, int max_iter, do
   const long long nfaces = (long long)(M.nx - 1) * M.ny + (long long)M.nx * (M.ny - 1);
   const long long nl = nfaces * S::NL;
   const size_t per_e = (size_t)S::MM * S::MM + (size_t)S::NJ * S::NL4 + S::NJ + S::N + (size_t)S::NL4 * S::NL4 +
-                       S::NL4 + S::NL4;
+                       S::NL4;
   const size_t vec = (size_t)std::max(1LL, nl);
-  const size_t total = per_e * E + 11 * vec + 2 * kDotBlocks + 2;
+  const size_t nsc = (size_t)max_iter + 2;
+  const HrtTab tab = make_hrt_tab(P, M.m);
+  std::vector<double> refh;
+  make_hrt_ref<P>(tab, refh);
+  const size_t total = per_e * E + 10 * vec + (size_t)std::max(1LL, nfaces) * S::NL * S::NL +
+                       (size_t)kNumDots * kKB + 3 * nsc + 4 + refh.size();
   vef_status st = ensure_buffer((void**)&M.work, &M.work_cap, total * sizeof(double));
   if (st != VEF_OK) return st;
   double* base = M.work;
-  HrtWork w{};
-  w.Li = base; base += (size_t)S::MM * S::MM * E;
-  w.C2 = base; base += (size_t)S::NJ * S::NL4 * E;
-  w.g = base; base += (size_t)S::NJ * E;
-  w.f = base; base += (size_t)S::N * E;
-  w.He = base; base += (size_t)S::NL4 * S::NL4 * E;
-  w.re = base; base += (size_t)S::NL4 * E;
-  w.z = base; base += (size_t)S::NL4 * E;
-  double* lam = lambda;
-  w.r = base; base += vec;
-  if (!lam) { lam = base; } base += vec;
-  w.rh = base; base += vec;
-  w.pv = base; base += vec;
-  w.vv = base; base += vec;
-  w.sv = base; base += vec;
-  w.tv = base; base += vec;
-  w.ph = base; base += vec;
-  w.sh = base; base += vec;
-  w.diag = base; base += vec;
-  w.part = base; base += 2 * kDotBlocks;
-  w.dots = base;
-  double* diag = w.diag;
-  const HrtTab tab = make_hrt_tab(P, M.m);
-  HrtOut out{w.Li, w.C2, w.g, w.f, w.He, w.re};
+  auto take = [&](size_t n) { double* q = base; base += n; return q; };
+  double* Li = take((size_t)S::MM * S::MM * E);
+  double* C2 = take((size_t)S::NJ * S::NL4 * E);
+  double* g = take((size_t)S::NJ * E);
+  double* f = take((size_t)S::N * E);
+  double* He = take((size_t)S::NL4 * S::NL4 * E);
+  double* re = take((size_t)S::NL4 * E);
+  Kry k{};
+  k.nx = M.nx; k.ny = M.ny; k.nfaces = nfaces; k.nl = nl; k.He = He;
+  k.x = lambda ? lambda : take(vec);
+  if (lambda) take(vec);
+  k.r = take(vec); k.rh = take(vec); k.p = take(vec); k.v = take(vec); k.s = take(vec);
+  k.t = take(vec); k.ph = take(vec); k.sh = take(vec);
+  double* Minv = take((size_t)std::max(1LL, nfaces) * S::NL * S::NL);
+  k.Minv = Minv;
+  k.part = take((size_t)kNumDots * kKB);
+  k.sc = reinterpret_cast<KScal*>(take(3 * nsc));
+  k.st = reinterpret_cast<KState*>(take(4));
+  k.tol2 = tol * tol;
+  double* refd = take(refh.size());
+  // pageable source: the copy has taken the data when the call returns
+  VEF_CUDA_TRY(cudaMemcpyAsync(refd, refh.data(), refh.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  const HrtRef ref{refd, refd + (size_t)S::N * S::NJ};
+  HrtOut out{Li, C2, g, f, He, re};
   const size_t smem = sizeof(HrtSmem<P>);
   VEF_CUDA_TRY(cudaFuncSetAttribute(hrt_local_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, sms = 0;
@@ -697,80 +962,53 @@ static vef_status hrt_run(Mesh& M, const HrtIn& in, double tol, int max_iter, do
   {
     KTimer kt(&M, VEF_K_HRT, s);
     hrt_local_kernel<P><<<(unsigned)std::min<long long>(E, (long long)sms * 8), 256, smem, s>>>(
-        E, M.nx, M.ny, tab, in, out, M.dev_status);
+        E, M.nx, M.ny, tab, ref, in, out, M.dev_status);
     VEF_CUDA_TRY(cudaGetLastError());
   }
-  auto matvec = [&](const double* x, double* y) -> vef_status {
-    hrt_local_apply_kernel<P><<<nblk(E * S::NL4, 256), 256, 0, s>>>(E, M.nx, M.ny, w.He, x, w.z);
-    hrt_gather_kernel<P><<<nblk(nl, 256), 256, 0, s>>>(M.nx, M.ny, nfaces, w.z, w.He, y);
-    VEF_CUDA_TRY(cudaGetLastError());
-    return VEF_OK;
-  };
-  auto dot2 = [&](const double* a, const double* b, const double* c, const double* d, double h[2]) -> vef_status {
-    dot_partial_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(nl, a, b, c, d, w.part);
-    dot_final_kernel<<<1, kDotThreads, 0, s>>>(kDotBlocks, w.part, w.dots);
-    VEF_CUDA_TRY(cudaMemcpyAsync(h, w.dots, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    VEF_CUDA_TRY(cudaStreamSynchronize(s));
-    return VEF_OK;
-  };
-  const unsigned vb = nblk(nl, 256);
   int it = 0;
-  double rel = 0.0;
+  KState hs{0, 0, 0.0, 0.0};
   if (nl > 0) {
-    // the reduced right-hand side r = sum_e r_e, then BiCGStab with the diagonal of H
-    hrt_gather_kernel<P><<<vb, 256, 0, s>>>(M.nx, M.ny, nfaces, w.re, nullptr, w.r);   // z = r_e layout
-    hrt_gather_kernel<P><<<vb, 256, 0, s>>>(M.nx, M.ny, nfaces, nullptr, w.He, diag);
-    VEF_CUDA_TRY(cudaMemsetAsync(lam, 0, nl * sizeof(double), s));
-    VEF_CUDA_TRY(cudaMemcpyAsync(w.rh, w.r, nl * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    VEF_CUDA_TRY(cudaMemsetAsync(w.pv, 0, nl * sizeof(double), s));
-    VEF_CUDA_TRY(cudaMemsetAsync(w.vv, 0, nl * sizeof(double), s));
-    double h[2];
-    if ((st = dot2(w.r, w.r, nullptr, nullptr, h)) != VEF_OK) return st;
-    const double bnorm = std::sqrt(h[0]);
-    double rho = 1.0, alpha = 1.0, omega = 1.0;
-    rel = bnorm > 0.0 ? 1.0 : 0.0;
-    while (bnorm > 0.0 && it < max_iter && rel > tol) {
-      if ((st = dot2(w.rh, w.r, nullptr, nullptr, h)) != VEF_OK) return st;
-      const double rho_new = h[0];
-      if (rho_new == 0.0) break;
-      const double beta = (rho_new / rho) * (alpha / omega);
-      rho = rho_new;
-      // p = r + beta (p - omega v)
-      axpby_kernel<<<vb, 256, 0, s>>>(nl, 1.0, w.r, beta, w.pv, -beta * omega, w.vv);
-      jacobi_kernel<<<vb, 256, 0, s>>>(nl, w.pv, diag, w.ph);
-      if ((st = matvec(w.ph, w.vv)) != VEF_OK) return st;
-      if ((st = dot2(w.rh, w.vv, nullptr, nullptr, h)) != VEF_OK) return st;
-      alpha = rho / h[0];
-      // s = r - alpha v
-      VEF_CUDA_TRY(cudaMemcpyAsync(w.sv, w.r, nl * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      axpby_kernel<<<vb, 256, 0, s>>>(nl, -alpha, w.vv, 1.0, w.sv, 0.0, nullptr);
-      jacobi_kernel<<<vb, 256, 0, s>>>(nl, w.sv, diag, w.sh);
-      if ((st = matvec(w.sh, w.tv)) != VEF_OK) return st;
-      if ((st = dot2(w.tv, w.sv, w.tv, w.tv, h)) != VEF_OK) return st;
-      omega = h[1] > 0.0 ? h[0] / h[1] : 0.0;
-      // lambda += alpha p_hat + omega s_hat ; r = s - omega t
-      axpby_kernel<<<vb, 256, 0, s>>>(nl, alpha, w.ph, 1.0, lam, omega, w.sh);
-      VEF_CUDA_TRY(cudaMemcpyAsync(w.r, w.sv, nl * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      axpby_kernel<<<vb, 256, 0, s>>>(nl, -omega, w.tv, 1.0, w.r, 0.0, nullptr);
-      ++it;
-      if ((st = dot2(w.r, w.r, nullptr, nullptr, h)) != VEF_OK) return st;
-      rel = std::sqrt(h[0]) / bnorm;
-      if (omega == 0.0) break;
+    hrt_gather_kernel<P><<<nblk(nl, 256), 256, 0, s>>>(M.nx, M.ny, nfaces, re, k.r);
+    hrt_face_block_kernel<P><<<nblk(nfaces, 128), 128, 0, s>>>(M.nx, M.ny, nfaces, He, Minv, M.dev_status);
+    kry_init_kernel<<<kKB, kKT, 0, s>>>(k);
+    VEF_CUDA_TRY(cudaGetLastError());
+    while (it < max_iter) {
+      const int n = std::min(kCheck, max_iter - it);
+      for (int j = 0; j < n; ++j, ++it) {
+        kry_p_kernel<P><<<kKB, kKT, 0, s>>>(k, it, true);
+        kry_matvec_kernel<P><<<kKB, kKT, 0, s>>>(k, k.ph, k.v, k.rh, kDotRV, -1);
+        kry_s_kernel<P><<<kKB, kKT, 0, s>>>(k, it);
+        kry_matvec_kernel<P><<<kKB, kKT, 0, s>>>(k, k.sh, k.t, k.s, kDotTS, kDotTT);
+        kry_x_kernel<<<kKB, kKT, 0, s>>>(k, it);
+      }
+      VEF_CUDA_TRY(cudaGetLastError());
+      VEF_CUDA_TRY(cudaMemcpyAsync(&hs, k.st, sizeof(KState), cudaMemcpyDeviceToHost, s));
+      VEF_CUDA_TRY(cudaStreamSynchronize(s));
+      if (hs.done) break;
     }
+    if (!hs.done) {   // the test after the last iteration
+      kry_p_kernel<P><<<kKB, kKT, 0, s>>>(k, it, false);
+      VEF_CUDA_TRY(cudaMemcpyAsync(&hs, k.st, sizeof(KState), cudaMemcpyDeviceToHost, s));
+      VEF_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    if (hs.done) it = hs.iters;
   }
   {
     KTimer kt(&M, VEF_K_HRT, s);
     hrt_recover_kernel<P><<<(unsigned)std::min<long long>(E, (long long)sms * 8), 128, 0, s>>>(
-        E, M.nx, M.ny, w.Li, w.C2, w.g, w.f, lam, J, phi);
+        E, M.nx, M.ny, Li, C2, g, f, k.x, J, phi);
     VEF_CUDA_TRY(cudaGetLastError());
   }
+  const bool conv = nl == 0 || hs.done == 1;
+  const double rel = nl == 0 || hs.bb <= 0.0 ? 0.0 : std::sqrt(hs.rr / hs.bb);
   if (info) {
     info->iterations = it;
     info->rel_residual = rel;
     info->multipliers = nl;
   }
-  if (nl > 0 && rel > tol) {
-    set_last_error("HRT multiplier solve did not reach its tolerance");
+  if (!conv) {
+    set_last_error(hs.done == 2 ? "HRT multiplier solve broke down (BiCGStab)"
+                                : "HRT multiplier solve did not reach its tolerance");
     return VEF_ERR_NOT_CONVERGED;
   }
   return VEF_OK;

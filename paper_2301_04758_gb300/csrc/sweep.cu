@@ -1422,8 +1422,11 @@ static vef_status launch_sweep_cta(const SweepCall& c, SweepArgs<T>& a) {
   const int workers = per_sm * sms - S.D;
   cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
   VEF_CUDA_TRY(cudaStreamIsCapturing(c.stream, &capturing));
-  // graph capture keeps the plain launch pair (no cooperative node in the graph)
-  if (c.y_ready || c.apply_separate || workers < kMinApplyCtas || capturing != cudaStreamCaptureStatusNone) {
+  // graph capture keeps the plain launch pair (no cooperative node in the graph); from p = 3
+  // the apply's A^{-1} stream (n^2 words per task) is faster on every SM before the sweep
+  // than on the SMs the directions leave free during it
+  if (c.y_ready || c.apply_separate || P >= 3 || workers < kMinApplyCtas ||
+      capturing != cudaStreamCaptureStatusNone) {
     if (!c.y_ready) {   // y already formed by the factorisation otherwise
       vef_status st = launch_apply<P, T, MODE>(c, a);
       if (st != VEF_OK) return st;
