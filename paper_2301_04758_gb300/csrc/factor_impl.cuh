@@ -407,7 +407,7 @@ factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const 
       sC[warp][u][f][kk] = sW[kk] * (mu * sN[(f * NQ + kk) * 2] + eta * sN[(f * NQ + kk) * 2 + 1]);
     }
     __syncwarp();
-    // assemble the owned rows: sigma_t M - mu Gx - eta Gy plus the outflow face terms
+    // assemble the owned rows: sigma_t M - mu Gx - eta Gy ...
     T row[RPL][N];
 #pragma unroll
     for (int r = 0; r < RPL; ++r) {
@@ -415,22 +415,44 @@ factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const 
 #pragma unroll
       for (int j = 0; j < N; ++j)
         row[r][j] = i < N ? st * sM[i * LD + j] - mu * sX[i * LD + j] - eta * sY[i * LD + j] : (T)0;
-      if (i >= N) continue;
-      const int ia = i % Q, ib = i / Q;
+    }
+    // ... plus the outflow face terms: row a of face f's matrix sum_k max(c_k, 0) l_a l_t is
+    // formed on lane a of the task and shuffled to the lane that owns face node a (faces
+    // without an outflow point in any of the warp's tasks are skipped)
 #pragma unroll
-      for (int f = 0; f < 4; ++f) {
+    for (int f = 0; f < 4; ++f) {
+      bool out_f = false;
+#pragma unroll
+      for (int k = 0; k < NQ; ++k) out_f = out_f || sC[warp][uc][f][k] > (T)0;
+      if (!__any_sync(FULL, valid && out_f)) continue;
+      const int fa = li < Q ? li : Q - 1;   // lanes past the face's p+1 rows form a copy
+      T fo[Q];
+#pragma unroll
+      for (int t = 0; t < Q; ++t) fo[t] = 0;
+#pragma unroll
+      for (int k = 0; k < NQ; ++k) {
+        const T s = sC[warp][uc][f][k];
+        const T sp = s > (T)0 ? s : (T)0;
+#pragma unroll
+        for (int t = 0; t < Q; ++t) fo[t] = fma(sp, sLL[fa][t][k], fo[t]);
+      }
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        const int i = li + LPU * r;
+        const int ia = i % Q, ib = i / Q;
         int pos = -1;
-        if (f == 0 && ib == 0) pos = ia;
-        if (f == 1 && ia == P) pos = ib;
-        if (f == 2 && ib == P) pos = ia;
-        if (f == 3 && ia == 0) pos = ib;
-        if (pos < 0) continue;
+        if (i < N) {
+          if (f == 0 && ib == 0) pos = ia;
+          if (f == 1 && ia == P) pos = ib;
+          if (f == 2 && ib == P) pos = ia;
+          if (f == 3 && ia == 0) pos = ib;
+        }
+        if (!__any_sync(FULL, pos >= 0)) continue;
+        const int src = (base + (pos > 0 ? pos : 0)) & 31;
 #pragma unroll
-        for (int k = 0; k < NQ; ++k) {
-          const T s = sC[warp][uc][f][k];
-          if (!(s > (T)0)) continue;
-#pragma unroll
-          for (int t = 0; t < Q; ++t) row[r][face_dof<P>(f, t)] = fma(s, sLL[pos][t][k], row[r][face_dof<P>(f, t)]);
+        for (int t = 0; t < Q; ++t) {
+          const T v = __shfl_sync(FULL, fo[t], src);
+          if (pos >= 0) row[r][face_dof<P>(f, t)] += v;
         }
       }
     }
