@@ -172,6 +172,12 @@ struct Mesh {
   size_t ready_cap = 0;
   void* vef_work = nullptr;      // VEF fixed-point iteration: iterates, moments, closures
   size_t vef_work_cap = 0;
+  // the HRT multiplier solve's graph of one block of Krylov iterations, with the scratch
+  // layout it was captured for
+  cudaGraphExec_t hrt_graph = nullptr;
+  const void* hrt_graph_work = nullptr;
+  long long hrt_graph_nl = -1;
+  int hrt_graph_p = 0;
   ~Mesh();
 };
 

@@ -710,7 +710,9 @@ __global__ void hrt_recover_kernel(long long E, int nx, int ny, const double* __
 // partials in the same order), so the iteration is deterministic and no kernel waits on
 // the host; the host reads the convergence state once every kCheck iterations.  One
 // iteration is five launches: p and its preconditioned copy; v = H p_hat with r_hat.v;
-// s and s_hat; t = H s_hat with t.s and t.t; lambda and r with r_hat.r and r.r.
+// s and s_hat; t = H s_hat with t.s and t.t; lambda and r with r_hat.r and r.r.  The
+// kernels take their iteration as an offset from a base index held on the device, so one
+// CUDA graph of kCheck iterations (and the base's advance) is replayed block after block.
 constexpr int kKB = 256, kKT = 256, kCheck = 16;
 enum { kDotRV = 0, kDotTS = 1, kDotTT = 2, kDotRR_hat = 3, kDotRR = 4, kNumDots = 5 };
 
@@ -718,9 +720,13 @@ struct KScal { double rho, alpha, omega; };
 struct KState {
   int done;      // 1: converged, 2: breakdown
   int iters;     // iterations completed when done was set
+  int base;      // iterations launched before the current block
+  int pad;
   double bb;     // ||r0||^2
   double rr;     // ||r||^2 at the last check
+  double tol2;   // squared relative tolerance
 };
+static_assert(sizeof(KState) % sizeof(double) == 0, "KState is carved from a double buffer");
 
 struct Kry {
   int nx, ny;
@@ -731,7 +737,6 @@ struct Kry {
   double* part;   // [kNumDots][kKB]
   KScal* sc;      // [iterations + 1]: sc[i] holds iteration i's rho, alpha, omega (sc[0] = 1)
   KState* st;
-  double tol2;
 };
 
 // whether an earlier launch ended the iteration (read once per block, so the whole block
@@ -793,7 +798,7 @@ __device__ __forceinline__ void kry_precond(const Kry& k, long long fid, const d
 }
 
 // r_hat = r, x = p = v = 0, partials of r_hat.r and r.r, sc[0] = 1, state cleared
-__global__ void kry_init_kernel(Kry k) {
+__global__ void kry_init_kernel(Kry k, double tol2) {
   double a = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < k.nl; i += (long long)gridDim.x * blockDim.x) {
     const double ri = k.r[i];
@@ -804,21 +809,23 @@ __global__ void kry_init_kernel(Kry k) {
   kry_partial(a, a, k.part, kDotRR_hat, kDotRR);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     k.sc[0] = KScal{1.0, 1.0, 1.0};
-    *k.st = KState{0, 0, 0.0, 0.0};
+    *k.st = KState{0, 0, 0, 0, 0.0, 0.0, tol2};
   }
 }
 
-// iteration it, step 1: convergence test on the previous residual, rho, p, p_hat.  With
-// update == false it only records the state (the final check after the last iteration).
+// iteration base + j, step 1: convergence test on the previous residual, rho, p, p_hat.
+// With update == false it only records the state (the final check after the last
+// iteration).
 template <int P>
-__global__ void kry_p_kernel(Kry k, int it, bool update) {
+__global__ void kry_p_kernel(Kry k, int j, bool update) {
   constexpr int NL = P + 1;
   __shared__ double red;
   if (kry_stopped(k)) return;
+  const int it = k.st->base + j;
   const double rr = kry_sum(k.part, kDotRR, &red);
   const double rho = kry_sum(k.part, kDotRR_hat, &red);
   const double bb = it == 0 ? rr : k.st->bb;
-  const bool conv = rr <= k.tol2 * bb;
+  const bool conv = rr <= k.st->tol2 * bb;
   const KScal pv = k.sc[it];
   const bool brk = !conv && update && (rho == 0.0 || !isfinite(rho) || pv.omega == 0.0);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -864,10 +871,11 @@ __global__ void kry_matvec_kernel(Kry k, const double* __restrict__ x, double* _
 
 // step 3: alpha, s = r - alpha v, s_hat
 template <int P>
-__global__ void kry_s_kernel(Kry k, int it) {
+__global__ void kry_s_kernel(Kry k, int j) {
   constexpr int NL = P + 1;
   __shared__ double red;
   if (kry_stopped(k)) return;
+  const int it = k.st->base + j;
   const double rv = kry_sum(k.part, kDotRV, &red);
   const double alpha = k.sc[it + 1].rho / rv;
   if (!isfinite(alpha)) {
@@ -890,9 +898,10 @@ __global__ void kry_s_kernel(Kry k, int it) {
 
 // step 5: omega, lambda += alpha p_hat + omega s_hat, r = s - omega t, and the partials of
 // r_hat.r and r.r for the next iteration's test
-__global__ void kry_x_kernel(Kry k, int it) {
+__global__ void kry_x_kernel(Kry k, int j) {
   __shared__ double red;
   if (kry_stopped(k)) return;
+  const int it = k.st->base + j;
   const double ts = kry_sum(k.part, kDotTS, &red);
   const double tt = kry_sum(k.part, kDotTT, &red);
   const double alpha = k.sc[it + 1].alpha;
@@ -909,7 +918,58 @@ __global__ void kry_x_kernel(Kry k, int it) {
   kry_partial(a, b, k.part, kDotRR_hat, kDotRR);
 }
 
+// the base index advances past a block of n iterations
+__global__ void kry_bump_kernel(KState* st, int n) { st->base += n; }
+
 static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// n iterations starting at offset 0 from the device's base, then the base's advance
+template <int P>
+static void kry_block(const Kry& k, int n, cudaStream_t s) {
+  for (int j = 0; j < n; ++j) {
+    kry_p_kernel<P><<<kKB, kKT, 0, s>>>(k, j, true);
+    kry_matvec_kernel<P><<<kKB, kKT, 0, s>>>(k, k.ph, k.v, k.rh, kDotRV, -1);
+    kry_s_kernel<P><<<kKB, kKT, 0, s>>>(k, j);
+    kry_matvec_kernel<P><<<kKB, kKT, 0, s>>>(k, k.sh, k.t, k.s, kDotTS, kDotTT);
+    kry_x_kernel<<<kKB, kKT, 0, s>>>(k, j);
+  }
+  kry_bump_kernel<<<1, 1, 0, s>>>(k.st, n);
+}
+
+// The graph of one block of kCheck iterations for the mesh's current scratch layout,
+// captured once and kept on the handle while the layout stays.
+template <int P>
+static vef_status kry_graph(Mesh& M, const Kry& k, cudaGraphExec_t* out) {
+  if (M.hrt_graph && M.hrt_graph_work == (const void*)M.work && M.hrt_graph_nl == k.nl && M.hrt_graph_p == P) {
+    *out = M.hrt_graph;
+    return VEF_OK;
+  }
+  if (M.hrt_graph) {
+    cudaGraphExecDestroy(M.hrt_graph);
+    M.hrt_graph = nullptr;
+  }
+  cudaStream_t cs;
+  VEF_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    kry_block<P>(k, kCheck, cs);
+    e = cudaStreamEndCapture(cs, &g);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&M.hrt_graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    M.hrt_graph = nullptr;
+    set_last_error(std::string("CUDA error capturing the multiplier iteration: ") + cudaGetErrorString(e));
+    return VEF_ERR_CUDA;
+  }
+  M.hrt_graph_work = M.work;
+  M.hrt_graph_nl = k.nl;
+  M.hrt_graph_p = P;
+  *out = M.hrt_graph;
+  return VEF_OK;
+}
 
 template <int P>
 static vef_status hrt_run(Mesh& M, const HrtIn& in, double tol, int max_iter, double* phi, double* J,
@@ -926,7 +986,7 @@ static vef_status hrt_run(Mesh& M, const HrtIn& in, double tol, int max_iter, do
   std::vector<double> refh;
   make_hrt_ref<P>(tab, refh);
   const size_t total = per_e * E + 10 * vec + (size_t)std::max(1LL, nfaces) * S::NL * S::NL +
-                       (size_t)kNumDots * kKB + 3 * nsc + 4 + refh.size();
+                       (size_t)kNumDots * kKB + 3 * nsc + sizeof(KState) / sizeof(double) + refh.size();
   vef_status st = ensure_buffer((void**)&M.work, &M.work_cap, total * sizeof(double));
   if (st != VEF_OK) return st;
   double* base = M.work;
@@ -939,16 +999,14 @@ static vef_status hrt_run(Mesh& M, const HrtIn& in, double tol, int max_iter, do
   double* re = take((size_t)S::NL4 * E);
   Kry k{};
   k.nx = M.nx; k.ny = M.ny; k.nfaces = nfaces; k.nl = nl; k.He = He;
-  k.x = lambda ? lambda : take(vec);
-  if (lambda) take(vec);
+  k.x = take(vec);   // copied to lambda at the end (the graph keeps one layout)
   k.r = take(vec); k.rh = take(vec); k.p = take(vec); k.v = take(vec); k.s = take(vec);
   k.t = take(vec); k.ph = take(vec); k.sh = take(vec);
   double* Minv = take((size_t)std::max(1LL, nfaces) * S::NL * S::NL);
   k.Minv = Minv;
   k.part = take((size_t)kNumDots * kKB);
-  k.sc = reinterpret_cast<KScal*>(take(3 * nsc));
-  k.st = reinterpret_cast<KState*>(take(4));
-  k.tol2 = tol * tol;
+  k.st = reinterpret_cast<KState*>(take(sizeof(KState) / sizeof(double)));
+  k.sc = reinterpret_cast<KScal*>(take(3 * nsc));   // last: its length follows max_iter
   double* refd = take(refh.size());
   // pageable source: the copy has taken the data when the call returns
   VEF_CUDA_TRY(cudaMemcpyAsync(refd, refh.data(), refh.size() * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -966,32 +1024,31 @@ static vef_status hrt_run(Mesh& M, const HrtIn& in, double tol, int max_iter, do
     VEF_CUDA_TRY(cudaGetLastError());
   }
   int it = 0;
-  KState hs{0, 0, 0.0, 0.0};
+  KState hs{};
   if (nl > 0) {
     hrt_gather_kernel<P><<<nblk(nl, 256), 256, 0, s>>>(M.nx, M.ny, nfaces, re, k.r);
     hrt_face_block_kernel<P><<<nblk(nfaces, 128), 128, 0, s>>>(M.nx, M.ny, nfaces, He, Minv, M.dev_status);
-    kry_init_kernel<<<kKB, kKT, 0, s>>>(k);
+    kry_init_kernel<<<kKB, kKT, 0, s>>>(k, tol * tol);
     VEF_CUDA_TRY(cudaGetLastError());
+    cudaGraphExec_t graph = nullptr;
+    if (max_iter >= kCheck && (st = kry_graph<P>(M, k, &graph)) != VEF_OK) return st;
     while (it < max_iter) {
       const int n = std::min(kCheck, max_iter - it);
-      for (int j = 0; j < n; ++j, ++it) {
-        kry_p_kernel<P><<<kKB, kKT, 0, s>>>(k, it, true);
-        kry_matvec_kernel<P><<<kKB, kKT, 0, s>>>(k, k.ph, k.v, k.rh, kDotRV, -1);
-        kry_s_kernel<P><<<kKB, kKT, 0, s>>>(k, it);
-        kry_matvec_kernel<P><<<kKB, kKT, 0, s>>>(k, k.sh, k.t, k.s, kDotTS, kDotTT);
-        kry_x_kernel<<<kKB, kKT, 0, s>>>(k, it);
-      }
+      if (n == kCheck) VEF_CUDA_TRY(cudaGraphLaunch(graph, s));
+      else kry_block<P>(k, n, s);
+      it += n;
       VEF_CUDA_TRY(cudaGetLastError());
       VEF_CUDA_TRY(cudaMemcpyAsync(&hs, k.st, sizeof(KState), cudaMemcpyDeviceToHost, s));
       VEF_CUDA_TRY(cudaStreamSynchronize(s));
       if (hs.done) break;
     }
     if (!hs.done) {   // the test after the last iteration
-      kry_p_kernel<P><<<kKB, kKT, 0, s>>>(k, it, false);
+      kry_p_kernel<P><<<kKB, kKT, 0, s>>>(k, 0, false);
       VEF_CUDA_TRY(cudaMemcpyAsync(&hs, k.st, sizeof(KState), cudaMemcpyDeviceToHost, s));
       VEF_CUDA_TRY(cudaStreamSynchronize(s));
     }
     if (hs.done) it = hs.iters;
+    if (lambda) VEF_CUDA_TRY(cudaMemcpyAsync(lambda, k.x, nl * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
   {
     KTimer kt(&M, VEF_K_HRT, s);

@@ -217,6 +217,7 @@ void destroy_events(Mesh& M);
 
 Mesh::~Mesh() {
   destroy_events(*this);
+  if (hrt_graph) cudaGraphExecDestroy(hrt_graph);
   schedules.clear();
   cudaFree(ctrl_dev);
   cudaFree(Mmat);
