@@ -150,28 +150,26 @@ __host__ __device__ __forceinline__ void face_pt(int f, int k, int nq, int& kx, 
   ky = f == 0 ? nq : (f == 1 ? k : (f == 2 ? nq + 1 : k));
 }
 
-// Eddington tensor (xx, xy, yy) of element e at a point where the DG basis values are
-// B[j] (from the element's nodal phi and P)
-template <int N>
-__device__ __forceinline__ void eddington_at(const double* __restrict__ phi, const double* __restrict__ P,
-                                             long long En, long long e, const double B[N], double Eo[3]) {
+// Eddington tensor (xx, xy, yy) of element e at table point (kx, ky), from the element's
+// nodal phi and P (the DG basis evaluated term by term)
+template <int P>
+__device__ __forceinline__ void eddington_pt(const HrtTab& t, const double* __restrict__ phi,
+                                             const double* __restrict__ Pm, long long En, long long e, int kx,
+                                             int ky, double Eo[3]) {
+  constexpr int Q = P + 1, N = Q * Q;
   double f = 0, a = 0, b = 0, c = 0;
+#pragma unroll
   for (int j = 0; j < N; ++j) {
+    const double Bj = t.dg[j % Q][kx] * t.dg[j / Q][ky];
     const size_t o = (size_t)e * N + j;
-    f += B[j] * phi[o];
-    a += B[j] * P[o];
-    b += B[j] * P[En + o];
-    c += B[j] * P[2 * En + o];
+    f += Bj * phi[o];
+    a += Bj * Pm[o];
+    b += Bj * Pm[En + o];
+    c += Bj * Pm[2 * En + o];
   }
   Eo[0] = a / f;
   Eo[1] = b / f;
   Eo[2] = c / f;
-}
-
-// DG basis values at table point (kx, ky)
-template <int P>
-__device__ __forceinline__ void dg_at(const HrtTab& t, int kx, int ky, double B[(P + 1) * (P + 1)]) {
-  for (int j = 0; j < (P + 1) * (P + 1); ++j) B[j] = t.dg[j % (P + 1)][kx] * t.dg[j / (P + 1)][ky];
 }
 
 struct HrtIn {
@@ -266,7 +264,7 @@ struct HrtSmem {
 };
 
 template <int P>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 hrt_local_kernel(long long E, int nx, int ny, HrtTab t, HrtRef ref, HrtIn in, HrtOut out, unsigned int* status) {
   using S = HrtShape<P>;
   constexpr int N = S::N, NQ = S::NQ, NQ2 = S::NQ2, NJ = S::NJ, MM = S::MM, LD = S::LD, NL = S::NL, NL4 = S::NL4;
@@ -292,9 +290,8 @@ hrt_local_kernel(long long E, int nx, int ny, HrtTab t, HrtRef ref, HrtIn in, Hr
       double F[4], H[8];
       map_geom(sm.ctrl, t, kx, ky, F, H);
       const double J = F[0] * F[3] - F[1] * F[2];
-      double B[N], Eo[3];
-      dg_at<P>(t, kx, ky, B);
-      eddington_at<N>(in.phi, in.P, En, e, B, Eo);
+      double Eo[3];
+      eddington_pt<P>(t, in.phi, in.P, En, e, kx, ky, Eo);
       if (vol) {
         double* g = sm.pv[pt];
         const double adj[4] = {F[3], -F[1], -F[2], F[0]};
@@ -308,8 +305,9 @@ hrt_local_kernel(long long E, int nx, int ny, HrtTab t, HrtRef ref, HrtIn in, Hr
         double q1x = 0.0, q1y = 0.0;
         if (in.Q1)
           for (int j = 0; j < N; ++j) {
-            q1x += B[j] * in.Q1[(size_t)e * N + j];
-            q1y += B[j] * in.Q1[En + (size_t)e * N + j];
+            const double Bj = t.dg[j % (P + 1)][kx] * t.dg[j / (P + 1)][ky];
+            q1x += Bj * in.Q1[(size_t)e * N + j];
+            q1y += Bj * in.Q1[En + (size_t)e * N + j];
           }
         g[18] = q1x;
         g[19] = q1y;
@@ -320,9 +318,8 @@ hrt_local_kernel(long long E, int nx, int ny, HrtTab t, HrtRef ref, HrtIn in, Hr
         if (nb >= 0) {
           int nkx, nky;
           face_pt((f + 2) & 3, k, NQ, nkx, nky);
-          double Bn[N], Enb[3];
-          dg_at<P>(t, nkx, nky, Bn);
-          eddington_at<N>(in.phi, in.P, En, nb, Bn, Enb);
+          double Enb[3];
+          eddington_pt<P>(t, in.phi, in.P, En, nb, nkx, nky, Enb);
           const double a00 = 0.5 * (Eo[0] + Enb[0]), a01 = 0.5 * (Eo[1] + Enb[1]), a11 = 0.5 * (Eo[2] + Enb[2]);
           const double En0 = a00 * nd[0] + a01 * nd[1], En1 = a01 * nd[0] + a11 * nd[1];
           // v_a . {E} n ds = v_hat_a . F^T ({E} n ds) / J
