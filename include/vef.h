@@ -73,7 +73,9 @@ typedef enum {
   VEF_ERR_TIMEOUT = 4,            /* a bounded device-side wait (staging copy) gave up */
   VEF_ERR_NOT_CONVERGED = 5,      /* an inner or defect-correction iteration hit its cap */
   VEF_ERR_NONPOSITIVE_DENOM = 6,  /* sum_d w_d psi_d <= 1e-300 at a closure point (NaN written) */
-  VEF_ERR_NOT_IMPLEMENTED = 7
+  VEF_ERR_NOT_IMPLEMENTED = 7,
+  VEF_ERR_BOUNDS = 8              /* bounds-checked build only: a kernel met an index outside its
+                                     array (the access was skipped; results are undefined) */
 } vef_status;
 
 enum { VEF_FP64 = 0, VEF_MIXED = 1 };
@@ -97,13 +99,17 @@ enum {
                                pivoting, as the library does by itself only for the systems
                                whose unpivoted elimination meets a small pivot (see
                                VEF_PIVOT_FLOOR_LOG2_FP64); slow, meant for testing */
-  VEF_REUSE_FACTORS = 16    /* keep the local factorisation of the previous call with this
+  VEF_REUSE_FACTORS = 16,   /* keep the local factorisation of the previous call with this
                                mesh and direction set in this precision instead of forming it
                                again (vef_sweep, vef_source_iterate, vef_batch_sweep): the
                                caller guarantees sigma_t is unchanged, as in the outer
                                iterations of the VEF method, where only the scattering
                                source changes.  Without a previous factorisation the call
                                factorises as usual. */
+  VEF_CKPT_FP32 = 32        /* vef_adjoint_sweep: psi_ckpt points to an FP32 copy of the
+                               forward psi (float [D][E][n], half the memory of the FP64
+                               checkpoint); the gradients then carry its rounding, about
+                               1e-7 relative */
 };
 
 typedef struct vef_mesh_s* vef_mesh;
@@ -242,7 +248,8 @@ vef_status vef_region_weights(vef_mesh mesh, double x0, double y0, double x1, do
  *   dR_dsigma_t[e] = - sum_d lambda_{d,e}^T M_e psi_{d,e},
  *   dR_dsigma_s[e] =   sum_d lambda_{d,e}^T M_e phi_in,e / (4 pi)
  * with M_e the element mass matrix.  psi_ckpt [device] [D][E][n] is the forward sweep's
- * psi (checkpoint); g [device] [E][n]; lambda [device] [D][E][n] output or NULL (then a
+ * psi (checkpoint; FP64, or FP32 with VEF_CKPT_FP32 in opts->flags, read as const float*);
+ * g [device] [E][n]; lambda [device] [D][E][n] output or NULL (then a
  * library buffer is used); dR_dsigma_t, dR_dsigma_s [device] [E] outputs.  opts: tol and
  * max_passes bound the inner iteration of coupled groups beyond the direct limits;
  * VEF_SWEEP_CLUSTER or a tile_override selects the cluster form of the backward sweep
@@ -423,14 +430,16 @@ vef_status vef_schedule_host(int nx, int ny, int p, const double* nds, const dou
 vef_status vef_wait_selftest(int kind, int satisfied, long long polls, void* stream);
 
 /* Device status bits: what a kernel records when a bounded wait runs out, an iteration
- * hits its cap, a closure denominator is not positive or an element system is singular;
- * the next synchronising call maps them to VEF_ERR_TIMEOUT, VEF_ERR_NOT_CONVERGED,
- * VEF_ERR_NONPOSITIVE_DENOM and VEF_ERR_NOT_CONVERGED. */
+ * hits its cap, a closure denominator is not positive, an element system is singular, or
+ * (bounds-checked build) an index falls outside its array; the next synchronising call
+ * maps them to VEF_ERR_TIMEOUT, VEF_ERR_NOT_CONVERGED, VEF_ERR_NONPOSITIVE_DENOM,
+ * VEF_ERR_NOT_CONVERGED and VEF_ERR_BOUNDS. */
 enum {
   VEF_STATUS_TIMEOUT = 1,
   VEF_STATUS_NOT_CONVERGED = 2,
   VEF_STATUS_NONPOSITIVE = 4,
-  VEF_STATUS_SINGULAR = 8
+  VEF_STATUS_SINGULAR = 8,
+  VEF_STATUS_BOUNDS = 16
 };
 
 /* Failure-detection test hook (the paper has no counterpart): ORs `bits` (VEF_STATUS_*)
@@ -439,9 +448,19 @@ enum {
  * set stops polling at once, and its warp stops reading staged data (the call's results are
  * then undefined), so a call made while a timeout is recorded and not yet collected returns
  * quickly; the next synchronising call returns the error and clears the word.
- * Errors: VEF_ERR_INVALID_ARG (NULL mesh, bits empty or outside the four values, another
+ * Errors: VEF_ERR_INVALID_ARG (NULL mesh, bits empty or outside the five values, another
  * device). */
 vef_status vef_mesh_inject_status(vef_mesh mesh, unsigned int bits, void* stream);
+
+/* 1 when this library is the bounds-checked build (libvef_checked.so: compiled with
+ * VEF_CHECKED, see the package's build(checked=True)), 0 for the normal build.  The checked
+ * build tests the indices the sweep, adjoint, group and factorisation kernels take from the
+ * schedule (record and member indices, element indices, shared-memory trace-slot ids)
+ * before each access; an index outside its array sets VEF_STATUS_BOUNDS and the access is
+ * skipped, so the next synchronising call returns VEF_ERR_BOUNDS instead of the kernel
+ * touching memory it does not own.  It stands in for a memory checker; the arithmetic is
+ * the normal build's. */
+int vef_build_checked(void);
 
 /* Eddington tensor without device allocation (the paper has no counterpart: this is a
  * library interface).  Same result as vef_moments with only Eten requested:

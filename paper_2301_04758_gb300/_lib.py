@@ -9,6 +9,8 @@ import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libvef.so")
+# the bounds-checked build (build(checked=True)); load() takes it when VEF_CHECKED=1
+CHECKED_LIB_PATH = os.path.join(_PKG, "libvef_checked.so")
 
 VEF_OK = 0
 VEF_ERR_INVALID_ARG = 1
@@ -18,6 +20,7 @@ VEF_ERR_TIMEOUT = 4
 VEF_ERR_NOT_CONVERGED = 5
 VEF_ERR_NONPOSITIVE_DENOM = 6
 VEF_ERR_NOT_IMPLEMENTED = 7
+VEF_ERR_BOUNDS = 8
 
 VEF_FP64 = 0
 VEF_MIXED = 1
@@ -26,10 +29,12 @@ VEF_SWEEP_CLUSTER = 2
 VEF_APPLY_SEPARATE = 4
 VEF_PIVOT_ALWAYS = 8
 VEF_REUSE_FACTORS = 16
+VEF_CKPT_FP32 = 32
 VEF_STATUS_TIMEOUT = 1
 VEF_STATUS_NOT_CONVERGED = 2
 VEF_STATUS_NONPOSITIVE = 4
 VEF_STATUS_SINGULAR = 8
+VEF_STATUS_BOUNDS = 16
 
 # every symbol include/vef.h declares
 EXPORTS = ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sync", "vef_sweep",
@@ -37,7 +42,7 @@ EXPORTS = ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sy
            "vef_profile_read", "vef_measure_fma_peak", "vef_wait_selftest", "vef_eddington_noalloc",
            "vef_batch_create", "vef_batch_destroy", "vef_batch_sweep", "vef_batch_tune",
            "vef_region_weights", "vef_schedule_host", "vef_mesh_inject_status", "vef_hrt_solve",
-           "vef_vef_iterate",
+           "vef_vef_iterate", "vef_build_checked",
            "vef_status_string", "vef_last_error")
 
 KERNEL_CLASSES = ("geometry", "factor", "sweep", "residual", "source", "moments", "adjoint", "group", "hrt")
@@ -137,14 +142,17 @@ def _declare(lib):
     lib.vef_status_string.restype = ctypes.c_char_p
     lib.vef_last_error.argtypes = []
     lib.vef_last_error.restype = ctypes.c_char_p
+    lib.vef_build_checked.argtypes = []
+    lib.vef_build_checked.restype = ctypes.c_int
 
 
 def load(path=None):
-    """Load libvef.so (built by paper_2301_04758_gb300.build.build())."""
+    """Load libvef.so (built by paper_2301_04758_gb300.build.build()), or with VEF_CHECKED=1
+    in the environment the bounds-checked libvef_checked.so (build(checked=True))."""
     global _lib
     if _lib is not None and path is None:
         return _lib
-    p = path or LIB_PATH
+    p = path or (CHECKED_LIB_PATH if os.environ.get("VEF_CHECKED") == "1" else LIB_PATH)
     if not os.path.exists(p):
         raise RuntimeError(f"libvef.so not found at {p}; build it with "
                            "`python -c 'import __graft_entry__ as g; g.build()'`")

@@ -232,6 +232,8 @@ class Mesh:
                 info=False, stream=None, kernel="cta"):
         """Gradients of R = sum g * phi: returns (dR/dsigma_t [E], dR/dsigma_s [E] or None, lambda).
 
+        psi: the forward sweep's psi [D][E][n] as checkpoint, float64, or float32 (an FP32
+        copy, half the memory; the gradients then carry its rounding).
         kernel: "cta" (one CTA per direction, the default) or "cluster"."""
         om, omp = _host(omega)
         w, wp = _host(weights)
@@ -241,6 +243,10 @@ class Mesh:
         dss = self._empty(self.E) if phi_in is not None else None
         inf = _lib.VefInfo() if info else None
         o = _opts(kernel=kernel)
+        if psi.dtype == torch.float32:
+            o.flags |= _lib.VEF_CKPT_FP32
+        elif psi.dtype != torch.float64:
+            raise TypeError("psi checkpoint must be float64 or float32")
         st = self.lib.vef_adjoint_sweep(self.handle, _ptr(sigma_t), _ptr(sigma_s), _ptr(phi_in), omp,
                                         wp, D, _ptr(psi), _ptr(g), _ptr(lam), _ptr(dst), _ptr(dss),
                                         ctypes.byref(o), ctypes.byref(inf) if info else None, _stream(stream))

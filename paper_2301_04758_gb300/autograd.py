@@ -14,9 +14,11 @@ import torch
 
 class _TransportPhi(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, sigma_t, sigma_s, mesh, omega, weights, phi_in, source, inflow):
+    def forward(ctx, sigma_t, sigma_s, mesh, omega, weights, phi_in, source, inflow, ckpt):
         psi = mesh.sweep(sigma_t, sigma_s, omega, weights, phi_in=phi_in, source=source, inflow=inflow)
         phi = mesh.moments(psi, omega, weights, outputs=("phi",))["phi"]
+        if ckpt == "fp32":   # the checkpoint at half the memory
+            psi = psi.float()
         ctx.save_for_backward(sigma_t, sigma_s, psi)   # psi kept per direction as checkpoint
         ctx.mesh, ctx.omega, ctx.weights, ctx.phi_in = mesh, omega, weights, phi_in
         return phi
@@ -30,14 +32,19 @@ class _TransportPhi(torch.autograd.Function):
             dst = None
         if not ctx.needs_input_grad[1]:
             dss = None
-        return dst, dss, None, None, None, None, None, None
+        return dst, dss, None, None, None, None, None, None, None
 
 
-def transport_phi(mesh, sigma_t, sigma_s, omega, weights, phi_in=None, source=None, inflow=None):
+def transport_phi(mesh, sigma_t, sigma_s, omega, weights, phi_in=None, source=None, inflow=None,
+                  ckpt="fp64"):
     """phi [E][n] of one transport inversion, differentiable in sigma_t and sigma_s.
 
     sigma_t, sigma_s: CUDA float64 [E] (leaf tensors may require grad); phi_in [E][n] or
     None (then dL/dsigma_s is zero: sigma_s has no effect); source [E][n] or [D][E][n];
-    inflow [D][N_bf][nq] or None; omega [D][2] and weights [D] on the host."""
-    phi = _TransportPhi.apply(sigma_t, sigma_s, mesh, omega, weights, phi_in, source, inflow)
+    inflow [D][N_bf][nq] or None; omega [D][2] and weights [D] on the host.  ckpt: "fp64"
+    keeps the forward psi for the backward pass as it is, "fp32" keeps an FP32 copy (half
+    the memory; the gradients then carry its rounding, about 1e-7 relative)."""
+    if ckpt not in ("fp64", "fp32"):
+        raise ValueError("ckpt must be 'fp64' or 'fp32'")
+    phi = _TransportPhi.apply(sigma_t, sigma_s, mesh, omega, weights, phi_in, source, inflow, ckpt)
     return phi

@@ -2,7 +2,8 @@
 
 Every translation unit under csrc/ is compiled in parallel to _build/ at the repository
 root and linked into paper_2301_04758_gb300/libvef.so.  Objects are rebuilt when their
-source, a header, or this file is newer.
+source, a header, or this file is newer.  build(checked=True) makes the bounds-checked
+variant instead (-DVEF_CHECKED, objects in _build/checked/, libvef_checked.so).
 """
 import concurrent.futures
 import os
@@ -15,6 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libvef.so")
+CHECKED_LIB = os.path.join(PKG, "libvef_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
@@ -38,11 +40,11 @@ def _headers_mtime():
     return max(os.path.getmtime(h) for h in hs)
 
 
-def _compile(src, verbose):
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src, verbose, checked=False):
+    obj = os.path.join(BUILD, "checked" if checked else "", os.path.basename(src) + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _headers_mtime()):
         return obj, ""
-    cmd = [_nvcc()] + FLAGS + ARCH + ["-c", src, "-o", obj]
+    cmd = [_nvcc()] + FLAGS + (["-DVEF_CHECKED"] if checked else []) + ARCH + ["-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -51,25 +53,26 @@ def _compile(src, verbose):
     return obj, r.stderr
 
 
-def build(verbose=False, jobs=None):
-    """Compile csrc/ and link libvef.so; returns the library path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose=False, jobs=None, checked=False):
+    """Compile csrc/ and link libvef.so (checked: libvef_checked.so); returns its path."""
+    lib = CHECKED_LIB if checked else LIB
+    os.makedirs(os.path.join(BUILD, "checked") if checked else BUILD, exist_ok=True)
     srcs = _sources()
     jobs = jobs or min(len(srcs), os.cpu_count() or 4)
     with concurrent.futures.ThreadPoolExecutor(jobs) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose), srcs))
+        results = list(ex.map(lambda s: _compile(s, verbose, checked), srcs))
     objs = [o for o, _ in results]
     if verbose:
         for o, log in results:
             if log:
                 sys.stderr.write(f"--- {os.path.basename(o)}\n{log}")
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        cmd = [_nvcc(), "-shared"] + ARCH + ["-o", LIB] + objs + ["-lpthread"]
+    if not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        cmd = [_nvcc(), "-shared"] + ARCH + ["-o", lib] + objs + ["-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv))
+    print(build(verbose="-v" in sys.argv, checked="--checked" in sys.argv))

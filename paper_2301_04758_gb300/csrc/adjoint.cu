@@ -45,7 +45,8 @@ struct AdjArgs {
   const double* recx;     // extra record array X
   long long nmem;
   const double* g;        // [E][n]
-  const double* psi;      // [D][E][n] forward checkpoint
+  const double* psi;      // [D][E][n] forward checkpoint (FP64), or
+  const float* psi32;     //   its FP32 copy (VEF_CKPT_FP32)
   const double* Mm;       // [E][n][n]
   const double* mphi;     // [E][n] M phi_in or null
   const uint32_t* link;   // [members][4] receiver member and W slot across each face
@@ -118,10 +119,15 @@ __device__ __forceinline__ void adj_finish(const AdjArgs& a, long long m, int d,
   if (act) {
     a.lambda[((size_t)d * a.E + e) * N + i] = lam;
     const double* Mr = a.Mm + ((size_t)e * N + i) * N;
-    const double* pe = a.psi + ((size_t)d * a.E + e) * N;
+    const size_t o = ((size_t)d * a.E + e) * N;
     double mp = 0.0;
+    if (a.psi32) {
 #pragma unroll
-    for (int j = 0; j < N; ++j) mp += Mr[j] * pe[j];
+      for (int j = 0; j < N; ++j) mp += Mr[j] * (double)a.psi32[o + j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < N; ++j) mp += Mr[j] * a.psi[o + j];
+    }
     gt = -lam * mp;
     if (a.mphi) gs = lam * a.mphi[(size_t)e * N + i] / kFourPi;
   }
@@ -482,6 +488,10 @@ __global__ void __maxnreg__(128) adjoint_cta_kernel(AdjArgs a) {
         const long long m0 = (long long)mb + r0;
         unsigned char* rb = ring + (size_t)b * Sh::kRound;
         fence_proxy_async_smem();
+        if (!(VEF_IN_RANGE(m0, a.nmem, a.status) && VEF_IN_RANGE(m0 + cnt - 1, a.nmem, a.status))) {
+          mbar_arrive_expect_tx(&full[b], 0u);   // the round completes without data
+          continue;
+        }
         mbar_arrive_expect_tx(&full[b], (unsigned)(cnt * (L::kStaged + L::kYBytes + 16)));
         bulk_g2s(rb, L::s_at(a.rec, m0), (unsigned)(cnt * L::kStaged), &full[b]);
         bulk_g2s(rb + Sh::kYOff, a.yadj + m0 * L::kYStride, (unsigned)(cnt * L::kYBytes), &full[b]);
@@ -509,6 +519,8 @@ __global__ void __maxnreg__(128) adjoint_cta_kernel(AdjArgs a) {
   if (ia == 0) on_face(3, ib);
   double* scratch = scratch_all + (compute ? warp : 0) * (SPC * 2 * Q * N);
   double* radj = a.radj + (size_t)d * a.E * N;
+  const int ntr = a.tr_bytes / (Q * (int)sizeof(double));   // trace slots in shared memory
+  (void)ntr;
   if (threadIdx.x < Q) tr[kTraceZero * Q + threadIdx.x] = 0.0;
   const int gidx = warp - Sh::kCompute;
   AdjGroupSmem<P>& gs = *reinterpret_cast<AdjGroupSmem<P>*>(gsm_all + (compute ? 0 : gidx) * Sh::kGs);
@@ -539,7 +551,7 @@ __global__ void __maxnreg__(128) adjoint_cta_kernel(AdjArgs a) {
             auto rd = [&](int f) {
               if (f < 0) return kTraceZero;
               const unsigned id = ((f >= 2 ? ts.z : ts.y) >> (16 * (f & 1))) & 0xffffu;
-              return id == kTraceSink ? kTraceZero : id;
+              return id == kTraceSink || !VEF_IN_RANGE(id, ntr, a.status) ? kTraceZero : id;
             };
             r -= tr[rd(fA) * Q + pA];
             r -= tr[rd(fB) * Q + pB];
@@ -555,6 +567,8 @@ __global__ void __maxnreg__(128) adjoint_cta_kernel(AdjArgs a) {
                 const uint32_t lk = a.link[m * 4 + f];
                 if (lk == ~0u) continue;
                 const long long mn = (long long)(lk >> 2);
+                if (!(VEF_IN_RANGE(mn, a.nmem, a.status) && VEF_IN_RANGE(nb_elem(a.nx, a.ny, e, f), a.E, a.status)))
+                  continue;
                 const double* W = L::slot(L::s_at(a.rec, mn), L::x_at(a.recx, mn), (int)(lk & 3u)) + t * N;
                 const double* rn = radj + (size_t)nb_elem(a.nx, a.ny, e, f) * N;
                 double acc = 0.0;
@@ -563,7 +577,7 @@ __global__ void __maxnreg__(128) adjoint_cta_kernel(AdjArgs a) {
                 r -= acc;
               }
             }
-            radj[(size_t)e * N + i] = r;
+            if (VEF_IN_RANGE(e, a.E, a.status)) radj[(size_t)e * N + i] = r;
             // this task's projections onto its donors' faces, W slots 0 and 1 (zero slots
             // of absent faces give zero products)
             const double* W = L::slot(rs, nullptr, 0);
@@ -580,7 +594,7 @@ __global__ void __maxnreg__(128) adjoint_cta_kernel(AdjArgs a) {
             if (tks >= cend) continue;
             const uint4 tss = *reinterpret_cast<const uint4*>(rb + Sh::kTsOff + tks * 16);
             const unsigned wid = (tss.x >> (16 * sl)) & 0xffffu;
-            if (wid == kTraceZero) continue;
+            if (wid == kTraceZero || !VEF_IN_RANGE(wid, ntr, a.status)) continue;
             const double* pr = scratch + ((s * 2 + sl) * Q + t) * N;
             double sum = 0.0;
 #pragma unroll
@@ -793,7 +807,8 @@ extern "C" vef_status vef_adjoint_sweep(vef_mesh mesh, const double* sigma_t, co
   a.rec = (const double*)S->rec64;
   a.nmem = S->members;
   a.g = g;
-  a.psi = psi_ckpt;
+  if (opts && (opts->flags & VEF_CKPT_FP32)) a.psi32 = reinterpret_cast<const float*>(psi_ckpt);
+  else a.psi = psi_ckpt;
   a.Mm = M.Mmat;
   a.radj = M.work2;
   a.lambda = lambda ? lambda : M.work2 + tot;

@@ -100,8 +100,17 @@ extern "C" const char* vef_status_string(vef_status s) {
     case VEF_ERR_NOT_CONVERGED: return "VEF_ERR_NOT_CONVERGED";
     case VEF_ERR_NONPOSITIVE_DENOM: return "VEF_ERR_NONPOSITIVE_DENOM";
     case VEF_ERR_NOT_IMPLEMENTED: return "VEF_ERR_NOT_IMPLEMENTED";
+    case VEF_ERR_BOUNDS: return "VEF_ERR_BOUNDS";
   }
   return "VEF_ERR_UNKNOWN";
 }
 
 extern "C" const char* vef_last_error(void) { return vef::g_last_error.c_str(); }
+
+extern "C" int vef_build_checked(void) {
+#ifdef VEF_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}

@@ -52,6 +52,7 @@ enum : unsigned int {
   kDevNotConverged = 2u,
   kDevNonpositive = 4u,
   kDevSingular = 8u,
+  kDevBounds = 16u,        // bounds-checked build: an index outside its array (access skipped)
 };
 // word of the device status array holding the number of tasks the last factorisation
 // refactorised with partial pivoting

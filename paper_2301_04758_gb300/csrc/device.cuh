@@ -8,6 +8,21 @@
 
 namespace vef {
 
+// Bounds-checked build (compiled with -DVEF_CHECKED into libvef_checked.so):
+// VEF_IN_RANGE(i, n, status) is false when i lies outside [0, n), after setting kDevBounds in
+// the device status word, and the access it guards is skipped; in the normal build it is the
+// constant true and the guard compiles away.
+#ifdef VEF_CHECKED
+__device__ __forceinline__ bool in_range_checked(long long i, long long n, unsigned int* status) {
+  if (i >= 0 && i < n) return true;
+  atomicOr(status, kDevBounds);
+  return false;
+}
+#define VEF_IN_RANGE(i, n, status) ::vef::in_range_checked((long long)(i), (long long)(n), (status))
+#else
+#define VEF_IN_RANGE(i, n, status) true
+#endif
+
 // Factor records of all (element, direction) pairs, in schedule order, as two arrays of
 // 16-byte-aligned blocks so the sweep can stage a run of consecutive tasks with one bulk
 // copy:

@@ -112,12 +112,13 @@ __global__ void inject_status_kernel(unsigned int* status, unsigned int bits) { 
 }  // namespace vef
 
 static_assert(VEF_STATUS_TIMEOUT == vef::kDevTimeout && VEF_STATUS_NOT_CONVERGED == vef::kDevNotConverged &&
-                  VEF_STATUS_NONPOSITIVE == vef::kDevNonpositive && VEF_STATUS_SINGULAR == vef::kDevSingular,
+                  VEF_STATUS_NONPOSITIVE == vef::kDevNonpositive && VEF_STATUS_SINGULAR == vef::kDevSingular &&
+                  VEF_STATUS_BOUNDS == vef::kDevBounds,
               "public status bits match the device status word");
 
 extern "C" vef_status vef_mesh_inject_status(vef_mesh mesh, unsigned int bits, void* stream) {
   if (!mesh) { vef::set_last_error("mesh is NULL"); return VEF_ERR_INVALID_ARG; }
-  if (bits == 0 || (bits & ~0xfu)) { vef::set_last_error("bits must be a non-empty set of VEF_STATUS_* values"); return VEF_ERR_INVALID_ARG; }
+  if (bits == 0 || (bits & ~0x1fu)) { vef::set_last_error("bits must be a non-empty set of VEF_STATUS_* values"); return VEF_ERR_INVALID_ARG; }
   int dev = 0;
   VEF_CUDA_TRY(cudaGetDevice(&dev));
   if (dev != mesh->impl.device) { vef::set_last_error("mesh belongs to another device"); return VEF_ERR_INVALID_ARG; }

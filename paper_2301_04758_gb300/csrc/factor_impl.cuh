@@ -134,6 +134,7 @@ __device__ __forceinline__ bool factor_task(long long m, long long nmem, const u
   using L = Rec<P, T>;
   const uint32_t c = code[m];
   const int d = (int)(c >> 22), e = (int)(c & 0x3fffffu);
+  if (!VEF_IN_RANGE(e, E, status)) return false;
   const T mu = (T)omega[2 * d], eta = (T)omega[2 * d + 1];
   const T st = (T)sigma_t[e];
   const uint16_t bits = finfo[(size_t)d * E + e];
@@ -336,8 +337,9 @@ factor_pivot_kernel(long long nmem, const uint32_t* __restrict__ code, const uin
   const long long cnt = (long long)*piv_count;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < cnt && t < nmem;
        t += (long long)gridDim.x * blockDim.x)
-    factor_task<P, T, true, true>((long long)piv_list[t], nmem, code, finfo, omega, sigma_t, Mm, Gxm, Gym, nds,
-                                  ft, fll, nx, ny, E, rec, status, rhs);
+    if (VEF_IN_RANGE(piv_list[t], nmem, status))
+      factor_task<P, T, true, true>((long long)piv_list[t], nmem, code, finfo, omega, sigma_t, Mm, Gxm, Gym, nds,
+                                    ft, fll, nx, ny, E, rec, status, rhs);
 }
 
 // Element-major factorisation (used for p >= 3, where a whole element matrix per thread
@@ -396,7 +398,7 @@ factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const 
   char* recx = (char*)rec + nmem * (long long)L::kStaged;
   for (int d0 = warp * UPW; d0 < D; d0 += nwarps * UPW) {
     const int d = d0 + u;
-    const bool valid = u < UPW && d < D;
+    bool valid = u < UPW && d < D;
     const int dd = valid ? d : 0;
     const T mu = (T)omega[2 * dd], eta = (T)omega[2 * dd + 1];
     const uint16_t bits = finfo[(size_t)dd * E + e];
@@ -489,6 +491,7 @@ factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const 
     }
     // records: A^{-1} column-major, then the W slots of the interior inflow faces
     const long long m = valid ? (long long)member_of[(size_t)dd * E + e] : 0;
+    valid = valid && VEF_IN_RANGE(m, nmem, status);
     char* out = L::s_at(rec, m);
     char* outx = L::x_at(recx, m);
     if (valid) {

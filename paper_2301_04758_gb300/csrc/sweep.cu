@@ -204,6 +204,7 @@ __device__ __forceinline__ void group_solve(const SweepArgs<T>& a, int d, int s0
   const int lane = threadIdx.x & 31;
   const int first = a.slot_first[s0];
   const int cnt = a.slot_count[s0];
+  if (!(VEF_IN_RANGE(first, a.nmem, a.status) && VEF_IN_RANGE(first + cnt - 1, a.nmem, a.status))) return;
   const int i = lane;
   const bool act = lane < N;
   int it = 0;
@@ -278,6 +279,7 @@ __device__ __forceinline__ void group_stage(const SweepArgs<T>& a, int s0, Group
   const int lane = threadIdx.x & 31;
   const int first = a.slot_first[s0];
   const int cnt = a.slot_count[s0];           // <= group_direct_members(P) <= 32
+  if (!(VEF_IN_RANGE(first, a.nmem, a.status) && VEF_IN_RANGE(first + cnt - 1, a.nmem, a.status))) return;
   const int gid = a.slot_gid[s0];
   uint4 info = make_uint4(0u, 0u, 0xffffffffu, 0u);
   uint32_t nbp = 0xffffffffu;
@@ -326,6 +328,8 @@ __device__ __forceinline__ void group_solve_direct(const SweepArgs<T>& a, int d,
   using L = Rec<P, T>;
   const int lane = threadIdx.x & 31;
   const int first = a.slot_first[s0];
+  if (!(VEF_IN_RANGE(first, a.nmem, a.status) && VEF_IN_RANGE(first + a.slot_count[s0] - 1, a.nmem, a.status)))
+    return;
   const int m = g.m, nt = g.nt;
   // z: y minus the couplings to elements outside the group (earlier levels)
   for (int idx = lane; idx < m * N; idx += 32) {
@@ -808,6 +812,10 @@ __device__ __forceinline__ void sweep_cta_direction(const SweepArgs<T>& a, const
         const long long m0 = (long long)mb + r0;
         unsigned char* rb = ring + (size_t)b * Sh::kRound;
         fence_proxy_async_smem();
+        if (!(VEF_IN_RANGE(m0, a.nmem, a.status) && VEF_IN_RANGE(m0 + cnt - 1, a.nmem, a.status))) {
+          mbar_arrive_expect_tx(&full[b], 0u);   // the round completes without data
+          continue;
+        }
         mbar_arrive_expect_tx(&full[b], (unsigned)(cnt * (L::kStaged + L::kYBytes + 16)));
         bulk_g2s(rb, L::s_at(a.rec, m0), (unsigned)(cnt * L::kStaged), &full[b]);
         bulk_g2s(rb + Sh::kYOff, a.y + m0 * L::kYStride, (unsigned)(cnt * L::kYBytes), &full[b]);
@@ -842,6 +850,8 @@ __device__ __forceinline__ void sweep_cta_direction(const SweepArgs<T>& a, const
   const unsigned keepA = fA >= 0 ? 0xffffu : 0u, keepB = fB >= 0 ? 0xffffu : 0u;
   const unsigned sinkA = fA >= 0 ? 0u : kTraceSink, sinkB = fB >= 0 ? 0u : kTraceSink;
   T* outd = a.out + (size_t)d * a.E * N;
+  const int ntr = a.tr_bytes / (Q * (int)sizeof(T));   // trace slots in shared memory
+  (void)ntr;
   if (threadIdx.x < Q) tr[kTraceZero * Q + threadIdx.x] = (T)0;
   auto direct = [&](int slot) { return a.slot_gid != nullptr && a.slot_gid[slot] >= 0; };
   const int gidx = warp - Sh::kCompute;   // group warp index (group warps only)
@@ -872,6 +882,9 @@ __device__ __forceinline__ void sweep_cta_direction(const SweepArgs<T>& a, const
             const char* rs = (const char*)rb + tk * L::kStaged;
             const uint4 info = *reinterpret_cast<const uint4*>(rs);
             const uint4 ts = *reinterpret_cast<const uint4*>(rb + Sh::kTsOff + tk * 16);
+            if (!(VEF_IN_RANGE(info.x, a.E, a.status) && VEF_IN_RANGE(ts.x & 0xffffu, ntr, a.status) &&
+                  VEF_IN_RANGE(ts.x >> 16, ntr, a.status)))
+              continue;
             const T* W = L::slot(rs, nullptr, 0);   // slots 0, 1 back to back; absent ones are zero
             const T* u0 = tr + (ts.x & 0xffffu) * Q;
             const T* u1 = tr + (ts.x >> 16) * Q;
@@ -900,7 +913,10 @@ __device__ __forceinline__ void sweep_cta_direction(const SweepArgs<T>& a, const
                 if (f == 0xffu || (sl < 2 && ((ts.x >> (16 * sl)) & 0xffffu) != kTraceZero)) continue;
                 const T* Ws = sl < 2 ? W + sl * L::kSlot
                                      : L::slot(nullptr, L::x_at(a.recx, (long long)mb + r0 + task), sl);
-                y -= face_term<P, T, false>(Ws, outd + (size_t)nb_elem(a.nx, a.ny, e, (int)f) * N, (int)f, i);
+                const int nb = nb_elem(a.nx, a.ny, e, (int)f);
+                if (!(VEF_IN_RANGE(nb, a.E, a.status) && VEF_IN_RANGE((long long)mb + r0 + task, a.nmem, a.status)))
+                  continue;
+                y -= face_term<P, T, false>(Ws, outd + (size_t)nb * N, (int)f, i);
               }
             }
             outd[(size_t)(e * N + i)] = y;
@@ -908,8 +924,8 @@ __device__ __forceinline__ void sweep_cta_direction(const SweepArgs<T>& a, const
             // faces nobody reads: id kTraceSink)
             const unsigned idA = (((zA ? ts.z : ts.y) >> shA) & keepA) | sinkA;
             const unsigned idB = (((zB ? ts.z : ts.y) >> shB) & keepB) | sinkB;
-            if (idA != kTraceSink) tr[idA * Q + pA] = y;
-            if (idB != kTraceSink) tr[idB * Q + pB] = y;
+            if (idA != kTraceSink && VEF_IN_RANGE(idA, ntr, a.status)) tr[idA * Q + pA] = y;
+            if (idB != kTraceSink && VEF_IN_RANGE(idB, ntr, a.status)) tr[idB * Q + pB] = y;
           }
         }
         __syncwarp();
@@ -1326,6 +1342,7 @@ static vef_status make_sweep_args(const SweepCall& c, const double* rhs, T* out,
   a.ny = M.ny;
   a.E = M.E;
   a.nbf = M.nbf;
+  a.nmem = S.members;
   const double eps = std::is_same<T, double>::value ? 2.2e-16 : 1.2e-7;
   a.tol = (T)std::max(c.tol, 8.0 * eps);
   a.max_inner = std::max(2, 4 * c.max_passes);
@@ -1649,6 +1666,7 @@ vef_status collect_status(Mesh& M, cudaStream_t stream, vef_info* info) {
     info->max_inner_iterations = (int)h[2];
     info->pivoted_tasks = (long long)h[kStatusPivoted];
   }
+  if (bits & kDevBounds) { set_last_error("bounds check: a kernel met an index outside its array"); return VEF_ERR_BOUNDS; }
   if (bits & kDevTimeout) { set_last_error("a sweep dependency wait ran out"); return VEF_ERR_TIMEOUT; }
   if (bits & kDevSingular) { set_last_error("singular local element system"); return VEF_ERR_NOT_CONVERGED; }
   if (bits & kDevNotConverged) { set_last_error("an iteration reached its cap"); return VEF_ERR_NOT_CONVERGED; }

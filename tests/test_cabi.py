@@ -133,6 +133,12 @@ def test_status_codes_agree_with_the_library(libpath):
     from paper_2301_04758_gb300 import _lib
     lib = _lib.load()
     names = ["VEF_OK", "VEF_ERR_INVALID_ARG", "VEF_ERR_CUDA", "VEF_ERR_OOM", "VEF_ERR_TIMEOUT",
-             "VEF_ERR_NOT_CONVERGED", "VEF_ERR_NONPOSITIVE_DENOM", "VEF_ERR_NOT_IMPLEMENTED"]
+             "VEF_ERR_NOT_CONVERGED", "VEF_ERR_NONPOSITIVE_DENOM", "VEF_ERR_NOT_IMPLEMENTED", "VEF_ERR_BOUNDS"]
     for name in names:
         assert lib.vef_status_string(getattr(_lib, name)).decode() == name
+    hdr = open(os.path.join(ROOT, "include", "vef.h")).read()
+    for name in names[1:] + ["VEF_STATUS_TIMEOUT", "VEF_STATUS_NOT_CONVERGED", "VEF_STATUS_NONPOSITIVE",
+                             "VEF_STATUS_SINGULAR", "VEF_STATUS_BOUNDS"]:
+        m = re.search(name + r"\s*=\s*(\d+)", hdr)
+        assert m and int(m.group(1)) == getattr(_lib, name), name
+    assert lib.vef_build_checked() == 0   # the normal build

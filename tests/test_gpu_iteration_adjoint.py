@@ -153,3 +153,37 @@ def test_autograd_transport_phi(lib):
     R.backward()
     assert rel(host(st_t.grad), dst) < 1e-12
     assert rel(host(ss_t.grad), dss) < 1e-12
+
+
+def test_adjoint_with_an_fp32_checkpoint(lib):
+    """The forward psi kept as an FP32 copy (VEF_CKPT_FP32): the adjoint solution lambda does
+    not depend on psi and stays at the oracle's to 1e-12; the gradients of sigma_t carry the
+    copy's rounding (relative 2^-24 per value, averaged over the sums) and sit within 1e-6
+    of the oracle's; through autograd with ckpt="fp32" the same."""
+    from paper_2301_04758_gb300.api import Mesh
+    from paper_2301_04758_gb300.autograd import transport_phi
+    nx, m, alpha, p = 9, 3, 0.08, 2
+    om, w = level_symmetric(8)
+    E, n = nx * nx, (p + 1) ** 2
+    st, ss = seeded_media(E, 5, log10_range=(-1.0, 1.0))
+    rng = np.random.default_rng(9)
+    phi_in = rng.uniform(0.5, 1.5, (E, n))
+    q = np.ones((E, n))
+    disc = Discretization(nx, nx, m, alpha, p)
+    g = region_weights(disc)
+    psi = o_sweep(disc, om, w, st, ss, phi_in=phi_in, source=q)
+    lam, dst, dss = o_adjoint(disc, om, w, st, ss, psi, g, phi_in=phi_in)
+    mesh = Mesh(nx, nx, m, p, alpha)
+    gpsi = mesh.sweep(dev(st), dev(ss), om, w, phi_in=dev(phi_in), source=dev(q))
+    gdst, gdss, glam = mesh.adjoint(dev(st), dev(ss), om, w, gpsi.float(), dev(g), phi_in=dev(phi_in),
+                                    want_lambda=True)
+    assert rel(host(glam), lam) < 1e-12
+    assert rel(host(gdss), dss) < 1e-12          # does not read psi
+    e32 = rel(host(gdst), dst)
+    assert 1e-10 < e32 < 1e-6, e32               # the copy's rounding, and only that
+    st_t = dev(st).requires_grad_()
+    ss_t = dev(ss).requires_grad_()
+    phi = transport_phi(mesh, st_t, ss_t, om, w, phi_in=dev(phi_in), source=dev(q), ckpt="fp32")
+    (dev(g) * phi).sum().backward()
+    assert rel(host(st_t.grad), dst) < 1e-6
+    assert rel(host(ss_t.grad), dss) < 1e-12
