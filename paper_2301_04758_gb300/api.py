@@ -14,11 +14,11 @@ from . import _lib
 _NULL = None
 
 
-def _ptr(t):
+def _ptr(t, dtype=torch.float64):
     if t is None:
         return _NULL
-    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
-        raise TypeError("expected a contiguous CUDA float64 tensor")
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"expected a contiguous CUDA {str(dtype).replace('torch.', '')} tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -248,7 +248,7 @@ class Mesh:
         elif psi.dtype != torch.float64:
             raise TypeError("psi checkpoint must be float64 or float32")
         st = self.lib.vef_adjoint_sweep(self.handle, _ptr(sigma_t), _ptr(sigma_s), _ptr(phi_in), omp,
-                                        wp, D, _ptr(psi), _ptr(g), _ptr(lam), _ptr(dst), _ptr(dss),
+                                        wp, D, _ptr(psi, psi.dtype), _ptr(g), _ptr(lam), _ptr(dst), _ptr(dss),
                                         ctypes.byref(o), ctypes.byref(inf) if info else None, _stream(stream))
         _lib.check(st, "vef_adjoint_sweep")
         res = (dst, dss, lam)

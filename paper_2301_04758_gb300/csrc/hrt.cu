@@ -265,13 +265,20 @@ struct HrtSmem {
 
 template <int P>
 __global__ void __launch_bounds__(256, 2)
-hrt_local_kernel(long long E, int nx, int ny, HrtTab t, HrtRef ref, HrtIn in, HrtOut out, unsigned int* status) {
+hrt_local_kernel(long long E, int nx, int ny, HrtTab tab, HrtRef ref, HrtIn in, HrtOut out, unsigned int* status) {
   using S = HrtShape<P>;
   constexpr int N = S::N, NQ = S::NQ, NQ2 = S::NQ2, NJ = S::NJ, MM = S::MM, LD = S::LD, NL = S::NL, NL4 = S::NL4;
   constexpr int NF = HrtSmem<P>::NF;
   extern __shared__ __align__(16) unsigned char hrt_smem[];
   HrtSmem<P>& sm = *reinterpret_cast<HrtSmem<P>*>(hrt_smem);
   const int tid = threadIdx.x, nth = blockDim.x;
+  // the 1D tables in shared memory: every loop below indexes them per thread, which the
+  // constant bank of a kernel parameter would serve one distinct address at a time
+  __shared__ HrtTab t;
+  static_assert(sizeof(HrtTab) % sizeof(double) == 0, "HrtTab is copied in 8-byte words");
+  for (int i = tid; i < (int)(sizeof(HrtTab) / sizeof(double)); i += nth)
+    reinterpret_cast<double*>(&t)[i] = reinterpret_cast<const double*>(&tab)[i];
+  __syncthreads();
   const long long En = E * N;
   const int qc = (t.m + 1) * (t.m + 1);
   for (long long e = blockIdx.x; e < E; e += gridDim.x) {
