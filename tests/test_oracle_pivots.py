@@ -88,3 +88,39 @@ def test_a_degenerate_matrix_falls_below_the_floor():
     assert rp[1] < floor64 < rp[0]
     # partial pivoting (the fallback's elimination) still inverts it accurately
     assert np.linalg.norm(np.linalg.inv(A) @ A - np.eye(3)) < 1e-2
+
+
+def _inflow_last_order(p, fx, fy):
+    """Node order with the nodes of the two inflow faces (x = 0 side unless fx, y = 0 side
+    unless fy, after reflection) eliminated last."""
+    Q = p + 1
+    inner, infl = [], []
+    for ibl in range(Q):
+        for ial in range(Q):
+            ia = p - ial if fx else ial
+            ib = p - ibl if fy else ibl
+            (infl if (ial == 0 or ibl == 0) else inner).append(ia + Q * ib)
+    return inner + infl
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_inflow_last_elimination_order_is_unstable_in_void(p):
+    """Why the factorisation keeps the natural (upwind-first) order: eliminating the
+    inflow-face nodes last would make the solves for W_f = A^{-1} Cin_f short, but on a
+    void element the remaining block (streaming only) is singular, so that order meets a
+    zero pivot where the natural order's smallest relative pivot stays far from zero."""
+    disc = Discretization(4, 4, 1, 0.0, p)
+    worst_nat, worst_perm = np.inf, np.inf
+    for sn in (4, 8):
+        om, _ = level_symmetric(sn)
+        st = np.zeros(disc.mesh.E)
+        for d in range(len(om)):
+            A, _ = disc.element_matrices(om[d], st)
+            worst_nat = min(worst_nat, relative_pivots(A).min())
+            fx, fy = om[d][0] < 0, om[d][1] < 0
+            o = _inflow_last_order(p, fx, fy)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                rp = relative_pivots(A[:, o][:, :, o])
+            worst_perm = min(worst_perm, np.nanmin(np.where(np.isfinite(rp), rp, 0.0)))
+    assert worst_nat > 0.05
+    assert worst_perm < 1e-12
