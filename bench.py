@@ -779,14 +779,15 @@ def suite_batch(args):
 
 
 def flops_hrt_local(p):
-    """Algorithmic flops of one element's hybridized RT elimination: the local blocks (A:
-    2 (p+2)^2 NJ^2 with NJ = 2 (p+2)(p+1); G: (p+2)^2 NJ (n + 8); D: 2 (p+2)^2 n NJ), the
+    """Algorithmic flops of one element's hybridized RT elimination: the element-dependent
+    local blocks (A: 2 (p+2)^2 NJ^2 with NJ = 2 (p+2)(p+1); G: (p+2)^2 NJ (n + 8); the
+    divergence block D is the same reference matrix on every element, formed once), the
     Gauss-Jordan inverse of the (NJ + n) system (2 m^3), and H_e = C1 (W C2), r_e (2 NJ^2 NL4
     + 2 NL4^2 NJ + 2 NJ m + 2 NL4 NJ, NL4 = 4 (p+1))."""
     n, nq2 = (p + 1) ** 2, (p + 2) ** 2
     nJ = 2 * (p + 2) * (p + 1)
     m, nl4 = nJ + n, 4 * (p + 1)
-    return (2 * nq2 * nJ * nJ + nq2 * nJ * (n + 8) + 2 * nq2 * n * nJ + 2 * m ** 3
+    return (2 * nq2 * nJ * nJ + nq2 * nJ * (n + 8) + 2 * m ** 3
             + 2 * nJ * nJ * nl4 + 2 * nl4 * nl4 * nJ + 2 * nJ * m + 2 * nl4 * nJ)
 
 

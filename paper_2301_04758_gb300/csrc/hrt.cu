@@ -12,9 +12,10 @@
 // with C2 lambda = int_G0 (v.{E} n) lambda (the face multipliers) and the constraint
 // C1 J = int_G0 mu [[J.n]] = 0.  hrt_local_kernel assembles these blocks for one element per
 // CTA in shared memory (the map's derivatives and the Eddington tensor evaluated once per
-// Gauss point; D and C1 are the same on every element and come from host tables), inverts
-// [[A, G], [D, Ma]] by Gauss-Jordan elimination with partial pivoting (the block is
-// indefinite in general), and forms the element's share of the reduced system,
+// Gauss point; D and C1 are the same on every element and come from host tables);
+// hrt_invert_kernel, at a higher occupancy, inverts [[A, G], [D, Ma]] by Gauss-Jordan
+// elimination with partial pivoting (the block is indefinite in general), and forms the
+// element's share of the reduced system,
 //     H_e = C1 W C2,   r_e = C1 (W g + X f),   [[W, X], [Y, Z]] = [[A, G], [D, Ma]]^{-1}.
 // The multiplier system H lambda = r (H = sum_e H_e over the interior faces, not symmetric
 // for a general Eddington tensor) is solved by BiCGStab with a face-block Jacobi
@@ -167,9 +168,10 @@ __device__ __forceinline__ void eddington_pt(const HrtTab& t, const double* __re
     b += Bj * Pm[En + o];
     c += Bj * Pm[2 * En + o];
   }
-  Eo[0] = a / f;
-  Eo[1] = b / f;
-  Eo[2] = c / f;
+  const double rf = 1.0 / f;
+  Eo[0] = a * rf;
+  Eo[1] = b * rf;
+  Eo[2] = c * rf;
 }
 
 struct HrtIn {
@@ -246,21 +248,16 @@ struct HrtSmem {
   double vq[S::NQ2][S::NJ][2];       // physical v at the volume points
   double sg[S::NJ][S::NQ2];          // -w J (grad v : E) at the volume points
   double wJ[S::NQ2];                 // w J at the volume points
-  double C1[S::NL4][S::NJ];
   double C2[S::NJ][S::NL4];
   double gv[S::NJ], fv[S::N];
-  double T1[S::NJ][S::NL4];          // W C2
-  double u[S::NJ];                   // W g + X f
-  double colk[S::MM];
   double ctrl[(kMaxM + 1) * (kMaxM + 1) * 2];
-  // per volume point: F (4, row-major), J, dJ/dxi (2), second derivatives (8), E (3), Q1 (2)
-  double pv[S::NQ2][20];
+  // per volume point: F (4, row-major), J, dJ/dxi (2), second derivatives (8), E (3), Q1 (2),
+  // 1 / J
+  double pv[S::NQ2][21];
   // per face point: interior faces w (F^T {E} n ds) / J (2); boundary faces (F^T E n^) / J (2),
   // (F^T n^) / J (2), w |n ds| / E_b and 2 w |n ds| J_in / E_b
   double pf[NF][6];
   double pa[S::NQ][S::NJ], pb[S::NQ][S::NJ];   // boundary face: v_hat . the two vectors above
-  int perm[S::MM];
-  int piv;
 };
 
 template <int P>
@@ -318,6 +315,7 @@ hrt_local_kernel(long long E, int nx, int ny, HrtTab tab, HrtRef ref, HrtIn in, 
           }
         g[18] = q1x;
         g[19] = q1y;
+        g[20] = 1.0 / J;
       } else {
         double* o = sm.pf[pt - NQ2];
         const double* nd = in.nds + (((size_t)e * 4 + f) * NQ + k) * 2;
@@ -353,25 +351,25 @@ hrt_local_kernel(long long E, int nx, int ny, HrtTab tab, HrtRef ref, HrtIn in, 
       const int q = idx / NJ, a = idx % NJ, k1 = q % NQ, k2 = q / NQ;
       const double* g = sm.pv[q];
       const double F[4] = {g[0], g[1], g[2], g[3]};
-      const double J = g[4];
+      const double J = g[4], rJ = g[20];
       const double adj[4] = {F[3], -F[1], -F[2], F[0]};
       double vh[2], dx[2], dy[2];
       rt_ref<P>(t, a, k1, k2, vh, dx, dy);
       double v[2], dv[2][2];   // dv[i][l] = d v_i / d xi_l
-      for (int i = 0; i < 2; ++i) v[i] = (F[2 * i] * vh[0] + F[2 * i + 1] * vh[1]) / J;
+      for (int i = 0; i < 2; ++i) v[i] = (F[2 * i] * vh[0] + F[2 * i + 1] * vh[1]) * rJ;
       for (int l = 0; l < 2; ++l) {
         const double* dvh = l == 0 ? dx : dy;
         for (int i = 0; i < 2; ++i) {
           const double dFv = g[7 + i * 4 + 0 * 2 + l] * vh[0] + g[7 + i * 4 + 1 * 2 + l] * vh[1];
           const double Fdv = F[2 * i] * dvh[0] + F[2 * i + 1] * dvh[1];
-          dv[i][l] = (dFv + Fdv) / J - g[5 + l] / J * v[i];
+          dv[i][l] = (dFv + Fdv - g[5 + l] * v[i]) * rJ;
         }
       }
       // grad v = dv F^{-1}, F^{-1} = adj / J; grad v : E
       double gE = 0.0;
       for (int i = 0; i < 2; ++i)
         for (int mcol = 0; mcol < 2; ++mcol) {
-          const double gim = (dv[i][0] * adj[0 * 2 + mcol] + dv[i][1] * adj[1 * 2 + mcol]) / J;
+          const double gim = (dv[i][0] * adj[0 * 2 + mcol] + dv[i][1] * adj[1 * 2 + mcol]) * rJ;
           const double Eim = (i == mcol) ? (i == 0 ? g[15] : g[17]) : g[16];
           gE += gim * Eim;
         }
@@ -381,11 +379,7 @@ hrt_local_kernel(long long E, int nx, int ny, HrtTab tab, HrtRef ref, HrtIn in, 
       sm.sg[a][q] = -w * J * gE;
       if (a == 0) sm.wJ[q] = w * J;
     }
-    for (int idx = tid; idx < NL4 * NJ; idx += nth) {
-      const int r = idx / NJ;
-      (&sm.C1[0][0])[idx] = nb_elem(nx, ny, (int)e, r / NL) >= 0 ? ref.C1[idx] : 0.0;
-      (&sm.C2[0][0])[idx] = 0.0;
-    }
+    for (int idx = tid; idx < NL4 * NJ; idx += nth) (&sm.C2[0][0])[idx] = 0.0;
     __syncthreads();
     // (3) A (symmetric: one triangle computed), G, D (reference), sigma_a M, f, g
     for (int idx = tid; idx < MM * MM; idx += nth) {
@@ -469,6 +463,53 @@ hrt_local_kernel(long long E, int nx, int ny, HrtTab tab, HrtRef ref, HrtIn in, 
       }
       __syncthreads();
     }
+    // the assembled local system (inverted by hrt_invert_kernel) and the couplings
+    for (int idx = tid; idx < MM * MM; idx += nth)
+      out.Li[(size_t)e * MM * MM + idx] = sm.L[(idx / MM) * LD + idx % MM];
+    for (int idx = tid; idx < NJ * NL4; idx += nth) out.C2[(size_t)e * NJ * NL4 + idx] = (&sm.C2[0][0])[idx];
+    for (int a = tid; a < NJ; a += nth) out.g[(size_t)e * NJ + a] = sm.gv[a];
+    for (int c = tid; c < N; c += nth) out.f[(size_t)e * N + c] = sm.fv[c];
+  }
+}
+
+// Inversion of the assembled local systems and the element's share of the reduced system,
+// apart from the assembly so that it runs many CTAs per SM: its Gauss-Jordan steps are
+// short and separated by barriers, and only the number of CTAs in flight hides them.
+template <int P>
+struct HrtInvSmem {
+  using S = HrtShape<P>;
+  double L[S::MM * S::LD];
+  double C1[S::NL4][S::NJ];
+  double C2[S::NJ][S::NL4];
+  double gv[S::NJ], fv[S::N];
+  double T1[S::NJ][S::NL4];          // W C2
+  double u[S::NJ];                   // W g + X f
+  double colk[S::MM];
+  double inv;                        // reciprocal of the current pivot
+  int perm[S::MM];
+  int piv;
+};
+
+template <int P>
+__global__ void __launch_bounds__(128)
+hrt_invert_kernel(long long E, int nx, int ny, HrtRef ref, HrtOut out, unsigned int* status) {
+  using S = HrtShape<P>;
+  constexpr int N = S::N, NJ = S::NJ, MM = S::MM, LD = S::LD, NL = S::NL, NL4 = S::NL4;
+  extern __shared__ __align__(16) unsigned char hrt_inv_smem[];
+  HrtInvSmem<P>& sm = *reinterpret_cast<HrtInvSmem<P>*>(hrt_inv_smem);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (long long e = blockIdx.x; e < E; e += gridDim.x) {
+    __syncthreads();
+    for (int idx = tid; idx < MM * MM; idx += nth)
+      sm.L[(idx / MM) * LD + idx % MM] = out.Li[(size_t)e * MM * MM + idx];
+    for (int idx = tid; idx < NL4 * NJ; idx += nth) {
+      const int r = idx / NJ;
+      (&sm.C1[0][0])[idx] = nb_elem(nx, ny, (int)e, r / NL) >= 0 ? ref.C1[idx] : 0.0;
+      (&sm.C2[0][0])[idx] = out.C2[(size_t)e * NJ * NL4 + idx];
+    }
+    for (int a = tid; a < NJ; a += nth) sm.gv[a] = out.g[(size_t)e * NJ + a];
+    for (int c = tid; c < N; c += nth) sm.fv[c] = out.f[(size_t)e * N + c];
+    __syncthreads();
     // in-place Gauss-Jordan inversion of L with partial pivoting
     for (int k = 0; k < MM; ++k) {
       if (tid < 32) {
@@ -486,6 +527,7 @@ hrt_local_kernel(long long E, int nx, int ny, HrtTab tab, HrtRef ref, HrtIn in, 
         if (tid == 0) {
           sm.piv = bi;
           sm.perm[k] = bi;
+          sm.inv = 1.0 / sm.L[bi * LD + k];   // one FP64 division per step, not one per thread
           if (!(best > 1e-300)) atomicOr(status, kDevSingular);
         }
       }
@@ -498,7 +540,7 @@ hrt_local_kernel(long long E, int nx, int ny, HrtTab tab, HrtRef ref, HrtIn in, 
           sm.L[pr * LD + j] = tmp;
         }
       __syncthreads();
-      const double inv = 1.0 / sm.L[k * LD + k];
+      const double inv = sm.inv;
       for (int i = tid; i < MM; i += nth) sm.colk[i] = sm.L[i * LD + k];
       __syncthreads();
       for (int j = tid; j < MM; j += nth)
@@ -554,9 +596,6 @@ hrt_local_kernel(long long E, int nx, int ny, HrtTab tab, HrtRef ref, HrtIn in, 
     }
     for (int idx = tid; idx < MM * MM; idx += nth)
       out.Li[(size_t)e * MM * MM + idx] = sm.L[(idx / MM) * LD + idx % MM];
-    for (int idx = tid; idx < NJ * NL4; idx += nth) out.C2[(size_t)e * NJ * NL4 + idx] = (&sm.C2[0][0])[idx];
-    for (int a = tid; a < NJ; a += nth) out.g[(size_t)e * NJ + a] = sm.gv[a];
-    for (int c = tid; c < N; c += nth) out.f[(size_t)e * N + c] = sm.fv[c];
   }
 }
 
@@ -1016,15 +1055,19 @@ static vef_status hrt_run(Mesh& M, const HrtIn& in, double tol, int max_iter, do
   VEF_CUDA_TRY(cudaMemcpyAsync(refd, refh.data(), refh.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   const HrtRef ref{refd, refd + (size_t)S::N * S::NJ};
   HrtOut out{Li, C2, g, f, He, re};
-  const size_t smem = sizeof(HrtSmem<P>);
+  const size_t smem = sizeof(HrtSmem<P>), ismem = sizeof(HrtInvSmem<P>);
   VEF_CUDA_TRY(cudaFuncSetAttribute(hrt_local_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int dev = 0, sms = 0;
+  VEF_CUDA_TRY(cudaFuncSetAttribute(hrt_invert_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem));
+  int dev = 0, sms = 0, inv_per_sm = 0;
   VEF_CUDA_TRY(cudaGetDevice(&dev));
   VEF_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  VEF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&inv_per_sm, hrt_invert_kernel<P>, 128, ismem));
   {
     KTimer kt(&M, VEF_K_HRT, s);
     hrt_local_kernel<P><<<(unsigned)std::min<long long>(E, (long long)sms * 8), 256, smem, s>>>(
         E, M.nx, M.ny, tab, ref, in, out, M.dev_status);
+    hrt_invert_kernel<P><<<(unsigned)std::min<long long>(E, (long long)sms * std::max(1, inv_per_sm)), 128, ismem,
+                           s>>>(E, M.nx, M.ny, ref, out, M.dev_status);
     VEF_CUDA_TRY(cudaGetLastError());
   }
   int it = 0;
