@@ -429,6 +429,14 @@ vef_status vef_schedule_host(int nx, int ny, int p, const double* nds, const dou
  * frees 8 bytes of device memory. */
 vef_status vef_wait_selftest(int kind, int satisfied, long long polls, void* stream);
 
+/* The elimination pivots' reciprocal (an approximate reciprocal refined by two
+ * Newton-Raphson steps; FP32: the correctly rounded reciprocal) against the correctly
+ * rounded 1/x, on n device-generated inputs across the normal range (exponents -500..500,
+ * hashed mantissas, both signs; FP32 inputs within 2^+-99): *max_rel_err and
+ * *max_rel_err_f32 receive the largest relative differences.  n in 1..2^30, else
+ * VEF_ERR_INVALID_ARG.  Synchronous (default stream); allocates 16 bytes of device memory. */
+vef_status vef_rcp_selftest(long long n, double* max_rel_err, double* max_rel_err_f32);
+
 /* Device status bits: what a kernel records when a bounded wait runs out, an iteration
  * hits its cap, a closure denominator is not positive, an element system is singular, or
  * (bounds-checked build) an index falls outside its array; the next synchronising call

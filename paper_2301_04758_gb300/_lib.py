@@ -42,7 +42,7 @@ EXPORTS = ("vef_mesh_create", "vef_mesh_destroy", "vef_mesh_query", "vef_mesh_sy
            "vef_profile_read", "vef_measure_fma_peak", "vef_wait_selftest", "vef_eddington_noalloc",
            "vef_batch_create", "vef_batch_destroy", "vef_batch_sweep", "vef_batch_tune",
            "vef_region_weights", "vef_schedule_host", "vef_mesh_inject_status", "vef_hrt_solve",
-           "vef_vef_iterate", "vef_build_checked",
+           "vef_vef_iterate", "vef_build_checked", "vef_rcp_selftest",
            "vef_status_string", "vef_last_error")
 
 KERNEL_CLASSES = ("geometry", "factor", "sweep", "residual", "source", "moments", "adjoint", "group", "hrt")
@@ -144,6 +144,9 @@ def _declare(lib):
     lib.vef_last_error.restype = ctypes.c_char_p
     lib.vef_build_checked.argtypes = []
     lib.vef_build_checked.restype = ctypes.c_int
+    lib.vef_rcp_selftest.argtypes = [ctypes.c_longlong, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]
+    lib.vef_rcp_selftest.restype = ctypes.c_int
 
 
 def load(path=None):

@@ -73,6 +73,22 @@ template <typename T> __host__ __device__ constexpr T tiny_pivot();
 template <> __host__ __device__ constexpr double tiny_pivot<double>() { return 1e-300; }
 template <> __host__ __device__ constexpr float tiny_pivot<float>() { return 1e-37f; }
 
+// Reciprocal of an elimination pivot: the approximate reciprocal instruction
+// (rcp.approx.ftz.f64) refined by two Newton-Raphson steps r <- r + r (1 - x r), each of
+// which squares the relative error, so the result is within an ulp or two of 1/x for
+// normal x, at five FP64-pipe operations instead of a correctly rounded division.  The
+// unpivoted eliminations use it; a pivot the guard rejects (tiny, huge or not finite) goes
+// to the partial-pivoting path, which divides.  vef_rcp_selftest measures it against 1/x.
+__device__ __forceinline__ double pivot_rcp(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+__device__ __forceinline__ float pivot_rcp(float x) { return __frcp_rn(x); }
+
 // face-node -> element-dof maps (GLL nodes on the face, in increasing reference coordinate)
 template <int P>
 __host__ __device__ __forceinline__ int face_dof(int f, int t) {

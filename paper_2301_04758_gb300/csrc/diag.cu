@@ -111,9 +111,11 @@ namespace vef {
 __global__ void inject_status_kernel(unsigned int* status, unsigned int bits) { atomicOr(status, bits); }
 }  // namespace vef
 
-static_assert(VEF_STATUS_TIMEOUT == vef::kDevTimeout && VEF_STATUS_NOT_CONVERGED == vef::kDevNotConverged &&
-                  VEF_STATUS_NONPOSITIVE == vef::kDevNonpositive && VEF_STATUS_SINGULAR == vef::kDevSingular &&
-                  VEF_STATUS_BOUNDS == vef::kDevBounds,
+static_assert((unsigned)VEF_STATUS_TIMEOUT == (unsigned)vef::kDevTimeout &&
+                  (unsigned)VEF_STATUS_NOT_CONVERGED == (unsigned)vef::kDevNotConverged &&
+                  (unsigned)VEF_STATUS_NONPOSITIVE == (unsigned)vef::kDevNonpositive &&
+                  (unsigned)VEF_STATUS_SINGULAR == (unsigned)vef::kDevSingular &&
+                  (unsigned)VEF_STATUS_BOUNDS == (unsigned)vef::kDevBounds,
               "public status bits match the device status word");
 
 extern "C" vef_status vef_mesh_inject_status(vef_mesh mesh, unsigned int bits, void* stream) {
@@ -124,5 +126,55 @@ extern "C" vef_status vef_mesh_inject_status(vef_mesh mesh, unsigned int bits, v
   if (dev != mesh->impl.device) { vef::set_last_error("mesh belongs to another device"); return VEF_ERR_INVALID_ARG; }
   vef::inject_status_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(mesh->impl.dev_status, bits);
   VEF_CUDA_TRY(cudaGetLastError());
+  return VEF_OK;
+}
+
+namespace vef {
+namespace {
+
+// pivot_rcp against the correctly rounded reciprocal over n inputs spread across the
+// normal range (exponents -500..500 and hashed mantissas, both signs): the largest
+// relative difference, as a non-negative double's bit pattern (ordered like an integer)
+__global__ void rcp_selftest_kernel(long long n, unsigned long long* worst64, unsigned int* worst32) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long h = (unsigned long long)i * 0x9E3779B97F4A7C15ull;
+    h ^= h >> 29;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 32;
+    const double m = 1.0 + (double)(h >> 12) * 0x1.0p-52;   // [1, 2)
+    const int ex = (int)(i % 1001) - 500;
+    const double x = ((i & 1) ? -1.0 : 1.0) * ldexp(m, ex);
+    const double r = pivot_rcp(x), q = 1.0 / x;
+    const double d = fabs(r - q) / fabs(q);
+    atomicMax(worst64, (unsigned long long)__double_as_longlong(d));
+    const float xf = (float)ldexp(m, ex % 100);
+    const float rf = pivot_rcp(xf), qf = 1.0f / xf;
+    const float df = fabsf(rf - qf) / fabsf(qf);
+    atomicMax(worst32, (unsigned int)__float_as_int(df));
+  }
+}
+
+}  // namespace
+}  // namespace vef
+
+extern "C" vef_status vef_rcp_selftest(long long n, double* max_rel_err, double* max_rel_err_f32) {
+  if (n < 1 || n > (1LL << 30) || !max_rel_err || !max_rel_err_f32) {
+    vef::set_last_error("n must be in 1..2^30 and both outputs given");
+    return VEF_ERR_INVALID_ARG;
+  }
+  unsigned long long* w = nullptr;
+  VEF_CUDA_TRY(cudaMalloc(&w, 16));
+  cudaError_t e = cudaMemset(w, 0, 16);
+  if (e == cudaSuccess) {
+    vef::rcp_selftest_kernel<<<256, 256>>>(n, w, reinterpret_cast<unsigned int*>(w + 1));
+    e = cudaGetLastError();
+  }
+  unsigned long long h[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(h, w, 16, cudaMemcpyDeviceToHost);
+  cudaFree(w);
+  if (e != cudaSuccess) return vef::cuda_fail(e, "vef_rcp_selftest");
+  *max_rel_err = __builtin_bit_cast(double, h[0]);
+  const unsigned int f = (unsigned int)h[1];
+  *max_rel_err_f32 = (double)__builtin_bit_cast(float, f);
   return VEF_OK;
 }

@@ -95,23 +95,27 @@ __device__ __forceinline__ T rhs_b(const RhsArgs<T>& r, const FaceTab<T>& ft, co
 // ------------------------------------------------------------------- pivot guard
 // The element solves eliminate without pivoting.  A task whose pivot at some step falls
 // below 2^VEF_PIVOT_FLOOR_LOG2_* times the largest entry of that row of the assembled
-// matrix (or is zero or not finite) is appended to a list and refactorised with partial
-// pivoting by factor_pivot_kernel, which overwrites its record.  Magnitudes are compared
-// through the high word of their bit pattern with the sign cleared (exponent and leading
-// mantissa bits), so the guard costs integer operations only.
+// matrix (or is zero, not finite, or above 2^1000) is appended to a list and refactorised
+// with partial pivoting by factor_pivot_kernel, which overwrites its record.  Magnitudes
+// are compared through the high word of their bit pattern with the sign cleared (exponent
+// and leading mantissa bits), so the guard costs integer operations only.
 template <typename T> struct PivotFloor;
 template <> struct PivotFloor<double> {
   static __device__ __forceinline__ int mag(double x) { return __double2hiint(x) & 0x7fffffff; }
   static constexpr int kShift = (-VEF_PIVOT_FLOOR_LOG2_FP64) << 20;
+  static constexpr int kHuge = (1000 + 1023) << 20;   // 2^1000: its reciprocal would flush
 };
 template <> struct PivotFloor<float> {
   static __device__ __forceinline__ int mag(float x) { return __float_as_int(x) & 0x7fffffff; }
   static constexpr int kShift = (-VEF_PIVOT_FLOOR_LOG2_FP32) << 23;
+  static constexpr int kHuge = (120 + 127) << 23;      // 2^120
 };
-// pivot too small against the row scale (given as mag() of the row's largest entry)
+// pivot too small against the row scale (given as mag() of the row's largest entry), or
+// too large for the reciprocal of pivot_rcp
 template <typename T>
 __device__ __forceinline__ bool small_pivot(T piv, int scale_mag) {
-  return !(fabs(piv) > tiny_pivot<T>()) || PivotFloor<T>::mag(piv) < scale_mag - PivotFloor<T>::kShift;
+  return !(fabs(piv) > tiny_pivot<T>()) || PivotFloor<T>::mag(piv) < scale_mag - PivotFloor<T>::kShift ||
+         PivotFloor<T>::mag(piv) >= PivotFloor<T>::kHuge;
 }
 __device__ __forceinline__ void pivot_list_append(unsigned int* count, unsigned int* list, long long m) {
   const unsigned idx = atomicAdd(count, 1u);
@@ -202,7 +206,7 @@ __device__ __forceinline__ bool factor_task(long long m, long long nmem, const u
     for (int k = 0; k < N; ++k) {
       const T piv = A[k * N + k];
       bad = bad || small_pivot<T>(piv, scl[k]);
-      const T inv = (T)1 / piv;
+      const T inv = pivot_rcp(piv);
 #pragma unroll
       for (int j = 0; j < N; ++j)
         if (j != k) A[k * N + j] *= inv;
@@ -477,7 +481,7 @@ factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const 
 #pragma unroll
       for (int j = 0; j < N; ++j) pr[j] = __shfl_sync(FULL, row[slot][j], (base + owner) & 31);
       if (li == owner) bad = bad || small_pivot<T>(pr[k], scl[slot]);
-      const T inv = (T)1 / pr[k];
+      const T inv = pivot_rcp(pr[k]);
 #pragma unroll
       for (int r = 0; r < RPL; ++r) {
         const int i = li + LPU * r;
