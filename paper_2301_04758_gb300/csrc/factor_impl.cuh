@@ -357,8 +357,11 @@ factor_pivot_kernel(long long nmem, const uint32_t* __restrict__ code, const uin
 // column k then becomes -A[i][k] / r[k], or 1 / r[k] on the pivot row.  With several rows
 // per lane the reciprocal and the broadcast are shared by RPL rows' FMAs.
 template <int P> struct ElemShape;
-template <> struct ElemShape<3> { static constexpr int RPL = 4, LPU = 4; };
-template <> struct ElemShape<4> { static constexpr int RPL = 2, LPU = 13; };
+// EPC elements per CTA: at p = 3 a warp holds 8 tasks, and the level-symmetric sets have
+// D = 4 (mod 8) directions for S4 and S12, so one element per CTA would leave half a warp of
+// padding tasks computing; two elements per CTA fill every warp (2 D = 0 mod 8).
+template <> struct ElemShape<3> { static constexpr int RPL = 4, LPU = 4, EPC = 2; };
+template <> struct ElemShape<4> { static constexpr int RPL = 2, LPU = 13, EPC = 1; };
 
 template <int P, typename T, bool Y>
 __global__ void __launch_bounds__(128)
@@ -369,26 +372,28 @@ factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const 
                    T* __restrict__ rec, unsigned int* status, unsigned int* piv_count,
                    unsigned int* piv_list, int force_pivot, RhsArgs<T> rhs) {
   constexpr int Q = P + 1, N = Q * Q, NQ = P + 2;
-  constexpr int RPL = ElemShape<P>::RPL, LPU = ElemShape<P>::LPU, UPW = 32 / LPU;
+  constexpr int RPL = ElemShape<P>::RPL, LPU = ElemShape<P>::LPU, UPW = 32 / LPU, EPC = ElemShape<P>::EPC;
   constexpr int LD = N + 1;                  // padded shared-memory row stride
   constexpr int CPL = (Q * Q + LPU - 1) / LPU;   // inflow-coupling entries computed per lane
   constexpr unsigned FULL = 0xffffffffu;
   using L = Rec<P, T>;
-  __shared__ T sM[N * LD], sX[N * LD], sY[N * LD];
-  __shared__ T sN[4 * NQ * 2];
+  __shared__ T sM[EPC][N * LD], sX[EPC][N * LD], sY[EPC][N * LD];   // sigma_t M (scaled once), Gx, Gy
+  __shared__ T sN[EPC][4 * NQ * 2];
   __shared__ T sLL[Q][Q][NQ];          // l_a(s_k) l_t(s_k): face basis products
   __shared__ T sW[NQ];                 // face Gauss weights
   __shared__ T sC[4][UPW][4][NQ];      // per warp and task: w_k Omega . (n ds)_k of each face
-  const long long e = blockIdx.x;
+  const long long e0 = (long long)blockIdx.x * EPC;
+  const int ne = (int)min((long long)EPC, E - e0);   // elements of this CTA
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < N * N; idx += blockDim.x) {
-    const int r = idx / N, j = idx % N;
-    const size_t g = (size_t)e * N * N + idx;
-    sM[r * LD + j] = Mm[g];
-    sX[r * LD + j] = Gxm[g];
-    sY[r * LD + j] = Gym[g];
+  for (int idx = tid; idx < ne * N * N; idx += blockDim.x) {
+    const int el = idx / (N * N), r = (idx / N) % N, j = idx % N;
+    const size_t g = (size_t)e0 * N * N + idx;
+    sM[el][r * LD + j] = (T)sigma_t[e0 + el] * Mm[g];
+    sX[el][r * LD + j] = Gxm[g];
+    sY[el][r * LD + j] = Gym[g];
   }
-  for (int idx = tid; idx < 4 * NQ * 2; idx += blockDim.x) sN[idx] = nds[(size_t)e * 4 * NQ * 2 + idx];
+  for (int idx = tid; idx < ne * 4 * NQ * 2; idx += blockDim.x)
+    sN[idx / (4 * NQ * 2)][idx % (4 * NQ * 2)] = nds[(size_t)e0 * 4 * NQ * 2 + idx];
   for (int idx = tid; idx < Q * Q * NQ; idx += blockDim.x) {
     const int qa = idx / (Q * NQ), qt = (idx / NQ) % Q, kk = idx % NQ;
     sLL[qa][qt][kk] = ft.l[qa][kk] * ft.l[qt][kk];
@@ -398,19 +403,21 @@ factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const 
   const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int u = lane / LPU, li = lane % LPU, base = u * LPU;
   const int uc = u < UPW ? u : UPW - 1;   // lanes past the last task read a valid slot
-  const T st = (T)sigma_t[e];
   char* recx = (char*)rec + nmem * (long long)L::kStaged;
-  for (int d0 = warp * UPW; d0 < D; d0 += nwarps * UPW) {
-    const int d = d0 + u;
-    bool valid = u < UPW && d < D;
-    const int dd = valid ? d : 0;
+  // tasks t = el D + d of the CTA's elements, UPW per warp and round
+  const int ntask = ne * D;
+  for (int t0 = warp * UPW; t0 < ntask; t0 += nwarps * UPW) {
+    const int t = t0 + u;
+    bool valid = u < UPW && t < ntask;
+    const int tt = valid ? t : 0, el = tt / D, dd = tt % D;
+    const long long e = e0 + el;
     const T mu = (T)omega[2 * dd], eta = (T)omega[2 * dd + 1];
     const uint16_t bits = finfo[(size_t)dd * E + e];
     // face coefficients of this task, once: its LPU lanes share the 4 NQ entries
     __syncwarp();
     for (int q = li; u < UPW && q < 4 * NQ; q += LPU) {
       const int f = q / NQ, kk = q % NQ;
-      sC[warp][u][f][kk] = sW[kk] * (mu * sN[(f * NQ + kk) * 2] + eta * sN[(f * NQ + kk) * 2 + 1]);
+      sC[warp][u][f][kk] = sW[kk] * (mu * sN[el][(f * NQ + kk) * 2] + eta * sN[el][(f * NQ + kk) * 2 + 1]);
     }
     __syncwarp();
     // assemble the owned rows: sigma_t M - mu Gx - eta Gy ...
@@ -420,7 +427,7 @@ factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const 
       const int i = li + LPU * r;
 #pragma unroll
       for (int j = 0; j < N; ++j)
-        row[r][j] = i < N ? st * sM[i * LD + j] - mu * sX[i * LD + j] - eta * sY[i * LD + j] : (T)0;
+        row[r][j] = i < N ? fma(-eta, sY[el][i * LD + j], fma(-mu, sX[el][i * LD + j], sM[el][i * LD + j])) : (T)0;
     }
     // ... plus the outflow face terms: row a of face f's matrix sum_k max(c_k, 0) l_a l_t is
     // formed on lane a of the task and shuffled to the lane that owns face node a (faces
@@ -1094,10 +1101,10 @@ static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, boo
   {
   KTimer kt(&M, VEF_K_FACTOR, stream);
   if constexpr (P >= 3) {
-    constexpr int UPW = 32 / ElemShape<P>::LPU;
-    const int warps = std::max(1, std::min(4, (S.D + UPW - 1) / UPW));
+    constexpr int UPW = 32 / ElemShape<P>::LPU, EPC = ElemShape<P>::EPC;
+    const int warps = std::max(1, std::min(4, (EPC * S.D + UPW - 1) / UPW));
     auto kern = rhs ? factor_elem_kernel<P, T, true> : factor_elem_kernel<P, T, false>;
-    kern<<<(unsigned)M.E, 32 * warps, 0, stream>>>(
+    kern<<<(unsigned)((M.E + EPC - 1) / EPC), 32 * warps, 0, stream>>>(
         S.D, M.E, S.member_of, S.faceinfo, S.omega_dev, sigma_t, Mm, Gx, Gy, nds, make_facetab<T>(M.tab),
         M.nx, M.ny, S.members, (T*)*recp, M.dev_status, piv_count, S.pivot_list, force_pivot, ra);
   } else {
