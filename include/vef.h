@@ -93,7 +93,7 @@ enum {
                                the sweep launch, which is then a
                                cooperative launch sized from the device's SM count (a
                                context limited to fewer SMs, e.g. under MPS, should set
-                               this flag: the driver refuses a cooperative grid that
+                               this flag: the CUDA driver refuses a cooperative grid that
                                does not fit, and the call returns VEF_ERR_CUDA) */
   VEF_PIVOT_ALWAYS = 8,     /* refactorise every (element, direction) system with partial
                                pivoting, as the library does by itself only for the systems
