@@ -364,7 +364,7 @@ template <> struct ElemShape<3> { static constexpr int RPL = 4, LPU = 4, EPC = 2
 template <> struct ElemShape<4> { static constexpr int RPL = 2, LPU = 13, EPC = 1; };
 
 template <int P, typename T, bool Y>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, std::is_same<T, float>::value ? 4 : 1)
 factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const uint16_t* __restrict__ finfo,
                    const double* __restrict__ omega, const double* __restrict__ sigma_t,
                    const T* __restrict__ Mm, const T* __restrict__ Gxm, const T* __restrict__ Gym,
