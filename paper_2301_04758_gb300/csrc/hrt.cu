@@ -18,10 +18,10 @@
 // element's share of the reduced system,
 //     H_e = C1 W C2,   r_e = C1 (W g + X f),   [[W, X], [Y, Z]] = [[A, G], [D, Ma]]^{-1}.
 // The multiplier system H lambda = r (H = sum_e H_e over the interior faces, not symmetric
-// for a general Eddington tensor) is solved by BiCGStab with a face-block Jacobi
-// preconditioner, the matrix applied face by face from the two sides' rows of H_e (no
-// atomics) and the Krylov scalars kept on the device.  hrt_recover_kernel then forms J and
-// phi element by element.
+// for a general Eddington tensor) is solved by BiCGStab with an element-patch additive
+// Schwarz preconditioner, the matrix applied face by face from the two sides' rows of H_e
+// (no atomics) and the Krylov scalars kept on the device.  hrt_recover_kernel then forms J
+// and phi element by element.
 //
 // Spaces (identical to the CPU reference of this discretisation): RT_p on the reference
 // square with the x component in Q_{p+1} x Q_p and the y component in Q_p x Q_{p+1}, nodal
@@ -653,61 +653,98 @@ __device__ __forceinline__ double he_row(int nx, int ny, const double* __restric
   return s;
 }
 
-// Face-block Jacobi preconditioner: the (p+1)-square diagonal block of H for each interior
-// face (the sum of its two sides' blocks of H_e), inverted by Gauss-Jordan with partial
-// pivoting, one face per thread.
+// Element-patch additive Schwarz preconditioner: for each element the restriction of H to
+// the multipliers of its interior faces, H_e plus, on each such face, the neighbour's
+// diagonal block of that face (its only contribution there), inverted; the preconditioner
+// applies every element's inverse to its faces' values and sums the two elements' results on
+// each face.  One warp per element with the matrix in shared memory, Gauss-Jordan with
+// partial pivoting; the rows and columns of boundary faces are the identity, so they stay
+// decoupled and carry zeros.
 template <int P>
-__global__ void hrt_face_block_kernel(int nx, int ny, long long nfaces, const double* __restrict__ He,
-                                      double* __restrict__ Minv, unsigned int* status) {
-  constexpr int NL = P + 1, NL4 = 4 * NL;
-  const long long fid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (fid >= nfaces) return;
-  long long e1, e2;
-  int f1, f2;
-  face_sides(nx, ny, fid, e1, f1, e2, f2);
-  double B[NL][NL], X[NL][NL];
+__global__ void __launch_bounds__(128)
+hrt_asm_setup_kernel(long long E, int nx, int ny, const double* __restrict__ He, double* __restrict__ Pinv,
+                     unsigned int* status) {
+  constexpr int NL = P + 1, NL4 = 4 * NL, LDP = NL4 + 1;
+  __shared__ double sm[4][NL4 * LDP];
+  __shared__ double scol[4][NL4];     // column k before the step
+  __shared__ int sperm[4][NL4];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long e = blockIdx.x * 4LL + w;
+  if (e >= E) return;   // whole warps leave together; the kernel has no block barrier
+  double* A = sm[w];
+  int nbe[4], nbf[4];
 #pragma unroll
-  for (int a = 0; a < NL; ++a)
-#pragma unroll
-    for (int b = 0; b < NL; ++b) {
-      B[a][b] = He[(size_t)e1 * NL4 * NL4 + (size_t)(f1 * NL + a) * NL4 + f1 * NL + b] +
-                He[(size_t)e2 * NL4 * NL4 + (size_t)(f2 * NL + a) * NL4 + f2 * NL + b];
-      X[a][b] = a == b ? 1.0 : 0.0;
-    }
-  bool singular = false;
-#pragma unroll
-  for (int k = 0; k < NL; ++k) {
-    int pr = k;
-#pragma unroll
-    for (int i = k + 1; i < NL; ++i)
-      if (fabs(B[i][k]) > fabs(B[pr][k])) pr = i;
-#pragma unroll
-    for (int i = k + 1; i < NL; ++i)   // swap rows k and pr (register-resident: by select)
-      if (i == pr) {
-#pragma unroll
-        for (int j = 0; j < NL; ++j) {
-          const double tb = B[k][j], tx = X[k][j];
-          B[k][j] = B[i][j]; B[i][j] = tb;
-          X[k][j] = X[i][j]; X[i][j] = tx;
-        }
-      }
-    singular = singular || !(fabs(B[k][k]) > 1e-300);
-    const double inv = 1.0 / B[k][k];
-#pragma unroll
-    for (int j = 0; j < NL; ++j) { B[k][j] *= inv; X[k][j] *= inv; }
-#pragma unroll
-    for (int i = 0; i < NL; ++i) {
-      if (i == k) continue;
-      const double fct = B[i][k];
-#pragma unroll
-      for (int j = 0; j < NL; ++j) { B[i][j] -= fct * B[k][j]; X[i][j] -= fct * X[k][j]; }
-    }
+  for (int f = 0; f < 4; ++f) {
+    nbe[f] = nb_elem(nx, ny, (int)e, f);
+    nbf[f] = (f + 2) & 3;
   }
-  if (singular) atomicOr(status, kDevSingular);
+  for (int idx = lane; idx < NL4 * NL4; idx += 32) {
+    const int r = idx / NL4, c = idx % NL4, fr = r / NL, fc = c / NL;
+    double v;
+    if (nbe[fr] < 0 || nbe[fc] < 0) {
+      v = r == c ? 1.0 : 0.0;
+    } else {
+      v = He[(size_t)e * NL4 * NL4 + idx];
+      if (fr == fc) {
+        const int on = nbf[fr] * NL;
+        v += He[(size_t)nbe[fr] * NL4 * NL4 + (size_t)(on + r % NL) * NL4 + on + c % NL];
+      }
+    }
+    A[r * LDP + c] = v;
+  }
+  __syncwarp();
+  bool singular = false;
+  for (int k = 0; k < NL4; ++k) {
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + lane; i < NL4; i += 32) {
+      const double v = fabs(A[i * LDP + k]);
+      if (v > best) { best = v; bi = i; }
+    }
 #pragma unroll
-  for (int a = 0; a < NL; ++a)
-#pragma unroll
-    for (int b = 0; b < NL; ++b) Minv[(size_t)fid * NL * NL + a * NL + b] = X[a][b];
+    for (int off = 16; off > 0; off >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    singular = singular || !(best > 1e-300);
+    if (lane == 0) sperm[w][k] = bi;
+    if (bi != k)
+      for (int j = lane; j < NL4; j += 32) {
+        const double t = A[k * LDP + j];
+        A[k * LDP + j] = A[bi * LDP + j];
+        A[bi * LDP + j] = t;
+      }
+    __syncwarp();
+    const double inv = 1.0 / A[k * LDP + k];
+    for (int i = lane; i < NL4; i += 32) scol[w][i] = A[i * LDP + k];
+    __syncwarp();
+    for (int j = lane; j < NL4; j += 32)
+      if (j != k) A[k * LDP + j] *= inv;
+    __syncwarp();
+    for (int idx = lane; idx < NL4 * NL4; idx += 32) {
+      const int i = idx / NL4, j = idx % NL4;
+      if (i == k) continue;
+      const double cik = scol[w][i];
+      if (j == k) A[i * LDP + k] = -cik * inv;
+      else A[i * LDP + j] -= cik * A[k * LDP + j];
+    }
+    __syncwarp();
+    if (lane == 0) A[k * LDP + k] = inv;
+    __syncwarp();
+  }
+  for (int k = NL4 - 1; k >= 0; --k) {   // undo the row interchanges as column interchanges
+    const int pr = sperm[w][k];
+    if (pr != k)
+      for (int i = lane; i < NL4; i += 32) {
+        const double t = A[i * LDP + k];
+        A[i * LDP + k] = A[i * LDP + pr];
+        A[i * LDP + pr] = t;
+      }
+    __syncwarp();
+  }
+  for (int idx = lane; idx < NL4 * NL4; idx += 32) Pinv[(size_t)e * NL4 * NL4 + idx] = A[(idx / NL4) * LDP + idx % NL4];
+  if (lane == 0 && singular) atomicOr(status, kDevSingular);
 }
 
 // [J; phi] = Li [g - C2 lambda_e; f]
@@ -747,13 +784,14 @@ __global__ void hrt_recover_kernel(long long E, int nx, int ny, const double* __
   }
 }
 
-// ---- the multiplier system's Krylov solve: BiCGStab (van der Vorst) with the face-block
-// Jacobi preconditioner above.  Its scalars stay on the device: every dot product is
+// ---- the multiplier system's Krylov solve: BiCGStab (van der Vorst) with the element-patch
+// Schwarz preconditioner above.  Its scalars stay on the device: every dot product is
 // reduced in two fixed stages (per-block partial sums, then each reader sums the kKB
 // partials in the same order), so the iteration is deterministic and no kernel waits on
 // the host; the host reads the convergence state once every kCheck iterations.  One
-// iteration is five launches: p and its preconditioned copy; v = H p_hat with r_hat.v;
-// s and s_hat; t = H s_hat with t.s and t.t; lambda and r with r_hat.r and r.r.  The
+// iteration is nine launches: p; p_hat = M^{-1} p (element half, face half); v = H p_hat
+// with r_hat.v; s; s_hat (two halves); t = H s_hat with t.s and t.t; lambda and r with
+// r_hat.r and r.r.  The
 // kernels take their iteration as an offset from a base index held on the device, so one
 // CUDA graph of kCheck iterations (and the base's advance) is replayed block after block.
 constexpr int kKB = 256, kKT = 256, kCheck = 16;
@@ -774,8 +812,10 @@ static_assert(sizeof(KState) % sizeof(double) == 0, "KState is carved from a dou
 struct Kry {
   int nx, ny;
   long long nfaces, nl;
+  long long E;
   const double* He;
-  const double* Minv;
+  const double* Pinv;   // [E][4 (p+1)][4 (p+1)] element-patch inverses of the preconditioner
+  double* z;            // [E][4 (p+1)] the preconditioner's element results
   double *x, *r, *rh, *p, *v, *s, *t, *ph, *sh;
   double* part;   // [kNumDots][kKB]
   KScal* sc;      // [iterations + 1]: sc[i] holds iteration i's rho, alpha, omega (sc[0] = 1)
@@ -826,17 +866,25 @@ __device__ void kry_partial(double a, double b, double* part, int qa, int qb) {
   }
 }
 
-// y = M^{-1} x on face fid's p+1 dofs
+// The preconditioner's element half: z_e = Pinv_e x|e for every element and row (the face
+// half, each face's two sides summed, is hrt_gather_kernel)
 template <int P>
-__device__ __forceinline__ void kry_precond(const Kry& k, long long fid, const double* xf, double* y) {
-  constexpr int NL = P + 1;
-  const double* Mi = k.Minv + (size_t)fid * NL * NL;
-#pragma unroll
-  for (int a = 0; a < NL; ++a) {
+__global__ void kry_asm_apply_kernel(Kry k, const double* __restrict__ x) {
+  constexpr int NL = P + 1, NL4 = 4 * NL;
+  if (kry_stopped(k)) return;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < k.E * NL4;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long e = t / NL4;
+    const double* row = k.Pinv + (size_t)t * NL4;
     double s = 0.0;
 #pragma unroll
-    for (int b = 0; b < NL; ++b) s = fma(Mi[a * NL + b], xf[b], s);
-    y[fid * NL + a] = s;
+    for (int g = 0; g < 4; ++g) {
+      const long long fi = face_index(k.nx, k.ny, (int)e, g);
+      if (fi < 0) continue;
+#pragma unroll
+      for (int u = 0; u < NL; ++u) s = fma(row[g * NL + u], x[fi * NL + u], s);
+    }
+    k.z[t] = s;
   }
 }
 
@@ -856,12 +904,11 @@ __global__ void kry_init_kernel(Kry k, double tol2) {
   }
 }
 
-// iteration base + j, step 1: convergence test on the previous residual, rho, p, p_hat.
+// iteration base + j, step 1: convergence test on the previous residual, rho, p.
 // With update == false it only records the state (the final check after the last
 // iteration).
 template <int P>
 __global__ void kry_p_kernel(Kry k, int j, bool update) {
-  constexpr int NL = P + 1;
   __shared__ double red;
   if (kry_stopped(k)) return;
   const int it = k.st->base + j;
@@ -879,17 +926,8 @@ __global__ void kry_p_kernel(Kry k, int j, bool update) {
   }
   if (conv || brk || !update) return;
   const double beta = (rho / pv.rho) * (pv.alpha / pv.omega);
-  for (long long fid = blockIdx.x * (long long)blockDim.x + threadIdx.x; fid < k.nfaces;
-       fid += (long long)gridDim.x * blockDim.x) {
-    double pf[NL];
-#pragma unroll
-    for (int a = 0; a < NL; ++a) {
-      const long long i = fid * NL + a;
-      pf[a] = k.r[i] + beta * (k.p[i] - pv.omega * k.v[i]);
-      k.p[i] = pf[a];
-    }
-    kry_precond<P>(k, fid, pf, k.ph);
-  }
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < k.nl; i += (long long)gridDim.x * blockDim.x)
+    k.p[i] = k.r[i] + beta * (k.p[i] - pv.omega * k.v[i]);
 }
 
 // y = H x with the partial dots w.y (into qa) and, when qb >= 0, y.y (into qb)
@@ -912,10 +950,9 @@ __global__ void kry_matvec_kernel(Kry k, const double* __restrict__ x, double* _
   kry_partial(a, b, k.part, qa, qb);
 }
 
-// step 3: alpha, s = r - alpha v, s_hat
+// step 3: alpha, s = r - alpha v
 template <int P>
 __global__ void kry_s_kernel(Kry k, int j) {
-  constexpr int NL = P + 1;
   __shared__ double red;
   if (kry_stopped(k)) return;
   const int it = k.st->base + j;
@@ -926,17 +963,8 @@ __global__ void kry_s_kernel(Kry k, int j) {
     return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) k.sc[it + 1].alpha = alpha;
-  for (long long fid = blockIdx.x * (long long)blockDim.x + threadIdx.x; fid < k.nfaces;
-       fid += (long long)gridDim.x * blockDim.x) {
-    double sf[NL];
-#pragma unroll
-    for (int a = 0; a < NL; ++a) {
-      const long long i = fid * NL + a;
-      sf[a] = k.r[i] - alpha * k.v[i];
-      k.s[i] = sf[a];
-    }
-    kry_precond<P>(k, fid, sf, k.sh);
-  }
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < k.nl; i += (long long)gridDim.x * blockDim.x)
+    k.s[i] = k.r[i] - alpha * k.v[i];
 }
 
 // step 5: omega, lambda += alpha p_hat + omega s_hat, r = s - omega t, and the partials of
@@ -969,10 +997,16 @@ static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1
 // n iterations starting at offset 0 from the device's base, then the base's advance
 template <int P>
 static void kry_block(const Kry& k, int n, cudaStream_t s) {
+  constexpr int NL4 = 4 * (P + 1);
+  const unsigned eb = nblk(k.E * NL4, 256), fb = nblk(k.nl, 256);
   for (int j = 0; j < n; ++j) {
     kry_p_kernel<P><<<kKB, kKT, 0, s>>>(k, j, true);
+    kry_asm_apply_kernel<P><<<eb, 256, 0, s>>>(k, k.p);                      // p_hat = M^{-1} p
+    hrt_gather_kernel<P><<<fb, 256, 0, s>>>(k.nx, k.ny, k.nfaces, k.z, k.ph);
     kry_matvec_kernel<P><<<kKB, kKT, 0, s>>>(k, k.ph, k.v, k.rh, kDotRV, -1);
     kry_s_kernel<P><<<kKB, kKT, 0, s>>>(k, j);
+    kry_asm_apply_kernel<P><<<eb, 256, 0, s>>>(k, k.s);                      // s_hat = M^{-1} s
+    hrt_gather_kernel<P><<<fb, 256, 0, s>>>(k.nx, k.ny, k.nfaces, k.z, k.sh);
     kry_matvec_kernel<P><<<kKB, kKT, 0, s>>>(k, k.sh, k.t, k.s, kDotTS, kDotTT);
     kry_x_kernel<<<kKB, kKT, 0, s>>>(k, j);
   }
@@ -1028,7 +1062,7 @@ static vef_status hrt_run(Mesh& M, const HrtIn& in, double tol, int max_iter, do
   const HrtTab tab = make_hrt_tab(P, M.m);
   std::vector<double> refh;
   make_hrt_ref<P>(tab, refh);
-  const size_t total = per_e * E + 10 * vec + (size_t)std::max(1LL, nfaces) * S::NL * S::NL +
+  const size_t total = per_e * E + 10 * vec + (size_t)(S::NL4 * S::NL4 + S::NL4) * E +
                        (size_t)kNumDots * kKB + 3 * nsc + sizeof(KState) / sizeof(double) + refh.size();
   vef_status st = ensure_buffer((void**)&M.work, &M.work_cap, total * sizeof(double));
   if (st != VEF_OK) return st;
@@ -1045,8 +1079,10 @@ static vef_status hrt_run(Mesh& M, const HrtIn& in, double tol, int max_iter, do
   k.x = take(vec);   // copied to lambda at the end (the graph keeps one layout)
   k.r = take(vec); k.rh = take(vec); k.p = take(vec); k.v = take(vec); k.s = take(vec);
   k.t = take(vec); k.ph = take(vec); k.sh = take(vec);
-  double* Minv = take((size_t)std::max(1LL, nfaces) * S::NL * S::NL);
-  k.Minv = Minv;
+  double* Pinv = take((size_t)S::NL4 * S::NL4 * E);
+  k.Pinv = Pinv;
+  k.z = take((size_t)S::NL4 * E);
+  k.E = E;
   k.part = take((size_t)kNumDots * kKB);
   k.st = reinterpret_cast<KState*>(take(sizeof(KState) / sizeof(double)));
   k.sc = reinterpret_cast<KScal*>(take(3 * nsc));   // last: its length follows max_iter
@@ -1074,7 +1110,7 @@ static vef_status hrt_run(Mesh& M, const HrtIn& in, double tol, int max_iter, do
   KState hs{};
   if (nl > 0) {
     hrt_gather_kernel<P><<<nblk(nl, 256), 256, 0, s>>>(M.nx, M.ny, nfaces, re, k.r);
-    hrt_face_block_kernel<P><<<nblk(nfaces, 128), 128, 0, s>>>(M.nx, M.ny, nfaces, He, Minv, M.dev_status);
+    hrt_asm_setup_kernel<P><<<(unsigned)((E + 3) / 4), 128, 0, s>>>(E, M.nx, M.ny, He, Pinv, M.dev_status);
     kry_init_kernel<<<kKB, kKT, 0, s>>>(k, tol * tol);
     VEF_CUDA_TRY(cudaGetLastError());
     cudaGraphExec_t graph = nullptr;

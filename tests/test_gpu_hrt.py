@@ -2,7 +2,7 @@
 
 The oracle (oracle/hrt.py, pinned in tests/test_oracle_hrt.py) eliminates the same element
 blocks and solves the multiplier system directly; the library eliminates them on the GPU and
-solves the multiplier system by face-block-Jacobi BiCGStab to a relative residual of
+solves the multiplier system by BiCGStab (element-patch Schwarz) to a relative residual of
 1e-14, so phi, J and lambda agree to about the conditioning of H times that.
 """
 import numpy as np
