@@ -816,6 +816,15 @@ struct Kry {
   const double* He;
   const double* Pinv;   // [E][4 (p+1)][4 (p+1)] element-patch inverses of the preconditioner
   double* z;            // [E][4 (p+1)] the preconditioner's element results
+  // coarse space of the preconditioner: bilinear functions on a grid of (ncx+1) x (ncy+1)
+  // vertices whose cells hold cx x cy elements (the last ones fewer)
+  int ncx, ncy, cx, cy, nc;
+  double gl[kMaxP + 1];   // the multiplier nodes on [0, 1]
+  int* cv;                // [nl] lower-left coarse vertex of each multiplier's coarse cell
+  double2* cw;            // [nl] its local coordinates (xi, eta) in that cell
+  double* A0;             // [nc][nc] the coarse operator R0 H R0^T, then its inverse
+  double* pc;             // [ncx ncy][4] per cell: its multipliers' restriction to its vertices
+  double* zc;             // [nc] coarse correction
   double *x, *r, *rh, *p, *v, *s, *t, *ph, *sh;
   double* part;   // [kNumDots][kKB]
   KScal* sc;      // [iterations + 1]: sc[i] holds iteration i's rho, alpha, omega (sc[0] = 1)
@@ -886,6 +895,341 @@ __global__ void kry_asm_apply_kernel(Kry k, const double* __restrict__ x) {
     }
     k.z[t] = s;
   }
+}
+
+// ---- coarse space of the preconditioner (two-level additive Schwarz): the coarse
+// functions are bilinear on a grid of at most 12 x 12 vertices laid over the elements, taken
+// at the multiplier nodes of every interior face; the coarse operator A0 = R0 H R0^T is
+// assembled from the elements' H_e and inverted once per solve, and each application adds
+// R0^T A0^{-1} R0 x to the element-patch part.
+// (144 vertices: the coarse operator, 162 KB in FP64, is inverted in one CTA's shared memory)
+constexpr int kCoarseMaxCells = 11, kCoarseMax = (kCoarseMaxCells + 1) * (kCoarseMaxCells + 1);
+
+// the coarse cell holding multiplier node tt of interior face fid (its lower-left vertex v0)
+// and the node's local coordinates in it.  A node on a cell's left or lower line belongs to
+// that cell, one on the domain's right or upper coarse line to the last cell: so vertical
+// faces on lines x = i0 .. i1 - 1 and horizontal faces on lines y = j0 .. j1 - 1 of the
+// cell's element range [i0, i1) x [j0, j1) are its own.
+__device__ __forceinline__ void coarse_coords(const Kry& k, long long fid, int tt, int& v0, double& xi,
+                                              double& eta) {
+  const long long nv = (long long)(k.nx - 1) * k.ny;
+  double X, Y;   // in element widths from the lower-left corner
+  if (fid < nv) {
+    const long long j = fid / (k.nx - 1), i = fid % (k.nx - 1);
+    X = (double)(i + 1);
+    Y = (double)j + k.gl[tt];
+  } else {
+    const long long h = fid - nv, j = h / k.nx, i = h % k.nx;
+    X = (double)i + k.gl[tt];
+    Y = (double)(j + 1);
+  }
+  const int kx = min((int)(X / k.cx), k.ncx - 1), ky = min((int)(Y / k.cy), k.ncy - 1);
+  const double x0 = (double)(kx * k.cx), x1 = (double)min((kx + 1) * k.cx, k.nx);
+  const double y0 = (double)(ky * k.cy), y1 = (double)min((ky + 1) * k.cy, k.ny);
+  xi = (X - x0) / (x1 - x0);
+  eta = (Y - y0) / (y1 - y0);
+  v0 = ky * (k.ncx + 1) + kx;
+}
+
+// the four bilinear weights, vertices in the order v0, v0 + 1, v0 + W, v0 + W + 1
+__device__ __forceinline__ void bilinear(double xi, double eta, double w[4]) {
+  w[0] = (1.0 - xi) * (1.0 - eta);
+  w[1] = xi * (1.0 - eta);
+  w[2] = (1.0 - xi) * eta;
+  w[3] = xi * eta;
+}
+
+// coarse vertices and bilinear weights of multiplier node tt of interior face fid
+__device__ __forceinline__ void coarse_weights(const Kry& k, long long fid, int tt, int v[4], double w[4]) {
+  double xi, eta;
+  coarse_coords(k, fid, tt, v[0], xi, eta);
+  const int W = k.ncx + 1;
+  v[1] = v[0] + 1;
+  v[2] = v[0] + W;
+  v[3] = v[2] + 1;
+  bilinear(xi, eta, w);
+}
+
+// the node table of the coarse space, once per solve
+template <int P>
+__global__ void hrt_coarse_nodes_kernel(Kry k) {
+  constexpr int NL = P + 1;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= k.nl) return;
+  int v0;
+  double xi, eta;
+  coarse_coords(k, t / NL, (int)(t % NL), v0, xi, eta);
+  k.cv[t] = v0;
+  k.cw[t] = make_double2(xi, eta);
+}
+
+// per coarse cell (one CTA): the sum over its elements of P_e^T H_e P_e, P_e the element's
+// multipliers' weights on the cell's four vertices (every face of an element inside the
+// cell lies in the cell's closure); threads take elements in a fixed stride and the block
+// sums in a fixed order
+template <int P>
+__global__ void __launch_bounds__(128) hrt_coarse_cell_kernel(Kry k, double* __restrict__ Acell) {
+  constexpr int NL = P + 1, NL4 = 4 * NL;
+  const int cell = blockIdx.x, kx = cell % k.ncx, ky = cell / k.ncx;
+  const int i0 = kx * k.cx, i1 = min(i0 + k.cx, k.nx), j0 = ky * k.cy, j1 = min(j0 + k.cy, k.ny);
+  const int ni = i1 - i0, nel = ni * (j1 - j0);
+  const int W = k.ncx + 1;
+  double acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+  for (int t = threadIdx.x; t < nel; t += blockDim.x) {
+    const long long e = (long long)(j0 + t / ni) * k.nx + i0 + t % ni;
+    double Pw[NL4][4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const long long fi = face_index(k.nx, k.ny, (int)e, g);
+#pragma unroll
+      for (int tt = 0; tt < NL; ++tt) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Pw[g * NL + tt][c] = 0.0;
+        if (fi < 0) continue;
+        int v[4];
+        double w[4];
+        coarse_weights(k, fi, tt, v, w);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          // a face on the cell's upper or right line may be assigned to the next cell, whose
+          // far vertices then carry weight zero: keep the cell's own four
+          const int lx = v[c] % W - kx, ly = v[c] / W - ky;
+          if (lx < 0 || lx > 1 || ly < 0 || ly > 1) continue;
+          Pw[g * NL + tt][ly * 2 + lx] += w[c];
+        }
+      }
+    }
+    const double* He = k.He + (size_t)e * NL4 * NL4;
+    for (int i = 0; i < NL4; ++i) {
+      double T[4] = {0.0, 0.0, 0.0, 0.0};   // (H_e P_e)[i][:]
+      for (int j = 0; j < NL4; ++j) {
+        const double h = He[i * NL4 + j];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) T[b] = fma(h, Pw[j][b], T[b]);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a * 4 + b] = fma(Pw[i][a], T[b], acc[a * 4 + b]);
+    }
+  }
+  __shared__ double red[4][16];   // blockDim 128: four warps
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    double x = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][q] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 16)
+    Acell[(size_t)cell * 16 + threadIdx.x] =
+        ((red[0][threadIdx.x] + red[1][threadIdx.x]) + red[2][threadIdx.x]) + red[3][threadIdx.x];
+}
+
+// the dense coarse operator, one row per thread from the cells around its vertex
+__global__ void hrt_coarse_assemble_kernel(Kry k, const double* __restrict__ Acell) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= k.nc) return;
+  const int W = k.ncx + 1, ax = a % W, ay = a / W;
+  double* row = k.A0 + (size_t)a * k.nc;
+  for (int b = 0; b < k.nc; ++b) row[b] = 0.0;
+  for (int cy = ay - 1; cy <= ay; ++cy)
+    for (int cx = ax - 1; cx <= ax; ++cx) {
+      if (cx < 0 || cy < 0 || cx >= k.ncx || cy >= k.ncy) continue;
+      const int cell = cy * k.ncx + cx, la = (ay - cy) * 2 + (ax - cx);
+      for (int lb = 0; lb < 4; ++lb) {
+        const int b = (cy + lb / 2) * W + cx + lb % 2;
+        row[b] += Acell[(size_t)cell * 16 + la * 4 + lb];
+      }
+    }
+  // a coarse function that vanishes on every interior face (a domain corner's when its cell
+  // is one element wide) has an empty row and column: put 1 on the diagonal, its restriction
+  // being zero, so it contributes nothing and A0 stays invertible
+  double mx = 0.0;
+  for (int b = 0; b < k.nc; ++b) mx = fmax(mx, fabs(row[b]));
+  if (mx == 0.0) row[a] = 1.0;
+}
+
+// Gauss-Jordan inverse of the coarse operator with partial pivoting, in FP32 in one CTA's
+// shared memory, of A0 scaled by its largest entry; written back in FP64 over A0.  The
+// coarse solve is part of the preconditioner only: its accuracy changes the iteration
+// count, not the FP64 Krylov iteration's answer.  (FP64 here is held to one SM's two FP64
+// FMA per clock: n^3 = 3 M FMA is 0.75 ms, FP32 runs at 64 times that rate.)
+// Per pivot step two barriers: every warp finds the pivot row itself (same order, same
+// result), the pivot row, the row it changes places with and the pivot column go to
+// buffers, and each thread then updates only its own entries, reading the row that moves
+// to row pr from the buffer.
+constexpr int kCoarseInvThreads = 512, kCoarsePerLane = (kCoarseMax + 31) / 32;
+__global__ void __launch_bounds__(kCoarseInvThreads) hrt_coarse_invert_kernel(Kry k, unsigned int* status) {
+  const int n = k.nc, ld = n | 1, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int nwarp = kCoarseInvThreads / 32;
+  extern __shared__ float A[];   // [n][ld]
+  __shared__ float R[kCoarseMax], krow[kCoarseMax], colk[kCoarseMax];
+  __shared__ int perm[kCoarseMax], src[kCoarseMax];
+  __shared__ double wmax[nwarp];
+  double m = 0.0;
+  for (int idx = tid; idx < n * n; idx += kCoarseInvThreads) m = fmax(m, fabs(k.A0[idx]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) wmax[warp] = m;
+  __syncthreads();
+  m = 0.0;
+  for (int w = 0; w < nwarp; ++w) m = fmax(m, wmax[w]);
+  const double rs = m > 0.0 ? 1.0 / m : 1.0;
+  for (int idx = tid; idx < n * n; idx += kCoarseInvThreads) A[(idx / n) * ld + idx % n] = (float)(k.A0[idx] * rs);
+  __syncthreads();
+  for (int kk = 0; kk < n; ++kk) {
+    float best = -1.0f;
+    int pr = kk;
+#pragma unroll
+    for (int q = 0; q < kCoarsePerLane; ++q) {
+      const int i = kk + lane + 32 * q;
+      const float v = i < n ? fabsf(A[i * ld + kk]) : -1.0f;
+      if (v > best) { best = v; pr = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, pr, o);
+      if (ob > best || (ob == best && oi < pr)) { best = ob; pr = oi; }
+    }
+    if (tid == 0) {
+      perm[kk] = pr;
+      if (!(best > 1e-30f)) atomicOr(status, kDevSingular);
+    }
+    const float iv = 1.0f / A[pr * ld + kk];
+    for (int j = tid; j < n; j += kCoarseInvThreads) {
+      R[j] = j == kk ? iv : A[pr * ld + j] * iv;
+      krow[j] = A[kk * ld + j];
+      colk[j] = j == kk ? A[pr * ld + kk] : (j == pr ? A[kk * ld + kk] : A[j * ld + kk]);
+    }
+    __syncthreads();
+    float r[kCoarsePerLane];   // this lane's columns of the new pivot row
+#pragma unroll
+    for (int q = 0; q < kCoarsePerLane; ++q) r[q] = lane + 32 * q < n ? R[lane + 32 * q] : 0.0f;
+    for (int i = warp; i < n; i += nwarp) {
+      float* Ai = A + i * ld;
+      const float c = colk[i];
+      const bool moved = i == pr;   // row pr now holds the old row kk
+      float a[kCoarsePerLane];      // all loads of the row before its stores
+#pragma unroll
+      for (int q = 0; q < kCoarsePerLane; ++q) {
+        const int j = lane + 32 * q;
+        a[q] = j < n ? (moved ? krow[j] : Ai[j]) : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < kCoarsePerLane; ++q) {
+        const int j = lane + 32 * q;
+        if (j < n) Ai[j] = i == kk ? r[q] : (j == kk ? -c * iv : fmaf(-c, r[q], a[q]));
+      }
+    }
+    __syncthreads();
+  }
+  // the row interchanges, undone as column interchanges in reverse order, as one gather
+  if (tid == 0) {
+    for (int j = 0; j < n; ++j) src[j] = j;
+    for (int kk = n - 1; kk >= 0; --kk) {
+      const int t = src[kk];
+      src[kk] = src[perm[kk]];
+      src[perm[kk]] = t;
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n * n; idx += kCoarseInvThreads) {
+    const int i = idx / n, j = idx % n;
+    k.A0[idx] = (double)A[i * ld + src[j]] * rs;
+  }
+}
+
+// per coarse cell (one CTA): the restriction of x to its four vertices from the multiplier
+// nodes the cell owns (coarse_coords), threads in a fixed stride and a fixed-order block sum
+template <int P>
+__global__ void __launch_bounds__(256) kry_coarse_restrict_kernel(Kry k, const double* __restrict__ x) {
+  constexpr int NL = P + 1;
+  if (kry_stopped(k)) return;
+  const int cell = blockIdx.x, kx = cell % k.ncx, ky = cell / k.ncx;
+  const int i0 = kx * k.cx, i1 = min(i0 + k.cx, k.nx), j0 = ky * k.cy, j1 = min(j0 + k.cy, k.ny);
+  const long long nv = (long long)(k.nx - 1) * k.ny;
+  const int xa = max(i0, 1), ya = max(j0, 1);
+  const int nvf = max(0, i1 - xa) * (j1 - j0), nhf = max(0, j1 - ya) * (i1 - i0);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int t = threadIdx.x; t < (nvf + nhf) * NL; t += blockDim.x) {
+    const int fl = t / NL, tt = t - fl * NL;
+    long long fid;
+    if (fl < nvf) {
+      const int xv = xa + fl / (j1 - j0), j = j0 + fl % (j1 - j0);
+      fid = (long long)j * (k.nx - 1) + (xv - 1);
+    } else {
+      const int g = fl - nvf, yh = ya + g / (i1 - i0), i = i0 + g % (i1 - i0);
+      fid = nv + (long long)(yh - 1) * k.nx + i;
+    }
+    const long long q = fid * NL + tt;
+    const double2 c = k.cw[q];
+    double w[4];
+    bilinear(c.x, c.y, w);
+    const double xq = x[q];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[b] = fma(w[b], xq, acc[b]);
+  }
+  __shared__ double red[8][4];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    double v = acc[b];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][b] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double sum = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) sum += red[i][threadIdx.x];
+    k.pc[(size_t)cell * 4 + threadIdx.x] = sum;
+  }
+}
+
+// zc = A0^{-1} vc, vc summed per vertex from the cells around it (fixed order) into shared
+// memory by every block, then one warp per row
+__global__ void __launch_bounds__(256) kry_coarse_solve_kernel(Kry k) {
+  if (kry_stopped(k)) return;
+  __shared__ double vc[kCoarseMax];
+  const int W = k.ncx + 1;
+  for (int a = threadIdx.x; a < k.nc; a += blockDim.x) {
+    const int ax = a % W, ay = a / W;
+    double v = 0.0;
+    for (int cy = ay - 1; cy <= ay; ++cy)
+      for (int cx = ax - 1; cx <= ax; ++cx) {
+        if (cx < 0 || cy < 0 || cx >= k.ncx || cy >= k.ncy) continue;
+        v += k.pc[(size_t)(cy * k.ncx + cx) * 4 + (ay - cy) * 2 + (ax - cx)];
+      }
+    vc[a] = v;
+  }
+  __syncthreads();
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= k.nc) return;
+  const double* Ar = k.A0 + (size_t)row * k.nc;
+  double s = 0.0;
+  for (int b = lane; b < k.nc; b += 32) s = fma(Ar[b], vc[b], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) k.zc[row] = s;
+}
+
+// y = M^{-1} x assembled per multiplier: the two sides' element-patch results plus the
+// coarse correction R0^T zc
+template <int P>
+__global__ void kry_precond_gather_kernel(Kry k, double* __restrict__ y) {
+  constexpr int NL = P + 1, NL4 = 4 * NL;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= k.nl) return;
+  long long e1, e2;
+  int f1, f2;
+  face_sides(k.nx, k.ny, t / NL, e1, f1, e2, f2);
+  const int tt = (int)(t % NL);
+  const int v0 = k.cv[t], W = k.ncx + 1;
+  const double2 c = k.cw[t];
+  double w[4];
+  bilinear(c.x, c.y, w);
+  const double cor = fma(w[3], k.zc[v0 + W + 1], fma(w[2], k.zc[v0 + W], fma(w[1], k.zc[v0 + 1], w[0] * k.zc[v0])));
+  y[t] = (k.z[e1 * NL4 + f1 * NL + tt] + k.z[e2 * NL4 + f2 * NL + tt]) + cor;
 }
 
 // r_hat = r, x = p = v = 0, partials of r_hat.r and r.r, sc[0] = 1, state cleared
@@ -999,14 +1343,19 @@ template <int P>
 static void kry_block(const Kry& k, int n, cudaStream_t s) {
   constexpr int NL4 = 4 * (P + 1);
   const unsigned eb = nblk(k.E * NL4, 256), fb = nblk(k.nl, 256);
+  // element patches, coarse restriction and solve, then per multiplier the sum
+  auto precond = [&](const double* x, double* y) {
+    kry_asm_apply_kernel<P><<<eb, 256, 0, s>>>(k, x);
+    kry_coarse_restrict_kernel<P><<<(unsigned)(k.ncx * k.ncy), 256, 0, s>>>(k, x);
+    kry_coarse_solve_kernel<<<(unsigned)((k.nc + 7) / 8), 256, 0, s>>>(k);
+    kry_precond_gather_kernel<P><<<fb, 256, 0, s>>>(k, y);
+  };
   for (int j = 0; j < n; ++j) {
     kry_p_kernel<P><<<kKB, kKT, 0, s>>>(k, j, true);
-    kry_asm_apply_kernel<P><<<eb, 256, 0, s>>>(k, k.p);                      // p_hat = M^{-1} p
-    hrt_gather_kernel<P><<<fb, 256, 0, s>>>(k.nx, k.ny, k.nfaces, k.z, k.ph);
+    precond(k.p, k.ph);                                                        // p_hat = M^{-1} p
     kry_matvec_kernel<P><<<kKB, kKT, 0, s>>>(k, k.ph, k.v, k.rh, kDotRV, -1);
     kry_s_kernel<P><<<kKB, kKT, 0, s>>>(k, j);
-    kry_asm_apply_kernel<P><<<eb, 256, 0, s>>>(k, k.s);                      // s_hat = M^{-1} s
-    hrt_gather_kernel<P><<<fb, 256, 0, s>>>(k.nx, k.ny, k.nfaces, k.z, k.sh);
+    precond(k.s, k.sh);                                                        // s_hat = M^{-1} s
     kry_matvec_kernel<P><<<kKB, kKT, 0, s>>>(k, k.sh, k.t, k.s, kDotTS, kDotTT);
     kry_x_kernel<<<kKB, kKT, 0, s>>>(k, j);
   }
@@ -1062,19 +1411,33 @@ static vef_status hrt_run(Mesh& M, const HrtIn& in, double tol, int max_iter, do
   const HrtTab tab = make_hrt_tab(P, M.m);
   std::vector<double> refh;
   make_hrt_ref<P>(tab, refh);
+  // the coarse grid: at most kCoarseMaxCells cells per direction
+  Kry k{};
+  k.cx = (M.nx + kCoarseMaxCells - 1) / kCoarseMaxCells;
+  k.cy = (M.ny + kCoarseMaxCells - 1) / kCoarseMaxCells;
+  k.ncx = (M.nx + k.cx - 1) / k.cx;
+  k.ncy = (M.ny + k.cy - 1) / k.cy;
+  const int nc = (k.ncx + 1) * (k.ncy + 1);
+  k.nc = nc;
+  {
+    double gw[kMaxP + 1];
+    gauss_legendre(P + 1, k.gl, gw);
+  }
   const size_t total = per_e * E + 10 * vec + (size_t)(S::NL4 * S::NL4 + S::NL4) * E +
-                       (size_t)kNumDots * kKB + 3 * nsc + sizeof(KState) / sizeof(double) + refh.size();
+                       (size_t)nc * nc + (size_t)nc + 20 * (size_t)k.ncx * k.ncy + 2 * vec + (vec + 1) / 2 +
+                       (size_t)kNumDots * kKB + 3 * nsc + sizeof(KState) / sizeof(double) + refh.size() +
+                       32;   // each of the takes below rounded up to two doubles
   vef_status st = ensure_buffer((void**)&M.work, &M.work_cap, total * sizeof(double));
   if (st != VEF_OK) return st;
   double* base = M.work;
-  auto take = [&](size_t n) { double* q = base; base += n; return q; };
+  // 16-byte aligned pieces (cw is read as double2)
+  auto take = [&](size_t n) { double* q = base; base += (n + 1) & ~(size_t)1; return q; };
   double* Li = take((size_t)S::MM * S::MM * E);
   double* C2 = take((size_t)S::NJ * S::NL4 * E);
   double* g = take((size_t)S::NJ * E);
   double* f = take((size_t)S::N * E);
   double* He = take((size_t)S::NL4 * S::NL4 * E);
   double* re = take((size_t)S::NL4 * E);
-  Kry k{};
   k.nx = M.nx; k.ny = M.ny; k.nfaces = nfaces; k.nl = nl; k.He = He;
   k.x = take(vec);   // copied to lambda at the end (the graph keeps one layout)
   k.r = take(vec); k.rh = take(vec); k.p = take(vec); k.v = take(vec); k.s = take(vec);
@@ -1083,6 +1446,12 @@ static vef_status hrt_run(Mesh& M, const HrtIn& in, double tol, int max_iter, do
   k.Pinv = Pinv;
   k.z = take((size_t)S::NL4 * E);
   k.E = E;
+  k.A0 = take((size_t)nc * nc);
+  k.pc = take((size_t)4 * k.ncx * k.ncy);
+  k.zc = take((size_t)nc);
+  double* Acell = take((size_t)16 * k.ncx * k.ncy);
+  k.cw = reinterpret_cast<double2*>(take(2 * vec));
+  k.cv = reinterpret_cast<int*>(take((vec + 1) / 2));
   k.part = take((size_t)kNumDots * kKB);
   k.st = reinterpret_cast<KState*>(take(sizeof(KState) / sizeof(double)));
   k.sc = reinterpret_cast<KScal*>(take(3 * nsc));   // last: its length follows max_iter
@@ -1094,6 +1463,8 @@ static vef_status hrt_run(Mesh& M, const HrtIn& in, double tol, int max_iter, do
   const size_t smem = sizeof(HrtSmem<P>), ismem = sizeof(HrtInvSmem<P>);
   VEF_CUDA_TRY(cudaFuncSetAttribute(hrt_local_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   VEF_CUDA_TRY(cudaFuncSetAttribute(hrt_invert_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem));
+  const size_t csmem = (size_t)nc * (nc | 1) * sizeof(float);
+  VEF_CUDA_TRY(cudaFuncSetAttribute(hrt_coarse_invert_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
   int dev = 0, sms = 0, inv_per_sm = 0;
   VEF_CUDA_TRY(cudaGetDevice(&dev));
   VEF_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1111,6 +1482,10 @@ static vef_status hrt_run(Mesh& M, const HrtIn& in, double tol, int max_iter, do
   if (nl > 0) {
     hrt_gather_kernel<P><<<nblk(nl, 256), 256, 0, s>>>(M.nx, M.ny, nfaces, re, k.r);
     hrt_asm_setup_kernel<P><<<(unsigned)((E + 3) / 4), 128, 0, s>>>(E, M.nx, M.ny, He, Pinv, M.dev_status);
+    hrt_coarse_nodes_kernel<P><<<nblk(nl, 256), 256, 0, s>>>(k);
+    hrt_coarse_cell_kernel<P><<<(unsigned)(k.ncx * k.ncy), 128, 0, s>>>(k, Acell);
+    hrt_coarse_assemble_kernel<<<nblk(nc, 128), 128, 0, s>>>(k, Acell);
+    hrt_coarse_invert_kernel<<<1, kCoarseInvThreads, csmem, s>>>(k, M.dev_status);
     kry_init_kernel<<<kKB, kKT, 0, s>>>(k, tol * tol);
     VEF_CUDA_TRY(cudaGetLastError());
     cudaGraphExec_t graph = nullptr;
