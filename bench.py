@@ -795,7 +795,8 @@ def suite_hrt(args):
     """Hybridized RT VEF solve after one transport inversion: 128 x 128 sine-curved Q3 mesh,
     DG Q2 (RT_2 current), S8, seed-2 media, q = 1, vacuum: the sweep's closures give E, E_b,
     J_in; the solve eliminates every element's local system on the GPU, solves the
-    multiplier system (BiCGStab, element-patch Schwarz) and recovers phi and J."""
+    multiplier system (BiCGStab, two-level Schwarz: element patches and a coarse bilinear
+    space) and recovers phi and J."""
     import torch
     from paper_2301_04758_gb300.api import Mesh
     from vef_inputs import level_symmetric, seeded_media

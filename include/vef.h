@@ -306,11 +306,13 @@ vef_status vef_batch_tune(vef_batch batch, void* stream, int* tiles_out);
  * flux and degree-p Lagrange multipliers on the interior faces (nodal at the p+1
  * Gauss-Legendre points; {E n} averaged from the two sides).  Each element's local mixed
  * system is assembled and inverted on the GPU (block inverse [[W, X], [Y, Z]]); its share
- * of the reduced system H = C1 W C2 for the multiplier is solved by BiCGStab with an
- * element-patch additive Schwarz preconditioner (per element, H restricted to its interior
- * faces' multipliers, inverted; standing in for the paper's algebraic multigrid), the
- * matrix applied face by face from the elements' H_e; the current and scalar flux then
- * follow element by element.
+ * of the reduced system H = C1 W C2 for the multiplier is solved by BiCGStab with a
+ * two-level additive Schwarz preconditioner standing in for the paper's algebraic
+ * multigrid: per element, H restricted to its interior faces' multipliers, inverted; plus
+ * a coarse correction on bilinear functions over a grid of at most 11 x 11 cells of whole
+ * elements (its operator R0 H R0^T inverted once per call, in FP32: it steers the FP64
+ * iteration, not its answer).  The matrix is applied face by face from the elements' H_e;
+ * the current and scalar flux then follow element by element.
  *   sigma_t, sigma_s [device] [E];  phi_tr [device] [E][n], P_tr [device] [3][E][n]: the
  *   transport's nodal scalar flux and second moment (vef_moments' phi and P), giving
  *   E = P / phi at the quadrature points and on each side of each face;  Eb, Jin [device]

@@ -1061,15 +1061,19 @@ __global__ void hrt_coarse_assemble_kernel(Kry k, const double* __restrict__ Ace
 // Per pivot step two barriers: every warp finds the pivot row itself (same order, same
 // result), the pivot row, the row it changes places with and the pivot column go to
 // buffers, and each thread then updates only its own entries, reading the row that moves
-// to row pr from the buffer.
+// to row pr from the buffer.  A pivot below 1e-30 of the largest entry (A0 singular in
+// FP32) drops the coarse part: the inverse is written as zero and the preconditioner is the
+// element patches alone.
 constexpr int kCoarseInvThreads = 512, kCoarsePerLane = (kCoarseMax + 31) / 32;
-__global__ void __launch_bounds__(kCoarseInvThreads) hrt_coarse_invert_kernel(Kry k, unsigned int* status) {
+__global__ void __launch_bounds__(kCoarseInvThreads) hrt_coarse_invert_kernel(Kry k) {
   const int n = k.nc, ld = n | 1, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int nwarp = kCoarseInvThreads / 32;
   extern __shared__ float A[];   // [n][ld]
   __shared__ float R[kCoarseMax], krow[kCoarseMax], colk[kCoarseMax];
   __shared__ int perm[kCoarseMax], src[kCoarseMax];
   __shared__ double wmax[nwarp];
+  __shared__ int singular;
+  if (tid == 0) singular = 0;
   double m = 0.0;
   for (int idx = tid; idx < n * n; idx += kCoarseInvThreads) m = fmax(m, fabs(k.A0[idx]));
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -1096,7 +1100,7 @@ __global__ void __launch_bounds__(kCoarseInvThreads) hrt_coarse_invert_kernel(Kr
     }
     if (tid == 0) {
       perm[kk] = pr;
-      if (!(best > 1e-30f)) atomicOr(status, kDevSingular);
+      if (!(best > 1e-30f)) singular = 1;
     }
     const float iv = 1.0f / A[pr * ld + kk];
     for (int j = tid; j < n; j += kCoarseInvThreads) {
@@ -1138,7 +1142,7 @@ __global__ void __launch_bounds__(kCoarseInvThreads) hrt_coarse_invert_kernel(Kr
   __syncthreads();
   for (int idx = tid; idx < n * n; idx += kCoarseInvThreads) {
     const int i = idx / n, j = idx % n;
-    k.A0[idx] = (double)A[i * ld + src[j]] * rs;
+    k.A0[idx] = singular ? 0.0 : (double)A[i * ld + src[j]] * rs;
   }
 }
 
@@ -1485,7 +1489,7 @@ static vef_status hrt_run(Mesh& M, const HrtIn& in, double tol, int max_iter, do
     hrt_coarse_nodes_kernel<P><<<nblk(nl, 256), 256, 0, s>>>(k);
     hrt_coarse_cell_kernel<P><<<(unsigned)(k.ncx * k.ncy), 128, 0, s>>>(k, Acell);
     hrt_coarse_assemble_kernel<<<nblk(nc, 128), 128, 0, s>>>(k, Acell);
-    hrt_coarse_invert_kernel<<<1, kCoarseInvThreads, csmem, s>>>(k, M.dev_status);
+    hrt_coarse_invert_kernel<<<1, kCoarseInvThreads, csmem, s>>>(k);
     kry_init_kernel<<<kKB, kKT, 0, s>>>(k, tol * tol);
     VEF_CUDA_TRY(cudaGetLastError());
     cudaGraphExec_t graph = nullptr;
