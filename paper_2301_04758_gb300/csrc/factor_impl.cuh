@@ -356,15 +356,19 @@ factor_pivot_kernel(long long nmem, const uint32_t* __restrict__ code, const uin
 // rows and beta = 1/r[k] - 1 on the pivot row itself (which turns it into r / r[k]);
 // column k then becomes -A[i][k] / r[k], or 1 / r[k] on the pivot row.  With several rows
 // per lane the reciprocal and the broadcast are shared by RPL rows' FMAs.
-template <int P> struct ElemShape;
-// EPC elements per CTA: at p = 3 a warp holds 8 tasks, and the level-symmetric sets have
-// D = 4 (mod 8) directions for S4 and S12, so one element per CTA would leave half a warp of
-// padding tasks computing; two elements per CTA fill every warp (2 D = 0 mod 8).
-template <> struct ElemShape<3> { static constexpr int RPL = 4, LPU = 4, EPC = 2; };
-template <> struct ElemShape<4> { static constexpr int RPL = 2, LPU = 13, EPC = 1; };
+template <int P, typename T> struct ElemShape;
+// EPC elements per CTA: at p = 3 in FP64 a warp holds 8 tasks, and the level-symmetric sets
+// have D = 4 (mod 8) directions for S4 and S12, so one element per CTA would leave half a
+// warp of padding tasks computing; two elements per CTA fill every warp (2 D = 0 mod 8).
+// FP64 is bound by its FP64 pipe, so four rows per lane share each pivot-row broadcast.
+// FP32 is bound by latency instead (four register-limited warps per scheduler at four rows
+// per lane): two rows per lane halve the registers, so six CTAs fit per SM.
+template <> struct ElemShape<3, double> { static constexpr int RPL = 4, LPU = 4, EPC = 2, MINB = 1; };
+template <> struct ElemShape<3, float> { static constexpr int RPL = 2, LPU = 8, EPC = 4, MINB = 6; };
+template <typename T> struct ElemShape<4, T> { static constexpr int RPL = 2, LPU = 13, EPC = 1, MINB = 1; };
 
 template <int P, typename T, bool Y>
-__global__ void __launch_bounds__(128, std::is_same<T, float>::value ? 4 : 1)
+__global__ void __launch_bounds__(128, ElemShape<P, T>::MINB)
 factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const uint16_t* __restrict__ finfo,
                    const double* __restrict__ omega, const double* __restrict__ sigma_t,
                    const T* __restrict__ Mm, const T* __restrict__ Gxm, const T* __restrict__ Gym,
@@ -372,7 +376,7 @@ factor_elem_kernel(int D, long long E, const int* __restrict__ member_of, const 
                    T* __restrict__ rec, unsigned int* status, unsigned int* piv_count,
                    unsigned int* piv_list, int force_pivot, RhsArgs<T> rhs) {
   constexpr int Q = P + 1, N = Q * Q, NQ = P + 2;
-  constexpr int RPL = ElemShape<P>::RPL, LPU = ElemShape<P>::LPU, UPW = 32 / LPU, EPC = ElemShape<P>::EPC;
+  constexpr int RPL = ElemShape<P, T>::RPL, LPU = ElemShape<P, T>::LPU, UPW = 32 / LPU, EPC = ElemShape<P, T>::EPC;
   constexpr int LD = N + 1;                  // padded shared-memory row stride
   constexpr int CPL = (Q * Q + LPU - 1) / LPU;   // inflow-coupling entries computed per lane
   constexpr unsigned FULL = 0xffffffffu;
@@ -1101,7 +1105,7 @@ static vef_status launch_factor(Mesh& M, Schedule& S, const double* sigma_t, boo
   {
   KTimer kt(&M, VEF_K_FACTOR, stream);
   if constexpr (P >= 3) {
-    constexpr int UPW = 32 / ElemShape<P>::LPU, EPC = ElemShape<P>::EPC;
+    constexpr int UPW = 32 / ElemShape<P, T>::LPU, EPC = ElemShape<P, T>::EPC;
     const int warps = std::max(1, std::min(4, (EPC * S.D + UPW - 1) / UPW));
     auto kern = rhs ? factor_elem_kernel<P, T, true> : factor_elem_kernel<P, T, false>;
     kern<<<(unsigned)((M.E + EPC - 1) / EPC), 32 * warps, 0, stream>>>(

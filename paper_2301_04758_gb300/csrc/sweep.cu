@@ -1095,7 +1095,10 @@ residual_kernel(long long nmem, long long E, int nx, int ny, long long nbf,
 // its directions; a task spans N lanes (row i on lane i), 32 / N tasks per warp.  The face
 // points (4 (p+2) per task) are spread over the task's lanes, their c_k psi_hat go through
 // shared memory to the lanes of the face-node rows.  Grid-stride over the elements.
-template <int P>
+// With FY it also forms the correction sweep's y = A^{-1} r from the FP32 records (the
+// apply pass, same arithmetic as apply_warp: r rounded to FP32, one FMA chain over j): the
+// kernel is bound by its FP64 work, which hides the A^{-1} reads.
+template <int P, bool FY>
 __global__ void __launch_bounds__(128)
 residual_mf_kernel(int D, long long E, int nx, int ny, long long nbf, const double* __restrict__ omega,
                    const double* __restrict__ sigma_t, const double* __restrict__ Mm,
@@ -1103,7 +1106,9 @@ residual_mf_kernel(int D, long long E, int nx, int ny, long long nbf, const doub
                    const double* __restrict__ nds, const double* __restrict__ bvol,
                    const double* __restrict__ src_aniso, const double* __restrict__ inflow,
                    const double* __restrict__ psi, FaceTab<double> ft, double* __restrict__ r,
-                   double* __restrict__ norms) {
+                   double* __restrict__ norms, const int* __restrict__ member_of,
+                   const float* __restrict__ recx32, float* __restrict__ y32, long long nmem,
+                   unsigned int* status) {
   constexpr int Q = P + 1, N = Q * Q, NQ = P + 2, LD = N + 1;
   constexpr int UPW = 32 / N, NPT = 4 * NQ, ROUNDS = (NPT + N - 1) / N;
   constexpr int GZ = NPT;                   // a zero block after the face points
@@ -1220,6 +1225,20 @@ residual_mf_kernel(int D, long long E, int nx, int ny, long long nbf, const doub
         r[rowbase + li] = ri;
         rr = fma(ri, ri, rr);
         bb = fma(b - bs, b - bs, bb);
+      }
+      if constexpr (FY) {
+        using L = Rec<P, float>;
+        const long long m = valid ? (long long)member_of[(size_t)dd * E + e] : 0;
+        const bool ok = valid && VEF_IN_RANGE(m, nmem, status);
+        const float rf = ok ? (float)ri : 0.0f;
+        const float* ai = L::ainv(L::x_at(recx32, ok ? m : 0));
+        float y = 0.0f;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const float bj = __shfl_sync(0xffffffffu, rf, (uc * N + j) & 31);
+          if (ok) y += ai[j * N + li] * bj;
+        }
+        if (ok) y32[(size_t)m * L::kYStride + li] = y;
       }
     }
   }
@@ -1519,8 +1538,11 @@ static vef_status launch_sweep(const SweepCall& c0, const double* rhs, T* out) {
   return VEF_OK;
 }
 
+// The FP64 residual of the mixed defect correction.  With form_y (matrix-free form only) it
+// also writes the FP32 correction sweep's y = A^{-1} r, so that sweep skips its apply.
 template <int P>
-static vef_status launch_residual(const SweepCall& c, const double* psi, double* r, double* norms) {
+static vef_status launch_residual(const SweepCall& c, const double* psi, double* r, double* norms,
+                                  bool form_y = false) {
   Mesh& M = *c.mesh;
   Schedule& S = *c.S;
   constexpr int N = (P + 1) * (P + 1);
@@ -1529,11 +1551,24 @@ static vef_status launch_residual(const SweepCall& c, const double* psi, double*
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   VEF_CUDA_TRY(cudaMemsetAsync(norms, 0, 2 * sizeof(double), c.stream));
   if (!c.residual_stored) {
+    const float* recx32 = nullptr;
+    float* y32 = nullptr;
+    if (form_y) {
+      vef_status st = ensure_buffer(&M.ybuf, &M.ybuf_cap, (size_t)S.members * Rec<P, float>::kYBytes);
+      if (st != VEF_OK) return st;
+      recx32 = (const float*)((const char*)S.rec32 + S.members * (long long)Rec<P, float>::kStaged);
+      y32 = (float*)M.ybuf;
+    }
     const unsigned egrid = (unsigned)std::min<long long>(M.E, (long long)sms * 16);
     KTimer kt(&M, VEF_K_RESIDUAL, c.stream);
-    residual_mf_kernel<P><<<egrid, 128, 0, c.stream>>>(
+    auto kern = residual_mf_kernel<P, false>;
+    if constexpr (P == 3) {   // the only order whose correction sweeps take y from here
+      if (form_y) kern = residual_mf_kernel<P, true>;
+    }
+    kern<<<egrid, 128, 0, c.stream>>>(
         S.D, M.E, M.nx, M.ny, M.nbf, S.omega_dev, c.sigma_t, M.Mmat, M.Gx, M.Gy, M.nds, M.bvol,
-        c.src_aniso, c.inflow, psi, make_facetab<double>(M.tab), r, norms);
+        c.src_aniso, c.inflow, psi, make_facetab<double>(M.tab), r, norms, S.member_of, recx32, y32,
+        S.members, M.dev_status);
     VEF_CUDA_TRY(cudaGetLastError());
     return VEF_OK;
   }
@@ -1570,14 +1605,17 @@ static vef_status solve_p(const SweepCall& c, double* psi, vef_info* info) {
     KTimer kt(&M, VEF_K_SOURCE, c.stream);
     cast_add_kernel<<<nblk(tot, 256), 256, 0, c.stream>>>(tot, delta, psi, 0);
   }
-  SweepCall cc = c;      // correction sweeps apply A^{-1} to the residual themselves
-  cc.y_ready = false;
+  // correction sweeps apply A^{-1} to the residual themselves, except at p = 3 (where the
+  // apply is a pass of its own) in the matrix-free form: there the residual kernel forms y
+  const bool y_in_residual = P == 3 && !c.residual_stored && S.rec32 != nullptr;
+  SweepCall cc = c;
+  cc.y_ready = y_in_residual;
   int passes = 1;
   double rel = -1.0;
   for (int pass = 0; pass < c.max_passes; ++pass) {
     // fixed passes: the last sweep's residual is not formed, and nothing is read back
     if (c.fixed_passes && pass == c.max_passes - 1) break;
-    if ((st = launch_residual<P>(c, psi, r, norms)) != VEF_OK) return st;
+    if ((st = launch_residual<P>(c, psi, r, norms, y_in_residual)) != VEF_OK) return st;
     if (!c.fixed_passes) {
       double h[2];
       VEF_CUDA_TRY(cudaMemcpyAsync(h, norms, sizeof(h), cudaMemcpyDeviceToHost, c.stream));
