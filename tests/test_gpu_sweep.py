@@ -251,6 +251,21 @@ def test_mixed_precision_defect_correction(lib):
     assert rel(host(out["E"]), rc["E"]) < 1e-10
 
 
+@pytest.mark.parametrize("kernel", ["cta", "cluster"])
+def test_mixed_p3_correction_takes_y_from_the_residual(lib, kernel):
+    """At p = 3 the FP64 residual kernel also forms the correction sweep's y = A^{-1} r,
+    and the correction sweep skips its apply: through the single-CTA and the cluster sweep,
+    with an anisotropic source, inflow and coupled groups, to the default tolerance (several
+    passes, each residual forming the next y) and with two fixed passes, psi matches the
+    FP64 oracle."""
+    prob = random_problem(11, 9, 3, 0.1, 3, 8, seed=47, aniso=True, sigma_range=(-1.0, 0.5))
+    _, ref = _oracle(prob)
+    for kw in (dict(), dict(tol=-1.0, max_passes=2)):
+        _, (psi, info) = _run(prob, precision="mixed", kernel=kernel, **kw)
+        assert info["timed_out"] == 0 and info["passes"] >= 2 and info["coupled_groups"] > 0, info
+        assert rel(host(psi), ref) < 1e-10, (kw, info)
+
+
 def test_mixed_precision_q3_s12_against_the_oracle(lib):
     """The precision workload's recipe (sine alpha 0.05, Q3 map, DG Q3, S12, seed-3 media,
     q = 1, vacuum) on a 48x48 mesh: the mixed-precision sweep (FP32 factorisation and
