@@ -18,10 +18,10 @@
 // element's share of the reduced system,
 //     H_e = C1 W C2,   r_e = C1 (W g + X f),   [[W, X], [Y, Z]] = [[A, G], [D, Ma]]^{-1}.
 // The multiplier system H lambda = r (H = sum_e H_e over the interior faces, not symmetric
-// for a general Eddington tensor) is solved by BiCGStab with an element-patch additive
-// Schwarz preconditioner, the matrix applied face by face from the two sides' rows of H_e
-// (no atomics) and the Krylov scalars kept on the device.  hrt_recover_kernel then forms J
-// and phi element by element.
+// for a general Eddington tensor) is solved by BiCGStab with a two-level additive Schwarz
+// preconditioner (element patches plus a coarse bilinear space), the matrix applied face by
+// face from the two sides' rows of H_e (no atomics) and the Krylov scalars kept on the
+// device.  hrt_recover_kernel then forms J and phi element by element.
 //
 // Spaces (identical to the CPU reference of this discretisation): RT_p on the reference
 // square with the x component in Q_{p+1} x Q_p and the y component in Q_p x Q_{p+1}, nodal
@@ -784,13 +784,14 @@ __global__ void hrt_recover_kernel(long long E, int nx, int ny, const double* __
   }
 }
 
-// ---- the multiplier system's Krylov solve: BiCGStab (van der Vorst) with the element-patch
-// Schwarz preconditioner above.  Its scalars stay on the device: every dot product is
-// reduced in two fixed stages (per-block partial sums, then each reader sums the kKB
-// partials in the same order), so the iteration is deterministic and no kernel waits on
-// the host; the host reads the convergence state once every kCheck iterations.  One
-// iteration is nine launches: p; p_hat = M^{-1} p (element half, face half); v = H p_hat
-// with r_hat.v; s; s_hat (two halves); t = H s_hat with t.s and t.t; lambda and r with
+// ---- the multiplier system's Krylov solve: BiCGStab (van der Vorst) with the two-level
+// Schwarz preconditioner (the element patches above and the coarse space below).  Its
+// scalars stay on the device: every dot product is reduced in two fixed stages (per-block
+// partial sums, then each reader sums the kKB partials in the same order), so the iteration
+// is deterministic and no kernel waits on the host; the host reads the convergence state
+// once every kCheck iterations.  One iteration is 13 launches: p; p_hat = M^{-1} p (element
+// patches, coarse restriction, coarse solve, per-multiplier gather); v = H p_hat with
+// r_hat.v; s; s_hat (the same four); t = H s_hat with t.s and t.t; lambda and r with
 // r_hat.r and r.r.  The
 // kernels take their iteration as an offset from a base index held on the device, so one
 // CUDA graph of kCheck iterations (and the base's advance) is replayed block after block.
