@@ -789,9 +789,9 @@ __global__ void hrt_recover_kernel(long long E, int nx, int ny, const double* __
 // scalars stay on the device: every dot product is reduced in two fixed stages (per-block
 // partial sums, then each reader sums the kKB partials in the same order), so the iteration
 // is deterministic and no kernel waits on the host; the host reads the convergence state
-// once every kCheck iterations.  One iteration is 13 launches: p; p_hat = M^{-1} p (element
-// patches, coarse restriction, coarse solve, per-multiplier gather); v = H p_hat with
-// r_hat.v; s; s_hat (the same four); t = H s_hat with t.s and t.t; lambda and r with
+// once every kCheck iterations.  One iteration is 11 launches: p; p_hat = M^{-1} p (element
+// patches with the coarse restriction, coarse solve, per-multiplier gather); v = H p_hat
+// with r_hat.v; s; s_hat (the same three); t = H s_hat with t.s and t.t; lambda and r with
 // r_hat.r and r.r.  The
 // kernels take their iteration as an offset from a base index held on the device, so one
 // CUDA graph of kCheck iterations (and the base's advance) is replayed block after block.
@@ -877,13 +877,12 @@ __device__ void kry_partial(double a, double b, double* part, int qa, int qb) {
 }
 
 // The preconditioner's element half: z_e = Pinv_e x|e for every element and row (the face
-// half, each face's two sides summed, is hrt_gather_kernel)
+// half, each face's two sides summed, is kry_precond_gather_kernel), on blocks b of nb
 template <int P>
-__global__ void kry_asm_apply_kernel(Kry k, const double* __restrict__ x) {
+__device__ __forceinline__ void asm_apply_blocks(const Kry& k, const double* __restrict__ x, unsigned b,
+                                                 unsigned nb) {
   constexpr int NL = P + 1, NL4 = 4 * NL;
-  if (kry_stopped(k)) return;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < k.E * NL4;
-       t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = b * (long long)blockDim.x + threadIdx.x; t < k.E * NL4; t += (long long)nb * blockDim.x) {
     const long long e = t / NL4;
     const double* row = k.Pinv + (size_t)t * NL4;
     double s = 0.0;
@@ -1150,10 +1149,9 @@ __global__ void __launch_bounds__(kCoarseInvThreads) hrt_coarse_invert_kernel(Kr
 // per coarse cell (one CTA): the restriction of x to its four vertices from the multiplier
 // nodes the cell owns (coarse_coords), threads in a fixed stride and a fixed-order block sum
 template <int P>
-__global__ void __launch_bounds__(256) kry_coarse_restrict_kernel(Kry k, const double* __restrict__ x) {
+__device__ __forceinline__ void coarse_restrict_cell(const Kry& k, const double* __restrict__ x, int cell) {
   constexpr int NL = P + 1;
-  if (kry_stopped(k)) return;
-  const int cell = blockIdx.x, kx = cell % k.ncx, ky = cell / k.ncx;
+  const int kx = cell % k.ncx, ky = cell / k.ncx;
   const int i0 = kx * k.cx, i1 = min(i0 + k.cx, k.nx), j0 = ky * k.cy, j1 = min(j0 + k.cy, k.ny);
   const long long nv = (long long)(k.nx - 1) * k.ny;
   const int xa = max(i0, 1), ya = max(j0, 1);
@@ -1190,6 +1188,16 @@ __global__ void __launch_bounds__(256) kry_coarse_restrict_kernel(Kry k, const d
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) sum += red[i][threadIdx.x];
     k.pc[(size_t)cell * 4 + threadIdx.x] = sum;
   }
+}
+
+// the two parts of an application that read only x, in one launch: blocks [0, napply) the
+// element patches, the rest one coarse cell each
+template <int P>
+__global__ void __launch_bounds__(256) kry_precond_local_kernel(Kry k, const double* __restrict__ x,
+                                                                unsigned napply) {
+  if (kry_stopped(k)) return;
+  if (blockIdx.x < napply) asm_apply_blocks<P>(k, x, blockIdx.x, napply);
+  else coarse_restrict_cell<P>(k, x, (int)(blockIdx.x - napply));
 }
 
 // zc = A0^{-1} vc, vc summed per vertex from the cells around it (fixed order) into shared
@@ -1350,8 +1358,7 @@ static void kry_block(const Kry& k, int n, cudaStream_t s) {
   const unsigned eb = nblk(k.E * NL4, 256), fb = nblk(k.nl, 256);
   // element patches, coarse restriction and solve, then per multiplier the sum
   auto precond = [&](const double* x, double* y) {
-    kry_asm_apply_kernel<P><<<eb, 256, 0, s>>>(k, x);
-    kry_coarse_restrict_kernel<P><<<(unsigned)(k.ncx * k.ncy), 256, 0, s>>>(k, x);
+    kry_precond_local_kernel<P><<<eb + (unsigned)(k.ncx * k.ncy), 256, 0, s>>>(k, x, eb);
     kry_coarse_solve_kernel<<<(unsigned)((k.nc + 7) / 8), 256, 0, s>>>(k);
     kry_precond_gather_kernel<P><<<fb, 256, 0, s>>>(k, y);
   };
